@@ -1,0 +1,354 @@
+"""Throughput benchmark of the FPO renderer: one step = one full frame.
+
+Workload: the depth-9 union octree of the animated 14-capsule body (about
+3.5M leaves, n1 = 31, n2 = 5, i.i.d. coefficients, seed 0), rendered at
+1920x1080 from the 16 ring cameras at integer frame times (a seeded order
+over the 16 x 60 grid).  The tree (2.4 GB of coefficient records) is larger
+than L2, so no flush is needed between frames.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
+oracle instead, on a bounded sample of pixels per step.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2202_08614_gb300 import synth  # noqa: E402
+
+METRIC = "FPO render Mrays/s, 1080p fps; plain FP32 vs BF16/latent at PSNR≥45dB vs FP64"
+ALG_READ_PER_LEAF = 4 * (31 + 135)   # coefficient bytes of one leaf (FP32)
+TABLE_BYTES_PER_LEAF = 4 * 28        # sigma(t) + 27 z(t)
+OUT_BYTES_PER_RAY = 12               # FP32 RGB
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fpo", choices=["fpo", "reference"])
+    ap.add_argument("--idft", default="auto", choices=["auto", "materialise", "fused"])
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def frames_for_rank(rank: int, n: int):
+    """Each rank renders its own frames: a seeded order over the 16 x 60 grid."""
+    return synth.frame_schedule(n, seed=1000 + rank)
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+
+
+def oracle_sample_rate(tree, cams, frames, budget_s, stride=61):
+    """Times the FP64 oracle on strided pixel samples of successive frames
+    until `budget_s` seconds of wall time; returns (Mrays/s, rays, seconds, threads)."""
+    import oracle
+
+    ot = oracle.OracleTree(tree.leaf_depth, tree.leaf_xyz, tree.max_depth)
+    threads = os.cpu_count() or 1
+    rays, spent, i = 0, 0.0, 0
+    while spent < budget_s:
+        k, t = frames[i % len(frames)]
+        cam = cams[k]
+        n = cam.width * cam.height
+        sel = np.arange(i % stride, n, stride, dtype=np.int64)
+        t0 = time.perf_counter()
+        oracle.render(ot, tree.coeffs, camera=cam, t=t, sel=sel, threads=threads)
+        spent += time.perf_counter() - t0
+        rays += sel.size
+        i += 1
+    return rays / spent / 1e6, rays, spent, threads
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    tree = synth.body_tree()
+    cams = synth.ring_cameras(16, args.width, args.height)
+    frames = frames_for_rank(0, args.steps + args.warmup)
+    import oracle
+
+    ot = oracle.OracleTree(tree.leaf_depth, tree.leaf_xyz, tree.max_depth)
+    threads = os.cpu_count() or 1
+    stride = 256  # each step renders every 256th pixel of its frame
+    times, rays = [], 0
+    for i, (k, t) in enumerate(frames):
+        cam = cams[k]
+        sel = np.arange(i % stride, cam.width * cam.height, stride, dtype=np.int64)
+        t0 = time.perf_counter()
+        oracle.render(ot, tree.coeffs, camera=cam, t=t, sel=sel, threads=threads)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            rays += sel.size
+    total = sum(times)
+    value = rays / total / 1e6
+    sample = (f"every {stride}th pixel of one {args.width}x{args.height} frame per step "
+              f"({rays // max(len(times), 1)} rays), {len(times)} steps")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mrays/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / max(len(times), 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(tree, args, "oracle"),
+        "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+
+
+def workload_config(tree, args, idft):
+    return {
+        "workload": (f"body union octree (14 animated capsules, 60 frames), depth 9, "
+                     f"{tree.n_leaves} leaves, n1=31 n2=5 SH deg 2, {args.width}x{args.height}, "
+                     f"16 ring cameras x 60 integer t"),
+        "leaves": tree.n_leaves,
+        "resolution": [args.width, args.height],
+        "idft": idft,
+        "l2": "inputs larger than L2 (2.4 GB of leaf records)",
+        "early_stop_T": 1e-4,
+    }
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(", ") for r in getattr(self, "out", "").strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("fpo_kernels.cu", "fpo_internal.h"):
+        with open(os.path.join(ROOT, "paper_2202_08614_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the kernel source changed since those counters were taken."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_sha") != kernel_source_sha():
+        return None
+    return e.get("dram_bytes_per_launch_full_workload")
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+
+    from paper_2202_08614_gb300 import fpo
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    tree = synth.body_tree()
+    cams = synth.ring_cameras(16, args.width, args.height)
+    K, W = args.steps, args.warmup
+    frames = frames_for_rank(rank, K + W)
+    r = fpo.Renderer(idft_mode=args.idft, device=local)
+    r.upload(tree)
+    info = r.info()
+    n_px = args.width * args.height
+    out = torch.empty((n_px, 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    mat = args.idft in ("auto", "materialise")
+
+    # warm-up
+    for k, t in frames[:W]:
+        r.render(camera=cams[k], t=t, out=out)
+    r.status()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    for e3 in ev:
+        for e in e3:
+            e.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for i, (k, t) in enumerate(frames[W:]):
+            r.render(camera=cams[k], t=t, out=out, events=ev[i])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    r.status()
+    elapsed_ms = start.elapsed_time(stop)
+    t_max = elapsed_ms
+    if pg:
+        tt = torch.tensor([elapsed_ms], device="cuda")
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_max = float(tt.item())
+    frame_ms = [ev[i][0].elapsed_time(ev[i][2]) for i in range(K)]
+    mat_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]
+    trav_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
+
+    # visited leaves per timed frame (a marking pass outside the timed region)
+    mark = torch.zeros(tree.n_leaves, dtype=torch.uint8, device="cuda")
+    n_vis = []
+    for k, t in frames[W:]:
+        mark.zero_()
+        r.render(camera=cams[k], t=t, out=out, leaf_mark=mark)
+        n_vis.append(int(mark.sum().item()))
+    r.status()
+
+    # end to end through the public API: pinned host output, copy inside the timed region
+    host = torch.empty((n_px, 3), dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k, t in frames[W:]:
+        r.render(camera=cams[k], t=t, out=out)
+        host.copy_(out, non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    r.status()
+
+    value = world * K * n_px / (t_max * 1e-3) / 1e6
+    res = {
+        "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(tree, args, "materialise" if mat else "fused"),
+    }
+    res["fps"] = 1e3 / statistics.median(frame_ms)
+    res["frame_ms"] = {"p10": float(np.percentile(frame_ms, 10)), "p50": statistics.median(frame_ms),
+                       "p90": float(np.percentile(frame_ms, 90))}
+    # roofline of the dominant kernel
+    avg_mat = statistics.mean(mat_ms) if mat else 0.0
+    avg_trav = statistics.mean(trav_ms)
+    mean_vis = statistics.mean(n_vis)
+    if mat:
+        kernels = {
+            "materialise_kernel": (avg_mat, tree.n_leaves * (ALG_READ_PER_LEAF + TABLE_BYTES_PER_LEAF)),
+            "traverse_kernel": (avg_trav, mean_vis * TABLE_BYTES_PER_LEAF + n_px * OUT_BYTES_PER_RAY),
+        }
+    else:
+        kernels = {"traverse_kernel": (avg_trav, mean_vis * ALG_READ_PER_LEAF + n_px * OUT_BYTES_PER_RAY)}
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    ms, nbytes = kernels[dom]
+    peak = 6791.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["hbm_gbs"])
+        peak_src = "measured"
+    except (OSError, ValueError, KeyError):
+        peak_src = "fallback"
+        peak = 6800.0
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    res["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                       "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                       "traffic": ncu_traffic(dom), "alg_bytes_per_launch": nbytes,
+                       "launch_ms": ms}
+    res["kernels_ms"] = {k: v[0] for k, v in kernels.items()}
+    res["visited_leaves_per_frame"] = mean_vis
+    res["e2e"] = {"value": world * K * n_px / e2e_s / 1e6, "unit": "Mrays/s",
+                  "h2d_bytes_per_step": int(fpo.C.sizeof(fpo.Rays) + fpo.C.sizeof(fpo.FrameOpts)),
+                  "d2h_bytes_per_step": int(n_px * 3 * 4)}
+    res["gpu_launches"] = K * (2 if mat else 1)
+    res["clocks"] = clk.summary()
+    res["tree"] = info
+    if rank == 0 and not args.no_cpu_baseline:
+        v, rays, secs, thr = oracle_sample_rate(tree, cams, frames[W:], args.cpu_seconds)
+        res["cpu_baseline"] = {"value": v, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
+                               "sample": f"{rays} rays: every 61st pixel of successive timed "
+                                         f"frames, {secs:.1f} s"}
+    r.close()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * fpo.h - C ABI of the GB300 (sm_103a) Fourier PlenOctree renderer.
+ *
+ * Fourier PlenOctrees (Wang et al., "Fourier PlenOctrees for Dynamic Radiance
+ * Field Rendering in Real-time", CVPR 2022) store, in every leaf of a union
+ * octree (Sec. 4.2), n1 Fourier coefficients of the density and n2 Fourier
+ * coefficients for each of the 3 (l_max+1)^2 SH colour coefficients
+ * (Sec. 4.1, Eq. 6).  Rendering a frame at time t (the problem of Sec. 4.3:
+ * the image of view i at frame t) evaluates the real inverse DFT of Eq. 7-9,
+ * the SH colour of Eq. 1 with a sigmoid, and composites the exact ray-leaf
+ * segments front to back (PlenOctree volume rendering, Sec. 3), stopping once
+ * the transmittance falls below a threshold.
+ *
+ * Conventions for every call:
+ *  - Return values are fpo_status codes; nothing throws across the ABI.
+ *    fpo_last_error() gives a message for the last failure on this thread.
+ *  - Pointers documented as "device" are CUDA device pointers owned by the
+ *    caller; "host" pointers are read during the call only and may be freed
+ *    afterwards.
+ *  - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
+ *    void *; NULL is the legacy default stream) and is asynchronous: outputs
+ *    are valid once that stream has been synchronised.
+ *  - Errors that only the device can see (a traversal step cap hit, a visit
+ *    log too small) set a status word in the context; fpo_status_sync()
+ *    reports and clears it.
+ *  - Leaf ids at the boundary (visit logs, leaf marks, gradients) are the
+ *    upload order of fpo_tree_desc, never internal addresses.
+ *  - A context is not thread-safe: calls on one context must not overlap.
+ */
+#ifndef FPO_H
+#define FPO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fpo_ctx fpo_ctx; /* opaque; owns the device copy of one tree */
+
+typedef enum {
+    FPO_OK = 0,
+    FPO_ERR_INVALID_ARG = -1,     /* a NULL or out-of-range argument */
+    FPO_ERR_OOM = -2,             /* device or host allocation failed */
+    FPO_ERR_CUDA = -3,            /* a CUDA runtime call failed */
+    FPO_ERR_BAD_TREE = -4,        /* leaves out of range, duplicated or nested */
+    FPO_ERR_NO_TREE = -5,         /* render before fpo_upload_tree */
+    FPO_ERR_TRAVERSAL_LIMIT = -6, /* device: a ray exceeded its step cap */
+    FPO_ERR_VISIT_OVERFLOW = -7,  /* device: a ray had more visits than visit_cap */
+    FPO_ERR_UNSUPPORTED = -8      /* a valid request this build does not implement */
+} fpo_status;
+
+/* Storage precision of the leaf coefficients (the math is FP32 throughout). */
+enum { FPO_STORAGE_F32 = 0, FPO_STORAGE_BF16 = 1, FPO_STORAGE_F16 = 2, FPO_STORAGE_FP8_E4M3 = 3 };
+
+/* Where the per-leaf inverse DFT (Eq. 7, Eq. 9) runs:
+ *  FUSED        at every ray-leaf visit, from the stored coefficients;
+ *  MATERIALISE  once per frame for every leaf (a 28-value table), which the
+ *               traversal then reads;
+ *  AUTO         the library's choice (currently MATERIALISE for camera frames,
+ *               FUSED for rays with per-ray times). */
+enum { FPO_IDFT_AUTO = 0, FPO_IDFT_FUSED = 1, FPO_IDFT_MATERIALISE = 2 };
+
+typedef struct {
+    int32_t n1;        /* density Fourier coefficients per leaf (paper: 31, Tab. 3) */
+    int32_t n2;        /* Fourier coefficients per SH coefficient (paper: 5) */
+    int32_t sh_degree; /* l_max (paper: 2, Sec. 5); only 2 is supported */
+    double period_T;   /* T of Eq. 8: the sequence length in frames */
+    int32_t storage;   /* FPO_STORAGE_* */
+    int32_t idft_mode; /* FPO_IDFT_* */
+    int32_t device;    /* CUDA device ordinal the context lives on */
+} fpo_config;
+
+/* A union octree given by its leaves (Sec. 4.2): leaf j is the cell
+ * leaf_xyz[j] (integer coordinates at level leaf_depth[j]) of the regular
+ * 2^leaf_depth grid over the cube [aabb_min, aabb_min + aabb_size]^3.  Leaves
+ * must be disjoint (no duplicates, no leaf inside another); anything not
+ * covered by a leaf is empty space.  coeffs holds per leaf, in canonical
+ * order, [k_sigma_0..k_sigma_{n1-1}] then [c=0..2][k=0..8][i=0..n2-1] with
+ * k = l(l+1)+m, i.e. n1 + 27*n2 floats.  All arrays are host memory. */
+typedef struct {
+    uint32_t n_leaves;
+    uint32_t max_depth; /* >= every leaf_depth; <= 12 */
+    const uint8_t *leaf_depth;  /* [n_leaves] */
+    const uint32_t *leaf_xyz;   /* [n_leaves][3] */
+    const float *coeffs;        /* [n_leaves][n1 + 27*n2] */
+    double aabb_min[3];
+    double aabb_size;
+} fpo_tree_desc;
+
+enum { FPO_RAYS_CAMERA = 0, FPO_RAYS_EXPLICIT = 1 };
+
+/* The rays of one render call.
+ * CAMERA: a pinhole camera at `eye` looking at `target` with `up`, vertical
+ *   field of view fov_y_deg, width x height pixels, row 0 at the top.  Pixel
+ *   (px, py) shoots the unit ray through the pixel centre:
+ *   d ~ f + sx r + sy u with f = |target - eye|, r = |f x up|, u = r x f,
+ *   sx = (2 (px + 0.5)/W - 1) tan(fov/2) W/H, sy = (1 - 2 (py + 0.5)/H) tan(fov/2).
+ *   Ray index = py * width + px.  All rays share the frame time t.
+ * EXPLICIT: n rays with device arrays o[n][3], d[n][3] (d is normalised by
+ *   the library; distances are measured along the unit direction) and an
+ *   optional device array t_per_ray[n] (else every ray uses t). */
+typedef struct {
+    int32_t mode;
+    double eye[3], target[3], up[3];
+    double fov_y_deg;
+    uint32_t width, height;
+    double t;
+    uint32_t n;
+    const float *o, *d, *t_per_ray;
+} fpo_rays;
+
+enum {
+    FPO_FLAG_RECORD_VISITS = 1, /* write visit_log / visit_count */
+    FPO_FLAG_OUT_T = 2,         /* write the final transmittance to out_T */
+    FPO_FLAG_MARK_LEAVES = 4    /* set leaf_mark[id] = 1 for every visited leaf */
+};
+
+/* Per-call options.  bg: background colour added with the final
+ * transmittance.  stop_T: early-stop threshold (the ray stops after the
+ * first update that leaves T < stop_T; 0 disables).  Device outputs, each
+ * used only when its flag is set: visit_log [rays][visit_cap] and
+ * visit_count [rays] (leaf ids in visit order, count may exceed visit_cap,
+ * which then also raises FPO_ERR_VISIT_OVERFLOW), out_T [rays], leaf_mark
+ * [n_leaves] (never cleared by the library).  events: optional cudaEvent_t
+ * handles recorded on the stream before the first kernel of the frame,
+ * between the IDFT pass and the traversal, and after the traversal. */
+typedef struct {
+    float bg[3];
+    float stop_T;
+    uint32_t flags;
+    uint32_t *visit_log;
+    uint32_t visit_cap;
+    uint32_t *visit_count;
+    float *out_T;
+    uint8_t *leaf_mark;
+    void *events[3];
+} fpo_frame_opts;
+
+typedef struct {
+    uint32_t n_leaves, n_nodes, max_depth, n_smem_nodes;
+    uint64_t node_bytes;      /* device bytes of the node array */
+    uint64_t leaf_bytes;      /* device bytes of the stored coefficients */
+    uint64_t leaf_record_bytes; /* stored bytes per leaf (padded) */
+    uint64_t table_bytes;     /* device bytes of the per-frame IDFT table (0 until used) */
+} fpo_tree_info;
+
+/* Creates a context on cfg->device.  Validates n1 in [1, 32], n2 in [1, 16],
+ * sh_degree == 2, period_T > 0, storage and idft_mode values.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA, OOM.  *out is NULL on failure. */
+int fpo_create(fpo_ctx **out, const fpo_config *cfg);
+
+/* Validates a tree description without any GPU (host only); the same checks
+ * fpo_upload_tree runs.  Errors: INVALID_ARG, BAD_TREE. */
+int fpo_validate_tree(const fpo_tree_desc *tree, const fpo_config *cfg);
+
+/* Packs the union octree (Sec. 4.2) breadth-first and copies it and the leaf
+ * coefficients (Sec. 4.1, Eq. 6) to the device, replacing any previous tree.
+ * Blocks until the copies are done.  Errors: INVALID_ARG, BAD_TREE, OOM, CUDA. */
+int fpo_upload_tree(fpo_ctx *ctx, const fpo_tree_desc *tree);
+
+/* Renders the rays at frame time t (Sec. 4.1, Eq. 7-9 and Eq. 1; compositing
+ * as in Sec. 3) into out_rgb, a device array [rays][3] of FP32 RGB.
+ * Zero rays is valid and launches nothing.  Errors (synchronous): NO_TREE,
+ * INVALID_ARG, CUDA.  Device-side errors: see fpo_status_sync. */
+int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
+               float *out_rgb, void *cuda_stream);
+
+/* Adjoint of fpo_render (the back-propagation of Sec. 4.3, Eq. 13): given
+ * dL/d(rgb) (device [rays][3]) accumulates dL/d(coefficients) into
+ * dL_dcoeffs, a device array [n_leaves][n1 + 27*n2] in canonical order and
+ * upload order.  out_rgb is the forward output for the same rays.
+ * Not implemented in this build: returns FPO_ERR_UNSUPPORTED. */
+int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
+                        const float *out_rgb, const float *dL_drgb, float *dL_dcoeffs,
+                        void *cuda_stream);
+
+/* Waits for cuda_stream and returns (then clears) the device status word:
+ * FPO_OK, FPO_ERR_TRAVERSAL_LIMIT or FPO_ERR_VISIT_OVERFLOW. */
+int fpo_status_sync(fpo_ctx *ctx, void *cuda_stream);
+
+/* Sizes of the uploaded tree.  Errors: INVALID_ARG, NO_TREE. */
+int fpo_tree_info_get(const fpo_ctx *ctx, fpo_tree_info *out);
+
+/* Releases every device and host allocation of the context.  NULL-safe. */
+void fpo_destroy(fpo_ctx *ctx);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *fpo_last_error(void);
+
+/* ABI version: 100 * major + minor. */
+int fpo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FPO_H */

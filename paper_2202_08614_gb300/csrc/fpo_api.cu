@@ -1,0 +1,393 @@
+// The C ABI of the FPO renderer (include/fpo.h): context, tree upload,
+// render dispatch and device status.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fpo_internal.h"
+
+using namespace fpo;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? FPO_ERR_OOM : FPO_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+void dfree(T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+constexpr uint32_t SMEM_NODE_BUDGET = 1024;  // 32 KB of top-level nodes per CTA
+
+}  // namespace
+
+struct fpo_ctx {
+    fpo_config cfg{};
+    int sm_count = 0;
+    uint32_t *d_status = nullptr;  // [0] status bits, [1] tile counter, [2] finished CTAs, [3] pad
+    // tree
+    bool has_tree = false;
+    uint32_t n_leaves = 0, n_nodes = 0, root_kind = ROOT_EMPTY, n_smem_nodes = 0;
+    int depth = 0;
+    uint32_t max_depth = 0;
+    double aabb_min[3] = {0, 0, 0}, aabb_size = 1.0;
+    uint32_t *d_nodes = nullptr;
+    uint32_t *d_perm = nullptr;
+    float *d_sig = nullptr;
+    float *d_z = nullptr;
+    float *d_table = nullptr;
+    size_t table_leaves = 0;
+
+    void free_tree()
+    {
+        dfree(d_nodes);
+        dfree(d_perm);
+        dfree(d_sig);
+        dfree(d_z);
+        dfree(d_table);
+        table_leaves = 0;
+        has_tree = false;
+    }
+};
+
+extern "C" {
+
+const char *fpo_last_error(void) { return g_err.c_str(); }
+
+int fpo_version(void) { return 100; }
+
+int fpo_create(fpo_ctx **out, const fpo_config *cfg)
+{
+    if (!out) return fail(FPO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(FPO_ERR_INVALID_ARG, "cfg is NULL");
+    if (cfg->n1 < 1 || cfg->n1 > 32) return fail(FPO_ERR_INVALID_ARG, "n1 must be in [1, 32]");
+    if (cfg->n2 < 1 || cfg->n2 > 16) return fail(FPO_ERR_INVALID_ARG, "n2 must be in [1, 16]");
+    if (cfg->sh_degree != 2) return fail(FPO_ERR_UNSUPPORTED, "only sh_degree 2 is supported");
+    if (!(cfg->period_T > 0.0) || !std::isfinite(cfg->period_T))
+        return fail(FPO_ERR_INVALID_ARG, "period_T must be finite and > 0");
+    if (cfg->storage < FPO_STORAGE_F32 || cfg->storage > FPO_STORAGE_FP8_E4M3)
+        return fail(FPO_ERR_INVALID_ARG, "unknown storage %d", cfg->storage);
+    if (cfg->storage != FPO_STORAGE_F32)
+        return fail(FPO_ERR_UNSUPPORTED, "storage %d is not implemented", cfg->storage);
+    if (cfg->idft_mode < FPO_IDFT_AUTO || cfg->idft_mode > FPO_IDFT_MATERIALISE)
+        return fail(FPO_ERR_INVALID_ARG, "unknown idft_mode %d", cfg->idft_mode);
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (cfg->device < 0 || cfg->device >= ndev)
+        return fail(FPO_ERR_INVALID_ARG, "device %d out of range (%d devices)", cfg->device, ndev);
+    DeviceGuard g(cfg->device);
+    if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice(%d) failed", cfg->device);
+    fpo_ctx *c = new (std::nothrow) fpo_ctx;
+    if (!c) return fail(FPO_ERR_OOM, "host allocation failed");
+    c->cfg = *cfg;
+    e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, cfg->device);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaDeviceGetAttribute"); }
+    e = cudaMalloc((void **)&c->d_status, 4 * sizeof(uint32_t));
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(status)"); }
+    e = cudaMemset(c->d_status, 0, 4 * sizeof(uint32_t));
+    if (e != cudaSuccess) { cudaFree(c->d_status); delete c; return cuda_fail(e, "cudaMemset"); }
+    *out = c;
+    g_err.clear();
+    return FPO_OK;
+}
+
+int fpo_validate_tree(const fpo_tree_desc *tree, const fpo_config *cfg)
+{
+    if (!cfg) return fail(FPO_ERR_INVALID_ARG, "cfg is NULL");
+    std::string err;
+    int st = validate_and_pack(tree, cfg->n1, cfg->n2, nullptr, &err);
+    if (st != FPO_OK) return fail(st, "%s", err.c_str());
+    return FPO_OK;
+}
+
+int fpo_upload_tree(fpo_ctx *ctx, const fpo_tree_desc *tree)
+{
+    if (!ctx) return fail(FPO_ERR_INVALID_ARG, "ctx is NULL");
+    PackedTree pk;
+    std::string err;
+    int st = validate_and_pack(tree, ctx->cfg.n1, ctx->cfg.n2, &pk, &err);
+    if (st != FPO_OK) return fail(st, "%s", err.c_str());
+    DeviceGuard g(ctx->cfg.device);
+    if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
+    ctx->free_tree();
+
+    const int n1 = ctx->cfg.n1, n2 = ctx->cfg.n2;
+    const int ss = sig_stride(n1), zs = z_stride(n2), nc = n1 + 27 * n2;
+    const size_t n = tree->n_leaves;
+    // Reorder the coefficients into breadth-first leaf order, split into
+    // the density and the SH record arrays, padded with zeros.
+    std::vector<float> sig((size_t)n * ss, 0.0f), zc((size_t)n * zs, 0.0f);
+    for (size_t i = 0; i < n; ++i) {
+        const float *src = tree->coeffs + (size_t)pk.perm[i] * nc;
+        std::memcpy(&sig[i * ss], src, sizeof(float) * n1);
+        std::memcpy(&zc[i * zs], src + n1, sizeof(float) * 27 * n2);
+    }
+    const size_t n_nodes = pk.nodes.size() / 8;
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void **dst, const void *src, size_t bytes, const char *what) -> int {
+        if (bytes == 0) return FPO_OK;
+        e = cudaMalloc(dst, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+        e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+        return FPO_OK;
+    };
+    if ((st = up((void **)&ctx->d_nodes, pk.nodes.data(), pk.nodes.size() * 4, "nodes")) ||
+        (st = up((void **)&ctx->d_perm, pk.perm.data(), pk.perm.size() * 4, "perm")) ||
+        (st = up((void **)&ctx->d_sig, sig.data(), sig.size() * 4, "sigma records")) ||
+        (st = up((void **)&ctx->d_z, zc.data(), zc.size() * 4, "SH records"))) {
+        ctx->free_tree();
+        return st;
+    }
+    ctx->n_leaves = (uint32_t)n;
+    ctx->n_nodes = (uint32_t)n_nodes;
+    ctx->root_kind = pk.root_kind;
+    ctx->depth = pk.depth;
+    ctx->max_depth = tree->max_depth;
+    ctx->n_smem_nodes = (uint32_t)(n_nodes < SMEM_NODE_BUDGET ? n_nodes : SMEM_NODE_BUDGET);
+    for (int k = 0; k < 3; ++k) ctx->aabb_min[k] = tree->aabb_min[k];
+    ctx->aabb_size = tree->aabb_size;
+    ctx->has_tree = true;
+    g_err.clear();
+    return FPO_OK;
+}
+
+int fpo_tree_info_get(const fpo_ctx *ctx, fpo_tree_info *out)
+{
+    if (!ctx || !out) return fail(FPO_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->has_tree) return fail(FPO_ERR_NO_TREE, "no tree uploaded");
+    out->n_leaves = ctx->n_leaves;
+    out->n_nodes = ctx->n_nodes;
+    out->max_depth = ctx->max_depth;
+    out->n_smem_nodes = ctx->n_smem_nodes;
+    out->node_bytes = (uint64_t)ctx->n_nodes * 32;
+    out->leaf_record_bytes = (uint64_t)(sig_stride(ctx->cfg.n1) + z_stride(ctx->cfg.n2)) * 4;
+    out->leaf_bytes = out->leaf_record_bytes * ctx->n_leaves;
+    out->table_bytes = (uint64_t)ctx->table_leaves * TABLE_STRIDE * 4;
+    return FPO_OK;
+}
+
+static int check_rays(const fpo_ctx *ctx, const fpo_rays *r, uint64_t *n_rays)
+{
+    if (r->mode == FPO_RAYS_CAMERA) {
+        const double fov = r->fov_y_deg;
+        if (!(fov > 0.0 && fov < 180.0)) return fail(FPO_ERR_INVALID_ARG, "fov_y_deg must be in (0, 180)");
+        double f[3], c[3];
+        for (int k = 0; k < 3; ++k) f[k] = r->target[k] - r->eye[k];
+        c[0] = f[1] * r->up[2] - f[2] * r->up[1];
+        c[1] = f[2] * r->up[0] - f[0] * r->up[2];
+        c[2] = f[0] * r->up[1] - f[1] * r->up[0];
+        const double fl = f[0] * f[0] + f[1] * f[1] + f[2] * f[2];
+        const double cl = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+        if (!(fl > 0.0) || !(cl > 0.0) || !std::isfinite(fl) || !std::isfinite(cl))
+            return fail(FPO_ERR_INVALID_ARG, "degenerate camera (eye == target or up parallel to the view)");
+        if (!std::isfinite(r->t)) return fail(FPO_ERR_INVALID_ARG, "t must be finite");
+        *n_rays = (uint64_t)r->width * r->height;
+    } else if (r->mode == FPO_RAYS_EXPLICIT) {
+        if (r->n > 0 && (!r->o || !r->d)) return fail(FPO_ERR_INVALID_ARG, "o and d must be non-NULL");
+        *n_rays = r->n;
+    } else {
+        return fail(FPO_ERR_INVALID_ARG, "unknown ray mode %d", r->mode);
+    }
+    if (*n_rays >= (1ull << 31)) return fail(FPO_ERR_INVALID_ARG, "too many rays");
+    (void)ctx;
+    return FPO_OK;
+}
+
+int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, float *out_rgb,
+               void *cuda_stream)
+{
+    if (!ctx || !rays || !opts) return fail(FPO_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->has_tree) return fail(FPO_ERR_NO_TREE, "render before fpo_upload_tree");
+    uint64_t n_rays = 0;
+    int st = check_rays(ctx, rays, &n_rays);
+    if (st != FPO_OK) return st;
+    if (n_rays > 0 && !out_rgb) return fail(FPO_ERR_INVALID_ARG, "out_rgb is NULL");
+    const uint32_t fl = opts->flags;
+    if ((fl & FPO_FLAG_RECORD_VISITS) && (!opts->visit_count || (opts->visit_cap && !opts->visit_log)))
+        return fail(FPO_ERR_INVALID_ARG, "RECORD_VISITS needs visit_count (and visit_log if visit_cap > 0)");
+    if ((fl & FPO_FLAG_OUT_T) && !opts->out_T) return fail(FPO_ERR_INVALID_ARG, "OUT_T needs out_T");
+    if ((fl & FPO_FLAG_MARK_LEAVES) && !opts->leaf_mark && ctx->n_leaves)
+        return fail(FPO_ERR_INVALID_ARG, "MARK_LEAVES needs leaf_mark");
+    if (!(opts->stop_T >= 0.0f)) return fail(FPO_ERR_INVALID_ARG, "stop_T must be >= 0");
+    const bool per_ray_t = rays->mode == FPO_RAYS_EXPLICIT && rays->t_per_ray;
+    int mode = ctx->cfg.idft_mode;
+    if (mode == FPO_IDFT_AUTO) mode = per_ray_t ? FPO_IDFT_FUSED : FPO_IDFT_MATERIALISE;
+    if (mode == FPO_IDFT_MATERIALISE && per_ray_t)
+        return fail(FPO_ERR_INVALID_ARG, "per-ray times need the FUSED IDFT mode");
+    const bool mat = mode == FPO_IDFT_MATERIALISE && ctx->n_leaves > 0;
+    if (!mat && !fused_supported(ctx->cfg.n1, ctx->cfg.n2))
+        return fail(FPO_ERR_UNSUPPORTED, "the fused IDFT supports (n1, n2) in {(31,5), (11,5), (21,5), (31,11)}");
+
+    DeviceGuard g(ctx->cfg.device);
+    if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e;
+    if (mat && ctx->table_leaves < ctx->n_leaves) {
+        dfree(ctx->d_table);
+        e = cudaMalloc((void **)&ctx->d_table, (size_t)ctx->n_leaves * TABLE_STRIDE * 4);
+        if (e != cudaSuccess) { ctx->table_leaves = 0; return cuda_fail(e, "cudaMalloc(table)"); }
+        ctx->table_leaves = ctx->n_leaves;
+    }
+    auto rec = [&](int i) -> cudaError_t {
+        return opts->events[i] ? cudaEventRecord((cudaEvent_t)opts->events[i], s) : cudaSuccess;
+    };
+    if ((e = rec(0)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if (n_rays == 0) {
+        if ((e = rec(1)) != cudaSuccess || (e = rec(2)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        return FPO_OK;
+    }
+    if (mat) {
+        MaterialiseParams mp{};
+        mp.sig = ctx->d_sig;
+        mp.zc = ctx->d_z;
+        mp.table = ctx->d_table;
+        mp.n_leaves = ctx->n_leaves;
+        mp.n1 = ctx->cfg.n1;
+        mp.n2 = ctx->cfg.n2;
+        mp.sig_stride = sig_stride(ctx->cfg.n1);
+        mp.z_stride = z_stride(ctx->cfg.n2);
+        mp.t = rays->t;
+        mp.period_T = ctx->cfg.period_T;
+        int ce = launch_materialise(mp, ctx->sm_count, s);
+        if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "materialise launch");
+    }
+    if ((e = rec(1)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+
+    TraverseParams p{};
+    p.fr.mode = rays->mode;
+    p.fr.width = rays->width;
+    p.fr.height = rays->height;
+    p.fr.n_rays = (uint32_t)n_rays;
+    for (int k = 0; k < 3; ++k) {
+        p.fr.eye[k] = rays->eye[k];
+        p.fr.target[k] = rays->target[k];
+        p.fr.up[k] = rays->up[k];
+    }
+    p.fr.fov_y_deg = rays->fov_y_deg;
+    p.fr.t = rays->t;
+    p.fr.period_T = ctx->cfg.period_T;
+    p.fr.ro = rays->o;
+    p.fr.rd = rays->d;
+    p.fr.rt = rays->t_per_ray;
+    p.nodes = ctx->d_nodes;
+    p.root_kind = ctx->root_kind;
+    p.depth = ctx->depth;
+    p.n_smem_nodes = ctx->n_smem_nodes;
+    p.grid_scale = (float)((double)(1u << ctx->depth) / ctx->aabb_size);
+    for (int k = 0; k < 3; ++k) p.amin[k] = (float)ctx->aabb_min[k];
+    p.table = reinterpret_cast<const float4 *>(ctx->d_table);
+    p.sig = reinterpret_cast<const float4 *>(ctx->d_sig);
+    p.zc = ctx->d_z;
+    p.n1 = ctx->cfg.n1;
+    p.n2 = ctx->cfg.n2;
+    p.sig_stride4 = sig_stride(ctx->cfg.n1) / 4;
+    p.z_stride = z_stride(ctx->cfg.n2);
+    for (int k = 0; k < 3; ++k) p.bg[k] = opts->bg[k];
+    p.stop_T = opts->stop_T;
+    p.flags = fl;
+    p.out_rgb = out_rgb;
+    p.out_T = opts->out_T;
+    p.visit_log = opts->visit_log;
+    p.visit_cap = opts->visit_cap;
+    p.visit_count = opts->visit_count;
+    p.leaf_mark = opts->leaf_mark;
+    p.perm = ctx->d_perm;
+    p.status = ctx->d_status;
+    if (rays->mode == FPO_RAYS_CAMERA) {
+        p.tiles_x = (rays->width + 7) / 8;
+        p.n_tiles = p.tiles_x * ((rays->height + 3) / 4);
+    } else {
+        p.tiles_x = 0;
+        p.n_tiles = (uint32_t)((n_rays + 31) / 32);
+    }
+    p.max_steps = 3u * (1u << ctx->depth) + 16u;
+    const bool dbg = (fl & (FPO_FLAG_RECORD_VISITS | FPO_FLAG_OUT_T | FPO_FLAG_MARK_LEAVES)) != 0;
+    int ce = launch_traverse(p, mat, dbg, ctx->sm_count, s);
+    if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "traverse launch");
+    if ((e = rec(2)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    return FPO_OK;
+}
+
+int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
+                        const float *out_rgb, const float *dL_drgb, float *dL_dcoeffs,
+                        void *cuda_stream)
+{
+    (void)ctx; (void)rays; (void)opts; (void)out_rgb; (void)dL_drgb; (void)dL_dcoeffs;
+    (void)cuda_stream;
+    return fail(FPO_ERR_UNSUPPORTED, "fpo_render_backward is not implemented in this build");
+}
+
+int fpo_status_sync(fpo_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx) return fail(FPO_ERR_INVALID_ARG, "ctx is NULL");
+    DeviceGuard g(ctx->cfg.device);
+    if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    uint32_t st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, ctx->d_status, sizeof st, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (st) {
+        e = cudaMemsetAsync(ctx->d_status, 0, sizeof st, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "status clear");
+    }
+    if (st & STATUS_TRAVERSAL_LIMIT) return fail(FPO_ERR_TRAVERSAL_LIMIT, "a ray exceeded its step cap");
+    if (st & STATUS_VISIT_OVERFLOW) return fail(FPO_ERR_VISIT_OVERFLOW, "a ray had more visits than visit_cap");
+    return FPO_OK;
+}
+
+void fpo_destroy(fpo_ctx *ctx)
+{
+    if (!ctx) return;
+    {
+        DeviceGuard g(ctx->cfg.device);
+        ctx->free_tree();
+        dfree(ctx->d_status);
+    }
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Internal declarations shared by the host packer, the ABI layer and the
+// CUDA kernels of the FPO renderer.  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <vector_types.h>
+
+#include "fpo.h"
+
+namespace fpo {
+
+// ---------------------------------------------------------------------------
+// Node array (breadth-first).  One node = 8 child slots of 32 bits = 32 bytes,
+// one L2 sector.  Slot values: 0 = empty space, LEAF_BIT | i = leaf with
+// internal index i, otherwise the index (>= 1) of an internal child node.
+// The root is node 0 and is never referenced from a slot; its own kind is
+// passed separately (ROOT_*).  Child c of a node covers the octant with
+// bit 0 = x, bit 1 = y, bit 2 = z of the next level's coordinates.
+constexpr uint32_t LEAF_BIT = 0x80000000u;
+constexpr uint32_t ROOT_EMPTY = 0, ROOT_LEAF = 1, ROOT_NODE = 2;
+constexpr int MAX_DEPTH = 12;
+
+// Leaf records.  FP32 storage: a density record of SIG_STRIDE(n1) floats
+// (n1 rounded up to a multiple of 4, 128 bytes for n1 = 31) and an SH record
+// of Z_STRIDE(n2) floats (27 n2 rounded up to a multiple of 4), both arrays
+// indexed by internal leaf index (breadth-first order, siblings adjacent).
+inline int sig_stride(int n1) { return (n1 + 3) & ~3; }
+inline int z_stride(int n2) { return (27 * n2 + 3) & ~3; }
+
+// Per-frame IDFT table: one 128-byte record per leaf,
+// [sigma(t) clamped at 0, z_{c,k}(t) for c = 0..2, k = 0..8 (27 values), 4 zeros].
+constexpr int TABLE_STRIDE = 32;
+
+// Device status word bits.
+constexpr uint32_t STATUS_TRAVERSAL_LIMIT = 1u, STATUS_VISIT_OVERFLOW = 2u;
+
+struct PackedTree {
+    uint32_t root_kind = ROOT_EMPTY;
+    int depth = 0;                 // grid depth D: finest cell = 1 / 2^D of the cube
+    std::vector<uint32_t> nodes;   // [n_nodes * 8]
+    std::vector<uint32_t> perm;    // internal leaf index -> upload index
+};
+
+// Validates a tree description (and packs it when `out` is non-null).
+// Returns FPO_OK, FPO_ERR_INVALID_ARG or FPO_ERR_BAD_TREE (message in *err).
+int validate_and_pack(const fpo_tree_desc *tree, int n1, int n2, PackedTree *out,
+                      std::string *err);
+
+// ---------------------------------------------------------------------------
+// Kernel parameters.
+
+struct FrameParams {
+    int mode;                 // FPO_RAYS_*
+    uint32_t width, height, n_rays;
+    double eye[3], target[3], up[3];
+    double fov_y_deg;
+    double t, period_T;
+    const float *ro, *rd, *rt; // explicit rays (device)
+};
+
+struct TraverseParams {
+    FrameParams fr;
+    // tree
+    const uint32_t *nodes;
+    uint32_t root_kind;
+    int depth;
+    uint32_t n_smem_nodes;
+    float grid_scale;         // 2^D / aabb_size
+    float amin[3];
+    // leaf data
+    const float4 *table;      // per-frame IDFT table (materialised mode)
+    const float4 *sig;        // density coefficient records (fused mode)
+    const float *zc;          // SH coefficient records (fused mode)
+    int n1, n2, sig_stride4, z_stride;
+    // options and outputs
+    float bg[3];
+    float stop_T;
+    uint32_t flags;
+    float *out_rgb;
+    float *out_T;
+    uint32_t *visit_log;
+    uint32_t visit_cap;
+    uint32_t *visit_count;
+    uint8_t *leaf_mark;
+    const uint32_t *perm;
+    // scheduling
+    uint32_t *status;         // [0] status bits, [1] tile counter, [2] finished CTAs
+    uint32_t n_tiles, tiles_x;
+    uint32_t max_steps;
+};
+
+struct MaterialiseParams {
+    const float *sig;
+    const float *zc;
+    float *table;
+    uint32_t n_leaves;
+    int n1, n2, sig_stride, z_stride;
+    double t, period_T;
+};
+
+// Launchers (return cudaError_t as int).
+int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream);
+int launch_traverse(const TraverseParams &p, bool materialised, bool debug, int sm_count,
+                    void *stream);
+int traverse_smem_bytes(uint32_t n_smem_nodes);
+bool fused_supported(int n1, int n2);
+int traverse_block_threads();
+
+}  // namespace fpo

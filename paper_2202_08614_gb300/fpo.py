@@ -1,0 +1,249 @@
+"""ctypes binding of libfpo.so (include/fpo.h).
+
+Argument marshalling only: every step of rendering runs in the CUDA library.
+PyTorch supplies device memory (tensor.data_ptr()) and streams
+(torch.cuda.current_stream().cuda_stream).  When the compiled library is
+missing, loading it raises instead of falling back to anything else.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libfpo.so")
+
+FPO_OK = 0
+ERRORS = {
+    -1: "FPO_ERR_INVALID_ARG", -2: "FPO_ERR_OOM", -3: "FPO_ERR_CUDA", -4: "FPO_ERR_BAD_TREE",
+    -5: "FPO_ERR_NO_TREE", -6: "FPO_ERR_TRAVERSAL_LIMIT", -7: "FPO_ERR_VISIT_OVERFLOW",
+    -8: "FPO_ERR_UNSUPPORTED",
+}
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "fp8": 3}
+IDFT = {"auto": 0, "fused": 1, "materialise": 2}
+RAYS_CAMERA, RAYS_EXPLICIT = 0, 1
+FLAG_RECORD_VISITS, FLAG_OUT_T, FLAG_MARK_LEAVES = 1, 2, 4
+
+# Every symbol include/fpo.h declares.
+EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
+           "fpo_render_backward", "fpo_status_sync", "fpo_tree_info_get", "fpo_destroy",
+           "fpo_last_error", "fpo_version"]
+
+
+class FPOError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("n1", C.c_int32), ("n2", C.c_int32), ("sh_degree", C.c_int32),
+                ("period_T", C.c_double), ("storage", C.c_int32), ("idft_mode", C.c_int32),
+                ("device", C.c_int32)]
+
+
+class TreeDesc(C.Structure):
+    _fields_ = [("n_leaves", C.c_uint32), ("max_depth", C.c_uint32), ("leaf_depth", C.c_void_p),
+                ("leaf_xyz", C.c_void_p), ("coeffs", C.c_void_p), ("aabb_min", C.c_double * 3),
+                ("aabb_size", C.c_double)]
+
+
+class Rays(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("eye", C.c_double * 3), ("target", C.c_double * 3),
+                ("up", C.c_double * 3), ("fov_y_deg", C.c_double), ("width", C.c_uint32),
+                ("height", C.c_uint32), ("t", C.c_double), ("n", C.c_uint32), ("o", C.c_void_p),
+                ("d", C.c_void_p), ("t_per_ray", C.c_void_p)]
+
+
+class FrameOpts(C.Structure):
+    _fields_ = [("bg", C.c_float * 3), ("stop_T", C.c_float), ("flags", C.c_uint32),
+                ("visit_log", C.c_void_p), ("visit_cap", C.c_uint32), ("visit_count", C.c_void_p),
+                ("out_T", C.c_void_p), ("leaf_mark", C.c_void_p), ("events", C.c_void_p * 3)]
+
+
+class TreeInfo(C.Structure):
+    _fields_ = [("n_leaves", C.c_uint32), ("n_nodes", C.c_uint32), ("max_depth", C.c_uint32),
+                ("n_smem_nodes", C.c_uint32), ("node_bytes", C.c_uint64),
+                ("leaf_bytes", C.c_uint64), ("leaf_record_bytes", C.c_uint64),
+                ("table_bytes", C.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libfpo.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libfpo.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.fpo_create.argtypes = [C.POINTER(P), C.POINTER(Config)]
+        L.fpo_validate_tree.argtypes = [C.POINTER(TreeDesc), C.POINTER(Config)]
+        L.fpo_upload_tree.argtypes = [P, C.POINTER(TreeDesc)]
+        L.fpo_render.argtypes = [P, C.POINTER(Rays), C.POINTER(FrameOpts), P, P]
+        L.fpo_render_backward.argtypes = [P, C.POINTER(Rays), C.POINTER(FrameOpts), P, P, P, P]
+        L.fpo_status_sync.argtypes = [P, P]
+        L.fpo_tree_info_get.argtypes = [P, C.POINTER(TreeInfo)]
+        L.fpo_destroy.argtypes = [P]
+        L.fpo_destroy.restype = None
+        L.fpo_last_error.restype = C.c_char_p
+        L.fpo_last_error.argtypes = []
+        L.fpo_version.argtypes = []
+        _lib = L
+    return _lib
+
+
+def check(code: int):
+    if code != FPO_OK:
+        raise FPOError(code, lib().fpo_last_error().decode())
+    return code
+
+
+def make_config(n1=31, n2=5, period_T=60.0, storage="f32", idft_mode="auto", device=0):
+    return Config(n1, n2, 2, float(period_T), STORAGE[storage], IDFT[idft_mode], device)
+
+
+def make_tree_desc(leaf_depth, leaf_xyz, coeffs, max_depth, aabb_min=(0.0, 0.0, 0.0),
+                   aabb_size=1.0):
+    """Returns (TreeDesc, keepalive) for host numpy arrays."""
+    d = np.ascontiguousarray(leaf_depth, np.uint8)
+    x = np.ascontiguousarray(leaf_xyz, np.uint32).reshape(-1, 3)
+    c = np.ascontiguousarray(coeffs, np.float32)
+    desc = TreeDesc(d.shape[0], int(max_depth), d.ctypes.data, x.ctypes.data, c.ctypes.data,
+                    (C.c_double * 3)(*aabb_min), float(aabb_size))
+    return desc, (d, x, c)
+
+
+def validate_tree(tree, n1=31, n2=5) -> None:
+    """Host-only validation (no GPU needed); raises FPOError."""
+    desc, keep = make_tree_desc(tree.leaf_depth, tree.leaf_xyz, tree.coeffs, tree.max_depth,
+                                tree.aabb_min, tree.aabb_size)
+    cfg = make_config(n1, n2)
+    check(lib().fpo_validate_tree(C.byref(desc), C.byref(cfg)))
+    del keep
+
+
+def _stream_handle(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Renderer:
+    """One fpo_ctx: a tree resident on one GPU, rendered frame by frame."""
+
+    def __init__(self, n1=31, n2=5, period_T=60.0, storage="f32", idft_mode="auto", device=0):
+        self.cfg = make_config(n1, n2, period_T, storage, idft_mode, device)
+        self.device = device
+        self.n1, self.n2 = n1, n2
+        h = C.c_void_p()
+        check(lib().fpo_create(C.byref(h), C.byref(self.cfg)))
+        self.h = h
+        self.n_leaves = 0
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().fpo_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def upload(self, tree):
+        desc, keep = make_tree_desc(tree.leaf_depth, tree.leaf_xyz, tree.coeffs, tree.max_depth,
+                                    tree.aabb_min, tree.aabb_size)
+        check(lib().fpo_upload_tree(self.h, C.byref(desc)))
+        self.n_leaves = int(desc.n_leaves)
+        del keep
+
+    def info(self) -> dict:
+        inf = TreeInfo()
+        check(lib().fpo_tree_info_get(self.h, C.byref(inf)))
+        return {k: int(getattr(inf, k)) for k, _ in TreeInfo._fields_}
+
+    def status(self, stream=None):
+        """Waits for the stream and raises FPOError on a device-side error."""
+        check(lib().fpo_status_sync(self.h, C.c_void_p(_stream_handle(stream))))
+
+    def render(self, camera=None, t=0.0, rays_o=None, rays_d=None, t_per_ray=None,
+               bg=(1.0, 1.0, 1.0), stop_T=1e-4, out=None, visit_cap=None, want_T=False,
+               leaf_mark=None, stream=None, events=None):
+        """Renders one frame; returns a dict of device tensors.
+
+        camera: an object with eye/target/up/fov_y_deg/width/height (pixel
+        index = row * width + column), or explicit rays as CUDA float32
+        tensors rays_o, rays_d [n, 3] and optional t_per_ray [n].
+        visit_cap: if not None, also returns visit_log [n, cap] and
+        visit_count [n] (leaf ids in upload order).  leaf_mark: optional CUDA
+        uint8 tensor [n_leaves] set to 1 for visited leaves.
+        """
+        import torch
+
+        dev = torch.device("cuda", self.device)
+        r = Rays()
+        keep = []
+        if camera is not None:
+            r.mode = RAYS_CAMERA
+            r.eye = (C.c_double * 3)(*camera.eye)
+            r.target = (C.c_double * 3)(*camera.target)
+            r.up = (C.c_double * 3)(*camera.up)
+            r.fov_y_deg = float(camera.fov_y_deg)
+            r.width, r.height = int(camera.width), int(camera.height)
+            n = int(camera.width) * int(camera.height)
+        else:
+            o = rays_o.to(dev, torch.float32).contiguous()
+            d = rays_d.to(dev, torch.float32).contiguous()
+            keep += [o, d]
+            r.mode = RAYS_EXPLICIT
+            n = o.shape[0]
+            r.n = n
+            r.o, r.d = o.data_ptr() if n else None, d.data_ptr() if n else None
+            if t_per_ray is not None:
+                tp = t_per_ray.to(dev, torch.float32).contiguous()
+                keep.append(tp)
+                r.t_per_ray = tp.data_ptr() if n else None
+        r.t = float(t)
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        res = {"rgb": out}
+        opts = FrameOpts()
+        opts.bg = (C.c_float * 3)(*bg)
+        opts.stop_T = float(stop_T)
+        flags = 0
+        if visit_cap is not None:
+            res["visit_log"] = torch.full((n, max(visit_cap, 1)), -1, dtype=torch.int32, device=dev)
+            res["visit_count"] = torch.zeros(n, dtype=torch.int32, device=dev)
+            opts.visit_log = res["visit_log"].data_ptr()
+            opts.visit_cap = int(visit_cap)
+            opts.visit_count = res["visit_count"].data_ptr()
+            flags |= FLAG_RECORD_VISITS
+        if want_T:
+            res["T"] = torch.empty(n, dtype=torch.float32, device=dev)
+            opts.out_T = res["T"].data_ptr()
+            flags |= FLAG_OUT_T
+        if leaf_mark is not None:
+            opts.leaf_mark = leaf_mark.data_ptr()
+            flags |= FLAG_MARK_LEAVES
+        opts.flags = flags
+        if events is not None:
+            for i, ev in enumerate(events):
+                if ev is None:
+                    continue
+                if not ev.cuda_event:  # torch creates the CUDA event at its first record
+                    ev.record(stream)
+                opts.events[i] = ev.cuda_event
+        check(lib().fpo_render(self.h, C.byref(r), C.byref(opts),
+                               C.c_void_p(out.data_ptr() if n else None),
+                               C.c_void_p(_stream_handle(stream))))
+        res["_keep"] = keep
+        return res
