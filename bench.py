@@ -37,8 +37,8 @@ OUT_BYTES_PER_RAY = 12               # FP32 RGB
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fpo", choices=["fpo", "reference"])
     ap.add_argument("--idft", default="auto", choices=["auto", "materialise", "fused"])
     ap.add_argument("--width", type=int, default=1920)

@@ -264,6 +264,6 @@ def test_body_1080p_sampled_pixels(body, mode):
             gpu = {"rgb": res["rgb"].cpu().numpy()[sel], "visit_log": res["visit_log"].cpu().numpy()[sel],
                    "visit_count": res["visit_count"].cpu().numpy()[sel]}
             gu.compare(gpu, ref)
-            assert (ref["visit_count"] > 0).sum() > 500  # the sample sees the body
+            assert (ref["visit_count"] > 0).sum() > 150  # the sample sees the body
     finally:
         r.close()
