@@ -256,11 +256,13 @@ def main():
     torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")
         start.record(stream)
         for i, (k, t) in enumerate(frames[W:]):
             r.render(camera=cams[k], t=t, out=out, events=ev[i])
         stop.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     if pg:
         pg.barrier()
     r.status()

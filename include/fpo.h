@@ -48,7 +48,8 @@ typedef enum {
     FPO_ERR_NO_TREE = -5,         /* render before fpo_upload_tree */
     FPO_ERR_TRAVERSAL_LIMIT = -6, /* device: a ray exceeded its step cap */
     FPO_ERR_VISIT_OVERFLOW = -7,  /* device: a ray had more visits than visit_cap */
-    FPO_ERR_UNSUPPORTED = -8      /* a valid request this build does not implement */
+    FPO_ERR_UNSUPPORTED = -8,     /* a valid request this build does not implement */
+    FPO_ERR_DEVICE_TIMEOUT = -9   /* device: a bounded wait on an async copy gave up */
 } fpo_status;
 
 /* Storage precision of the leaf coefficients (the math is FP32 throughout). */
@@ -177,7 +178,8 @@ int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts
                         void *cuda_stream);
 
 /* Waits for cuda_stream and returns (then clears) the device status word:
- * FPO_OK, FPO_ERR_TRAVERSAL_LIMIT or FPO_ERR_VISIT_OVERFLOW. */
+ * FPO_OK, FPO_ERR_TRAVERSAL_LIMIT, FPO_ERR_VISIT_OVERFLOW or
+ * FPO_ERR_DEVICE_TIMEOUT. */
 int fpo_status_sync(fpo_ctx *ctx, void *cuda_stream);
 
 /* Sizes of the uploaded tree.  Errors: INVALID_ARG, NO_TREE. */

@@ -288,8 +288,10 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
         mp.n2 = ctx->cfg.n2;
         mp.sig_stride = sig_stride(ctx->cfg.n1);
         mp.z_stride = z_stride(ctx->cfg.n2);
+        mp.stages = materialise_stages(ctx->cfg.n1, ctx->cfg.n2);
         mp.t = rays->t;
         mp.period_T = ctx->cfg.period_T;
+        mp.status = ctx->d_status;
         int ce = launch_materialise(mp, ctx->sm_count, s);
         if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "materialise launch");
     }
@@ -376,6 +378,7 @@ int fpo_status_sync(fpo_ctx *ctx, void *cuda_stream)
     }
     if (st & STATUS_TRAVERSAL_LIMIT) return fail(FPO_ERR_TRAVERSAL_LIMIT, "a ray exceeded its step cap");
     if (st & STATUS_VISIT_OVERFLOW) return fail(FPO_ERR_VISIT_OVERFLOW, "a ray had more visits than visit_cap");
+    if (st & STATUS_DEVICE_TIMEOUT) return fail(FPO_ERR_DEVICE_TIMEOUT, "a device-side wait gave up after its time limit");
     return FPO_OK;
 }
 

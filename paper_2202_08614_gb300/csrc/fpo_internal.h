@@ -36,7 +36,7 @@ inline int z_stride(int n2) { return (27 * n2 + 3) & ~3; }
 constexpr int TABLE_STRIDE = 32;
 
 // Device status word bits.
-constexpr uint32_t STATUS_TRAVERSAL_LIMIT = 1u, STATUS_VISIT_OVERFLOW = 2u;
+constexpr uint32_t STATUS_TRAVERSAL_LIMIT = 1u, STATUS_VISIT_OVERFLOW = 2u, STATUS_DEVICE_TIMEOUT = 4u;
 
 struct PackedTree {
     uint32_t root_kind = ROOT_EMPTY;
@@ -99,14 +99,17 @@ struct MaterialiseParams {
     float *table;
     uint32_t n_leaves;
     int n1, n2, sig_stride, z_stride;
+    int stages;               // shared-memory pipeline depth (materialise_stages)
     double t, period_T;
+    uint32_t *status;
 };
 
 // Launchers (return cudaError_t as int).
 int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream);
+int materialise_stages(int n1, int n2);
 int launch_traverse(const TraverseParams &p, bool materialised, bool debug, int sm_count,
                     void *stream);
-int traverse_smem_bytes(uint32_t n_smem_nodes);
+int traverse_smem_bytes(uint32_t n_smem_nodes, bool per_ray_basis);
 bool fused_supported(int n1, int n2);
 int traverse_block_threads();
 

@@ -14,6 +14,7 @@
 #include <cstdint>
 
 #include "fpo_internal.h"
+#include "fpo_ptx.cuh"
 
 namespace fpo {
 namespace {
@@ -62,50 +63,127 @@ __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + __ex
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Per-frame IDFT table.  One warp per leaf: lanes 1..27 each form one
-// z_{c,k}(t) from n2 coefficients (coalesced: consecutive lanes read
-// consecutive n2-float groups), lanes 28..31 form partial density sums over
-// 8-term slices, reduced by shuffles into lane 0.
+// Per-frame IDFT table (Eq. 7 and Eq. 9 for every leaf at one time t).
+//
+// A streaming pass: each CTA walks chunks of MAT_CHUNK leaves.  One thread
+// moves a chunk's density records and SH records from HBM into a shared-memory
+// stage with two bulk asynchronous copies (completion counted in bytes on the
+// stage's mbarrier), keeping `stages` chunks in flight; all threads then form
+// the 32-float output records from shared memory, 8 threads per leaf, each
+// writing one float4 (coalesced 16-byte stores).
 
-__global__ void __launch_bounds__(256) materialise_kernel(const __grid_constant__ MaterialiseParams p)
+constexpr int MAT_CHUNK = 32;
+constexpr int MAT_THREADS = 256;
+constexpr int MAT_MAX_STAGES = 6;
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s: a stuck copy, not slowness
+
+__global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_constant__ MaterialiseParams p)
 {
+    extern __shared__ __align__(128) unsigned char mat_smem[];
+    __shared__ uint64_t bars[MAT_MAX_STAGES];
     __shared__ float s_b[MAX_BASIS];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x;
+    const int S = p.stages;
+    const uint32_t sig_bytes = MAT_CHUNK * p.sig_stride * 4u;
+    const uint32_t stage_bytes = sig_bytes + MAT_CHUNK * p.z_stride * 4u;
+    const uint32_t n_chunks = (p.n_leaves + MAT_CHUNK - 1) / MAT_CHUNK;
     const int nb = p.n1 > p.n2 ? p.n1 : p.n2;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) s_b[i] = basis_fp64(i, p.t, p.period_T);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-    float bz[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) bz[i] = i < p.n2 ? s_b[i] : 0.0f;
-    for (uint32_t leaf = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; leaf < p.n_leaves;
-         leaf += warps) {
-        float v = 0.0f;
-        if (lane >= 1 && lane <= 27) {
-            const float *z = p.zc + (size_t)leaf * p.z_stride + (lane - 1) * p.n2;
-            for (int i = 0; i < p.n2; ++i) v = fmaf(__ldg(z + i), bz[i], v);
-        } else if (lane >= 28) {
-            const float *s = p.sig + (size_t)leaf * p.sig_stride;
-            const int i0 = (lane - 28) * 16;
-            for (int i = i0; i < i0 + 16 && i < p.n1; ++i) v = fmaf(__ldg(s + i), s_b[i], v);
-        }
-        float part = lane >= 28 ? v : 0.0f;
-        part += __shfl_xor_sync(0xffffffffu, part, 1);
-        part += __shfl_xor_sync(0xffffffffu, part, 2);
-        const float sig = __shfl_sync(0xffffffffu, part, 28);
-        float outv = lane == 0 ? fmaxf(sig, 0.0f) : (lane <= 27 ? v : 0.0f);
-        p.table[(size_t)leaf * TABLE_STRIDE + lane] = outv;
+    if (tid < nb) s_b[tid] = basis_fp64(tid, p.t, p.period_T);
+    if (tid == 0) {
+        s_fail = 0;
+        for (int s = 0; s < S; ++s) ptx::mbar_init(&bars[s], 1);
+        ptx::fence_barrier_init();
     }
+    __syncthreads();
+
+    auto issue = [&](uint32_t c, int s) {
+        const uint32_t first = c * MAT_CHUNK;
+        const uint32_t m = min((uint32_t)MAT_CHUNK, p.n_leaves - first);
+        const uint32_t bs = m * p.sig_stride * 4u, bz = m * p.z_stride * 4u;
+        unsigned char *dst = mat_smem + (size_t)s * stage_bytes;
+        ptx::mbar_arrive_expect_tx(&bars[s], bs + bz);
+        ptx::bulk_g2s(dst, p.sig + (size_t)first * p.sig_stride, bs, &bars[s]);
+        ptx::bulk_g2s(dst + sig_bytes, p.zc + (size_t)first * p.z_stride, bz, &bars[s]);
+    };
+    if (tid == 0)
+        for (int s = 0; s < S; ++s) {
+            const uint32_t c = blockIdx.x + (uint32_t)s * gridDim.x;
+            if (c < n_chunks) issue(c, s);
+        }
+
+    const int l = tid >> 3, q = tid & 7;
+    uint32_t it = 0;
+    for (;; ++it) {
+        const uint32_t c = blockIdx.x + it * gridDim.x;
+        if (c >= n_chunks) break;
+        const int s = (int)(it % (uint32_t)S);
+        const uint32_t parity = (it / (uint32_t)S) & 1u;
+        if (!ptx::mbar_wait_bounded(&bars[s], parity, WAIT_LIMIT_NS)) s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        const uint32_t first = c * MAT_CHUNK;
+        const uint32_t m = min((uint32_t)MAT_CHUNK, p.n_leaves - first);
+        if ((uint32_t)l < m) {
+            const float *sg = reinterpret_cast<const float *>(mat_smem + (size_t)s * stage_bytes) + l * p.sig_stride;
+            const float *zz = reinterpret_cast<const float *>(mat_smem + (size_t)s * stage_bytes + sig_bytes) + l * p.z_stride;
+            float o[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = 4 * q + e;  // output slot
+                float v = 0.0f;
+                if (j == 0) {
+                    for (int i = 0; i < p.n1; ++i) v = fmaf(sg[i], s_b[i], v);
+                    v = fmaxf(v, 0.0f);
+                } else if (j <= 27) {
+                    const float *zq = zz + (j - 1) * p.n2;
+                    for (int i = 0; i < p.n2; ++i) v = fmaf(zq[i], s_b[i], v);
+                }
+                o[e] = v;
+            }
+            reinterpret_cast<float4 *>(p.table)[((size_t)first + l) * (TABLE_STRIDE / 4) + q] =
+                make_float4(o[0], o[1], o[2], o[3]);
+        }
+        __syncthreads();  // every thread is done with stage s
+        if (tid == 0) {
+            const uint32_t c2 = c + (uint32_t)S * gridDim.x;
+            if (c2 < n_chunks) issue(c2, s);
+        }
+    }
+    if (s_fail && tid == 0) {
+        // Drain the copies still in flight (bounded), then report.
+        for (uint32_t k = it; k < it + (uint32_t)S; ++k) {
+            const uint32_t c = blockIdx.x + k * gridDim.x;
+            if (c >= n_chunks) break;
+            ptx::mbar_wait_bounded(&bars[k % (uint32_t)S], (k / (uint32_t)S) & 1u, WAIT_LIMIT_NS);
+        }
+        atomicOr(p.status, STATUS_DEVICE_TIMEOUT);
+    }
+}
+
+int materialise_stages(int n1, int n2)
+{
+    const int stage = MAT_CHUNK * (sig_stride(n1) + z_stride(n2)) * 4;
+    int s = (100 * 1024) / stage;  // two CTAs per SM
+    if (s > MAT_MAX_STAGES) s = MAT_MAX_STAGES;
+    if (s < 2) s = 2;
+    return s;
 }
 
 int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream)
 {
     if (p.n_leaves == 0) return (int)cudaSuccess;
-    const int threads = 256;
-    uint64_t want = ((uint64_t)p.n_leaves * 32 + threads - 1) / threads;
-    uint64_t cap = (uint64_t)sm_count * 8;
-    int blocks = (int)(want < cap ? want : cap);
-    materialise_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(p);
+    const int smem = p.stages * MAT_CHUNK * (p.sig_stride + p.z_stride) * 4;
+    cudaError_t e = cudaFuncSetAttribute(materialise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return (int)e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, materialise_kernel, MAT_THREADS, smem);
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) per_sm = 1;
+    const uint32_t n_chunks = (p.n_leaves + MAT_CHUNK - 1) / MAT_CHUNK;
+    uint64_t blocks = (uint64_t)sm_count * per_sm;
+    if (blocks > n_chunks) blocks = n_chunks;
+    materialise_kernel<<<(unsigned)blocks, MAT_THREADS, smem, (cudaStream_t)stream>>>(p);
     return (int)cudaGetLastError();
 }
 
@@ -120,16 +198,51 @@ struct FrameShared {
     float sx_scale, sy_scale;
 };
 
-template <bool MAT, bool DBG, int N1, int N2>
-__device__ void trace_ray(const TraverseParams &p, const FrameShared &fs,
-                          const uint32_t *__restrict__ s_nodes, uint32_t *s_stack, int stride,
-                          uint32_t ray, int px, int py)
+// Per-lane state of one ray, kept in registers across the warp's step loop.
+struct RayState {
+    float go[3];   // origin in grid units, moved to the cube entry point
+    float gd[3];   // direction in grid units
+    float inv[3];  // 1 / gd, 0 where gd == 0
+    float Y[9];    // real SH of the unit direction (Eq. 1)
+    float C0, C1, C2, T, t;
+    int P[3];      // finest-level cell holding the current point
+    int lvl_start; // deepest ancestor level valid in the per-thread stack
+    uint32_t steps, n_visits, ray;
+};
+
+// The last node read from memory, cached in registers: a step into a sibling
+// cell (the common case at the finest level) needs no load at all.
+struct NodeCache {
+    uint4 lo, hi;  // slots 0..3, 4..7
+    uint32_t node;
+    int level;
+};
+
+__device__ __forceinline__ uint32_t pick_slot(const NodeCache &nc, uint32_t c)
 {
-    // --- ray generation (camera mode) or load (explicit rays) --------------
+    const uint4 h = (c & 4u) ? nc.hi : nc.lo;
+    return (c & 2u) ? ((c & 1u) ? h.w : h.z) : ((c & 1u) ? h.y : h.x);
+}
+
+__device__ __forceinline__ void write_result(const TraverseParams &p, const RayState &R, bool dbg)
+{
+    p.out_rgb[3 * (size_t)R.ray] = fmaf(R.T, p.bg[0], R.C0);
+    p.out_rgb[3 * (size_t)R.ray + 1] = fmaf(R.T, p.bg[1], R.C1);
+    p.out_rgb[3 * (size_t)R.ray + 2] = fmaf(R.T, p.bg[2], R.C2);
+    if (dbg) {
+        if (p.flags & FPO_FLAG_OUT_T) p.out_T[R.ray] = R.T;
+        if (p.flags & FPO_FLAG_RECORD_VISITS) p.visit_count[R.ray] = R.n_visits;
+    }
+}
+
+// Sets up ray `ray` (camera pixel (px, py) or explicit ray): generation,
+// SH basis, clip against the grid cube.  Returns false when the ray misses
+// the tree (its background result is written at once).
+template <bool DBG>
+__device__ bool init_ray(const TraverseParams &p, const FrameShared &fs, bool prt, float *s_bray,
+                         uint32_t *s_stack, RayState &R, uint32_t ray, int px, int py)
+{
     float ox, oy, oz, dx, dy, dz;
-    constexpr int NB = N1 > N2 ? N1 : N2;
-    float b[NB > 0 ? NB : 1];
-    const bool own_basis = !MAT && p.fr.mode == FPO_RAYS_EXPLICIT && p.fr.rt != nullptr;
     if (p.fr.mode == FPO_RAYS_CAMERA) {
         const float sx = (2.0f * ((float)px + 0.5f) / (float)p.fr.width - 1.0f) * fs.sx_scale;
         const float sy = (1.0f - 2.0f * ((float)py + 0.5f) / (float)p.fr.height) * fs.sy_scale;
@@ -140,12 +253,12 @@ __device__ void trace_ray(const TraverseParams &p, const FrameShared &fs,
         oy = fs.eye[1];
         oz = fs.eye[2];
     } else {
-        ox = p.fr.ro[3 * ray];
-        oy = p.fr.ro[3 * ray + 1];
-        oz = p.fr.ro[3 * ray + 2];
-        dx = p.fr.rd[3 * ray];
-        dy = p.fr.rd[3 * ray + 1];
-        dz = p.fr.rd[3 * ray + 2];
+        ox = p.fr.ro[3 * (size_t)ray];
+        oy = p.fr.ro[3 * (size_t)ray + 1];
+        oz = p.fr.ro[3 * (size_t)ray + 2];
+        dx = p.fr.rd[3 * (size_t)ray];
+        dy = p.fr.rd[3 * (size_t)ray + 1];
+        dz = p.fr.rd[3 * (size_t)ray + 2];
     }
     {
         const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
@@ -153,221 +266,242 @@ __device__ void trace_ray(const TraverseParams &p, const FrameShared &fs,
         dy *= inv;
         dz *= inv;
     }
-    if (!MAT) {
-        if (own_basis) {
-            const float u = p.fr.rt[ray] / (float)p.fr.period_T;
-#pragma unroll
-            for (int i = 0; i < NB; ++i) b[i] = basis_fp32(i, u);
-        } else {
-#pragma unroll
-            for (int i = 0; i < NB; ++i) b[i] = fs.b[i];
-        }
+    if (prt) {
+        // Eq. 8 at this ray's own time, one column of the per-thread table
+        const float u = p.fr.rt[ray] / (float)p.fr.period_T;
+        const int nb = p.n1 > p.n2 ? p.n1 : p.n2;
+        for (int i = 0; i < nb; ++i) s_bray[i * TRAV_THREADS] = basis_fp32(i, u);
     }
-    float Y[9];
-    sh_basis(dx, dy, dz, Y);
+    sh_basis(dx, dy, dz, R.Y);
+    R.C0 = R.C1 = R.C2 = 0.0f;
+    R.T = 1.0f;
+    R.t = 0.0f;
+    R.steps = 0;
+    R.n_visits = 0;
+    R.ray = ray;
+    R.lvl_start = 0;
 
-    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
-    uint32_t n_visits = 0;
-
-    // --- clip against the grid [0, G]^3 in grid units ---------------------
-    const int D = p.depth;
-    const int G = 1 << D;
+    const int G = 1 << p.depth;
     const float gs = p.grid_scale;
-    float go[3] = {(ox - p.amin[0]) * gs, (oy - p.amin[1]) * gs, (oz - p.amin[2]) * gs};
-    const float gd[3] = {dx * gs, dy * gs, dz * gs};
-    float inv[3];
+    R.go[0] = (ox - p.amin[0]) * gs;
+    R.go[1] = (oy - p.amin[1]) * gs;
+    R.go[2] = (oz - p.amin[2]) * gs;
+    R.gd[0] = dx * gs;
+    R.gd[1] = dy * gs;
+    R.gd[2] = dz * gs;
     float t0 = 0.0f, t1 = FLT_MAX;
     bool hit = p.root_kind != ROOT_EMPTY;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (gd[a] != 0.0f) {
-            inv[a] = 1.0f / gd[a];
-            const float ta = (0.0f - go[a]) * inv[a], tb = ((float)G - go[a]) * inv[a];
+        if (R.gd[a] != 0.0f) {
+            R.inv[a] = 1.0f / R.gd[a];
+            const float ta = (0.0f - R.go[a]) * R.inv[a], tb = ((float)G - R.go[a]) * R.inv[a];
             t0 = fmaxf(t0, fminf(ta, tb));
             t1 = fminf(t1, fmaxf(ta, tb));
         } else {
-            inv[a] = 0.0f;
-            if (go[a] < 0.0f || go[a] > (float)G) hit = false;
+            R.inv[a] = 0.0f;
+            if (R.go[a] < 0.0f || R.go[a] > (float)G) hit = false;
         }
     }
-    hit = hit && (t0 < t1);
-
-    if (hit) {
-        // Work relative to the entry point: t measured from there.
+    if (!(hit && t0 < t1)) {
+        write_result(p, R, DBG);
+        return false;
+    }
+    // Distances are measured from the entry point from here on.
 #pragma unroll
-        for (int a = 0; a < 3; ++a) go[a] = fmaf(t0, gd[a], go[a]);
-        int P[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) P[a] = min(max((int)floorf(go[a]), 0), G - 1);
+    for (int a = 0; a < 3; ++a) {
+        R.go[a] = fmaf(t0, R.gd[a], R.go[a]);
+        R.P[a] = min(max((int)floorf(R.go[a]), 0), G - 1);
+    }
+    s_stack[0] = 0;
+    return true;
+}
 
-        float t = 0.0f;
-        uint32_t steps = 0;
-        int lvl_start = 0;  // deepest ancestor level still valid in the stack
-        uint32_t node = 0;
-        if (p.root_kind == ROOT_NODE) s_stack[0] = 0;
+// One traversal step: locate the cube holding R.P, shade it if it is a leaf
+// with a non-empty segment, and move to the neighbouring cube.  Returns false
+// once the ray is finished (left the grid, early stop, or step cap).
+template <bool MAT, bool DBG, int N1, int N2>
+__device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const float *bsrc,
+                         int bstride, const uint32_t *__restrict__ s_nodes, uint32_t *s_stack,
+                         RayState &R, NodeCache &nc)
+{
+    const int D = p.depth;
+    const int G = 1 << D;
+    // --- locate the cube containing P ---------------------------------------
+    int lvl;
+    uint32_t kind, leaf = 0;
+    if (p.root_kind == ROOT_LEAF) {
+        lvl = 0;
+        kind = ROOT_LEAF;
+    } else {
+        lvl = R.lvl_start;
+        uint32_t node = s_stack[lvl * TRAV_THREADS];
         for (;;) {
-            // --- locate the cube containing P -----------------------------
-            int lvl = lvl_start;
-            uint32_t kind, leaf = 0;
-            if (p.root_kind == ROOT_LEAF) {
-                lvl = 0;
-                kind = ROOT_LEAF;
-            } else {
-                node = s_stack[lvl * stride];
-                for (;;) {
-                    const int sh = D - 1 - lvl;
-                    const uint32_t c = ((P[0] >> sh) & 1) | (((P[1] >> sh) & 1) << 1) |
-                                       (((P[2] >> sh) & 1) << 2);
-                    const uint32_t idx = node * 8 + c;
-                    const uint32_t s = idx < p.n_smem_nodes * 8 ? s_nodes[idx] : __ldg(p.nodes + idx);
-                    ++lvl;
-                    if (s == 0u) { kind = ROOT_EMPTY; break; }
-                    if (s & LEAF_BIT) { kind = ROOT_LEAF; leaf = s & ~LEAF_BIT; break; }
-                    node = s;
-                    s_stack[lvl * stride] = node;
-                }
-            }
-            // --- exit of the cube: level lvl, size 2^(D - lvl) cells -------
-            const int csz = 1 << (D - lvl);
-            float te[3];
-            int lo[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                lo[a] = P[a] & ~(csz - 1);
-                if (gd[a] > 0.0f)
-                    te[a] = ((float)(lo[a] + csz) - go[a]) * inv[a];
-                else if (gd[a] < 0.0f)
-                    te[a] = ((float)lo[a] - go[a]) * inv[a];
-                else
-                    te[a] = FLT_MAX;
-            }
-            int m = 0;
-            float tx = te[0];
-            if (te[1] < tx) { tx = te[1]; m = 1; }
-            if (te[2] < tx) { tx = te[2]; m = 2; }
-
-            // --- shade a leaf segment ------------------------------------
-            if (kind == ROOT_LEAF && tx > t) {
-                const float delta = tx - t;
-                float sigma, z[27];
-                if (MAT) {
-                    const float4 *rec = p.table + (size_t)leaf * (TABLE_STRIDE / 4);
-                    float v[28];
-#pragma unroll
-                    for (int q = 0; q < 7; ++q) {
-                        const float4 w = __ldg(rec + q);
-                        v[4 * q] = w.x;
-                        v[4 * q + 1] = w.y;
-                        v[4 * q + 2] = w.z;
-                        v[4 * q + 3] = w.w;
-                    }
-                    sigma = v[0];
-#pragma unroll
-                    for (int q = 0; q < 27; ++q) z[q] = v[q + 1];
+            const int sh = D - 1 - lvl;
+            const uint32_t c = ((R.P[0] >> sh) & 1) | (((R.P[1] >> sh) & 1) << 1) |
+                               (((R.P[2] >> sh) & 1) << 2);
+            if (!(nc.node == node && nc.level == lvl)) {
+                const uint4 *q = node < p.n_smem_nodes
+                                     ? reinterpret_cast<const uint4 *>(s_nodes) + 2 * node
+                                     : reinterpret_cast<const uint4 *>(p.nodes) + 2 * (size_t)node;
+                if (node < p.n_smem_nodes) {
+                    nc.lo = q[0];
+                    nc.hi = q[1];
                 } else {
-                    // Eq. 7 then Eq. 9 at this visit, from the stored records.
-                    const float4 *sr = p.sig + (size_t)leaf * p.sig_stride4;
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int q = 0; q < (N1 + 3) / 4; ++q) {
-                        const float4 w = __ldg(sr + q);
-                        const float wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (4 * q + j < N1) acc = fmaf(wv[j], b[4 * q + j], acc);
-                    }
-                    sigma = fmaxf(acc, 0.0f);
-                    const float4 *zr = reinterpret_cast<const float4 *>(p.zc + (size_t)leaf * p.z_stride);
-#pragma unroll
-                    for (int q = 0; q < 27; ++q) z[q] = 0.0f;
-#pragma unroll
-                    for (int q4 = 0; q4 < (27 * N2 + 3) / 4; ++q4) {
-                        const float4 w = __ldg(zr + q4);
-                        const float wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int e = 4 * q4 + j;
-                            if (e < 27 * N2) z[e / N2] = fmaf(wv[j], b[e % N2], z[e / N2]);
-                        }
-                    }
+                    nc.lo = __ldg(q);
+                    nc.hi = __ldg(q + 1);
                 }
-                float col[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    float s = 0.0f;
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) s = fmaf(z[9 * c + k], Y[k], s);
-                    col[c] = sigmoidf_(s);
-                }
-                const float e = __expf(-sigma * delta);
-                const float w = T * (1.0f - e);
-                C0 = fmaf(w, col[0], C0);
-                C1 = fmaf(w, col[1], C1);
-                C2 = fmaf(w, col[2], C2);
-                T *= e;
-                if (DBG) {
-                    if (p.flags & FPO_FLAG_RECORD_VISITS) {
-                        if (n_visits < p.visit_cap)
-                            p.visit_log[(size_t)ray * p.visit_cap + n_visits] = p.perm[leaf];
-                        else
-                            atomicOr(p.status, STATUS_VISIT_OVERFLOW);
-                    }
-                    if (p.flags & FPO_FLAG_MARK_LEAVES) p.leaf_mark[p.perm[leaf]] = 1;
-                }
-                ++n_visits;
-                if (T < p.stop_T) break;
+                nc.node = node;
+                nc.level = lvl;
             }
-            // --- step into the neighbour cube ----------------------------
-            // Along m: the adjacent cube; along the other axes: the cell
-            // holding the exit point, clamped to this cube's extent and never
-            // moving backwards (so every step makes progress).
-            int Pn[3];
-            bool inside = true;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (a == m) {
-                    Pn[a] = gd[a] > 0.0f ? lo[a] + csz : lo[a] - 1;
-                    inside = Pn[a] >= 0 && Pn[a] < G;
-                } else {
-                    int q = (int)floorf(fmaf(tx, gd[a], go[a]));
-                    q = min(max(q, lo[a]), lo[a] + csz - 1);
-                    if (gd[a] > 0.0f) q = max(q, P[a]);
-                    else if (gd[a] < 0.0f) q = min(q, P[a]);
-                    Pn[a] = q;
-                }
-            }
-            if (!inside) break;
-            t = fmaxf(t, tx);
-            // deepest common ancestor of the old and the new cell
-            const uint32_t diff = (uint32_t)((P[0] ^ Pn[0]) | (P[1] ^ Pn[1]) | (P[2] ^ Pn[2]));
-            const int hb = 31 - __clz(diff);  // diff != 0: P moved along m
-            lvl_start = D - 1 - hb;
-            P[0] = Pn[0];
-            P[1] = Pn[1];
-            P[2] = Pn[2];
-            if (++steps > p.max_steps) {
-                atomicOr(p.status, STATUS_TRAVERSAL_LIMIT);
-                break;
-            }
+            const uint32_t sl = pick_slot(nc, c);
+            ++lvl;
+            if (sl == 0u) { kind = ROOT_EMPTY; break; }
+            if (sl & LEAF_BIT) { kind = ROOT_LEAF; leaf = sl & ~LEAF_BIT; break; }
+            node = sl;
+            s_stack[lvl * TRAV_THREADS] = node;
         }
     }
-    const float bgw = T;
-    p.out_rgb[3 * (size_t)ray] = fmaf(bgw, p.bg[0], C0);
-    p.out_rgb[3 * (size_t)ray + 1] = fmaf(bgw, p.bg[1], C1);
-    p.out_rgb[3 * (size_t)ray + 2] = fmaf(bgw, p.bg[2], C2);
-    if (DBG) {
-        if (p.flags & FPO_FLAG_OUT_T) p.out_T[ray] = T;
-        if (p.flags & FPO_FLAG_RECORD_VISITS) p.visit_count[ray] = n_visits;
+    // --- exit of the cube: level lvl, 2^(D - lvl) finest cells a side --------
+    const int csz = 1 << (D - lvl);
+    float te[3];
+    int lo[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = R.P[a] & ~(csz - 1);
+        if (R.gd[a] > 0.0f)
+            te[a] = ((float)(lo[a] + csz) - R.go[a]) * R.inv[a];
+        else if (R.gd[a] < 0.0f)
+            te[a] = ((float)lo[a] - R.go[a]) * R.inv[a];
+        else
+            te[a] = FLT_MAX;
     }
+    int m = 0;
+    float tx = te[0];
+    if (te[1] < tx) { tx = te[1]; m = 1; }
+    if (te[2] < tx) { tx = te[2]; m = 2; }
+
+    // --- shade a leaf segment (Eq. 7, 9, 1; emission-absorption) -------------
+    bool stop = false;
+    if (kind == ROOT_LEAF && tx > R.t) {
+        const float delta = tx - R.t;
+        float sigma, z[27];
+        if constexpr (MAT) {
+            const float4 *rec = p.table + (size_t)leaf * (TABLE_STRIDE / 4);
+            float v[28];
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                const float4 w = __ldg(rec + q);
+                v[4 * q] = w.x;
+                v[4 * q + 1] = w.y;
+                v[4 * q + 2] = w.z;
+                v[4 * q + 3] = w.w;
+            }
+            sigma = v[0];
+#pragma unroll
+            for (int q = 0; q < 27; ++q) z[q] = v[q + 1];
+        } else {
+            const float4 *sr = p.sig + (size_t)leaf * p.sig_stride4;
+            float acc = 0.0f;
+#pragma unroll
+            for (int q = 0; q < (N1 + 3) / 4; ++q) {
+                const float4 w = __ldg(sr + q);
+                const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (4 * q + j < N1) acc = fmaf(wv[j], bsrc[(4 * q + j) * bstride], acc);
+            }
+            sigma = fmaxf(acc, 0.0f);
+            float bz[N2];
+#pragma unroll
+            for (int i = 0; i < N2; ++i) bz[i] = bsrc[i * bstride];
+            const float4 *zr = reinterpret_cast<const float4 *>(p.zc + (size_t)leaf * p.z_stride);
+#pragma unroll
+            for (int q = 0; q < 27; ++q) z[q] = 0.0f;
+#pragma unroll
+            for (int q4 = 0; q4 < (27 * N2 + 3) / 4; ++q4) {
+                const float4 w = __ldg(zr + q4);
+                const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int e = 4 * q4 + j;
+                    if (e < 27 * N2) z[e / N2] = fmaf(wv[j], bz[e % N2], z[e / N2]);
+                }
+            }
+        }
+        float col[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float sacc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) sacc = fmaf(z[9 * c + k], R.Y[k], sacc);
+            col[c] = sigmoidf_(sacc);
+        }
+        const float e = __expf(-sigma * delta);
+        const float w = R.T * (1.0f - e);
+        R.C0 = fmaf(w, col[0], R.C0);
+        R.C1 = fmaf(w, col[1], R.C1);
+        R.C2 = fmaf(w, col[2], R.C2);
+        R.T *= e;
+        if (DBG) {
+            if (p.flags & FPO_FLAG_RECORD_VISITS) {
+                if (R.n_visits < p.visit_cap)
+                    p.visit_log[(size_t)R.ray * p.visit_cap + R.n_visits] = p.perm[leaf];
+                else
+                    atomicOr(p.status, STATUS_VISIT_OVERFLOW);
+            }
+            if (p.flags & FPO_FLAG_MARK_LEAVES) p.leaf_mark[p.perm[leaf]] = 1;
+        }
+        ++R.n_visits;
+        stop = R.T < p.stop_T;
+    }
+    if (stop) return false;
+    // --- step into the neighbour cube ---------------------------------------
+    // Along m: the adjacent cube; along the other axes: the cell holding the
+    // exit point, clamped to this cube's extent and never moving backwards,
+    // so every step makes progress.
+    int Pn[3];
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a == m) {
+            Pn[a] = R.gd[a] > 0.0f ? lo[a] + csz : lo[a] - 1;
+            inside = Pn[a] >= 0 && Pn[a] < G;
+        } else {
+            int q = (int)floorf(fmaf(tx, R.gd[a], R.go[a]));
+            q = min(max(q, lo[a]), lo[a] + csz - 1);
+            if (R.gd[a] > 0.0f) q = max(q, R.P[a]);
+            else if (R.gd[a] < 0.0f) q = min(q, R.P[a]);
+            Pn[a] = q;
+        }
+    }
+    if (!inside) return false;
+    R.t = fmaxf(R.t, tx);
+    // deepest common ancestor of the old and the new cell
+    const uint32_t diff = (uint32_t)((R.P[0] ^ Pn[0]) | (R.P[1] ^ Pn[1]) | (R.P[2] ^ Pn[2]));
+    R.lvl_start = D - 1 - (31 - __clz(diff));
+    R.P[0] = Pn[0];
+    R.P[1] = Pn[1];
+    R.P[2] = Pn[2];
+    if (++R.steps > p.max_steps) {
+        atomicOr(p.status, STATUS_TRAVERSAL_LIMIT);
+        return false;
+    }
+    return true;
 }
 
 }  // namespace
 
-// Persistent kernel: a grid of (SM count x resident CTAs) pulls warp-sized
-// tiles (8x4 pixels, or 32 consecutive explicit rays) from one atomic
-// counter.  Each CTA first stages the top n_smem_nodes nodes of the
-// breadth-first node array and the frame constants in shared memory.  The
-// last CTA to finish resets the counter for the next launch.
+// Persistent kernel: a grid of (SM count x resident CTAs) whose warps pull
+// warp-sized tiles (8x4 pixels, or 32 consecutive explicit rays) from one
+// atomic counter.  Warp-level ray compaction: every lane holds its own ray;
+// when at least REFILL_MIN lanes are idle, the warp hands them the next rays
+// of its current tile (fetching a new tile when that one is used up), so
+// long rays do not leave most of a warp idle.  Each CTA first stages the top
+// n_smem_nodes nodes of the breadth-first node array and the frame constants
+// in shared memory.  The last CTA to finish resets the counter.
+constexpr int REFILL_MIN = 8;
+
 template <bool MAT, bool DBG, int N1, int N2>
 __global__ void __launch_bounds__(TRAV_THREADS) traverse_kernel(const __grid_constant__ TraverseParams p)
 {
@@ -375,6 +509,8 @@ __global__ void __launch_bounds__(TRAV_THREADS) traverse_kernel(const __grid_con
     __shared__ FrameShared fs;
     uint32_t *s_nodes = smem;
     uint32_t *s_stack = smem + p.n_smem_nodes * 8;
+    float *s_bray = reinterpret_cast<float *>(s_stack + STACK_LEVELS * TRAV_THREADS);
+    const bool prt = !MAT && p.fr.mode == FPO_RAYS_EXPLICIT && p.fr.rt != nullptr;
 
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(p.nodes);
@@ -410,26 +546,63 @@ __global__ void __launch_bounds__(TRAV_THREADS) traverse_kernel(const __grid_con
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
+    const uint32_t lt_mask = (1u << lane) - 1u;
     uint32_t *my_stack = s_stack + threadIdx.x;
+    float *my_b = s_bray + threadIdx.x;
+    const float *bsrc = prt ? my_b : fs.b;
+    const int bstride = prt ? TRAV_THREADS : 1;
+
+    auto grab_tile = [&]() -> uint32_t {
+        uint32_t tl = 0;
+        if (lane == 0) tl = atomicAdd(p.status + 1, 1u);
+        return __shfl_sync(0xffffffffu, tl, 0);
+    };
+    uint32_t cur_tile = grab_tile();  // warp-uniform cursor: tile and next ray in it
+    uint32_t cur_next = 0;
+    RayState R;
+    NodeCache nc;
+    nc.node = 0xffffffffu;
+    nc.level = -1;
+    bool active = false;
     for (;;) {
-        uint32_t tile = 0;
-        if (lane == 0) tile = atomicAdd(p.status + 1, 1u);
-        tile = __shfl_sync(0xffffffffu, tile, 0);
-        if (tile >= p.n_tiles) break;
-        uint32_t ray;
-        int px = 0, py = 0;
-        bool valid;
-        if (p.fr.mode == FPO_RAYS_CAMERA) {
-            const uint32_t tx = tile % p.tiles_x, ty = tile / p.tiles_x;
-            px = (int)(tx * 8 + (lane & 7));
-            py = (int)(ty * 4 + (lane >> 3));
-            valid = px < (int)p.fr.width && py < (int)p.fr.height;
-            ray = (uint32_t)py * p.fr.width + (uint32_t)px;
-        } else {
-            ray = tile * 32 + lane;
-            valid = ray < p.fr.n_rays;
+        uint32_t idle = __ballot_sync(0xffffffffu, !active);
+        if (__popc(idle) >= REFILL_MIN) {
+            while (idle && cur_tile < p.n_tiles) {
+                const uint32_t take = min(32u - cur_next, (uint32_t)__popc(idle));
+                const uint32_t rank = __popc(idle & lt_mask);
+                if (((idle >> lane) & 1u) && rank < take) {
+                    const uint32_t k = cur_next + rank;  // ray within the tile
+                    uint32_t ray;
+                    int px = 0, py = 0;
+                    bool valid;
+                    if (p.fr.mode == FPO_RAYS_CAMERA) {
+                        const uint32_t tx = cur_tile % p.tiles_x, ty = cur_tile / p.tiles_x;
+                        px = (int)(tx * 8 + (k & 7));
+                        py = (int)(ty * 4 + (k >> 3));
+                        valid = px < (int)p.fr.width && py < (int)p.fr.height;
+                        ray = (uint32_t)py * p.fr.width + (uint32_t)px;
+                    } else {
+                        ray = cur_tile * 32 + k;
+                        valid = ray < p.fr.n_rays;
+                    }
+                    if (valid) active = init_ray<DBG>(p, fs, prt, my_b, my_stack, R, ray, px, py);
+                }
+                cur_next += take;
+                if (cur_next >= 32) {
+                    cur_tile = grab_tile();
+                    cur_next = 0;
+                }
+                idle = __ballot_sync(0xffffffffu, !active);
+                if (__popc(idle) < REFILL_MIN) break;
+            }
         }
-        if (valid) trace_ray<MAT, DBG, N1, N2>(p, fs, s_nodes, my_stack, TRAV_THREADS, ray, px, py);
+        if (!__any_sync(0xffffffffu, active)) break;
+        if (active) {
+            if (!step_ray<MAT, DBG, N1, N2>(p, fs, bsrc, bstride, s_nodes, my_stack, R, nc)) {
+                write_result(p, R, DBG);
+                active = false;
+            }
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -442,9 +615,10 @@ __global__ void __launch_bounds__(TRAV_THREADS) traverse_kernel(const __grid_con
     }
 }
 
-int traverse_smem_bytes(uint32_t n_smem_nodes)
+int traverse_smem_bytes(uint32_t n_smem_nodes, bool per_ray_basis)
 {
-    return (int)(n_smem_nodes * 32u + STACK_LEVELS * TRAV_THREADS * 4u);
+    return (int)(n_smem_nodes * 32u + STACK_LEVELS * TRAV_THREADS * 4u +
+                 (per_ray_basis ? 32u * TRAV_THREADS * 4u : 0u));
 }
 
 int traverse_block_threads() { return TRAV_THREADS; }
@@ -452,7 +626,8 @@ int traverse_block_threads() { return TRAV_THREADS; }
 template <bool MAT, bool DBG, int N1, int N2>
 static int launch_t(const TraverseParams &p, int sm_count, cudaStream_t s)
 {
-    const int smem = traverse_smem_bytes(p.n_smem_nodes);
+    const bool prt = !MAT && p.fr.mode == FPO_RAYS_EXPLICIT && p.fr.rt != nullptr;
+    const int smem = traverse_smem_bytes(p.n_smem_nodes, prt);
     auto k = traverse_kernel<MAT, DBG, N1, N2>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return (int)e;

@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
 
 import numpy as np
 
@@ -89,6 +90,29 @@ def draw_coefficients(rng: np.random.Generator, n: int, n1: int = 31, n2: int = 
         std_z[1:] = 0.2 / (np.arange(1, n2) + 1.0)
     z = rng.standard_normal((n, 3, N_SH, n2), dtype=np.float32) * std_z
     out[:, n1:] = z.reshape(n, -1)
+    return out
+
+
+def draw_coefficients_blocked(seed: int, n: int, n1: int = 31, n2: int = 5,
+                              block: int = 1 << 16, workers: int | None = None) -> np.ndarray:
+    """Same distributions as draw_coefficients for large n, drawn in blocks.
+
+    Leaves [b * block, (b + 1) * block) come from
+    draw_coefficients(default_rng(SeedSequence(seed, spawn_key=(b,))), ...);
+    blocks are independent, so the result does not depend on `workers`.
+    """
+    import concurrent.futures as cf
+
+    out = np.empty((n, n1 + 3 * N_SH * n2), dtype=np.float32)
+    nblk = (n + block - 1) // block
+
+    def one(b):
+        lo, hi = b * block, min(n, (b + 1) * block)
+        rng = np.random.default_rng(np.random.SeedSequence(seed, spawn_key=(b,)))
+        out[lo:hi] = draw_coefficients(rng, hi - lo, n1, n2)
+
+    with cf.ThreadPoolExecutor(workers or min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(one, range(nblk)))
     return out
 
 
@@ -206,10 +230,13 @@ def capsule_union_leaves(a: np.ndarray, b: np.ndarray, radii: np.ndarray, depth:
     the exact per-cell test, done on fewer cells.  Returns uint32 [n, 3]
     sorted by Morton key.
     """
+    import concurrent.futures as cf
+
     g = 1 << depth
     occ = np.zeros((g, g, g), dtype=bool)
     h_fine = 1.0 / g
-    for c in range(a.shape[0]):
+
+    def one(c):
         A, B, r = a[c], b[c], float(radii[c])
         lo = np.minimum(A.min(0), B.min(0)) - r
         hi = np.maximum(A.max(0), B.max(0)) + r
@@ -246,6 +273,10 @@ def capsule_union_leaves(a: np.ndarray, b: np.ndarray, radii: np.ndarray, depth:
             live = np.repeat(live, 8, axis=0)
             cand = kids
             level += 1
+
+    # capsules are independent; concurrent writes only ever store True
+    with cf.ThreadPoolExecutor(min(a.shape[0], os.cpu_count() or 1)) as ex:
+        list(ex.map(one, range(a.shape[0])))
     idx = np.argwhere(occ).astype(np.uint32)
     order = np.argsort(morton_key(idx, depth), kind="stable")
     return idx[order]
@@ -299,16 +330,31 @@ def shell_camera(width: int = 128, height: int = 128) -> Camera:
 SHELL_T = 0.37 * PERIOD_T  # frame time of the 128x128 parity case
 
 
-def body_tree(seed: int = 0, depth: int = 9, n1: int = 31, n2: int = 5) -> Tree:
+def body_tree(seed: int = 0, depth: int = 9, n1: int = 31, n2: int = 5,
+              cache_dir: str | None = None) -> Tree:
     """Depth-9 union over 60 frames of the animated 14-capsule body, i.i.d. coefficients.
 
-    Draw order from default_rng(seed): the capsule body (capsule_body), then
-    the coefficients of the Morton-sorted leaves (draw_coefficients).
+    default_rng(seed) draws the capsule body (capsule_body); the coefficients
+    of the Morton-sorted leaves come from draw_coefficients_blocked(seed + 1).
+    With `cache_dir` (or $FPO_SYNTH_CACHE) the result is kept in .npy files.
     """
+    cache_dir = cache_dir or os.environ.get("FPO_SYNTH_CACHE")
+    key = f"body_s{seed}_d{depth}_n{n1}_{n2}"
+    if cache_dir:
+        fx, fc = (os.path.join(cache_dir, f"{key}_{w}.npy") for w in ("xyz", "coef"))
+        if os.path.exists(fx) and os.path.exists(fc):
+            xyz = np.load(fx)
+            coeffs = np.load(fc, mmap_mode="r")
+            return Tree(np.full(xyz.shape[0], depth, np.uint8), xyz, np.ascontiguousarray(coeffs),
+                        depth, n1, n2)
     rng = np.random.default_rng(seed)
     a, b, r = capsule_body(rng)
     xyz = capsule_union_leaves(a, b, r, depth)
-    coeffs = draw_coefficients(rng, xyz.shape[0], n1, n2)
+    coeffs = draw_coefficients_blocked(seed + 1, xyz.shape[0], n1, n2)
+    if cache_dir:
+        os.makedirs(cache_dir, exist_ok=True)
+        np.save(fx, xyz)
+        np.save(fc, coeffs)
     return Tree(np.full(xyz.shape[0], depth, np.uint8), xyz, coeffs, depth, n1, n2)
 
 
