@@ -71,6 +71,11 @@ typedef struct {
     int32_t storage;   /* FPO_STORAGE_* */
     int32_t idft_mode; /* FPO_IDFT_* */
     int32_t device;    /* CUDA device ordinal the context lives on */
+    /* Launch tuning of the traversal (0 = library default): threads per CTA
+     * (128 or 256), and the number of idle lanes at which a warp refills them
+     * with new rays (1..32; 32 refills only a fully idle warp). */
+    int32_t traverse_threads;
+    int32_t refill_min;
 } fpo_config;
 
 /* A union octree given by its leaves (Sec. 4.2): leaf j is the cell
@@ -115,7 +120,8 @@ typedef struct {
 enum {
     FPO_FLAG_RECORD_VISITS = 1, /* write visit_log / visit_count */
     FPO_FLAG_OUT_T = 2,         /* write the final transmittance to out_T */
-    FPO_FLAG_MARK_LEAVES = 4    /* set leaf_mark[id] = 1 for every visited leaf */
+    FPO_FLAG_MARK_LEAVES = 4,   /* set leaf_mark[id] = 1 for every visited leaf */
+    FPO_FLAG_STATS = 8          /* add traversal counters to stats[0..2] */
 };
 
 /* Per-call options.  bg: background colour added with the final
@@ -124,7 +130,8 @@ enum {
  * used only when its flag is set: visit_log [rays][visit_cap] and
  * visit_count [rays] (leaf ids in visit order, count may exceed visit_cap,
  * which then also raises FPO_ERR_VISIT_OVERFLOW), out_T [rays], leaf_mark
- * [n_leaves] (never cleared by the library).  events: optional cudaEvent_t
+ * [n_leaves] (never cleared by the library), stats [3] (device, accumulated:
+ * traversal steps, leaf visits, rays that entered the tree).  events: optional cudaEvent_t
  * handles recorded on the stream before the first kernel of the frame,
  * between the IDFT pass and the traversal, and after the traversal. */
 typedef struct {
@@ -136,6 +143,7 @@ typedef struct {
     uint32_t *visit_count;
     float *out_T;
     uint8_t *leaf_mark;
+    uint64_t *stats;
     void *events[3];
 } fpo_frame_opts;
 
@@ -148,7 +156,7 @@ typedef struct {
 } fpo_tree_info;
 
 /* Creates a context on cfg->device.  Validates n1 in [1, 32], n2 in [1, 16],
- * sh_degree == 2, period_T > 0, storage and idft_mode values.
+ * sh_degree == 2, period_T > 0, storage, idft_mode and tuning values.
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA, OOM.  *out is NULL on failure. */
 int fpo_create(fpo_ctx **out, const fpo_config *cfg);
 

@@ -40,16 +40,22 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          defines: tuple = (), lib: str | None = None) -> str:
+    """Compiles libfpo.so.  `defines` (e.g. ("FPO_TRAV_MIN_BLOCKS=4",)) and
+    `lib` (an output path) build tuning variants next to the default library."""
+    target = lib or LIB
+    if not force and not defines and lib is None and up_to_date():
         return LIB
     os.makedirs(OUT, exist_ok=True)
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+    common += [f"-D{d}" for d in defines]
+    tag = "" if lib is None else "_" + os.path.splitext(os.path.basename(lib))[0]
     if ptxas_info:
         common += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(OUT, os.path.splitext(src)[0] + tag + ".o")
         cmd = [nvcc()] + ARCH + common + ["-c", os.path.join(SRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -62,13 +68,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         for _, log in results:
             if log.strip():
                 print(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = target + f".tmp{os.getpid()}"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, target)
+    return target
 
 
 if __name__ == "__main__":

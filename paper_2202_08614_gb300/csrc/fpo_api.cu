@@ -56,7 +56,9 @@ void dfree(T *&p)
     p = nullptr;
 }
 
-constexpr uint32_t SMEM_NODE_BUDGET = 1024;  // 32 KB of top-level nodes per CTA
+constexpr uint32_t SMEM_NODE_BUDGET = 512;  // 16 KB of top-level nodes per CTA
+constexpr int DEFAULT_TRAVERSE_THREADS = 128;
+constexpr uint32_t DEFAULT_REFILL_MIN = 32;
 
 }  // namespace
 
@@ -111,6 +113,10 @@ int fpo_create(fpo_ctx **out, const fpo_config *cfg)
         return fail(FPO_ERR_UNSUPPORTED, "storage %d is not implemented", cfg->storage);
     if (cfg->idft_mode < FPO_IDFT_AUTO || cfg->idft_mode > FPO_IDFT_MATERIALISE)
         return fail(FPO_ERR_INVALID_ARG, "unknown idft_mode %d", cfg->idft_mode);
+    if (cfg->traverse_threads != 0 && cfg->traverse_threads != 128 && cfg->traverse_threads != 256)
+        return fail(FPO_ERR_INVALID_ARG, "traverse_threads must be 0, 128 or 256");
+    if (cfg->refill_min < 0 || cfg->refill_min > 32)
+        return fail(FPO_ERR_INVALID_ARG, "refill_min must be in [0, 32]");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
@@ -248,6 +254,7 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
     if ((fl & FPO_FLAG_RECORD_VISITS) && (!opts->visit_count || (opts->visit_cap && !opts->visit_log)))
         return fail(FPO_ERR_INVALID_ARG, "RECORD_VISITS needs visit_count (and visit_log if visit_cap > 0)");
     if ((fl & FPO_FLAG_OUT_T) && !opts->out_T) return fail(FPO_ERR_INVALID_ARG, "OUT_T needs out_T");
+    if ((fl & FPO_FLAG_STATS) && !opts->stats) return fail(FPO_ERR_INVALID_ARG, "STATS needs stats");
     if ((fl & FPO_FLAG_MARK_LEAVES) && !opts->leaf_mark && ctx->n_leaves)
         return fail(FPO_ERR_INVALID_ARG, "MARK_LEAVES needs leaf_mark");
     if (!(opts->stop_T >= 0.0f)) return fail(FPO_ERR_INVALID_ARG, "stop_T must be >= 0");
@@ -345,7 +352,11 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
         p.n_tiles = (uint32_t)((n_rays + 31) / 32);
     }
     p.max_steps = 3u * (1u << ctx->depth) + 16u;
-    const bool dbg = (fl & (FPO_FLAG_RECORD_VISITS | FPO_FLAG_OUT_T | FPO_FLAG_MARK_LEAVES)) != 0;
+    p.block_threads = ctx->cfg.traverse_threads ? ctx->cfg.traverse_threads : DEFAULT_TRAVERSE_THREADS;
+    p.refill_min = ctx->cfg.refill_min ? (uint32_t)ctx->cfg.refill_min : DEFAULT_REFILL_MIN;
+    p.stats = reinterpret_cast<unsigned long long *>(opts->stats);
+    const bool dbg = (fl & (FPO_FLAG_RECORD_VISITS | FPO_FLAG_OUT_T | FPO_FLAG_MARK_LEAVES |
+                            FPO_FLAG_STATS)) != 0;
     int ce = launch_traverse(p, mat, dbg, ctx->sm_count, s);
     if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "traverse launch");
     if ((e = rec(2)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");

@@ -91,6 +91,9 @@ struct TraverseParams {
     uint32_t *status;         // [0] status bits, [1] tile counter, [2] finished CTAs
     uint32_t n_tiles, tiles_x;
     uint32_t max_steps;
+    uint32_t refill_min;      // warp refills its idle lanes once this many are idle (32: whole tiles)
+    int block_threads;        // 128 or 256
+    unsigned long long *stats; // FPO_FLAG_STATS: [steps, leaf visits, rays entering the tree]
 };
 
 struct MaterialiseParams {
@@ -109,8 +112,7 @@ int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream);
 int materialise_stages(int n1, int n2);
 int launch_traverse(const TraverseParams &p, bool materialised, bool debug, int sm_count,
                     void *stream);
-int traverse_smem_bytes(uint32_t n_smem_nodes, bool per_ray_basis);
+int traverse_smem_bytes(uint32_t n_smem_nodes, bool per_ray_basis, int threads);
 bool fused_supported(int n1, int n2);
-int traverse_block_threads();
 
 }  // namespace fpo

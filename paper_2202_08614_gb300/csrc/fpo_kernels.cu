@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
             if (c < n_chunks) issue(c, s);
         }
 
-    const int l = tid >> 3, q = tid & 7;
+    const int warp = tid >> 5, lane = tid & 31;
     uint32_t it = 0;
     for (;; ++it) {
         const uint32_t c = blockIdx.x + it * gridDim.x;
@@ -123,26 +123,29 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
         __syncthreads();
         if (s_fail) break;
         const uint32_t first = c * MAT_CHUNK;
-        const uint32_t m = min((uint32_t)MAT_CHUNK, p.n_leaves - first);
-        if ((uint32_t)l < m) {
-            const float *sg = reinterpret_cast<const float *>(mat_smem + (size_t)s * stage_bytes) + l * p.sig_stride;
-            const float *zz = reinterpret_cast<const float *>(mat_smem + (size_t)s * stage_bytes + sig_bytes) + l * p.z_stride;
-            float o[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int j = 4 * q + e;  // output slot
-                float v = 0.0f;
-                if (j == 0) {
-                    for (int i = 0; i < p.n1; ++i) v = fmaf(sg[i], s_b[i], v);
-                    v = fmaxf(v, 0.0f);
-                } else if (j <= 27) {
-                    const float *zq = zz + (j - 1) * p.n2;
-                    for (int i = 0; i < p.n2; ++i) v = fmaf(zq[i], s_b[i], v);
-                }
-                o[e] = v;
+        const int m = (int)min((uint32_t)MAT_CHUNK, p.n_leaves - first);
+        const float *stage_sig = reinterpret_cast<const float *>(mat_smem + (size_t)s * stage_bytes);
+        const float *stage_z = reinterpret_cast<const float *>(mat_smem + (size_t)s * stage_bytes + sig_bytes);
+        // One warp per leaf: lanes 0..26 form z_{lane}(t) (n2 consecutive
+        // floats per lane: conflict-free for odd n2), lanes 27..31 form
+        // partial density sums over 7-term slices, summed by a butterfly.
+        for (int l = warp; l < m; l += MAT_THREADS / 32) {
+            const float *sg = stage_sig + l * p.sig_stride;
+            const float *zz = stage_z + l * p.z_stride;
+            float v = 0.0f;
+            if (lane < 27) {
+                const float *zq = zz + lane * p.n2;
+                for (int i = 0; i < p.n2; ++i) v = fmaf(zq[i], s_b[i], v);
+            } else {
+                const int i0 = (lane - 27) * 7;
+                for (int i = i0; i < i0 + 7 && i < p.n1; ++i) v = fmaf(sg[i], s_b[i], v);
             }
-            reinterpret_cast<float4 *>(p.table)[((size_t)first + l) * (TABLE_STRIDE / 4) + q] =
-                make_float4(o[0], o[1], o[2], o[3]);
+            float part = lane >= 27 ? v : 0.0f;
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            const float zprev = __shfl_up_sync(0xffffffffu, v, 1);
+            const float outv = lane == 0 ? fmaxf(part, 0.0f) : (lane <= 27 ? zprev : 0.0f);
+            p.table[((size_t)first + l) * TABLE_STRIDE + lane] = outv;
         }
         __syncthreads();  // every thread is done with stage s
         if (tid == 0) {
@@ -240,7 +243,7 @@ __device__ __forceinline__ void write_result(const TraverseParams &p, const RayS
 // the tree (its background result is written at once).
 template <bool DBG>
 __device__ bool init_ray(const TraverseParams &p, const FrameShared &fs, bool prt, float *s_bray,
-                         uint32_t *s_stack, RayState &R, uint32_t ray, int px, int py)
+                         int stride, uint32_t *s_stack, RayState &R, uint32_t ray, int px, int py)
 {
     float ox, oy, oz, dx, dy, dz;
     if (p.fr.mode == FPO_RAYS_CAMERA) {
@@ -270,7 +273,7 @@ __device__ bool init_ray(const TraverseParams &p, const FrameShared &fs, bool pr
         // Eq. 8 at this ray's own time, one column of the per-thread table
         const float u = p.fr.rt[ray] / (float)p.fr.period_T;
         const int nb = p.n1 > p.n2 ? p.n1 : p.n2;
-        for (int i = 0; i < nb; ++i) s_bray[i * TRAV_THREADS] = basis_fp32(i, u);
+        for (int i = 0; i < nb; ++i) s_bray[i * stride] = basis_fp32(i, u);
     }
     sh_basis(dx, dy, dz, R.Y);
     R.C0 = R.C1 = R.C2 = 0.0f;
@@ -323,7 +326,7 @@ __device__ bool init_ray(const TraverseParams &p, const FrameShared &fs, bool pr
 template <bool MAT, bool DBG, int N1, int N2>
 __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const float *bsrc,
                          int bstride, const uint32_t *__restrict__ s_nodes, uint32_t *s_stack,
-                         RayState &R, NodeCache &nc)
+                         int stride, RayState &R, NodeCache &nc)
 {
     const int D = p.depth;
     const int G = 1 << D;
@@ -335,7 +338,7 @@ __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const f
         kind = ROOT_LEAF;
     } else {
         lvl = R.lvl_start;
-        uint32_t node = s_stack[lvl * TRAV_THREADS];
+        uint32_t node = s_stack[lvl * stride];
         for (;;) {
             const int sh = D - 1 - lvl;
             const uint32_t c = ((R.P[0] >> sh) & 1) | (((R.P[1] >> sh) & 1) << 1) |
@@ -359,7 +362,7 @@ __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const f
             if (sl == 0u) { kind = ROOT_EMPTY; break; }
             if (sl & LEAF_BIT) { kind = ROOT_LEAF; leaf = sl & ~LEAF_BIT; break; }
             node = sl;
-            s_stack[lvl * TRAV_THREADS] = node;
+            s_stack[lvl * stride] = node;
         }
     }
     // --- exit of the cube: level lvl, 2^(D - lvl) finest cells a side --------
@@ -459,20 +462,32 @@ __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const f
     // --- step into the neighbour cube ---------------------------------------
     // Along m: the adjacent cube; along the other axes: the cell holding the
     // exit point, clamped to this cube's extent and never moving backwards,
-    // so every step makes progress.
+    // so every step makes progress.  A finest-level cube (one cell) keeps the
+    // other two coordinates as they are.
     int Pn[3];
     bool inside = true;
+    if (csz == 1) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (a == m) {
-            Pn[a] = R.gd[a] > 0.0f ? lo[a] + csz : lo[a] - 1;
-            inside = Pn[a] >= 0 && Pn[a] < G;
-        } else {
-            int q = (int)floorf(fmaf(tx, R.gd[a], R.go[a]));
-            q = min(max(q, lo[a]), lo[a] + csz - 1);
-            if (R.gd[a] > 0.0f) q = max(q, R.P[a]);
-            else if (R.gd[a] < 0.0f) q = min(q, R.P[a]);
-            Pn[a] = q;
+        for (int a = 0; a < 3; ++a) {
+            Pn[a] = R.P[a];
+            if (a == m) {
+                Pn[a] += R.gd[a] > 0.0f ? 1 : -1;
+                inside = Pn[a] >= 0 && Pn[a] < G;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a == m) {
+                Pn[a] = R.gd[a] > 0.0f ? lo[a] + csz : lo[a] - 1;
+                inside = Pn[a] >= 0 && Pn[a] < G;
+            } else {
+                int q = (int)floorf(fmaf(tx, R.gd[a], R.go[a]));
+                q = min(max(q, lo[a]), lo[a] + csz - 1);
+                if (R.gd[a] > 0.0f) q = max(q, R.P[a]);
+                else if (R.gd[a] < 0.0f) q = min(q, R.P[a]);
+                Pn[a] = q;
+            }
         }
     }
     if (!inside) return false;
@@ -500,16 +515,19 @@ __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const f
 // long rays do not leave most of a warp idle.  Each CTA first stages the top
 // n_smem_nodes nodes of the breadth-first node array and the frame constants
 // in shared memory.  The last CTA to finish resets the counter.
-constexpr int REFILL_MIN = 8;
+#ifndef FPO_TRAV_MIN_BLOCKS
+#define FPO_TRAV_MIN_BLOCKS 1
+#endif
 
 template <bool MAT, bool DBG, int N1, int N2>
-__global__ void __launch_bounds__(TRAV_THREADS) traverse_kernel(const __grid_constant__ TraverseParams p)
+__global__ void __launch_bounds__(TRAV_THREADS, FPO_TRAV_MIN_BLOCKS) traverse_kernel(const __grid_constant__ TraverseParams p)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ FrameShared fs;
+    const int stride = blockDim.x;
     uint32_t *s_nodes = smem;
     uint32_t *s_stack = smem + p.n_smem_nodes * 8;
-    float *s_bray = reinterpret_cast<float *>(s_stack + STACK_LEVELS * TRAV_THREADS);
+    float *s_bray = reinterpret_cast<float *>(s_stack + STACK_LEVELS * stride);
     const bool prt = !MAT && p.fr.mode == FPO_RAYS_EXPLICIT && p.fr.rt != nullptr;
 
     {
@@ -550,7 +568,8 @@ __global__ void __launch_bounds__(TRAV_THREADS) traverse_kernel(const __grid_con
     uint32_t *my_stack = s_stack + threadIdx.x;
     float *my_b = s_bray + threadIdx.x;
     const float *bsrc = prt ? my_b : fs.b;
-    const int bstride = prt ? TRAV_THREADS : 1;
+    const int bstride = prt ? stride : 1;
+    const uint32_t refill_min = p.refill_min;
 
     auto grab_tile = [&]() -> uint32_t {
         uint32_t tl = 0;
@@ -566,7 +585,7 @@ __global__ void __launch_bounds__(TRAV_THREADS) traverse_kernel(const __grid_con
     bool active = false;
     for (;;) {
         uint32_t idle = __ballot_sync(0xffffffffu, !active);
-        if (__popc(idle) >= REFILL_MIN) {
+        if ((uint32_t)__popc(idle) >= refill_min) {
             while (idle && cur_tile < p.n_tiles) {
                 const uint32_t take = min(32u - cur_next, (uint32_t)__popc(idle));
                 const uint32_t rank = __popc(idle & lt_mask);
@@ -585,7 +604,7 @@ __global__ void __launch_bounds__(TRAV_THREADS) traverse_kernel(const __grid_con
                         ray = cur_tile * 32 + k;
                         valid = ray < p.fr.n_rays;
                     }
-                    if (valid) active = init_ray<DBG>(p, fs, prt, my_b, my_stack, R, ray, px, py);
+                    if (valid) active = init_ray<DBG>(p, fs, prt, my_b, stride, my_stack, R, ray, px, py);
                 }
                 cur_next += take;
                 if (cur_next >= 32) {
@@ -593,52 +612,59 @@ __global__ void __launch_bounds__(TRAV_THREADS) traverse_kernel(const __grid_con
                     cur_next = 0;
                 }
                 idle = __ballot_sync(0xffffffffu, !active);
-                if (__popc(idle) < REFILL_MIN) break;
+                if ((uint32_t)__popc(idle) < refill_min) break;
             }
         }
         if (!__any_sync(0xffffffffu, active)) break;
         if (active) {
-            if (!step_ray<MAT, DBG, N1, N2>(p, fs, bsrc, bstride, s_nodes, my_stack, R, nc)) {
+            if (!step_ray<MAT, DBG, N1, N2>(p, fs, bsrc, bstride, s_nodes, my_stack, stride, R, nc)) {
                 write_result(p, R, DBG);
+                if (DBG && (p.flags & FPO_FLAG_STATS)) {
+                    atomicAdd(p.stats, (unsigned long long)R.steps + 1ull);
+                    atomicAdd(p.stats + 1, (unsigned long long)R.n_visits);
+                    atomicAdd(p.stats + 2, 1ull);
+                }
                 active = false;
             }
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    // The last warp of the grid to finish resets the tile counter for the
+    // next launch (every warp has made its final grab before counting itself).
+    if (lane == 0) {
         __threadfence();
         const uint32_t done = atomicAdd(p.status + 2, 1u);
-        if (done == gridDim.x - 1) {
+        if (done == gridDim.x * (blockDim.x / 32) - 1) {
             atomicExch(p.status + 1, 0u);
             atomicExch(p.status + 2, 0u);
         }
     }
 }
 
-int traverse_smem_bytes(uint32_t n_smem_nodes, bool per_ray_basis)
+
+int traverse_smem_bytes(uint32_t n_smem_nodes, bool per_ray_basis, int threads)
 {
-    return (int)(n_smem_nodes * 32u + STACK_LEVELS * TRAV_THREADS * 4u +
-                 (per_ray_basis ? 32u * TRAV_THREADS * 4u : 0u));
+    return (int)(n_smem_nodes * 32u + STACK_LEVELS * threads * 4u +
+                 (per_ray_basis ? 32u * threads * 4u : 0u));
 }
 
-int traverse_block_threads() { return TRAV_THREADS; }
 
 template <bool MAT, bool DBG, int N1, int N2>
 static int launch_t(const TraverseParams &p, int sm_count, cudaStream_t s)
 {
     const bool prt = !MAT && p.fr.mode == FPO_RAYS_EXPLICIT && p.fr.rt != nullptr;
-    const int smem = traverse_smem_bytes(p.n_smem_nodes, prt);
+    const int threads = p.block_threads;
+    const int smem = traverse_smem_bytes(p.n_smem_nodes, prt, threads);
     auto k = traverse_kernel<MAT, DBG, N1, N2>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, TRAV_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) per_sm = 1;
     uint64_t blocks = (uint64_t)sm_count * per_sm;
-    const uint64_t need = (p.n_tiles + (TRAV_THREADS / 32) - 1) / (TRAV_THREADS / 32);
+    const uint64_t need = (p.n_tiles + (threads / 32) - 1) / (threads / 32);
     if (need < blocks) blocks = need ? need : 1;
-    k<<<(unsigned)blocks, TRAV_THREADS, smem, s>>>(p);
+    k<<<(unsigned)blocks, threads, smem, s>>>(p);
     return (int)cudaGetLastError();
 }
 

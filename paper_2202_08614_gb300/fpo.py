@@ -25,7 +25,7 @@ ERRORS = {
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "fp8": 3}
 IDFT = {"auto": 0, "fused": 1, "materialise": 2}
 RAYS_CAMERA, RAYS_EXPLICIT = 0, 1
-FLAG_RECORD_VISITS, FLAG_OUT_T, FLAG_MARK_LEAVES = 1, 2, 4
+FLAG_RECORD_VISITS, FLAG_OUT_T, FLAG_MARK_LEAVES, FLAG_STATS = 1, 2, 4, 8
 
 # Every symbol include/fpo.h declares.
 EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
@@ -42,7 +42,7 @@ class FPOError(RuntimeError):
 class Config(C.Structure):
     _fields_ = [("n1", C.c_int32), ("n2", C.c_int32), ("sh_degree", C.c_int32),
                 ("period_T", C.c_double), ("storage", C.c_int32), ("idft_mode", C.c_int32),
-                ("device", C.c_int32)]
+                ("device", C.c_int32), ("traverse_threads", C.c_int32), ("refill_min", C.c_int32)]
 
 
 class TreeDesc(C.Structure):
@@ -61,7 +61,8 @@ class Rays(C.Structure):
 class FrameOpts(C.Structure):
     _fields_ = [("bg", C.c_float * 3), ("stop_T", C.c_float), ("flags", C.c_uint32),
                 ("visit_log", C.c_void_p), ("visit_cap", C.c_uint32), ("visit_count", C.c_void_p),
-                ("out_T", C.c_void_p), ("leaf_mark", C.c_void_p), ("events", C.c_void_p * 3)]
+                ("out_T", C.c_void_p), ("leaf_mark", C.c_void_p), ("stats", C.c_void_p),
+                ("events", C.c_void_p * 3)]
 
 
 class TreeInfo(C.Structure):
@@ -104,8 +105,10 @@ def check(code: int):
     return code
 
 
-def make_config(n1=31, n2=5, period_T=60.0, storage="f32", idft_mode="auto", device=0):
-    return Config(n1, n2, 2, float(period_T), STORAGE[storage], IDFT[idft_mode], device)
+def make_config(n1=31, n2=5, period_T=60.0, storage="f32", idft_mode="auto", device=0,
+                traverse_threads=0, refill_min=0):
+    return Config(n1, n2, 2, float(period_T), STORAGE[storage], IDFT[idft_mode], device,
+                  traverse_threads, refill_min)
 
 
 def make_tree_desc(leaf_depth, leaf_xyz, coeffs, max_depth, aabb_min=(0.0, 0.0, 0.0),
@@ -139,8 +142,10 @@ def _stream_handle(stream):
 class Renderer:
     """One fpo_ctx: a tree resident on one GPU, rendered frame by frame."""
 
-    def __init__(self, n1=31, n2=5, period_T=60.0, storage="f32", idft_mode="auto", device=0):
-        self.cfg = make_config(n1, n2, period_T, storage, idft_mode, device)
+    def __init__(self, n1=31, n2=5, period_T=60.0, storage="f32", idft_mode="auto", device=0,
+                 traverse_threads=0, refill_min=0):
+        self.cfg = make_config(n1, n2, period_T, storage, idft_mode, device, traverse_threads,
+                               refill_min)
         self.device = device
         self.n1, self.n2 = n1, n2
         h = C.c_void_p()
@@ -177,7 +182,7 @@ class Renderer:
 
     def render(self, camera=None, t=0.0, rays_o=None, rays_d=None, t_per_ray=None,
                bg=(1.0, 1.0, 1.0), stop_T=1e-4, out=None, visit_cap=None, want_T=False,
-               leaf_mark=None, stream=None, events=None):
+               leaf_mark=None, stats=None, stream=None, events=None):
         """Renders one frame; returns a dict of device tensors.
 
         camera: an object with eye/target/up/fov_y_deg/width/height (pixel
@@ -234,6 +239,9 @@ class Renderer:
         if leaf_mark is not None:
             opts.leaf_mark = leaf_mark.data_ptr()
             flags |= FLAG_MARK_LEAVES
+        if stats is not None:  # CUDA int64 tensor [3], accumulated
+            opts.stats = stats.data_ptr()
+            flags |= FLAG_STATS
         opts.flags = flags
         if events is not None:
             for i, ev in enumerate(events):
