@@ -72,10 +72,13 @@ typedef struct {
     int32_t idft_mode; /* FPO_IDFT_* */
     int32_t device;    /* CUDA device ordinal the context lives on */
     /* Launch tuning of the traversal (0 = library default): threads per CTA
-     * (128 or 256), and the number of idle lanes at which a warp refills them
-     * with new rays (1..32; 32 refills only a fully idle warp). */
+     * (128 or 256); the number of idle lanes at which a warp refills them
+     * with new rays (1..32; 32 refills only a fully idle warp); the number of
+     * steps a lane takes between two such checks (default: to the end of its
+     * ray). */
     int32_t traverse_threads;
     int32_t refill_min;
+    int32_t inner_steps;
 } fpo_config;
 
 /* A union octree given by its leaves (Sec. 4.2): leaf j is the cell

@@ -59,6 +59,7 @@ void dfree(T *&p)
 constexpr uint32_t SMEM_NODE_BUDGET = 512;  // 16 KB of top-level nodes per CTA
 constexpr int DEFAULT_TRAVERSE_THREADS = 128;
 constexpr uint32_t DEFAULT_REFILL_MIN = 32;
+constexpr uint32_t DEFAULT_INNER_STEPS = 0xffffffffu;  // a lane runs its ray to the end
 
 }  // namespace
 
@@ -117,6 +118,7 @@ int fpo_create(fpo_ctx **out, const fpo_config *cfg)
         return fail(FPO_ERR_INVALID_ARG, "traverse_threads must be 0, 128 or 256");
     if (cfg->refill_min < 0 || cfg->refill_min > 32)
         return fail(FPO_ERR_INVALID_ARG, "refill_min must be in [0, 32]");
+    if (cfg->inner_steps < 0) return fail(FPO_ERR_INVALID_ARG, "inner_steps must be >= 0");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
@@ -354,6 +356,7 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
     p.max_steps = 3u * (1u << ctx->depth) + 16u;
     p.block_threads = ctx->cfg.traverse_threads ? ctx->cfg.traverse_threads : DEFAULT_TRAVERSE_THREADS;
     p.refill_min = ctx->cfg.refill_min ? (uint32_t)ctx->cfg.refill_min : DEFAULT_REFILL_MIN;
+    p.inner_steps = ctx->cfg.inner_steps ? (uint32_t)ctx->cfg.inner_steps : DEFAULT_INNER_STEPS;
     p.stats = reinterpret_cast<unsigned long long *>(opts->stats);
     const bool dbg = (fl & (FPO_FLAG_RECORD_VISITS | FPO_FLAG_OUT_T | FPO_FLAG_MARK_LEAVES |
                             FPO_FLAG_STATS)) != 0;

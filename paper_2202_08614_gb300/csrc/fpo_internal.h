@@ -92,6 +92,7 @@ struct TraverseParams {
     uint32_t n_tiles, tiles_x;
     uint32_t max_steps;
     uint32_t refill_min;      // warp refills its idle lanes once this many are idle (32: whole tiles)
+    uint32_t inner_steps;     // steps a lane takes between two refill checks
     int block_threads;        // 128 or 256
     unsigned long long *stats; // FPO_FLAG_STATS: [steps, leaf visits, rays entering the tree]
 };

@@ -16,6 +16,13 @@
 #include "fpo_internal.h"
 #include "fpo_ptx.cuh"
 
+#ifndef FPO_NODE_CACHE
+#define FPO_NODE_CACHE 1
+#endif
+#ifndef FPO_FAST_STEP
+#define FPO_FAST_STEP 1
+#endif
+
 namespace fpo {
 namespace {
 
@@ -77,6 +84,7 @@ constexpr int MAT_THREADS = 256;
 constexpr int MAT_MAX_STAGES = 6;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s: a stuck copy, not slowness
 
+template <int N2>
 __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_constant__ MaterialiseParams p)
 {
     extern __shared__ __align__(128) unsigned char mat_smem[];
@@ -113,6 +121,10 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
         }
 
     const int warp = tid >> 5, lane = tid & 31;
+    const float b_lane = lane < nb ? s_b[lane] : 0.0f;
+    float bz[N2 > 0 ? N2 : 1];
+#pragma unroll
+    for (int i = 0; i < (N2 > 0 ? N2 : 1); ++i) bz[i] = s_b[i];
     uint32_t it = 0;
     for (;; ++it) {
         const uint32_t c = blockIdx.x + it * gridDim.x;
@@ -126,23 +138,26 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
         const int m = (int)min((uint32_t)MAT_CHUNK, p.n_leaves - first);
         const float *stage_sig = reinterpret_cast<const float *>(mat_smem + (size_t)s * stage_bytes);
         const float *stage_z = reinterpret_cast<const float *>(mat_smem + (size_t)s * stage_bytes + sig_bytes);
-        // One warp per leaf: lanes 0..26 form z_{lane}(t) (n2 consecutive
-        // floats per lane: conflict-free for odd n2), lanes 27..31 form
-        // partial density sums over 7-term slices, summed by a butterfly.
+        // One warp per leaf: lane i < n1 forms k_sigma_i b_i and a butterfly
+        // sums the density; lanes 0..26 form z_{lane}(t) from n2 consecutive
+        // floats (conflict-free for odd n2).  Lane j then stores output j.
         for (int l = warp; l < m; l += MAT_THREADS / 32) {
             const float *sg = stage_sig + l * p.sig_stride;
             const float *zz = stage_z + l * p.z_stride;
-            float v = 0.0f;
-            if (lane < 27) {
-                const float *zq = zz + lane * p.n2;
-                for (int i = 0; i < p.n2; ++i) v = fmaf(zq[i], s_b[i], v);
-            } else {
-                const int i0 = (lane - 27) * 7;
-                for (int i = i0; i < i0 + 7 && i < p.n1; ++i) v = fmaf(sg[i], s_b[i], v);
-            }
-            float part = lane >= 27 ? v : 0.0f;
+            float part = lane < p.n1 ? sg[lane] * b_lane : 0.0f;
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            float v = 0.0f;
+            if (lane < 27) {
+                if constexpr (N2 > 0) {
+                    const float *zq = zz + lane * N2;
+#pragma unroll
+                    for (int i = 0; i < N2; ++i) v = fmaf(zq[i], bz[i], v);
+                } else {
+                    const float *zq = zz + lane * p.n2;
+                    for (int i = 0; i < p.n2; ++i) v = fmaf(zq[i], s_b[i], v);
+                }
+            }
             const float zprev = __shfl_up_sync(0xffffffffu, v, 1);
             const float outv = lane == 0 ? fmaxf(part, 0.0f) : (lane <= 27 ? zprev : 0.0f);
             p.table[((size_t)first + l) * TABLE_STRIDE + lane] = outv;
@@ -177,16 +192,17 @@ int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream)
 {
     if (p.n_leaves == 0) return (int)cudaSuccess;
     const int smem = p.stages * MAT_CHUNK * (p.sig_stride + p.z_stride) * 4;
-    cudaError_t e = cudaFuncSetAttribute(materialise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = p.n2 == 5 ? materialise_kernel<5> : (p.n2 == 11 ? materialise_kernel<11> : materialise_kernel<0>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, materialise_kernel, MAT_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MAT_THREADS, smem);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) per_sm = 1;
     const uint32_t n_chunks = (p.n_leaves + MAT_CHUNK - 1) / MAT_CHUNK;
     uint64_t blocks = (uint64_t)sm_count * per_sm;
     if (blocks > n_chunks) blocks = n_chunks;
-    materialise_kernel<<<(unsigned)blocks, MAT_THREADS, smem, (cudaStream_t)stream>>>(p);
+    kern<<<(unsigned)blocks, MAT_THREADS, smem, (cudaStream_t)stream>>>(p);
     return (int)cudaGetLastError();
 }
 
@@ -343,7 +359,7 @@ __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const f
             const int sh = D - 1 - lvl;
             const uint32_t c = ((R.P[0] >> sh) & 1) | (((R.P[1] >> sh) & 1) << 1) |
                                (((R.P[2] >> sh) & 1) << 2);
-            if (!(nc.node == node && nc.level == lvl)) {
+            if (!(FPO_NODE_CACHE && nc.node == node && nc.level == lvl)) {
                 const uint4 *q = node < p.n_smem_nodes
                                      ? reinterpret_cast<const uint4 *>(s_nodes) + 2 * node
                                      : reinterpret_cast<const uint4 *>(p.nodes) + 2 * (size_t)node;
@@ -466,7 +482,7 @@ __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const f
     // other two coordinates as they are.
     int Pn[3];
     bool inside = true;
-    if (csz == 1) {
+    if (FPO_FAST_STEP && csz == 1) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             Pn[a] = R.P[a];
@@ -617,14 +633,19 @@ __global__ void __launch_bounds__(TRAV_THREADS, FPO_TRAV_MIN_BLOCKS) traverse_ke
         }
         if (!__any_sync(0xffffffffu, active)) break;
         if (active) {
-            if (!step_ray<MAT, DBG, N1, N2>(p, fs, bsrc, bstride, s_nodes, my_stack, stride, R, nc)) {
-                write_result(p, R, DBG);
-                if (DBG && (p.flags & FPO_FLAG_STATS)) {
-                    atomicAdd(p.stats, (unsigned long long)R.steps + 1ull);
-                    atomicAdd(p.stats + 1, (unsigned long long)R.n_visits);
-                    atomicAdd(p.stats + 2, 1ull);
+            // up to inner_steps steps before the warp looks at its idle lanes again
+#pragma unroll 1
+            for (uint32_t k = 0; k < p.inner_steps; ++k) {
+                if (!step_ray<MAT, DBG, N1, N2>(p, fs, bsrc, bstride, s_nodes, my_stack, stride, R, nc)) {
+                    write_result(p, R, DBG);
+                    if (DBG && (p.flags & FPO_FLAG_STATS)) {
+                        atomicAdd(p.stats, (unsigned long long)R.steps + 1ull);
+                        atomicAdd(p.stats + 1, (unsigned long long)R.n_visits);
+                        atomicAdd(p.stats + 2, 1ull);
+                    }
+                    active = false;
+                    break;
                 }
-                active = false;
             }
         }
     }
