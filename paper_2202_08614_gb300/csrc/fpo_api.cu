@@ -56,7 +56,10 @@ void dfree(T *&p)
     p = nullptr;
 }
 
-constexpr uint32_t SMEM_NODE_BUDGET = 512;  // 16 KB of top-level nodes per CTA
+#ifndef FPO_SMEM_NODES
+#define FPO_SMEM_NODES 512
+#endif
+constexpr uint32_t SMEM_NODE_BUDGET = FPO_SMEM_NODES;  // top-level nodes staged per CTA (32 B each)
 constexpr int DEFAULT_TRAVERSE_THREADS = 128;
 constexpr uint32_t DEFAULT_REFILL_MIN = 32;
 constexpr uint32_t DEFAULT_INNER_STEPS = 0xffffffffu;  // a lane runs its ray to the end

@@ -17,7 +17,7 @@
 #include "fpo_ptx.cuh"
 
 #ifndef FPO_NODE_CACHE
-#define FPO_NODE_CACHE 1
+#define FPO_NODE_CACHE 0
 #endif
 #ifndef FPO_FAST_STEP
 #define FPO_FAST_STEP 1
@@ -359,7 +359,8 @@ __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const f
             const int sh = D - 1 - lvl;
             const uint32_t c = ((R.P[0] >> sh) & 1) | (((R.P[1] >> sh) & 1) << 1) |
                                (((R.P[2] >> sh) & 1) << 2);
-            if (!(FPO_NODE_CACHE && nc.node == node && nc.level == lvl)) {
+#if FPO_NODE_CACHE
+            if (!(nc.node == node && nc.level == lvl)) {
                 const uint4 *q = node < p.n_smem_nodes
                                      ? reinterpret_cast<const uint4 *>(s_nodes) + 2 * node
                                      : reinterpret_cast<const uint4 *>(p.nodes) + 2 * (size_t)node;
@@ -374,6 +375,10 @@ __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const f
                 nc.level = lvl;
             }
             const uint32_t sl = pick_slot(nc, c);
+#else
+            const uint32_t idx = node * 8 + c;
+            const uint32_t sl = node < p.n_smem_nodes ? s_nodes[idx] : __ldg(p.nodes + idx);
+#endif
             ++lvl;
             if (sl == 0u) { kind = ROOT_EMPTY; break; }
             if (sl & LEAF_BIT) { kind = ROOT_LEAF; leaf = sl & ~LEAF_BIT; break; }
@@ -531,12 +536,17 @@ __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const f
 // long rays do not leave most of a warp idle.  Each CTA first stages the top
 // n_smem_nodes nodes of the breadth-first node array and the frame constants
 // in shared memory.  The last CTA to finish resets the counter.
-#ifndef FPO_TRAV_MIN_BLOCKS
-#define FPO_TRAV_MIN_BLOCKS 1
+// Register caps: 80 lets six 128-thread (or three 256-thread) CTAs share an
+// SM in materialised mode; the fused per-visit IDFT needs more.
+#ifndef FPO_TRAV_MAXNREG_MAT
+#define FPO_TRAV_MAXNREG_MAT 80
+#endif
+#ifndef FPO_TRAV_MAXNREG_FUSED
+#define FPO_TRAV_MAXNREG_FUSED 128
 #endif
 
-template <bool MAT, bool DBG, int N1, int N2>
-__global__ void __launch_bounds__(TRAV_THREADS, FPO_TRAV_MIN_BLOCKS) traverse_kernel(const __grid_constant__ TraverseParams p)
+template <bool MAT, bool DBG, int N1, int N2, bool COMPACT>
+__global__ void __maxnreg__(MAT ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED) traverse_kernel(const __grid_constant__ TraverseParams p)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ FrameShared fs;
@@ -580,71 +590,99 @@ __global__ void __launch_bounds__(TRAV_THREADS, FPO_TRAV_MIN_BLOCKS) traverse_ke
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
-    const uint32_t lt_mask = (1u << lane) - 1u;
     uint32_t *my_stack = s_stack + threadIdx.x;
     float *my_b = s_bray + threadIdx.x;
     const float *bsrc = prt ? my_b : fs.b;
     const int bstride = prt ? stride : 1;
-    const uint32_t refill_min = p.refill_min;
 
     auto grab_tile = [&]() -> uint32_t {
         uint32_t tl = 0;
         if (lane == 0) tl = atomicAdd(p.status + 1, 1u);
         return __shfl_sync(0xffffffffu, tl, 0);
     };
-    uint32_t cur_tile = grab_tile();  // warp-uniform cursor: tile and next ray in it
-    uint32_t cur_next = 0;
-    RayState R;
-    NodeCache nc;
-    nc.node = 0xffffffffu;
-    nc.level = -1;
-    bool active = false;
-    for (;;) {
-        uint32_t idle = __ballot_sync(0xffffffffu, !active);
-        if ((uint32_t)__popc(idle) >= refill_min) {
-            while (idle && cur_tile < p.n_tiles) {
-                const uint32_t take = min(32u - cur_next, (uint32_t)__popc(idle));
-                const uint32_t rank = __popc(idle & lt_mask);
-                if (((idle >> lane) & 1u) && rank < take) {
-                    const uint32_t k = cur_next + rank;  // ray within the tile
-                    uint32_t ray;
-                    int px = 0, py = 0;
-                    bool valid;
-                    if (p.fr.mode == FPO_RAYS_CAMERA) {
-                        const uint32_t tx = cur_tile % p.tiles_x, ty = cur_tile / p.tiles_x;
-                        px = (int)(tx * 8 + (k & 7));
-                        py = (int)(ty * 4 + (k >> 3));
-                        valid = px < (int)p.fr.width && py < (int)p.fr.height;
-                        ray = (uint32_t)py * p.fr.width + (uint32_t)px;
-                    } else {
-                        ray = cur_tile * 32 + k;
-                        valid = ray < p.fr.n_rays;
+    // ray k (0..31) of a tile: camera pixel (8x4 block) or explicit ray
+    auto tile_ray = [&](uint32_t tile, uint32_t k, uint32_t &ray, int &px, int &py) -> bool {
+        if (p.fr.mode == FPO_RAYS_CAMERA) {
+            const uint32_t tx = tile % p.tiles_x, ty = tile / p.tiles_x;
+            px = (int)(tx * 8 + (k & 7));
+            py = (int)(ty * 4 + (k >> 3));
+            ray = (uint32_t)py * p.fr.width + (uint32_t)px;
+            return px < (int)p.fr.width && py < (int)p.fr.height;
+        }
+        ray = tile * 32 + k;
+        return ray < p.fr.n_rays;
+    };
+    auto finish = [&](const RayState &R) {
+        write_result(p, R, DBG);
+        if (DBG && (p.flags & FPO_FLAG_STATS)) {
+            atomicAdd(p.stats, (unsigned long long)R.steps + 1ull);
+            atomicAdd(p.stats + 1, (unsigned long long)R.n_visits);
+            atomicAdd(p.stats + 2, 1ull);
+        }
+    };
+
+    if constexpr (!COMPACT) {
+        // One tile per warp at a time; every lane runs its ray to the end.
+        for (;;) {
+            const uint32_t tile = grab_tile();
+            if (tile >= p.n_tiles) break;
+            uint32_t ray;
+            int px = 0, py = 0;
+            if (tile_ray(tile, (uint32_t)lane, ray, px, py)) {
+                RayState R;
+                if (init_ray<DBG>(p, fs, prt, my_b, stride, my_stack, R, ray, px, py)) {
+                    NodeCache nc;
+                    nc.node = 0xffffffffu;
+                    nc.level = -1;
+                    while (step_ray<MAT, DBG, N1, N2>(p, fs, bsrc, bstride, s_nodes, my_stack, stride, R, nc)) {
                     }
-                    if (valid) active = init_ray<DBG>(p, fs, prt, my_b, stride, my_stack, R, ray, px, py);
+                    finish(R);
                 }
-                cur_next += take;
-                if (cur_next >= 32) {
-                    cur_tile = grab_tile();
-                    cur_next = 0;
-                }
-                idle = __ballot_sync(0xffffffffu, !active);
-                if ((uint32_t)__popc(idle) < refill_min) break;
             }
         }
-        if (!__any_sync(0xffffffffu, active)) break;
-        if (active) {
-            // up to inner_steps steps before the warp looks at its idle lanes again
-#pragma unroll 1
-            for (uint32_t k = 0; k < p.inner_steps; ++k) {
-                if (!step_ray<MAT, DBG, N1, N2>(p, fs, bsrc, bstride, s_nodes, my_stack, stride, R, nc)) {
-                    write_result(p, R, DBG);
-                    if (DBG && (p.flags & FPO_FLAG_STATS)) {
-                        atomicAdd(p.stats, (unsigned long long)R.steps + 1ull);
-                        atomicAdd(p.stats + 1, (unsigned long long)R.n_visits);
-                        atomicAdd(p.stats + 2, 1ull);
+    } else {
+        // Warp-level ray compaction: once refill_min lanes are idle, they take
+        // the next rays of the warp's current tile (a new tile when it is used
+        // up); lanes take up to inner_steps steps between two checks.
+        const uint32_t lt_mask = (1u << lane) - 1u;
+        const uint32_t refill_min = p.refill_min;
+        uint32_t cur_tile = grab_tile();  // warp-uniform cursor: tile and next ray in it
+        uint32_t cur_next = 0;
+        RayState R;
+        NodeCache nc;
+        nc.node = 0xffffffffu;
+        nc.level = -1;
+        bool active = false;
+        for (;;) {
+            uint32_t idle = __ballot_sync(0xffffffffu, !active);
+            if ((uint32_t)__popc(idle) >= refill_min) {
+                while (idle && cur_tile < p.n_tiles) {
+                    const uint32_t take = min(32u - cur_next, (uint32_t)__popc(idle));
+                    const uint32_t rank = __popc(idle & lt_mask);
+                    if (((idle >> lane) & 1u) && rank < take) {
+                        uint32_t ray;
+                        int px = 0, py = 0;
+                        if (tile_ray(cur_tile, cur_next + rank, ray, px, py))
+                            active = init_ray<DBG>(p, fs, prt, my_b, stride, my_stack, R, ray, px, py);
                     }
-                    active = false;
-                    break;
+                    cur_next += take;
+                    if (cur_next >= 32) {
+                        cur_tile = grab_tile();
+                        cur_next = 0;
+                    }
+                    idle = __ballot_sync(0xffffffffu, !active);
+                    if ((uint32_t)__popc(idle) < refill_min) break;
+                }
+            }
+            if (!__any_sync(0xffffffffu, active)) break;
+            if (active) {
+#pragma unroll 1
+                for (uint32_t k = 0; k < p.inner_steps; ++k) {
+                    if (!step_ray<MAT, DBG, N1, N2>(p, fs, bsrc, bstride, s_nodes, my_stack, stride, R, nc)) {
+                        finish(R);
+                        active = false;
+                        break;
+                    }
                 }
             }
         }
@@ -669,13 +707,13 @@ int traverse_smem_bytes(uint32_t n_smem_nodes, bool per_ray_basis, int threads)
 }
 
 
-template <bool MAT, bool DBG, int N1, int N2>
+template <bool MAT, bool DBG, int N1, int N2, bool COMPACT>
 static int launch_t(const TraverseParams &p, int sm_count, cudaStream_t s)
 {
     const bool prt = !MAT && p.fr.mode == FPO_RAYS_EXPLICIT && p.fr.rt != nullptr;
     const int threads = p.block_threads;
     const int smem = traverse_smem_bytes(p.n_smem_nodes, prt, threads);
-    auto k = traverse_kernel<MAT, DBG, N1, N2>;
+    auto k = traverse_kernel<MAT, DBG, N1, N2, COMPACT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
@@ -689,14 +727,22 @@ static int launch_t(const TraverseParams &p, int sm_count, cudaStream_t s)
     return (int)cudaGetLastError();
 }
 
-template <bool DBG>
-static int launch_fused(const TraverseParams &p, int sm_count, cudaStream_t s)
+// Debug outputs use the plain schedule (their results do not depend on it).
+template <bool MAT, int N1, int N2>
+static int launch_sched(const TraverseParams &p, bool debug, int sm_count, cudaStream_t s)
+{
+    if (debug) return launch_t<MAT, true, N1, N2, false>(p, sm_count, s);
+    if (p.refill_min < 32) return launch_t<MAT, false, N1, N2, true>(p, sm_count, s);
+    return launch_t<MAT, false, N1, N2, false>(p, sm_count, s);
+}
+
+static int launch_fused(const TraverseParams &p, bool debug, int sm_count, cudaStream_t s)
 {
     // Fused per-visit IDFT: compile-time Fourier sizes (the settings of Tab. 3).
-    if (p.n1 == 31 && p.n2 == 5) return launch_t<false, DBG, 31, 5>(p, sm_count, s);
-    if (p.n1 == 11 && p.n2 == 5) return launch_t<false, DBG, 11, 5>(p, sm_count, s);
-    if (p.n1 == 21 && p.n2 == 5) return launch_t<false, DBG, 21, 5>(p, sm_count, s);
-    if (p.n1 == 31 && p.n2 == 11) return launch_t<false, DBG, 31, 11>(p, sm_count, s);
+    if (p.n1 == 31 && p.n2 == 5) return launch_sched<false, 31, 5>(p, debug, sm_count, s);
+    if (p.n1 == 11 && p.n2 == 5) return launch_sched<false, 11, 5>(p, debug, sm_count, s);
+    if (p.n1 == 21 && p.n2 == 5) return launch_sched<false, 21, 5>(p, debug, sm_count, s);
+    if (p.n1 == 31 && p.n2 == 11) return launch_sched<false, 31, 11>(p, debug, sm_count, s);
     return -1;
 }
 
@@ -710,9 +756,8 @@ int launch_traverse(const TraverseParams &p, bool materialised, bool debug, int 
                     void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
-    if (materialised)
-        return debug ? launch_t<true, true, 0, 0>(p, sm_count, s) : launch_t<true, false, 0, 0>(p, sm_count, s);
-    return debug ? launch_fused<true>(p, sm_count, s) : launch_fused<false>(p, sm_count, s);
+    if (materialised) return launch_sched<true, 0, 0>(p, debug, sm_count, s);
+    return launch_fused(p, debug, sm_count, s);
 }
 
 }  // namespace fpo
