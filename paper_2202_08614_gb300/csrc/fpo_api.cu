@@ -56,11 +56,14 @@ void dfree(T *&p)
     p = nullptr;
 }
 
+#ifndef FPO_SUPER_TILE
+#define FPO_SUPER_TILE 0
+#endif
 #ifndef FPO_SMEM_NODES
 #define FPO_SMEM_NODES 512
 #endif
 constexpr uint32_t SMEM_NODE_BUDGET = FPO_SMEM_NODES;  // top-level nodes staged per CTA (32 B each)
-constexpr int DEFAULT_TRAVERSE_THREADS = 128;
+constexpr int DEFAULT_TRAVERSE_THREADS = 256;
 constexpr uint32_t DEFAULT_REFILL_MIN = 32;
 constexpr uint32_t DEFAULT_INNER_STEPS = 0xffffffffu;  // a lane runs its ray to the end
 
@@ -351,7 +354,14 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
     p.status = ctx->d_status;
     if (rays->mode == FPO_RAYS_CAMERA) {
         p.tiles_x = (rays->width + 7) / 8;
-        p.n_tiles = p.tiles_x * ((rays->height + 3) / 4);
+        const uint32_t tiles_y = (rays->height + 3) / 4;
+        p.super_tile = FPO_SUPER_TILE;
+        if (p.super_tile) {
+            const uint32_t S = p.super_tile;
+            p.n_tiles = ((p.tiles_x + S - 1) / S) * ((tiles_y + S - 1) / S) * S * S;
+        } else {
+            p.n_tiles = p.tiles_x * tiles_y;
+        }
     } else {
         p.tiles_x = 0;
         p.n_tiles = (uint32_t)((n_rays + 31) / 32);

@@ -22,6 +22,9 @@
 #ifndef FPO_FAST_STEP
 #define FPO_FAST_STEP 1
 #endif
+#ifndef FPO_PREFETCH
+#define FPO_PREFETCH 1
+#endif
 
 namespace fpo {
 namespace {
@@ -336,60 +339,69 @@ __device__ bool init_ray(const TraverseParams &p, const FrameShared &fs, bool pr
     return true;
 }
 
-// One traversal step: locate the cube holding R.P, shade it if it is a leaf
-// with a non-empty segment, and move to the neighbouring cube.  Returns false
-// once the ray is finished (left the grid, early stop, or step cap).
-template <bool MAT, bool DBG, int N1, int N2>
-__device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const float *bsrc,
-                         int bstride, const uint32_t *__restrict__ s_nodes, uint32_t *s_stack,
-                         int stride, RayState &R, NodeCache &nc)
-{
-    const int D = p.depth;
-    const int G = 1 << D;
-    // --- locate the cube containing P ---------------------------------------
+// The cube holding cell R.P: its kind (ROOT_EMPTY / ROOT_LEAF), leaf index and
+// level.  Descends from the deepest still-valid ancestor in the per-thread
+// stack, updating the stack on the way down.
+struct Cube {
+    uint32_t kind, leaf;
     int lvl;
-    uint32_t kind, leaf = 0;
+};
+
+__device__ __forceinline__ Cube locate(const TraverseParams &p, const uint32_t *__restrict__ s_nodes,
+                                       uint32_t *s_stack, int stride, const int P[3], int lvl_start,
+                                       NodeCache &nc)
+{
+    Cube cb;
+    cb.leaf = 0;
     if (p.root_kind == ROOT_LEAF) {
-        lvl = 0;
-        kind = ROOT_LEAF;
-    } else {
-        lvl = R.lvl_start;
-        uint32_t node = s_stack[lvl * stride];
-        for (;;) {
-            const int sh = D - 1 - lvl;
-            const uint32_t c = ((R.P[0] >> sh) & 1) | (((R.P[1] >> sh) & 1) << 1) |
-                               (((R.P[2] >> sh) & 1) << 2);
-#if FPO_NODE_CACHE
-            if (!(nc.node == node && nc.level == lvl)) {
-                const uint4 *q = node < p.n_smem_nodes
-                                     ? reinterpret_cast<const uint4 *>(s_nodes) + 2 * node
-                                     : reinterpret_cast<const uint4 *>(p.nodes) + 2 * (size_t)node;
-                if (node < p.n_smem_nodes) {
-                    nc.lo = q[0];
-                    nc.hi = q[1];
-                } else {
-                    nc.lo = __ldg(q);
-                    nc.hi = __ldg(q + 1);
-                }
-                nc.node = node;
-                nc.level = lvl;
-            }
-            const uint32_t sl = pick_slot(nc, c);
-#else
-            const uint32_t idx = node * 8 + c;
-            const uint32_t sl = node < p.n_smem_nodes ? s_nodes[idx] : __ldg(p.nodes + idx);
-#endif
-            ++lvl;
-            if (sl == 0u) { kind = ROOT_EMPTY; break; }
-            if (sl & LEAF_BIT) { kind = ROOT_LEAF; leaf = sl & ~LEAF_BIT; break; }
-            node = sl;
-            s_stack[lvl * stride] = node;
-        }
+        cb.lvl = 0;
+        cb.kind = ROOT_LEAF;
+        return cb;
     }
-    // --- exit of the cube: level lvl, 2^(D - lvl) finest cells a side --------
-    const int csz = 1 << (D - lvl);
+    const int D = p.depth;
+    int lvl = lvl_start;
+    uint32_t node = s_stack[lvl * stride];
+    for (;;) {
+        const int sh = D - 1 - lvl;
+        const uint32_t c = ((P[0] >> sh) & 1) | (((P[1] >> sh) & 1) << 1) | (((P[2] >> sh) & 1) << 2);
+#if FPO_NODE_CACHE
+        if (!(nc.node == node && nc.level == lvl)) {
+            const uint4 *q = node < p.n_smem_nodes
+                                 ? reinterpret_cast<const uint4 *>(s_nodes) + 2 * node
+                                 : reinterpret_cast<const uint4 *>(p.nodes) + 2 * (size_t)node;
+            if (node < p.n_smem_nodes) {
+                nc.lo = q[0];
+                nc.hi = q[1];
+            } else {
+                nc.lo = __ldg(q);
+                nc.hi = __ldg(q + 1);
+            }
+            nc.node = node;
+            nc.level = lvl;
+        }
+        const uint32_t sl = pick_slot(nc, c);
+#else
+        (void)nc;
+        const uint32_t idx = node * 8 + c;
+        const uint32_t sl = node < p.n_smem_nodes ? s_nodes[idx] : __ldg(p.nodes + idx);
+#endif
+        ++lvl;
+        if (sl == 0u) { cb.kind = ROOT_EMPTY; break; }
+        if (sl & LEAF_BIT) { cb.kind = ROOT_LEAF; cb.leaf = sl & ~LEAF_BIT; break; }
+        node = sl;
+        s_stack[lvl * stride] = node;
+    }
+    cb.lvl = lvl;
+    return cb;
+}
+
+// Exit of cube (level lvl, 2^(D - lvl) finest cells a side) holding R.P:
+// the exit distance tx along the ray, the exit axis m (ties: x < y < z) and
+// the cube's lower corner lo.
+__device__ __forceinline__ float cube_exit(const RayState &R, int D, int lvl, int &m, int lo[3], int &csz)
+{
+    csz = 1 << (D - lvl);
     float te[3];
-    int lo[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         lo[a] = R.P[a] & ~(csz - 1);
@@ -400,92 +412,21 @@ __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const f
         else
             te[a] = FLT_MAX;
     }
-    int m = 0;
+    m = 0;
     float tx = te[0];
     if (te[1] < tx) { tx = te[1]; m = 1; }
     if (te[2] < tx) { tx = te[2]; m = 2; }
+    return tx;
+}
 
-    // --- shade a leaf segment (Eq. 7, 9, 1; emission-absorption) -------------
-    bool stop = false;
-    if (kind == ROOT_LEAF && tx > R.t) {
-        const float delta = tx - R.t;
-        float sigma, z[27];
-        if constexpr (MAT) {
-            const float4 *rec = p.table + (size_t)leaf * (TABLE_STRIDE / 4);
-            float v[28];
-#pragma unroll
-            for (int q = 0; q < 7; ++q) {
-                const float4 w = __ldg(rec + q);
-                v[4 * q] = w.x;
-                v[4 * q + 1] = w.y;
-                v[4 * q + 2] = w.z;
-                v[4 * q + 3] = w.w;
-            }
-            sigma = v[0];
-#pragma unroll
-            for (int q = 0; q < 27; ++q) z[q] = v[q + 1];
-        } else {
-            const float4 *sr = p.sig + (size_t)leaf * p.sig_stride4;
-            float acc = 0.0f;
-#pragma unroll
-            for (int q = 0; q < (N1 + 3) / 4; ++q) {
-                const float4 w = __ldg(sr + q);
-                const float wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (4 * q + j < N1) acc = fmaf(wv[j], bsrc[(4 * q + j) * bstride], acc);
-            }
-            sigma = fmaxf(acc, 0.0f);
-            float bz[N2];
-#pragma unroll
-            for (int i = 0; i < N2; ++i) bz[i] = bsrc[i * bstride];
-            const float4 *zr = reinterpret_cast<const float4 *>(p.zc + (size_t)leaf * p.z_stride);
-#pragma unroll
-            for (int q = 0; q < 27; ++q) z[q] = 0.0f;
-#pragma unroll
-            for (int q4 = 0; q4 < (27 * N2 + 3) / 4; ++q4) {
-                const float4 w = __ldg(zr + q4);
-                const float wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int e = 4 * q4 + j;
-                    if (e < 27 * N2) z[e / N2] = fmaf(wv[j], bz[e % N2], z[e / N2]);
-                }
-            }
-        }
-        float col[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float sacc = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) sacc = fmaf(z[9 * c + k], R.Y[k], sacc);
-            col[c] = sigmoidf_(sacc);
-        }
-        const float e = __expf(-sigma * delta);
-        const float w = R.T * (1.0f - e);
-        R.C0 = fmaf(w, col[0], R.C0);
-        R.C1 = fmaf(w, col[1], R.C1);
-        R.C2 = fmaf(w, col[2], R.C2);
-        R.T *= e;
-        if (DBG) {
-            if (p.flags & FPO_FLAG_RECORD_VISITS) {
-                if (R.n_visits < p.visit_cap)
-                    p.visit_log[(size_t)R.ray * p.visit_cap + R.n_visits] = p.perm[leaf];
-                else
-                    atomicOr(p.status, STATUS_VISIT_OVERFLOW);
-            }
-            if (p.flags & FPO_FLAG_MARK_LEAVES) p.leaf_mark[p.perm[leaf]] = 1;
-        }
-        ++R.n_visits;
-        stop = R.T < p.stop_T;
-    }
-    if (stop) return false;
-    // --- step into the neighbour cube ---------------------------------------
-    // Along m: the adjacent cube; along the other axes: the cell holding the
-    // exit point, clamped to this cube's extent and never moving backwards,
-    // so every step makes progress.  A finest-level cube (one cell) keeps the
-    // other two coordinates as they are.
-    int Pn[3];
+// Next cell after leaving the cube through axis m at distance tx.  Along m:
+// the adjacent cube; along the other axes: the cell holding the exit point,
+// clamped to this cube's extent and never moving backwards, so every step
+// makes progress.  A finest-level cube keeps the other two coordinates.
+// Returns false when the ray leaves the grid.
+__device__ __forceinline__ bool next_cell(const RayState &R, int G, int m, const int lo[3], int csz,
+                                          float tx, int Pn[3])
+{
     bool inside = true;
     if (FPO_FAST_STEP && csz == 1) {
 #pragma unroll
@@ -511,19 +452,166 @@ __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const f
             }
         }
     }
-    if (!inside) return false;
+    return inside;
+}
+
+// Moves R to cell Pn: the deepest common ancestor level of the old and the
+// new cell becomes the next descent's starting level.
+__device__ __forceinline__ void move_to(RayState &R, int D, const int Pn[3], float tx)
+{
     R.t = fmaxf(R.t, tx);
-    // deepest common ancestor of the old and the new cell
     const uint32_t diff = (uint32_t)((R.P[0] ^ Pn[0]) | (R.P[1] ^ Pn[1]) | (R.P[2] ^ Pn[2]));
     R.lvl_start = D - 1 - (31 - __clz(diff));
     R.P[0] = Pn[0];
     R.P[1] = Pn[1];
     R.P[2] = Pn[2];
+}
+
+__device__ __forceinline__ const float4 *table_record(const TraverseParams &p, uint32_t leaf)
+{
+    return p.table + (size_t)leaf * (TABLE_STRIDE / 4);
+}
+
+// Shades one leaf segment of length delta (Eq. 7 and 9 from the table or
+// fused, Eq. 1 colour, emission-absorption update).  Returns true when the
+// transmittance fell below stop_T.
+template <bool MAT, bool DBG, int N1, int N2>
+__device__ __forceinline__ bool shade(const TraverseParams &p, const float *bsrc, int bstride,
+                                      RayState &R, uint32_t leaf, float delta)
+{
+    float sigma, z[27];
+    if constexpr (MAT) {
+        const float4 *rec = table_record(p, leaf);
+        float v[28];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const float4 w = __ldg(rec + q);
+            v[4 * q] = w.x;
+            v[4 * q + 1] = w.y;
+            v[4 * q + 2] = w.z;
+            v[4 * q + 3] = w.w;
+        }
+        sigma = v[0];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) z[q] = v[q + 1];
+    } else {
+        const float4 *sr = p.sig + (size_t)leaf * p.sig_stride4;
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < (N1 + 3) / 4; ++q) {
+            const float4 w = __ldg(sr + q);
+            const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (4 * q + j < N1) acc = fmaf(wv[j], bsrc[(4 * q + j) * bstride], acc);
+        }
+        sigma = fmaxf(acc, 0.0f);
+        float bz[N2];
+#pragma unroll
+        for (int i = 0; i < N2; ++i) bz[i] = bsrc[i * bstride];
+        const float4 *zr = reinterpret_cast<const float4 *>(p.zc + (size_t)leaf * p.z_stride);
+#pragma unroll
+        for (int q = 0; q < 27; ++q) z[q] = 0.0f;
+#pragma unroll
+        for (int q4 = 0; q4 < (27 * N2 + 3) / 4; ++q4) {
+            const float4 w = __ldg(zr + q4);
+            const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int e = 4 * q4 + j;
+                if (e < 27 * N2) z[e / N2] = fmaf(wv[j], bz[e % N2], z[e / N2]);
+            }
+        }
+    }
+    float col[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float sacc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) sacc = fmaf(z[9 * c + k], R.Y[k], sacc);
+        col[c] = sigmoidf_(sacc);
+    }
+    const float e = __expf(-sigma * delta);
+    const float w = R.T * (1.0f - e);
+    R.C0 = fmaf(w, col[0], R.C0);
+    R.C1 = fmaf(w, col[1], R.C1);
+    R.C2 = fmaf(w, col[2], R.C2);
+    R.T *= e;
+    if (DBG) {
+        if (p.flags & FPO_FLAG_RECORD_VISITS) {
+            if (R.n_visits < p.visit_cap)
+                p.visit_log[(size_t)R.ray * p.visit_cap + R.n_visits] = p.perm[leaf];
+            else
+                atomicOr(p.status, STATUS_VISIT_OVERFLOW);
+        }
+        if (p.flags & FPO_FLAG_MARK_LEAVES) p.leaf_mark[p.perm[leaf]] = 1;
+    }
+    ++R.n_visits;
+    return R.T < p.stop_T;
+}
+
+__device__ __forceinline__ bool step_cap(const TraverseParams &p, RayState &R)
+{
     if (++R.steps > p.max_steps) {
         atomicOr(p.status, STATUS_TRAVERSAL_LIMIT);
-        return false;
+        return true;
     }
-    return true;
+    return false;
+}
+
+// One traversal step (compaction schedule): locate, shade, move.  Returns
+// false once the ray is finished (left the grid, early stop, or step cap).
+template <bool MAT, bool DBG, int N1, int N2>
+__device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const float *bsrc,
+                         int bstride, const uint32_t *__restrict__ s_nodes, uint32_t *s_stack,
+                         int stride, RayState &R, NodeCache &nc)
+{
+    (void)fs;
+    const int D = p.depth, G = 1 << D;
+    const Cube cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start, nc);
+    int m, lo[3], csz;
+    const float tx = cube_exit(R, D, cb.lvl, m, lo, csz);
+    if (cb.kind == ROOT_LEAF && tx > R.t)
+        if (shade<MAT, DBG, N1, N2>(p, bsrc, bstride, R, cb.leaf, tx - R.t)) return false;
+    int Pn[3];
+    if (!next_cell(R, G, m, lo, csz, tx, Pn)) return false;
+    move_to(R, D, Pn, tx);
+    return !step_cap(p, R);
+}
+
+// A whole ray (lane-loop schedule).  Software-pipelined: the next cube is
+// located, and its table record prefetched into L1, before the current cube
+// is shaded, so the record's latency hides behind the shading arithmetic.
+template <bool MAT, bool DBG, int N1, int N2>
+__device__ void trace_ray(const TraverseParams &p, const float *bsrc, int bstride,
+                          const uint32_t *__restrict__ s_nodes, uint32_t *s_stack, int stride,
+                          RayState &R, NodeCache &nc)
+{
+    const int D = p.depth, G = 1 << D;
+    Cube cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start, nc);
+    for (;;) {
+        int m, lo[3], csz;
+        const float tx = cube_exit(R, D, cb.lvl, m, lo, csz);
+        int Pn[3];
+        const bool inside = next_cell(R, G, m, lo, csz, tx, Pn);
+        Cube nx;
+        nx.kind = ROOT_EMPTY;
+        if (FPO_PREFETCH && inside) {
+            const uint32_t diff = (uint32_t)((R.P[0] ^ Pn[0]) | (R.P[1] ^ Pn[1]) | (R.P[2] ^ Pn[2]));
+            nx = locate(p, s_nodes, s_stack, stride, Pn, D - 1 - (31 - __clz(diff)), nc);
+            if (MAT && nx.kind == ROOT_LEAF)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record(p, nx.leaf)));
+        }
+        if (cb.kind == ROOT_LEAF && tx > R.t)
+            if (shade<MAT, DBG, N1, N2>(p, bsrc, bstride, R, cb.leaf, tx - R.t)) return;
+        if (!inside) return;
+        move_to(R, D, Pn, tx);
+        if (step_cap(p, R)) return;
+        if (FPO_PREFETCH)
+            cb = nx;
+        else
+            cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start, nc);
+    }
 }
 
 }  // namespace
@@ -603,7 +691,17 @@ __global__ void __maxnreg__(MAT ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED)
     // ray k (0..31) of a tile: camera pixel (8x4 block) or explicit ray
     auto tile_ray = [&](uint32_t tile, uint32_t k, uint32_t &ray, int &px, int &py) -> bool {
         if (p.fr.mode == FPO_RAYS_CAMERA) {
-            const uint32_t tx = tile % p.tiles_x, ty = tile / p.tiles_x;
+            uint32_t tx, ty;
+            if (p.super_tile) {  // square groups of super_tile^2 tiles, row-major
+                const uint32_t S = p.super_tile, per = S * S;
+                const uint32_t g = tile / per, w = tile % per, gx = (p.tiles_x + S - 1) / S;
+                tx = (g % gx) * S + w % S;
+                ty = (g / gx) * S + w / S;
+                if (tx >= p.tiles_x) return false;
+            } else {
+                tx = tile % p.tiles_x;
+                ty = tile / p.tiles_x;
+            }
             px = (int)(tx * 8 + (k & 7));
             py = (int)(ty * 4 + (k >> 3));
             ray = (uint32_t)py * p.fr.width + (uint32_t)px;
@@ -634,8 +732,7 @@ __global__ void __maxnreg__(MAT ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED)
                     NodeCache nc;
                     nc.node = 0xffffffffu;
                     nc.level = -1;
-                    while (step_ray<MAT, DBG, N1, N2>(p, fs, bsrc, bstride, s_nodes, my_stack, stride, R, nc)) {
-                    }
+                    trace_ray<MAT, DBG, N1, N2>(p, bsrc, bstride, s_nodes, my_stack, stride, R, nc);
                     finish(R);
                 }
             }
