@@ -225,6 +225,8 @@ struct RayState {
     float go[3];   // origin in grid units, moved to the cube entry point
     float gd[3];   // direction in grid units
     float inv[3];  // 1 / gd, 0 where gd == 0
+    int pos[3];    // 1 where gd > 0: exit plane = lo + pos * size
+    int zmask;     // bit a set where gd[a] == 0 (that axis is never crossed)
     float Y[9];    // real SH of the unit direction (Eq. 1)
     float C0, C1, C2, T, t;
     int P[3];      // finest-level cell holding the current point
@@ -334,7 +336,9 @@ __device__ bool init_ray(const TraverseParams &p, const FrameShared &fs, bool pr
     for (int a = 0; a < 3; ++a) {
         R.go[a] = fmaf(t0, R.gd[a], R.go[a]);
         R.P[a] = min(max((int)floorf(R.go[a]), 0), G - 1);
+        R.pos[a] = R.gd[a] > 0.0f ? 1 : 0;
     }
+    R.zmask = (R.gd[0] == 0.0f ? 1 : 0) | (R.gd[1] == 0.0f ? 2 : 0) | (R.gd[2] == 0.0f ? 4 : 0);
     s_stack[0] = 0;
     return true;
 }
@@ -405,12 +409,9 @@ __device__ __forceinline__ float cube_exit(const RayState &R, int D, int lvl, in
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         lo[a] = R.P[a] & ~(csz - 1);
-        if (R.gd[a] > 0.0f)
-            te[a] = ((float)(lo[a] + csz) - R.go[a]) * R.inv[a];
-        else if (R.gd[a] < 0.0f)
-            te[a] = ((float)lo[a] - R.go[a]) * R.inv[a];
-        else
-            te[a] = FLT_MAX;
+        // (plane - go) is exact for nearby planes (Sterbenz), so te carries
+        // one rounding of the product
+        te[a] = (R.zmask >> a) & 1 ? FLT_MAX : ((float)(lo[a] + R.pos[a] * csz) - R.go[a]) * R.inv[a];
     }
     m = 0;
     float tx = te[0];
@@ -433,16 +434,16 @@ __device__ __forceinline__ bool next_cell(const RayState &R, int G, int m, const
         for (int a = 0; a < 3; ++a) {
             Pn[a] = R.P[a];
             if (a == m) {
-                Pn[a] += R.gd[a] > 0.0f ? 1 : -1;
-                inside = Pn[a] >= 0 && Pn[a] < G;
+                Pn[a] += 2 * R.pos[a] - 1;
+                inside = (unsigned)Pn[a] < (unsigned)G;
             }
         }
     } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             if (a == m) {
-                Pn[a] = R.gd[a] > 0.0f ? lo[a] + csz : lo[a] - 1;
-                inside = Pn[a] >= 0 && Pn[a] < G;
+                Pn[a] = R.pos[a] ? lo[a] + csz : lo[a] - 1;
+                inside = (unsigned)Pn[a] < (unsigned)G;
             } else {
                 int q = (int)floorf(fmaf(tx, R.gd[a], R.go[a]));
                 q = min(max(q, lo[a]), lo[a] + csz - 1);
