@@ -188,6 +188,26 @@ int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts
                         const float *out_rgb, const float *dL_drgb, float *dL_dcoeffs,
                         void *cuda_stream);
 
+/* Renders like fpo_render in the MATERIALISE mode, but allocates nothing.
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * call cudaMalloc when they render (for example a host framework that owns
+ * all device memory through its own allocator, or a real-time loop that
+ * forbids allocation after start-up).  fpo_render allocates the per-frame
+ * IDFT table on first use; this call instead keeps it in a fixed array of
+ * device memory inside the library: 8 MiB, loaded on every GPU that loads
+ * the library and held until the process exits, enough for trees of at most
+ * 65536 leaves.  Larger trees, and explicit rays with per-ray times, are
+ * rejected with FPO_ERR_INVALID_ARG.  Inputs: ctx (a context whose tree was
+ * uploaded beforehand) and rays; output: out_rgb as in fpo_render; opts and
+ * device-side errors as in fpo_render (read them with fpo_status_sync).
+ * The array is shared by all calls on a device and keeps the last call's
+ * table: calls whose GPU work overlaps (different streams, or different
+ * contexts on the same device) race on it and must be ordered.  The first
+ * call on each device looks up the array's device address (once, under a
+ * lock); make that first call before any stream capture begins. */
+int fpo_render_noalloc(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
+                       float *out_rgb, void *cuda_stream);
+
 /* Waits for cuda_stream and returns (then clears) the device status word:
  * FPO_OK, FPO_ERR_TRAVERSAL_LIMIT, FPO_ERR_VISIT_OVERFLOW or
  * FPO_ERR_DEVICE_TIMEOUT. */

@@ -98,6 +98,39 @@ struct fpo_ctx {
     }
 };
 
+namespace fpo {
+
+CtxView ctx_view(const fpo_ctx *c)
+{
+    CtxView v{};
+    v.device = c->cfg.device;
+    v.sm_count = c->sm_count;
+    v.n1 = c->cfg.n1;
+    v.n2 = c->cfg.n2;
+    v.period_T = c->cfg.period_T;
+    v.traverse_threads = c->cfg.traverse_threads;
+    v.refill_min = c->cfg.refill_min;
+    v.inner_steps = c->cfg.inner_steps;
+    v.d_status = c->d_status;
+    v.has_tree = c->has_tree;
+    v.n_leaves = c->n_leaves;
+    v.n_nodes = c->n_nodes;
+    v.root_kind = c->root_kind;
+    v.n_smem_nodes = c->n_smem_nodes;
+    v.depth = c->depth;
+    for (int k = 0; k < 3; ++k) v.aabb_min[k] = c->aabb_min[k];
+    v.aabb_size = c->aabb_size;
+    v.d_nodes = c->d_nodes;
+    v.d_perm = c->d_perm;
+    v.d_sig = c->d_sig;
+    v.d_z = c->d_z;
+    return v;
+}
+
+int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
+}  // namespace fpo
+
 extern "C" {
 
 const char *fpo_last_error(void) { return g_err.c_str(); }

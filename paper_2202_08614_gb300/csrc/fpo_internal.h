@@ -109,6 +109,24 @@ struct MaterialiseParams {
     uint32_t *status;
 };
 
+// Read-only view of a context's uploaded tree and launch settings.
+struct CtxView {
+    int device, sm_count;
+    int n1, n2;
+    double period_T;
+    int traverse_threads, refill_min, inner_steps;
+    uint32_t *d_status;
+    bool has_tree;
+    uint32_t n_leaves, n_nodes, root_kind, n_smem_nodes;
+    int depth;
+    double aabb_min[3], aabb_size;
+    const uint32_t *d_nodes, *d_perm;
+    const float *d_sig, *d_z;
+};
+CtxView ctx_view(const fpo_ctx *ctx);
+// Records `msg` as the calling thread's last error; returns `code`.
+int set_last_error(int code, const char *msg);
+
 // Launchers (return cudaError_t as int).
 int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream);
 int materialise_stages(int n1, int n2);

@@ -30,7 +30,7 @@ FLAG_RECORD_VISITS, FLAG_OUT_T, FLAG_MARK_LEAVES, FLAG_STATS = 1, 2, 4, 8
 # Every symbol include/fpo.h declares.
 EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
            "fpo_render_backward", "fpo_status_sync", "fpo_tree_info_get", "fpo_destroy",
-           "fpo_last_error", "fpo_version"]
+           "fpo_last_error", "fpo_version", "fpo_render_noalloc"]
 
 
 class FPOError(RuntimeError):
@@ -89,6 +89,7 @@ def lib():
         L.fpo_upload_tree.argtypes = [P, C.POINTER(TreeDesc)]
         L.fpo_render.argtypes = [P, C.POINTER(Rays), C.POINTER(FrameOpts), P, P]
         L.fpo_render_backward.argtypes = [P, C.POINTER(Rays), C.POINTER(FrameOpts), P, P, P, P]
+        L.fpo_render_noalloc.argtypes = [P, C.POINTER(Rays), C.POINTER(FrameOpts), P, P]
         L.fpo_status_sync.argtypes = [P, P]
         L.fpo_tree_info_get.argtypes = [P, C.POINTER(TreeInfo)]
         L.fpo_destroy.argtypes = [P]
