@@ -1,0 +1,63 @@
+"""CPU checks of bench.py: the multi-rank logic under gloo (world size 2) and
+the reference arm's JSON line (the FP64 oracle on a small sample)."""
+
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        t = bench.max_over_ranks(10.0 + rank, dist, "cpu")
+        frames = bench.frames_for_rank(rank, 8)
+        q.put((rank, t, frames))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_gloo_max_time_and_own_frames():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29500 + (os.getpid() % 1000)
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict()
+    for _ in range(2):
+        rank, t, frames = q.get(timeout=120)
+        res[rank] = (t, frames)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0][0] == res[1][0] == 11.0  # slowest rank's time on every rank
+    assert res[0][1] != res[1][1]  # each rank renders its own frames
+    sys.path.insert(0, ROOT)
+    import bench
+
+    # whole-job throughput counts both ranks' frames
+    assert bench.mrays_per_s(2, 10, 1_000_000, 1000.0) == 2 * bench.mrays_per_s(1, 10, 1_000_000, 1000.0)
+
+
+def test_reference_arm_json_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "2", "--warmup", "1"], capture_output=True, text=True,
+                         timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "Mrays/s" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["higher_is_better"] is True
