@@ -81,8 +81,9 @@ struct fpo_ctx {
     double aabb_min[3] = {0, 0, 0}, aabb_size = 1.0;
     uint32_t *d_nodes = nullptr;
     uint32_t *d_perm = nullptr;
-    float *d_sig = nullptr;
-    float *d_z = nullptr;
+    void *d_sig = nullptr;    // density records (storage precision)
+    void *d_z = nullptr;      // SH records (storage precision)
+    float *d_scale = nullptr; // FP8: per-leaf scale, padded to a multiple of 4 leaves
     float *d_table = nullptr;
     size_t table_leaves = 0;
 
@@ -92,6 +93,7 @@ struct fpo_ctx {
         dfree(d_perm);
         dfree(d_sig);
         dfree(d_z);
+        dfree(d_scale);
         dfree(d_table);
         table_leaves = 0;
         has_tree = false;
@@ -122,8 +124,10 @@ CtxView ctx_view(const fpo_ctx *c)
     v.aabb_size = c->aabb_size;
     v.d_nodes = c->d_nodes;
     v.d_perm = c->d_perm;
+    v.storage = c->cfg.storage;
     v.d_sig = c->d_sig;
     v.d_z = c->d_z;
+    v.d_scale = c->d_scale;
     return v;
 }
 
@@ -149,8 +153,6 @@ int fpo_create(fpo_ctx **out, const fpo_config *cfg)
         return fail(FPO_ERR_INVALID_ARG, "period_T must be finite and > 0");
     if (cfg->storage < FPO_STORAGE_F32 || cfg->storage > FPO_STORAGE_FP8_E4M3)
         return fail(FPO_ERR_INVALID_ARG, "unknown storage %d", cfg->storage);
-    if (cfg->storage != FPO_STORAGE_F32)
-        return fail(FPO_ERR_UNSUPPORTED, "storage %d is not implemented", cfg->storage);
     if (cfg->idft_mode < FPO_IDFT_AUTO || cfg->idft_mode > FPO_IDFT_MATERIALISE)
         return fail(FPO_ERR_INVALID_ARG, "unknown idft_mode %d", cfg->idft_mode);
     if (cfg->traverse_threads != 0 && cfg->traverse_threads != 128 && cfg->traverse_threads != 256)
@@ -199,16 +201,37 @@ int fpo_upload_tree(fpo_ctx *ctx, const fpo_tree_desc *tree)
     if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
     ctx->free_tree();
 
-    const int n1 = ctx->cfg.n1, n2 = ctx->cfg.n2;
-    const int ss = sig_stride(n1), zs = z_stride(n2), nc = n1 + 27 * n2;
+    const int n1 = ctx->cfg.n1, n2 = ctx->cfg.n2, nc = n1 + 27 * n2;
+    const int storage = ctx->cfg.storage;
+    const RecordLayout L = record_layout(storage, n1, n2);
     const size_t n = tree->n_leaves;
-    // Reorder the coefficients into breadth-first leaf order, split into
-    // the density and the SH record arrays, padded with zeros.
-    std::vector<float> sig((size_t)n * ss, 0.0f), zc((size_t)n * zs, 0.0f);
+    // Reorder the coefficients into breadth-first leaf order, split into the
+    // density and the SH record arrays (zero padded), encoded in the storage
+    // precision; FP8 codes hold coefficient / scale with a per-leaf scale
+    // max|k| / 448 (448 = the largest E4M3 value).
+    std::vector<uint8_t> sig(n * L.sig_bytes(), 0), zc(n * L.z_bytes(), 0);
+    std::vector<float> scale(L.scaled ? (n + 3) / 4 * 4 : 0, 0.0f);
+    auto put = [&](uint8_t *rec, int j, float v) {
+        switch (storage) {
+        case FPO_STORAGE_BF16: { const uint16_t c = encode_bf16(v); std::memcpy(rec + 2 * j, &c, 2); break; }
+        case FPO_STORAGE_F16: { const uint16_t c = encode_f16(v); std::memcpy(rec + 2 * j, &c, 2); break; }
+        case FPO_STORAGE_FP8_E4M3: rec[j] = encode_e4m3(v); break;
+        default: std::memcpy(rec + 4 * j, &v, 4);
+        }
+    };
     for (size_t i = 0; i < n; ++i) {
         const float *src = tree->coeffs + (size_t)pk.perm[i] * nc;
-        std::memcpy(&sig[i * ss], src, sizeof(float) * n1);
-        std::memcpy(&zc[i * zs], src + n1, sizeof(float) * 27 * n2);
+        float sc = 1.0f;
+        if (L.scaled) {
+            float mx = 0.0f;
+            for (int j = 0; j < nc; ++j) mx = std::fmax(mx, std::fabs(src[j]));
+            sc = mx > 0.0f ? mx / 448.0f : 1.0f;
+            scale[i] = sc;
+        }
+        uint8_t *rs = &sig[i * L.sig_bytes()];
+        uint8_t *rz = &zc[i * L.z_bytes()];
+        for (int j = 0; j < n1; ++j) put(rs, j, L.scaled ? src[j] / sc : src[j]);
+        for (int j = 0; j < 27 * n2; ++j) put(rz, j, L.scaled ? src[n1 + j] / sc : src[n1 + j]);
     }
     const size_t n_nodes = pk.nodes.size() / 8;
     cudaError_t e = cudaSuccess;
@@ -222,8 +245,9 @@ int fpo_upload_tree(fpo_ctx *ctx, const fpo_tree_desc *tree)
     };
     if ((st = up((void **)&ctx->d_nodes, pk.nodes.data(), pk.nodes.size() * 4, "nodes")) ||
         (st = up((void **)&ctx->d_perm, pk.perm.data(), pk.perm.size() * 4, "perm")) ||
-        (st = up((void **)&ctx->d_sig, sig.data(), sig.size() * 4, "sigma records")) ||
-        (st = up((void **)&ctx->d_z, zc.data(), zc.size() * 4, "SH records"))) {
+        (st = up((void **)&ctx->d_sig, sig.data(), sig.size(), "sigma records")) ||
+        (st = up((void **)&ctx->d_z, zc.data(), zc.size(), "SH records")) ||
+        (st = up((void **)&ctx->d_scale, scale.data(), scale.size() * 4, "FP8 scales"))) {
         ctx->free_tree();
         return st;
     }
@@ -249,7 +273,8 @@ int fpo_tree_info_get(const fpo_ctx *ctx, fpo_tree_info *out)
     out->max_depth = ctx->max_depth;
     out->n_smem_nodes = ctx->n_smem_nodes;
     out->node_bytes = (uint64_t)ctx->n_nodes * 32;
-    out->leaf_record_bytes = (uint64_t)(sig_stride(ctx->cfg.n1) + z_stride(ctx->cfg.n2)) * 4;
+    const RecordLayout L = record_layout(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2);
+    out->leaf_record_bytes = (uint64_t)(L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
     out->leaf_bytes = out->leaf_record_bytes * ctx->n_leaves;
     out->table_bytes = (uint64_t)ctx->table_leaves * TABLE_STRIDE * 4;
     return FPO_OK;
@@ -305,6 +330,8 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
     if (mode == FPO_IDFT_MATERIALISE && per_ray_t)
         return fail(FPO_ERR_INVALID_ARG, "per-ray times need the FUSED IDFT mode");
     const bool mat = mode == FPO_IDFT_MATERIALISE && ctx->n_leaves > 0;
+    if (!mat && ctx->n_leaves > 0 && ctx->cfg.storage != FPO_STORAGE_F32)
+        return fail(FPO_ERR_UNSUPPORTED, "the fused IDFT reads FP32 records only; use the table mode");
     if (!mat && !fused_supported(ctx->cfg.n1, ctx->cfg.n2))
         return fail(FPO_ERR_UNSUPPORTED, "the fused IDFT supports (n1, n2) in {(31,5), (11,5), (21,5), (31,11)}");
 
@@ -328,15 +355,18 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
     }
     if (mat) {
         MaterialiseParams mp{};
+        const RecordLayout L = record_layout(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2);
         mp.sig = ctx->d_sig;
         mp.zc = ctx->d_z;
+        mp.scale = ctx->d_scale;
         mp.table = ctx->d_table;
         mp.n_leaves = ctx->n_leaves;
+        mp.storage = ctx->cfg.storage;
         mp.n1 = ctx->cfg.n1;
         mp.n2 = ctx->cfg.n2;
-        mp.sig_stride = sig_stride(ctx->cfg.n1);
-        mp.z_stride = z_stride(ctx->cfg.n2);
-        mp.stages = materialise_stages(ctx->cfg.n1, ctx->cfg.n2);
+        mp.sig_stride = L.sig_elems;
+        mp.z_stride = L.z_elems;
+        mp.stages = materialise_stages(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2);
         mp.t = rays->t;
         mp.period_T = ctx->cfg.period_T;
         mp.status = ctx->d_status;
@@ -369,7 +399,7 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
     for (int k = 0; k < 3; ++k) p.amin[k] = (float)ctx->aabb_min[k];
     p.table = reinterpret_cast<const float4 *>(ctx->d_table);
     p.sig = reinterpret_cast<const float4 *>(ctx->d_sig);
-    p.zc = ctx->d_z;
+    p.zc = static_cast<const float *>(ctx->d_z);
     p.n1 = ctx->cfg.n1;
     p.n2 = ctx->cfg.n2;
     p.sig_stride4 = sig_stride(ctx->cfg.n1) / 4;

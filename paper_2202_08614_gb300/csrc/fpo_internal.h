@@ -31,6 +31,35 @@ constexpr int MAX_DEPTH = 12;
 inline int sig_stride(int n1) { return (n1 + 3) & ~3; }
 inline int z_stride(int n2) { return (27 * n2 + 3) & ~3; }
 
+// Stored record layout for any storage precision: element counts padded so
+// that each record is a multiple of 16 bytes (bulk-copy granularity).  FP32
+// gives sig_stride / z_stride above.  FP8 adds one FP32 scale per leaf in a
+// separate array (codes are coefficient / scale).
+struct RecordLayout {
+    int sig_elems, z_elems, elem_bytes;
+    bool scaled;
+    int sig_bytes() const { return sig_elems * elem_bytes; }
+    int z_bytes() const { return z_elems * elem_bytes; }
+};
+inline RecordLayout record_layout(int storage, int n1, int n2)
+{
+    const int eb = storage == FPO_STORAGE_F32 ? 4 : (storage == FPO_STORAGE_FP8_E4M3 ? 1 : 2);
+    const int per16 = 16 / eb;
+    RecordLayout L;
+    L.elem_bytes = eb;
+    L.sig_elems = (n1 + per16 - 1) / per16 * per16;
+    L.z_elems = (27 * n2 + per16 - 1) / per16 * per16;
+    L.scaled = storage == FPO_STORAGE_FP8_E4M3;
+    return L;
+}
+
+// Host encoders (round to nearest even) from the format definitions:
+// bfloat16 (1-8-7), IEEE binary16 (1-5-10, overflow to infinity) and
+// FP8 E4M3 (1-4-3, bias 7, no infinities, saturating at +-448).
+uint16_t encode_bf16(float x);
+uint16_t encode_f16(float x);
+uint8_t encode_e4m3(float x);
+
 // Per-frame IDFT table: one 128-byte record per leaf,
 // [sigma(t) clamped at 0, z_{c,k}(t) for c = 0..2, k = 0..8 (27 values), 4 zeros].
 constexpr int TABLE_STRIDE = 32;
@@ -99,11 +128,13 @@ struct TraverseParams {
 };
 
 struct MaterialiseParams {
-    const float *sig;
-    const float *zc;
+    const void *sig;          // [n_leaves] records of sig_stride elements
+    const void *zc;           // [n_leaves] records of z_stride elements
+    const float *scale;       // [n_leaves] (FP8 storage) or nullptr
     float *table;
     uint32_t n_leaves;
-    int n1, n2, sig_stride, z_stride;
+    int storage;              // FPO_STORAGE_*
+    int n1, n2, sig_stride, z_stride;  // strides in elements
     int stages;               // shared-memory pipeline depth (materialise_stages)
     double t, period_T;
     uint32_t *status;
@@ -121,7 +152,9 @@ struct CtxView {
     int depth;
     double aabb_min[3], aabb_size;
     const uint32_t *d_nodes, *d_perm;
-    const float *d_sig, *d_z;
+    int storage;
+    const void *d_sig, *d_z;
+    const float *d_scale;
 };
 CtxView ctx_view(const fpo_ctx *ctx);
 // Records `msg` as the calling thread's last error; returns `code`.
@@ -129,7 +162,7 @@ int set_last_error(int code, const char *msg);
 
 // Launchers (return cudaError_t as int).
 int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream);
-int materialise_stages(int n1, int n2);
+int materialise_stages(int storage, int n1, int n2);
 int launch_traverse(const TraverseParams &p, bool materialised, bool debug, int sm_count,
                     void *stream);
 int traverse_smem_bytes(uint32_t n_smem_nodes, bool per_ray_basis, int threads);

@@ -8,6 +8,9 @@
 //                       SH colour + sigmoid (Eq. 1) and front-to-back
 //                       compositing with early stop; the IDFT either read
 //                       from the per-frame table or fused per visit.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -87,7 +90,17 @@ constexpr int MAT_THREADS = 256;
 constexpr int MAT_MAX_STAGES = 6;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s: a stuck copy, not slowness
 
-template <int N2>
+// Element i of a stored record in shared memory, as FP32 (storage ST).
+template <int ST>
+__device__ __forceinline__ float stored(const unsigned char *rec, int i)
+{
+    if constexpr (ST == FPO_STORAGE_F32) return reinterpret_cast<const float *>(rec)[i];
+    else if constexpr (ST == FPO_STORAGE_BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(rec)[i]);
+    else if constexpr (ST == FPO_STORAGE_F16) return __half2float(reinterpret_cast<const __half *>(rec)[i]);
+    else return static_cast<float>(reinterpret_cast<const __nv_fp8_e4m3 *>(rec)[i]);
+}
+
+template <int N2, int ST>
 __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_constant__ MaterialiseParams p)
 {
     extern __shared__ __align__(128) unsigned char mat_smem[];
@@ -96,8 +109,12 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
     __shared__ int s_fail;
     const int tid = threadIdx.x;
     const int S = p.stages;
-    const uint32_t sig_bytes = MAT_CHUNK * p.sig_stride * 4u;
-    const uint32_t stage_bytes = sig_bytes + MAT_CHUNK * p.z_stride * 4u;
+    constexpr uint32_t EB = ST == FPO_STORAGE_F32 ? 4u : (ST == FPO_STORAGE_FP8_E4M3 ? 1u : 2u);
+    constexpr bool SCALED = ST == FPO_STORAGE_FP8_E4M3;
+    const uint32_t rec_sig = p.sig_stride * EB, rec_z = p.z_stride * EB;  // bytes per leaf
+    const uint32_t sig_bytes = MAT_CHUNK * rec_sig;
+    const uint32_t z_bytes = MAT_CHUNK * rec_z;
+    const uint32_t stage_bytes = sig_bytes + z_bytes + (SCALED ? MAT_CHUNK * 4u : 0u);
     const uint32_t n_chunks = (p.n_leaves + MAT_CHUNK - 1) / MAT_CHUNK;
     const int nb = p.n1 > p.n2 ? p.n1 : p.n2;
     if (tid < nb) s_b[tid] = basis_fp64(tid, p.t, p.period_T);
@@ -111,11 +128,15 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
     auto issue = [&](uint32_t c, int s) {
         const uint32_t first = c * MAT_CHUNK;
         const uint32_t m = min((uint32_t)MAT_CHUNK, p.n_leaves - first);
-        const uint32_t bs = m * p.sig_stride * 4u, bz = m * p.z_stride * 4u;
+        const uint32_t bs = m * rec_sig, bz = m * rec_z;
         unsigned char *dst = mat_smem + (size_t)s * stage_bytes;
-        ptx::mbar_arrive_expect_tx(&bars[s], bs + bz);
-        ptx::bulk_g2s(dst, p.sig + (size_t)first * p.sig_stride, bs, &bars[s]);
-        ptx::bulk_g2s(dst + sig_bytes, p.zc + (size_t)first * p.z_stride, bz, &bars[s]);
+        // FP8 scales: 4 bytes per leaf, copied in 16-byte units (the scale
+        // array is padded to a multiple of 4 leaves)
+        const uint32_t bsc = SCALED ? ((m + 3u) & ~3u) * 4u : 0u;
+        ptx::mbar_arrive_expect_tx(&bars[s], bs + bz + bsc);
+        ptx::bulk_g2s(dst, static_cast<const unsigned char *>(p.sig) + (size_t)first * rec_sig, bs, &bars[s]);
+        ptx::bulk_g2s(dst + sig_bytes, static_cast<const unsigned char *>(p.zc) + (size_t)first * rec_z, bz, &bars[s]);
+        if (SCALED) ptx::bulk_g2s(dst + sig_bytes + z_bytes, p.scale + first, bsc, &bars[s]);
     };
     if (tid == 0)
         for (int s = 0; s < S; ++s) {
@@ -139,27 +160,31 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
         if (s_fail) break;
         const uint32_t first = c * MAT_CHUNK;
         const int m = (int)min((uint32_t)MAT_CHUNK, p.n_leaves - first);
-        const float *stage_sig = reinterpret_cast<const float *>(mat_smem + (size_t)s * stage_bytes);
-        const float *stage_z = reinterpret_cast<const float *>(mat_smem + (size_t)s * stage_bytes + sig_bytes);
+        const unsigned char *stage_sig = mat_smem + (size_t)s * stage_bytes;
+        const unsigned char *stage_z = stage_sig + sig_bytes;
+        const float *stage_scale = reinterpret_cast<const float *>(stage_z + z_bytes);
         // One warp per leaf: lane i < n1 forms k_sigma_i b_i and a butterfly
         // sums the density; lanes 0..26 form z_{lane}(t) from n2 consecutive
-        // floats (conflict-free for odd n2).  Lane j then stores output j.
+        // elements.  Lane j then stores output j.
         for (int l = warp; l < m; l += MAT_THREADS / 32) {
-            const float *sg = stage_sig + l * p.sig_stride;
-            const float *zz = stage_z + l * p.z_stride;
-            float part = lane < p.n1 ? sg[lane] * b_lane : 0.0f;
+            const unsigned char *sg = stage_sig + l * rec_sig;
+            const unsigned char *zz = stage_z + l * rec_z;
+            float part = lane < p.n1 ? stored<ST>(sg, lane) * b_lane : 0.0f;
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
             float v = 0.0f;
             if (lane < 27) {
                 if constexpr (N2 > 0) {
-                    const float *zq = zz + lane * N2;
 #pragma unroll
-                    for (int i = 0; i < N2; ++i) v = fmaf(zq[i], bz[i], v);
+                    for (int i = 0; i < N2; ++i) v = fmaf(stored<ST>(zz, lane * N2 + i), bz[i], v);
                 } else {
-                    const float *zq = zz + lane * p.n2;
-                    for (int i = 0; i < p.n2; ++i) v = fmaf(zq[i], s_b[i], v);
+                    for (int i = 0; i < p.n2; ++i) v = fmaf(stored<ST>(zz, lane * p.n2 + i), s_b[i], v);
                 }
+            }
+            if (SCALED) {
+                const float sc = stage_scale[l];
+                part *= sc;
+                v *= sc;
             }
             const float zprev = __shfl_up_sync(0xffffffffu, v, 1);
             const float outv = lane == 0 ? fmaxf(part, 0.0f) : (lane <= 27 ? zprev : 0.0f);
@@ -182,20 +207,34 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
     }
 }
 
-int materialise_stages(int n1, int n2)
+int materialise_stages(int storage, int n1, int n2)
 {
-    const int stage = MAT_CHUNK * (sig_stride(n1) + z_stride(n2)) * 4;
+    const RecordLayout L = record_layout(storage, n1, n2);
+    const int stage = MAT_CHUNK * (L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
     int s = (100 * 1024) / stage;  // two CTAs per SM
     if (s > MAT_MAX_STAGES) s = MAT_MAX_STAGES;
     if (s < 2) s = 2;
     return s;
 }
 
+template <int N2>
+static void *pick_materialise(int storage)
+{
+    switch (storage) {
+    case FPO_STORAGE_BF16: return (void *)materialise_kernel<N2, FPO_STORAGE_BF16>;
+    case FPO_STORAGE_F16: return (void *)materialise_kernel<N2, FPO_STORAGE_F16>;
+    case FPO_STORAGE_FP8_E4M3: return (void *)materialise_kernel<N2, FPO_STORAGE_FP8_E4M3>;
+    default: return (void *)materialise_kernel<N2, FPO_STORAGE_F32>;
+    }
+}
+
 int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream)
 {
     if (p.n_leaves == 0) return (int)cudaSuccess;
-    const int smem = p.stages * MAT_CHUNK * (p.sig_stride + p.z_stride) * 4;
-    auto kern = p.n2 == 5 ? materialise_kernel<5> : (p.n2 == 11 ? materialise_kernel<11> : materialise_kernel<0>);
+    const RecordLayout L = record_layout(p.storage, p.n1, p.n2);
+    const int smem = p.stages * MAT_CHUNK * (L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
+    const void *kern = p.n2 == 5 ? pick_materialise<5>(p.storage)
+                                 : (p.n2 == 11 ? pick_materialise<11>(p.storage) : pick_materialise<0>(p.storage));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
@@ -205,7 +244,9 @@ int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream)
     const uint32_t n_chunks = (p.n_leaves + MAT_CHUNK - 1) / MAT_CHUNK;
     uint64_t blocks = (uint64_t)sm_count * per_sm;
     if (blocks > n_chunks) blocks = n_chunks;
-    kern<<<(unsigned)blocks, MAT_THREADS, smem, (cudaStream_t)stream>>>(p);
+    void *args[] = {(void *)&p};
+    e = cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(MAT_THREADS), args, smem, (cudaStream_t)stream);
+    if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }
 

@@ -128,15 +128,18 @@ extern "C" int fpo_render_noalloc(fpo_ctx *ctx, const fpo_rays *rays, const fpo_
     if (mat) {
         // Every table entry the traversal reads is written first: nothing to clear.
         MaterialiseParams mp{};
+        const RecordLayout L = record_layout(c.storage, c.n1, c.n2);
         mp.sig = c.d_sig;
         mp.zc = c.d_z;
+        mp.scale = c.d_scale;
         mp.table = table;
         mp.n_leaves = c.n_leaves;
+        mp.storage = c.storage;
         mp.n1 = c.n1;
         mp.n2 = c.n2;
-        mp.sig_stride = sig_stride(c.n1);
-        mp.z_stride = z_stride(c.n2);
-        mp.stages = materialise_stages(c.n1, c.n2);
+        mp.sig_stride = L.sig_elems;
+        mp.z_stride = L.z_elems;
+        mp.stages = materialise_stages(c.storage, c.n1, c.n2);
         mp.t = rays->t;
         mp.period_T = c.period_T;
         mp.status = c.d_status;
@@ -168,7 +171,7 @@ extern "C" int fpo_render_noalloc(fpo_ctx *ctx, const fpo_rays *rays, const fpo_
     for (int k = 0; k < 3; ++k) p.amin[k] = (float)c.aabb_min[k];
     p.table = reinterpret_cast<const float4 *>(table);
     p.sig = reinterpret_cast<const float4 *>(c.d_sig);
-    p.zc = c.d_z;
+    p.zc = static_cast<const float *>(c.d_z);
     p.n1 = c.n1;
     p.n2 = c.n2;
     p.sig_stride4 = sig_stride(c.n1) / 4;

@@ -151,4 +151,63 @@ int validate_and_pack(const fpo_tree_desc *tree, int n1, int n2, PackedTree *out
     return FPO_OK;
 }
 
+namespace {
+
+// Encodes |x| into a sign-less minifloat with E exponent bits, M mantissa
+// bits and the given bias, rounding to nearest even; returns the code or -1
+// when the rounded value exceeds the largest finite value max_val.
+long minifloat_abs(double a, int E, int M, int bias, double max_val)
+{
+    if (a == 0.0) return 0;
+    int e2;
+    std::frexp(a, &e2);           // a = f * 2^e2, f in [0.5, 1)
+    int ue = e2 - 1;              // a = 1.x * 2^ue
+    const int emin = 1 - bias;    // smallest normal exponent
+    long code;
+    if (ue < emin) {              // subnormal: units of 2^(emin - M)
+        const double q = std::nearbyint(std::ldexp(a, M - emin));
+        code = (long)q;           // q == 2^M rolls into the smallest normal
+    } else {
+        double q = std::nearbyint(std::ldexp(a, M - ue));  // in [2^M, 2^(M+1)]
+        if (q >= std::ldexp(1.0, M + 1)) {
+            q *= 0.5;
+            ++ue;
+        }
+        code = ((long)(ue + bias) << M) | ((long)q - (1L << M));
+    }
+    // decode to compare against the largest finite value
+    const long ef = code >> M, mf = code & ((1L << M) - 1);
+    const double v = ef == 0 ? std::ldexp((double)mf, emin - M)
+                             : std::ldexp(1.0 + std::ldexp((double)mf, -M), (int)ef - bias);
+    if (v > max_val || ef >= (1L << E)) return -1;
+    return code;
+}
+
+}  // namespace
+
+uint16_t encode_bf16(float x)
+{
+    if (std::isnan(x)) return 0x7FC0;
+    const uint16_t s = std::signbit(x) ? 0x8000 : 0;
+    const long c = minifloat_abs(std::fabs((double)x), 8, 7, 127, 3.3895313892515355e38);
+    return (uint16_t)(s | (c < 0 ? 0x7F80 : c));  // overflow -> infinity
+}
+
+uint16_t encode_f16(float x)
+{
+    if (std::isnan(x)) return 0x7E00;
+    const uint16_t s = std::signbit(x) ? 0x8000 : 0;
+    const long c = minifloat_abs(std::fabs((double)x), 5, 10, 15, 65504.0);
+    return (uint16_t)(s | (c < 0 ? 0x7C00 : c));  // overflow -> infinity
+}
+
+uint8_t encode_e4m3(float x)
+{
+    if (std::isnan(x)) return 0x7F;
+    const uint8_t s = std::signbit(x) ? 0x80 : 0;
+    long c = minifloat_abs(std::fabs((double)x), 4, 3, 7, 448.0);
+    if (c < 0 || c > 0x7E) c = 0x7E;  // saturate at 448 (0x7F is NaN)
+    return (uint8_t)(s | c);
+}
+
 }  // namespace fpo
