@@ -30,6 +30,7 @@ from paper_2202_08614_gb300 import synth  # noqa: E402
 
 METRIC = "FPO render Mrays/s, 1080p fps; plain FP32 vs BF16/latent at PSNR≥45dB vs FP64"
 ALG_READ_PER_LEAF = 4 * (31 + 135)   # coefficient bytes of one leaf (FP32)
+STORED_PER_LEAF = {"f32": 4 * 166, "bf16": 2 * 166, "f16": 2 * 166, "fp8": 166 + 4}  # + FP8 scale
 TABLE_BYTES_PER_LEAF = 4 * 28        # sigma(t) + 27 z(t)
 OUT_BYTES_PER_RAY = 12               # FP32 RGB
 
@@ -41,6 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fpo", choices=["fpo", "reference"])
     ap.add_argument("--idft", default="auto", choices=["auto", "materialise", "fused"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16", "fp8"])
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
@@ -249,7 +251,7 @@ def main():
     cams = synth.ring_cameras(16, args.width, args.height)
     K, W = args.steps, args.warmup
     frames = frames_for_rank(rank, K + W)
-    r = fpo.Renderer(idft_mode=args.idft, device=local)
+    r = fpo.Renderer(idft_mode=args.idft, storage=args.storage, device=local)
     r.upload(tree)
     info = r.info()
     n_px = args.width * args.height
@@ -315,6 +317,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(tree, args, "materialise" if mat else "fused"),
     }
+    res["config"]["storage"] = args.storage
     res["fps"] = 1e3 / statistics.median(frame_ms)
     res["frame_ms"] = {"p10": float(np.percentile(frame_ms, 10)), "p50": statistics.median(frame_ms),
                        "p90": float(np.percentile(frame_ms, 90))}
@@ -324,7 +327,7 @@ def main():
     mean_vis = statistics.mean(n_vis)
     if mat:
         kernels = {
-            "materialise_kernel": (avg_mat, tree.n_leaves * (ALG_READ_PER_LEAF + TABLE_BYTES_PER_LEAF)),
+            "materialise_kernel": (avg_mat, tree.n_leaves * (STORED_PER_LEAF[args.storage] + TABLE_BYTES_PER_LEAF)),
             "traverse_kernel": (avg_trav, mean_vis * TABLE_BYTES_PER_LEAF + n_px * OUT_BYTES_PER_RAY),
         }
     else:
