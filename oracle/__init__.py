@@ -10,6 +10,8 @@ Functions and the passages they follow (Wang et al., CVPR 2022):
   sh(d, degree)      Eq. 1, real SH Y_{m,l}(d), l <= 2                  (Sec. 3)
   render(...)        Eq. 7, 9 and 1 per leaf segment, then
                      emission-absorption compositing with early stop   (Sec. 4.1, 3)
+  render_grad(...)   dL/d(coefficients) of render for a given dL/d(rgb):
+                     the back-propagation of the fine-tuning stage     (Sec. 4.3, Eq. 13)
 """
 
 from __future__ import annotations
@@ -74,6 +76,8 @@ def lib():
         L.oracle_tree_free.argtypes = [C.c_void_p]
         L.oracle_render.argtypes = [C.c_void_p, C.POINTER(Scene), C.POINTER(Rays),
                                     C.POINTER(Out), C.c_int]
+        L.oracle_render_grad.argtypes = [C.c_void_p, C.POINTER(Scene), C.POINTER(Rays),
+                                         C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -130,7 +134,48 @@ def render(tree, coeffs, *, n1=31, n2=5, sh_degree=2, period=60.0, aabb_min=(0, 
     of ray (pixel) indices.  Returns a dict with rgb [n,3], T [n], flags [n]
     and, when visit_cap > 0, visit_log [n, cap] and visit_count [n].
     """
+    sc, r, keep, n = _setup(coeffs, n1, n2, sh_degree, period, aabb_min, aabb_size, bg, stop_T,
+                            camera, t, rays_o, rays_d, t_per_ray, sel)
     L = lib()
+    res = {"rgb": np.zeros((n, 3), np.float64), "T": np.zeros(n, np.float64),
+           "flags": np.zeros(n, np.uint8)}
+    o = Out(_ptr(res["rgb"]), _ptr(res["T"]), None, 0, None, None, None, _ptr(res["flags"]))
+    if visit_cap:
+        res["visit_log"] = np.full((n, visit_cap), 0xFFFFFFFF, np.uint32)
+        res["visit_count"] = np.zeros(n, np.uint32)
+        o.visit_log, o.visit_cap = _ptr(res["visit_log"]), visit_cap
+        o.visit_count = _ptr(res["visit_count"])
+        if want_delta:
+            res["visit_delta"] = np.zeros((n, visit_cap), np.float64)
+            o.visit_delta = _ptr(res["visit_delta"])
+        if want_weight:
+            res["visit_weight"] = np.zeros((n, visit_cap), np.float64)
+            o.visit_weight = _ptr(res["visit_weight"])
+    if threads is None:
+        threads = os.cpu_count() or 1
+    st = L.oracle_render(tree.h, C.byref(sc), C.byref(r), C.byref(o), int(threads))
+    if st != 0:
+        raise RuntimeError(f"oracle_render failed with status {st}")
+    return res
+
+
+def render_grad(tree, coeffs, dL_drgb, *, n1=31, n2=5, sh_degree=2, period=60.0,
+                aabb_min=(0, 0, 0), aabb_size=1.0, bg=(1.0, 1.0, 1.0), stop_T=1e-4, camera=None,
+                t=0.0, rays_o=None, rays_d=None, t_per_ray=None, sel=None):
+    """Sec. 4.3: dL/dk [n_leaves, ncoef] (FP64, canonical order) for dL/drgb [n, 3]."""
+    sc, r, keep, n = _setup(coeffs, n1, n2, sh_degree, period, aabb_min, aabb_size, bg, stop_T,
+                            camera, t, rays_o, rays_d, t_per_ray, sel)
+    g = np.ascontiguousarray(dL_drgb, np.float64).reshape(n, 3)
+    coeffs = keep[0]
+    grad = np.zeros(coeffs.shape, np.float64)
+    st = lib().oracle_render_grad(tree.h, C.byref(sc), C.byref(r), _ptr(g), _ptr(grad))
+    if st != 0:
+        raise RuntimeError(f"oracle_render_grad failed with status {st}")
+    return grad
+
+
+def _setup(coeffs, n1, n2, sh_degree, period, aabb_min, aabb_size, bg, stop_T, camera, t,
+           rays_o, rays_d, t_per_ray, sel):
     coeffs = np.ascontiguousarray(coeffs, np.float32)
     sc = Scene(n1, n2, sh_degree, float(period), _ptr(coeffs) if coeffs.size else None,
                (C.c_double * 3)(*aabb_min), float(aabb_size), (C.c_double * 3)(*bg),
@@ -165,23 +210,4 @@ def render(tree, coeffs, *, n1=31, n2=5, sh_degree=2, period=60.0, aabb_min=(0, 
         n = s.shape[0]
     else:
         n = n_all
-    res = {"rgb": np.zeros((n, 3), np.float64), "T": np.zeros(n, np.float64),
-           "flags": np.zeros(n, np.uint8)}
-    o = Out(_ptr(res["rgb"]), _ptr(res["T"]), None, 0, None, None, None, _ptr(res["flags"]))
-    if visit_cap:
-        res["visit_log"] = np.full((n, visit_cap), 0xFFFFFFFF, np.uint32)
-        res["visit_count"] = np.zeros(n, np.uint32)
-        o.visit_log, o.visit_cap = _ptr(res["visit_log"]), visit_cap
-        o.visit_count = _ptr(res["visit_count"])
-        if want_delta:
-            res["visit_delta"] = np.zeros((n, visit_cap), np.float64)
-            o.visit_delta = _ptr(res["visit_delta"])
-        if want_weight:
-            res["visit_weight"] = np.zeros((n, visit_cap), np.float64)
-            o.visit_weight = _ptr(res["visit_weight"])
-    if threads is None:
-        threads = os.cpu_count() or 1
-    st = L.oracle_render(tree.h, C.byref(sc), C.byref(r), C.byref(o), int(threads))
-    if st != 0:
-        raise RuntimeError(f"oracle_render failed with status {st}")
-    return res
+    return sc, r, keep, n

@@ -461,3 +461,115 @@ int oracle_render(const void *tree, const oracle_scene *sc, const oracle_rays *r
         if (jobs[i].status != ORC_OK) st = jobs[i].status;
     return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of the render (Sec. 4.3: fine-tuning by back-propagation through
+ * the IDFT, Eq. 13).  For loss L with dL/dC given per ray and channel, this
+ * accumulates dL/dk into grad [n_leaves][ncoef] (canonical order, upload
+ * ids).  The visited segment list (including the early stop) is held fixed,
+ * i.e. it is treated as part of the function.  Per ray, with w_j = T_j a_j:
+ *   dC/dc_j = w_j,  dC/dsigma_j = delta_j (T_{j+1} c_j - S_j),
+ *   S_j = sum_{k>j} w_k c_k + T_end bg   (accumulated back to front),
+ *   dc/du = c (1 - c), du/dz_{c,k} = Y_k, dz/dk_{c,k,i} = IDFT_i(t),
+ *   dsigma/dk_sigma_i = IDFT_i(t) where sigma_raw > 0, else 0.
+ * Single-threaded and O(segments) memory per ray: small cases only. */
+int oracle_render_grad(const void *tree, const oracle_scene *sc, const oracle_rays *rays,
+                       const double *dL_drgb, double *grad)
+{
+    const otree *tr = (const otree *)tree;
+    if (!tr || !sc || !rays || !dL_drgb || !grad) return ORC_ERR_ARG;
+    if (sc->n1 < 1 || sc->n1 > 64 || sc->n2 < 1 || sc->n2 > 64 || sc->sh_degree < 0 ||
+        sc->sh_degree > 2 || sc->period_T <= 0.0 || sc->aabb_size <= 0.0)
+        return ORC_ERR_ARG;
+    int64_t n_all = rays->mode == 0 ? (int64_t)rays->width * rays->height : rays->n;
+    int64_t n_out = rays->sel ? rays->n_sel : n_all;
+    const int n1 = sc->n1, n2 = sc->n2, nsh = (sc->sh_degree + 1) * (sc->sh_degree + 1);
+    const int ncoef = n1 + 3 * nsh * n2;
+    segbuf buf = {0};
+    size_t cap = 0;
+    double *col = NULL, *wgt = NULL, *Tb = NULL, *sraw = NULL, *del = NULL;
+    int status = ORC_OK;
+    for (int64_t j = 0; j < n_out && status == ORC_OK; ++j) {
+        int64_t idx = rays->sel ? rays->sel[j] : j;
+        double o[3], d[3], t_frame = rays->t;
+        if (rays->mode == 0) {
+            camera_ray(rays, idx, o, d);
+        } else {
+            for (int k = 0; k < 3; ++k) { o[k] = rays->o[3 * idx + k]; d[k] = rays->d[3 * idx + k]; }
+            if (rays->t_per_ray) t_frame = rays->t_per_ray[idx];
+        }
+        double dl = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        for (int k = 0; k < 3; ++k) d[k] /= dl;
+        buf.n = 0;
+        buf.near_face = 0;
+        if (tr->n_leaves > 0) {
+            walk_ctx w = {tr, o, d, sc->aabb_size, sc->aabb_min};
+            collect(&w, 0, 0, 0, 0, 0, &buf);
+        }
+        if (buf.oom) { status = ORC_ERR_OOM; break; }
+        qsort(buf.s, buf.n, sizeof(seg), seg_cmp);
+        if (buf.n + 1 > cap) {
+            cap = buf.n + 1;
+            col = (double *)realloc(col, 3 * cap * sizeof(double));
+            wgt = (double *)realloc(wgt, cap * sizeof(double));
+            Tb = (double *)realloc(Tb, (cap + 1) * sizeof(double));
+            sraw = (double *)realloc(sraw, cap * sizeof(double));
+            del = (double *)realloc(del, cap * sizeof(double));
+            if (!col || !wgt || !Tb || !sraw || !del) { status = ORC_ERR_OOM; break; }
+        }
+        double b[64], Y[9];
+        oracle_basis(n1 > n2 ? n1 : n2, t_frame, sc->period_T, b);
+        oracle_sh(sc->sh_degree, d, Y);
+        /* forward, keeping every segment's values */
+        double T = 1.0;
+        size_t used = 0;
+        for (size_t s = 0; s < buf.n; ++s) {
+            const float *k = sc->coeffs + (size_t)buf.s[s].leaf * ncoef;
+            double delta = buf.s[s].t_out - buf.s[s].t_in, sr = 0.0;
+            for (int i = 0; i < n1; ++i) sr += (double)k[i] * b[i];
+            double sigma = sr > 0.0 ? sr : 0.0;
+            for (int c = 0; c < 3; ++c) {
+                double acc = 0.0;
+                for (int q = 0; q < nsh; ++q) {
+                    double zq = 0.0;
+                    for (int i = 0; i < n2; ++i) zq += (double)k[n1 + (c * nsh + q) * n2 + i] * b[i];
+                    acc += zq * Y[q];
+                }
+                col[3 * s + c] = 1.0 / (1.0 + exp(-acc));
+            }
+            double alpha = 1.0 - exp(-sigma * delta);
+            Tb[s] = T;
+            wgt[s] = T * alpha;
+            sraw[s] = sr;
+            del[s] = delta;
+            T *= 1.0 - alpha;
+            used = s + 1;
+            if (T < sc->stop_T) break;
+        }
+        Tb[used] = T;
+        /* backward: S_j accumulated from the back */
+        const double *g = dL_drgb + 3 * j;
+        double S[3] = {T * sc->bg[0], T * sc->bg[1], T * sc->bg[2]};
+        for (size_t s = used; s-- > 0;) {
+            double *gk = grad + (size_t)buf.s[s].leaf * ncoef;
+            double dsig = 0.0;
+            for (int c = 0; c < 3; ++c) dsig += g[c] * del[s] * (Tb[s + 1] * col[3 * s + c] - S[c]);
+            if (sraw[s] > 0.0)
+                for (int i = 0; i < n1; ++i) gk[i] += dsig * b[i];
+            for (int c = 0; c < 3; ++c) {
+                double cc = col[3 * s + c];
+                double du = g[c] * wgt[s] * cc * (1.0 - cc);
+                for (int q = 0; q < nsh; ++q)
+                    for (int i = 0; i < n2; ++i) gk[n1 + (c * nsh + q) * n2 + i] += du * Y[q] * b[i];
+            }
+            for (int c = 0; c < 3; ++c) S[c] += wgt[s] * col[3 * s + c];
+        }
+    }
+    free(buf.s);
+    free(col);
+    free(wgt);
+    free(Tb);
+    free(sraw);
+    free(del);
+    return status;
+}

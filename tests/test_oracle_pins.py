@@ -414,3 +414,47 @@ def test_tree_validation():
         _tree([2], [(4, 0, 0)], 2)  # out of range
     with pytest.raises(ValueError):
         _tree([3], [(0, 0, 0)], 2)  # deeper than max depth
+
+
+# --------------------------------------------------------------------------
+# Sec. 4.3 gradient, pinned by central differences of the forward render
+
+
+@pytest.mark.parametrize("stop_T", [0.0, 1e-4])
+def test_gradient_matches_finite_differences(stop_T):
+    tree = synth.shell_tree()
+    ot = oracle.OracleTree(tree.leaf_depth, tree.leaf_xyz, tree.max_depth)
+    cam = synth.shell_camera(20, 16)
+    t = 22.2
+    bg = (0.3, 0.6, 0.9)
+    rng = np.random.default_rng(9)
+    g = rng.normal(size=(cam.width * cam.height, 3))
+    base = oracle.render(ot, tree.coeffs, camera=cam, t=t, stop_T=stop_T, bg=bg)
+    G = oracle.render_grad(ot, tree.coeffs, g, camera=cam, t=t, stop_T=stop_T, bg=bg)
+    touched = np.nonzero(np.abs(G).sum(1))[0]
+    assert touched.size > 50
+    b = oracle.basis(N1, t, PERIOD)
+    sraw = tree.coeffs[:, :N1].astype(np.float64) @ b
+    picks = []
+    for leaf in rng.choice(touched, 40, replace=False):
+        for j in rng.choice(NCOEF, 5, replace=False):
+            if j < N1 and abs(sraw[leaf]) < 0.05:
+                continue  # the ReLU kink of the density
+            picks.append((leaf, j))
+    checked = 0
+    for leaf, j in picks:
+        k0 = tree.coeffs[leaf, j]
+        eps = 1e-3 * max(1.0, abs(float(k0)))
+        kp, km = np.float32(k0 + eps), np.float32(k0 - eps)
+        co = tree.coeffs.copy()
+        co[leaf, j] = kp
+        rp = oracle.render(ot, co, camera=cam, t=t, stop_T=stop_T, bg=bg)
+        co[leaf, j] = km
+        rm = oracle.render(ot, co, camera=cam, t=t, stop_T=stop_T, bg=bg)
+        if stop_T > 0 and not (np.array_equal(rp["T"] < stop_T, base["T"] < stop_T)
+                               and np.array_equal(rm["T"] < stop_T, base["T"] < stop_T)):
+            continue  # the perturbation moved an early stop: not differentiable there
+        fd = np.sum(g * (rp["rgb"] - rm["rgb"])) / (float(kp) - float(km))
+        assert abs(G[leaf, j] - fd) <= 1e-3 * abs(fd) + 1e-7, (leaf, j, G[leaf, j], fd)
+        checked += 1
+    assert checked > 100
