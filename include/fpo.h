@@ -179,11 +179,17 @@ int fpo_upload_tree(fpo_ctx *ctx, const fpo_tree_desc *tree);
 int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
                float *out_rgb, void *cuda_stream);
 
-/* Adjoint of fpo_render (the back-propagation of Sec. 4.3, Eq. 13): given
- * dL/d(rgb) (device [rays][3]) accumulates dL/d(coefficients) into
- * dL_dcoeffs, a device array [n_leaves][n1 + 27*n2] in canonical order and
- * upload order.  out_rgb is the forward output for the same rays.
- * Not implemented in this build: returns FPO_ERR_UNSUPPORTED. */
+/* Adjoint of fpo_render (the back-propagation of Sec. 4.3, used to fine-tune
+ * the leaf coefficients against the loss of Eq. 13): given dL/d(rgb) (device
+ * [rays][3]) it accumulates dL/d(coefficients) into dL_dcoeffs, a device
+ * array [n_leaves][n1 + 27*n2] in canonical order and upload order (the
+ * caller zeroes it).  out_rgb is the forward colour of the same rays and
+ * options.  Each ray is replayed with the per-visit IDFT, so the segments and
+ * the early stop are those of a FUSED-mode forward (treated as fixed: the
+ * truncation is part of the function); sigma = max(0, sigma_raw) passes no
+ * gradient where sigma_raw <= 0.  Needs FP32 storage and (n1, n2) in
+ * {(31,5), (11,5), (21,5), (31,11)}; otherwise FPO_ERR_UNSUPPORTED.
+ * Errors: INVALID_ARG, NO_TREE, UNSUPPORTED, CUDA. */
 int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
                         const float *out_rgb, const float *dL_drgb, float *dL_dcoeffs,
                         void *cuda_stream);
@@ -207,6 +213,13 @@ int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts
  * lock); make that first call before any stream capture begins. */
 int fpo_render_noalloc(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
                        float *out_rgb, void *cuda_stream);
+
+/* Replaces the coefficients of the uploaded tree with `coeffs`, a device
+ * array [n_leaves][n1 + 27*n2] in canonical order and upload order (the
+ * in-place update of the fine-tuning stage, Sec. 4.3).  Enqueued on the
+ * stream.  Needs FP32 storage (else FPO_ERR_UNSUPPORTED).
+ * Errors: INVALID_ARG, NO_TREE, UNSUPPORTED, CUDA. */
+int fpo_set_coeffs(fpo_ctx *ctx, const float *coeffs, void *cuda_stream);
 
 /* Waits for cuda_stream and returns (then clears) the device status word:
  * FPO_OK, FPO_ERR_TRAVERSAL_LIMIT, FPO_ERR_VISIT_OVERFLOW or

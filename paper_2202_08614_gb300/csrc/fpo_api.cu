@@ -307,6 +307,74 @@ static int check_rays(const fpo_ctx *ctx, const fpo_rays *r, uint64_t *n_rays)
     return FPO_OK;
 }
 
+// Kernel parameters of one render (or adjoint) call from the context, rays
+// and options.
+static TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
+                                      float *out_rgb, uint64_t n_rays)
+{
+    const uint32_t fl = opts->flags;
+    TraverseParams p{};
+    p.fr.mode = rays->mode;
+    p.fr.width = rays->width;
+    p.fr.height = rays->height;
+    p.fr.n_rays = (uint32_t)n_rays;
+    for (int k = 0; k < 3; ++k) {
+        p.fr.eye[k] = rays->eye[k];
+        p.fr.target[k] = rays->target[k];
+        p.fr.up[k] = rays->up[k];
+    }
+    p.fr.fov_y_deg = rays->fov_y_deg;
+    p.fr.t = rays->t;
+    p.fr.period_T = ctx->cfg.period_T;
+    p.fr.ro = rays->o;
+    p.fr.rd = rays->d;
+    p.fr.rt = rays->t_per_ray;
+    p.nodes = ctx->d_nodes;
+    p.root_kind = ctx->root_kind;
+    p.depth = ctx->depth;
+    p.n_smem_nodes = ctx->n_smem_nodes;
+    p.grid_scale = (float)((double)(1u << ctx->depth) / ctx->aabb_size);
+    for (int k = 0; k < 3; ++k) p.amin[k] = (float)ctx->aabb_min[k];
+    p.table = reinterpret_cast<const float4 *>(ctx->d_table);
+    p.sig = reinterpret_cast<const float4 *>(ctx->d_sig);
+    p.zc = static_cast<const float *>(ctx->d_z);
+    p.n1 = ctx->cfg.n1;
+    p.n2 = ctx->cfg.n2;
+    p.sig_stride4 = sig_stride(ctx->cfg.n1) / 4;
+    p.z_stride = z_stride(ctx->cfg.n2);
+    for (int k = 0; k < 3; ++k) p.bg[k] = opts->bg[k];
+    p.stop_T = opts->stop_T;
+    p.flags = fl;
+    p.out_rgb = out_rgb;
+    p.out_T = opts->out_T;
+    p.visit_log = opts->visit_log;
+    p.visit_cap = opts->visit_cap;
+    p.visit_count = opts->visit_count;
+    p.leaf_mark = opts->leaf_mark;
+    p.perm = ctx->d_perm;
+    p.status = ctx->d_status;
+    if (rays->mode == FPO_RAYS_CAMERA) {
+        p.tiles_x = (rays->width + 7) / 8;
+        const uint32_t tiles_y = (rays->height + 3) / 4;
+        p.super_tile = FPO_SUPER_TILE;
+        if (p.super_tile) {
+            const uint32_t S = p.super_tile;
+            p.n_tiles = ((p.tiles_x + S - 1) / S) * ((tiles_y + S - 1) / S) * S * S;
+        } else {
+            p.n_tiles = p.tiles_x * tiles_y;
+        }
+    } else {
+        p.tiles_x = 0;
+        p.n_tiles = (uint32_t)((n_rays + 31) / 32);
+    }
+    p.max_steps = 3u * (1u << ctx->depth) + 16u;
+    p.block_threads = ctx->cfg.traverse_threads ? ctx->cfg.traverse_threads : DEFAULT_TRAVERSE_THREADS;
+    p.refill_min = ctx->cfg.refill_min ? (uint32_t)ctx->cfg.refill_min : DEFAULT_REFILL_MIN;
+    p.inner_steps = ctx->cfg.inner_steps ? (uint32_t)ctx->cfg.inner_steps : DEFAULT_INNER_STEPS;
+    p.stats = reinterpret_cast<unsigned long long *>(opts->stats);
+    return p;
+}
+
 int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, float *out_rgb,
                void *cuda_stream)
 {
@@ -375,65 +443,7 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
     }
     if ((e = rec(1)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
 
-    TraverseParams p{};
-    p.fr.mode = rays->mode;
-    p.fr.width = rays->width;
-    p.fr.height = rays->height;
-    p.fr.n_rays = (uint32_t)n_rays;
-    for (int k = 0; k < 3; ++k) {
-        p.fr.eye[k] = rays->eye[k];
-        p.fr.target[k] = rays->target[k];
-        p.fr.up[k] = rays->up[k];
-    }
-    p.fr.fov_y_deg = rays->fov_y_deg;
-    p.fr.t = rays->t;
-    p.fr.period_T = ctx->cfg.period_T;
-    p.fr.ro = rays->o;
-    p.fr.rd = rays->d;
-    p.fr.rt = rays->t_per_ray;
-    p.nodes = ctx->d_nodes;
-    p.root_kind = ctx->root_kind;
-    p.depth = ctx->depth;
-    p.n_smem_nodes = ctx->n_smem_nodes;
-    p.grid_scale = (float)((double)(1u << ctx->depth) / ctx->aabb_size);
-    for (int k = 0; k < 3; ++k) p.amin[k] = (float)ctx->aabb_min[k];
-    p.table = reinterpret_cast<const float4 *>(ctx->d_table);
-    p.sig = reinterpret_cast<const float4 *>(ctx->d_sig);
-    p.zc = static_cast<const float *>(ctx->d_z);
-    p.n1 = ctx->cfg.n1;
-    p.n2 = ctx->cfg.n2;
-    p.sig_stride4 = sig_stride(ctx->cfg.n1) / 4;
-    p.z_stride = z_stride(ctx->cfg.n2);
-    for (int k = 0; k < 3; ++k) p.bg[k] = opts->bg[k];
-    p.stop_T = opts->stop_T;
-    p.flags = fl;
-    p.out_rgb = out_rgb;
-    p.out_T = opts->out_T;
-    p.visit_log = opts->visit_log;
-    p.visit_cap = opts->visit_cap;
-    p.visit_count = opts->visit_count;
-    p.leaf_mark = opts->leaf_mark;
-    p.perm = ctx->d_perm;
-    p.status = ctx->d_status;
-    if (rays->mode == FPO_RAYS_CAMERA) {
-        p.tiles_x = (rays->width + 7) / 8;
-        const uint32_t tiles_y = (rays->height + 3) / 4;
-        p.super_tile = FPO_SUPER_TILE;
-        if (p.super_tile) {
-            const uint32_t S = p.super_tile;
-            p.n_tiles = ((p.tiles_x + S - 1) / S) * ((tiles_y + S - 1) / S) * S * S;
-        } else {
-            p.n_tiles = p.tiles_x * tiles_y;
-        }
-    } else {
-        p.tiles_x = 0;
-        p.n_tiles = (uint32_t)((n_rays + 31) / 32);
-    }
-    p.max_steps = 3u * (1u << ctx->depth) + 16u;
-    p.block_threads = ctx->cfg.traverse_threads ? ctx->cfg.traverse_threads : DEFAULT_TRAVERSE_THREADS;
-    p.refill_min = ctx->cfg.refill_min ? (uint32_t)ctx->cfg.refill_min : DEFAULT_REFILL_MIN;
-    p.inner_steps = ctx->cfg.inner_steps ? (uint32_t)ctx->cfg.inner_steps : DEFAULT_INNER_STEPS;
-    p.stats = reinterpret_cast<unsigned long long *>(opts->stats);
+    TraverseParams p = traverse_params(ctx, rays, opts, out_rgb, n_rays);
     const bool dbg = (fl & (FPO_FLAG_RECORD_VISITS | FPO_FLAG_OUT_T | FPO_FLAG_MARK_LEAVES |
                             FPO_FLAG_STATS)) != 0;
     int ce = launch_traverse(p, mat, dbg, ctx->sm_count, s);
@@ -446,9 +456,48 @@ int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts
                         const float *out_rgb, const float *dL_drgb, float *dL_dcoeffs,
                         void *cuda_stream)
 {
-    (void)ctx; (void)rays; (void)opts; (void)out_rgb; (void)dL_drgb; (void)dL_dcoeffs;
-    (void)cuda_stream;
-    return fail(FPO_ERR_UNSUPPORTED, "fpo_render_backward is not implemented in this build");
+    if (!ctx || !rays || !opts) return fail(FPO_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->has_tree) return fail(FPO_ERR_NO_TREE, "backward before fpo_upload_tree");
+    uint64_t n_rays = 0;
+    int st = check_rays(ctx, rays, &n_rays);
+    if (st != FPO_OK) return st;
+    if (ctx->cfg.storage != FPO_STORAGE_F32)
+        return fail(FPO_ERR_UNSUPPORTED, "gradients are taken with respect to FP32 records only");
+    if (!fused_supported(ctx->cfg.n1, ctx->cfg.n2))
+        return fail(FPO_ERR_UNSUPPORTED, "the adjoint supports (n1, n2) in {(31,5), (11,5), (21,5), (31,11)}");
+    if (n_rays > 0 && (!out_rgb || !dL_drgb)) return fail(FPO_ERR_INVALID_ARG, "out_rgb and dL_drgb must be non-NULL");
+    if (ctx->n_leaves > 0 && !dL_dcoeffs) return fail(FPO_ERR_INVALID_ARG, "dL_dcoeffs is NULL");
+    if (!(opts->stop_T >= 0.0f)) return fail(FPO_ERR_INVALID_ARG, "stop_T must be >= 0");
+    if (n_rays == 0 || ctx->n_leaves == 0) return FPO_OK;
+    DeviceGuard g(ctx->cfg.device);
+    if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
+    fpo_frame_opts o = *opts;
+    o.flags = 0;  // debug outputs belong to the forward
+    BackwardParams q{};
+    q.tp = traverse_params(ctx, rays, &o, nullptr, n_rays);
+    q.out_rgb = out_rgb;
+    q.dL_drgb = dL_drgb;
+    q.dL_dcoeffs = dL_dcoeffs;
+    const int ce = launch_backward(q, ctx->sm_count, cuda_stream);
+    if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "backward launch");
+    return FPO_OK;
+}
+
+int fpo_set_coeffs(fpo_ctx *ctx, const float *coeffs, void *cuda_stream)
+{
+    if (!ctx) return fail(FPO_ERR_INVALID_ARG, "ctx is NULL");
+    if (!ctx->has_tree) return fail(FPO_ERR_NO_TREE, "set_coeffs before fpo_upload_tree");
+    if (ctx->cfg.storage != FPO_STORAGE_F32)
+        return fail(FPO_ERR_UNSUPPORTED, "in-place coefficient updates need FP32 storage");
+    if (ctx->n_leaves == 0) return FPO_OK;
+    if (!coeffs) return fail(FPO_ERR_INVALID_ARG, "coeffs is NULL");
+    DeviceGuard g(ctx->cfg.device);
+    if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
+    const int ce = launch_set_coeffs(coeffs, ctx->d_perm, static_cast<float *>(ctx->d_sig),
+                                     static_cast<float *>(ctx->d_z), ctx->n_leaves, ctx->cfg.n1,
+                                     ctx->cfg.n2, ctx->sm_count, cuda_stream);
+    if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "set_coeffs launch");
+    return FPO_OK;
 }
 
 int fpo_status_sync(fpo_ctx *ctx, void *cuda_stream)

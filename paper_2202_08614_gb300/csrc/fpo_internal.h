@@ -160,9 +160,19 @@ CtxView ctx_view(const fpo_ctx *ctx);
 // Records `msg` as the calling thread's last error; returns `code`.
 int set_last_error(int code, const char *msg);
 
+struct BackwardParams {
+    TraverseParams tp;          // rays, tree and options as for the fused forward
+    const float *out_rgb;       // forward colour [rays][3]
+    const float *dL_drgb;       // [rays][3]
+    float *dL_dcoeffs;          // [n_leaves][n1 + 27 n2], canonical, upload order (accumulated)
+};
+
 // Launchers (return cudaError_t as int).
 int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream);
 int materialise_stages(int storage, int n1, int n2);
+int launch_backward(const BackwardParams &q, int sm_count, void *stream);
+int launch_set_coeffs(const float *src, const uint32_t *perm, float *sig, float *zc, uint32_t n_leaves,
+                      int n1, int n2, int sm_count, void *stream);
 int launch_traverse(const TraverseParams &p, bool materialised, bool debug, int sm_count,
                     void *stream);
 int traverse_smem_bytes(uint32_t n_smem_nodes, bool per_ray_basis, int threads);

@@ -303,9 +303,8 @@ __device__ __forceinline__ void write_result(const TraverseParams &p, const RayS
 // Sets up ray `ray` (camera pixel (px, py) or explicit ray): generation,
 // SH basis, clip against the grid cube.  Returns false when the ray misses
 // the tree (its background result is written at once).
-template <bool DBG>
-__device__ bool init_ray(const TraverseParams &p, const FrameShared &fs, bool prt, float *s_bray,
-                         int stride, uint32_t *s_stack, RayState &R, uint32_t ray, int px, int py)
+__device__ bool init_ray_geom(const TraverseParams &p, const FrameShared &fs, bool prt, float *s_bray,
+                              int stride, uint32_t *s_stack, RayState &R, uint32_t ray, int px, int py)
 {
     float ox, oy, oz, dx, dy, dz;
     if (p.fr.mode == FPO_RAYS_CAMERA) {
@@ -368,10 +367,7 @@ __device__ bool init_ray(const TraverseParams &p, const FrameShared &fs, bool pr
             if (R.go[a] < 0.0f || R.go[a] > (float)G) hit = false;
         }
     }
-    if (!(hit && t0 < t1)) {
-        write_result(p, R, DBG);
-        return false;
-    }
+    if (!(hit && t0 < t1)) return false;
     // Distances are measured from the entry point from here on.
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -382,6 +378,17 @@ __device__ bool init_ray(const TraverseParams &p, const FrameShared &fs, bool pr
     R.zmask = (R.gd[0] == 0.0f ? 1 : 0) | (R.gd[1] == 0.0f ? 2 : 0) | (R.gd[2] == 0.0f ? 4 : 0);
     s_stack[0] = 0;
     return true;
+}
+
+// As init_ray_geom; a ray that misses the tree gets its background result.
+template <bool DBG>
+__device__ __forceinline__ bool init_ray(const TraverseParams &p, const FrameShared &fs, bool prt,
+                                         float *s_bray, int stride, uint32_t *s_stack, RayState &R,
+                                         uint32_t ray, int px, int py)
+{
+    if (init_ray_geom(p, fs, prt, s_bray, stride, s_stack, R, ray, px, py)) return true;
+    write_result(p, R, DBG);
+    return false;
 }
 
 // The cube holding cell R.P: its kind (ROOT_EMPTY / ROOT_LEAF), leaf index and
@@ -658,6 +665,70 @@ __device__ void trace_ray(const TraverseParams &p, const float *bsrc, int bstrid
 
 }  // namespace
 
+namespace {
+
+// CTA prologue: stage the top n_smem_nodes nodes in shared memory; the frame
+// basis (Eq. 8 at the shared t, FP64 then FP32) and the camera frame (FP64).
+__device__ void frame_prologue(const TraverseParams &p, uint32_t *s_nodes, FrameShared &fs)
+{
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.nodes);
+    uint4 *dst = reinterpret_cast<uint4 *>(s_nodes);
+    for (uint32_t i = threadIdx.x; i < p.n_smem_nodes * 2; i += blockDim.x) dst[i] = __ldg(src + i);
+    const int nb = p.n1 > p.n2 ? p.n1 : p.n2;
+    if (threadIdx.x < MAX_BASIS)
+        fs.b[threadIdx.x] = (int)threadIdx.x < nb ? basis_fp64(threadIdx.x, p.fr.t, p.fr.period_T) : 0.0f;
+    if (threadIdx.x == MAX_BASIS && p.fr.mode == FPO_RAYS_CAMERA) {
+        double f[3], r[3], u[3];
+        for (int k = 0; k < 3; ++k) f[k] = p.fr.target[k] - p.fr.eye[k];
+        double fl = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        for (int k = 0; k < 3; ++k) f[k] /= fl;
+        r[0] = f[1] * p.fr.up[2] - f[2] * p.fr.up[1];
+        r[1] = f[2] * p.fr.up[0] - f[0] * p.fr.up[2];
+        r[2] = f[0] * p.fr.up[1] - f[1] * p.fr.up[0];
+        double rl = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        for (int k = 0; k < 3; ++k) r[k] /= rl;
+        u[0] = r[1] * f[2] - r[2] * f[1];
+        u[1] = r[2] * f[0] - r[0] * f[2];
+        u[2] = r[0] * f[1] - r[1] * f[0];
+        const double th = tan(0.5 * p.fr.fov_y_deg * 3.14159265358979323846 / 180.0);
+        for (int k = 0; k < 3; ++k) {
+            fs.f[k] = (float)f[k];
+            fs.r[k] = (float)r[k];
+            fs.u[k] = (float)u[k];
+            fs.eye[k] = (float)p.fr.eye[k];
+        }
+        fs.sx_scale = (float)(th * (double)p.fr.width / (double)p.fr.height);
+        fs.sy_scale = (float)th;
+    }
+}
+
+// Ray k (0..31) of a tile: a camera pixel of an 8x4 block, or an explicit ray.
+__device__ __forceinline__ bool tile_ray(const TraverseParams &p, uint32_t tile, uint32_t k, uint32_t &ray,
+                                         int &px, int &py)
+{
+    if (p.fr.mode == FPO_RAYS_CAMERA) {
+        uint32_t tx, ty;
+        if (p.super_tile) {  // square groups of super_tile^2 tiles, row-major
+            const uint32_t S = p.super_tile, per = S * S;
+            const uint32_t g = tile / per, w = tile % per, gx = (p.tiles_x + S - 1) / S;
+            tx = (g % gx) * S + w % S;
+            ty = (g / gx) * S + w / S;
+            if (tx >= p.tiles_x) return false;
+        } else {
+            tx = tile % p.tiles_x;
+            ty = tile / p.tiles_x;
+        }
+        px = (int)(tx * 8 + (k & 7));
+        py = (int)(ty * 4 + (k >> 3));
+        ray = (uint32_t)py * p.fr.width + (uint32_t)px;
+        return px < (int)p.fr.width && py < (int)p.fr.height;
+    }
+    ray = tile * 32 + k;
+    return ray < p.fr.n_rays;
+}
+
+}  // namespace
+
 // Persistent kernel: a grid of (SM count x resident CTAs) whose warps pull
 // warp-sized tiles (8x4 pixels, or 32 consecutive explicit rays) from one
 // atomic counter.  Warp-level ray compaction: every lane holds its own ray;
@@ -686,37 +757,7 @@ __global__ void __maxnreg__(MAT ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED)
     float *s_bray = reinterpret_cast<float *>(s_stack + STACK_LEVELS * stride);
     const bool prt = !MAT && p.fr.mode == FPO_RAYS_EXPLICIT && p.fr.rt != nullptr;
 
-    {
-        const uint4 *src = reinterpret_cast<const uint4 *>(p.nodes);
-        uint4 *dst = reinterpret_cast<uint4 *>(s_nodes);
-        for (uint32_t i = threadIdx.x; i < p.n_smem_nodes * 2; i += blockDim.x) dst[i] = __ldg(src + i);
-        const int nb = p.n1 > p.n2 ? p.n1 : p.n2;
-        if (threadIdx.x < MAX_BASIS)
-            fs.b[threadIdx.x] = (int)threadIdx.x < nb ? basis_fp64(threadIdx.x, p.fr.t, p.fr.period_T) : 0.0f;
-        if (threadIdx.x == MAX_BASIS && p.fr.mode == FPO_RAYS_CAMERA) {
-            double f[3], r[3], u[3];
-            for (int k = 0; k < 3; ++k) f[k] = p.fr.target[k] - p.fr.eye[k];
-            double fl = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
-            for (int k = 0; k < 3; ++k) f[k] /= fl;
-            r[0] = f[1] * p.fr.up[2] - f[2] * p.fr.up[1];
-            r[1] = f[2] * p.fr.up[0] - f[0] * p.fr.up[2];
-            r[2] = f[0] * p.fr.up[1] - f[1] * p.fr.up[0];
-            double rl = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-            for (int k = 0; k < 3; ++k) r[k] /= rl;
-            u[0] = r[1] * f[2] - r[2] * f[1];
-            u[1] = r[2] * f[0] - r[0] * f[2];
-            u[2] = r[0] * f[1] - r[1] * f[0];
-            const double th = tan(0.5 * p.fr.fov_y_deg * 3.14159265358979323846 / 180.0);
-            for (int k = 0; k < 3; ++k) {
-                fs.f[k] = (float)f[k];
-                fs.r[k] = (float)r[k];
-                fs.u[k] = (float)u[k];
-                fs.eye[k] = (float)p.fr.eye[k];
-            }
-            fs.sx_scale = (float)(th * (double)p.fr.width / (double)p.fr.height);
-            fs.sy_scale = (float)th;
-        }
-    }
+    frame_prologue(p, s_nodes, fs);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -729,28 +770,6 @@ __global__ void __maxnreg__(MAT ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED)
         uint32_t tl = 0;
         if (lane == 0) tl = atomicAdd(p.status + 1, 1u);
         return __shfl_sync(0xffffffffu, tl, 0);
-    };
-    // ray k (0..31) of a tile: camera pixel (8x4 block) or explicit ray
-    auto tile_ray = [&](uint32_t tile, uint32_t k, uint32_t &ray, int &px, int &py) -> bool {
-        if (p.fr.mode == FPO_RAYS_CAMERA) {
-            uint32_t tx, ty;
-            if (p.super_tile) {  // square groups of super_tile^2 tiles, row-major
-                const uint32_t S = p.super_tile, per = S * S;
-                const uint32_t g = tile / per, w = tile % per, gx = (p.tiles_x + S - 1) / S;
-                tx = (g % gx) * S + w % S;
-                ty = (g / gx) * S + w / S;
-                if (tx >= p.tiles_x) return false;
-            } else {
-                tx = tile % p.tiles_x;
-                ty = tile / p.tiles_x;
-            }
-            px = (int)(tx * 8 + (k & 7));
-            py = (int)(ty * 4 + (k >> 3));
-            ray = (uint32_t)py * p.fr.width + (uint32_t)px;
-            return px < (int)p.fr.width && py < (int)p.fr.height;
-        }
-        ray = tile * 32 + k;
-        return ray < p.fr.n_rays;
     };
     auto finish = [&](const RayState &R) {
         write_result(p, R, DBG);
@@ -768,7 +787,7 @@ __global__ void __maxnreg__(MAT ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED)
             if (tile >= p.n_tiles) break;
             uint32_t ray;
             int px = 0, py = 0;
-            if (tile_ray(tile, (uint32_t)lane, ray, px, py)) {
+            if (tile_ray(p, tile, (uint32_t)lane, ray, px, py)) {
                 RayState R;
                 if (init_ray<DBG>(p, fs, prt, my_b, stride, my_stack, R, ray, px, py)) {
                     NodeCache nc;
@@ -801,7 +820,7 @@ __global__ void __maxnreg__(MAT ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED)
                     if (((idle >> lane) & 1u) && rank < take) {
                         uint32_t ray;
                         int px = 0, py = 0;
-                        if (tile_ray(cur_tile, cur_next + rank, ray, px, py))
+                        if (tile_ray(p, cur_tile, cur_next + rank, ray, px, py))
                             active = init_ray<DBG>(p, fs, prt, my_b, stride, my_stack, R, ray, px, py);
                     }
                     cur_next += take;
@@ -897,6 +916,223 @@ int launch_traverse(const TraverseParams &p, bool materialised, bool debug, int 
     cudaStream_t s = (cudaStream_t)stream;
     if (materialised) return launch_sched<true, 0, 0>(p, debug, sm_count, s);
     return launch_fused(p, debug, sm_count, s);
+}
+
+
+// ---------------------------------------------------------------------------
+// Adjoint of the render (Sec. 4.3: back-propagation through the IDFT).
+//
+// Each ray is replayed front to back with the fused per-visit IDFT (the same
+// stepping and arithmetic as the fused forward, so the same segments and the
+// same early stop), recomputing the transmittance instead of storing
+// samples.  With w_j = T_j alpha_j and C the forward colour (which includes
+// T_end bg), S_j = C - sum_{k<=j} w_k c_k is the colour behind segment j and
+//   dL/dsigma_j = delta_j sum_c g_c (T_{j+1} c_jc - S_jc),
+//   dL/du_jc    = g_c w_j c_jc (1 - c_jc),   u = sum_k z_ck Y_k,
+//   dL/dk_sigma_i += dL/dsigma_j [sigma_raw > 0] IDFT_i(t),
+//   dL/dk_cki     += dL/du_jc Y_k IDFT_i(t),
+// accumulated with 8-byte vector atomics into the canonical gradient row of
+// the leaf's upload id (rows of n1 + 27 n2 floats are 8-byte aligned).
+
+template <int N1, int N2>
+__device__ void backward_ray(const BackwardParams &q, const float *bsrc, int bstride,
+                             const uint32_t *__restrict__ s_nodes, uint32_t *s_stack, int stride,
+                             RayState &R, NodeCache &nc)
+{
+    constexpr int NC = N1 + 27 * N2;
+    static_assert(NC % 2 == 0, "gradient rows are written in pairs");
+    const TraverseParams &p = q.tp;
+    const int D = p.depth, G = 1 << D;
+    const float g0 = q.dL_drgb[3 * (size_t)R.ray], g1 = q.dL_drgb[3 * (size_t)R.ray + 1],
+                g2 = q.dL_drgb[3 * (size_t)R.ray + 2];
+    const float Cf0 = q.out_rgb[3 * (size_t)R.ray], Cf1 = q.out_rgb[3 * (size_t)R.ray + 1],
+                Cf2 = q.out_rgb[3 * (size_t)R.ray + 2];
+    float P0 = 0.0f, P1 = 0.0f, P2 = 0.0f;  // sum_{k<=j} w_k c_k
+    float b[N1 > N2 ? N1 : N2];
+#pragma unroll
+    for (int i = 0; i < (N1 > N2 ? N1 : N2); ++i) b[i] = bsrc[i * bstride];
+    Cube cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start, nc);
+    for (;;) {
+        int m, lo[3], csz;
+        const float tx = cube_exit(R, D, cb.lvl, m, lo, csz);
+        if (cb.kind == ROOT_LEAF && tx > R.t) {
+            const float delta = tx - R.t;
+            const float4 *sr = p.sig + (size_t)cb.leaf * p.sig_stride4;
+            float sraw = 0.0f;
+#pragma unroll
+            for (int k4 = 0; k4 < (N1 + 3) / 4; ++k4) {
+                const float4 w = __ldg(sr + k4);
+                const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (4 * k4 + j < N1) sraw = fmaf(wv[j], b[4 * k4 + j], sraw);
+            }
+            const float sigma = fmaxf(sraw, 0.0f);
+            float z[27];
+#pragma unroll
+            for (int k = 0; k < 27; ++k) z[k] = 0.0f;
+            const float4 *zr = reinterpret_cast<const float4 *>(p.zc + (size_t)cb.leaf * p.z_stride);
+#pragma unroll
+            for (int k4 = 0; k4 < (27 * N2 + 3) / 4; ++k4) {
+                const float4 w = __ldg(zr + k4);
+                const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int e = 4 * k4 + j;
+                    if (e < 27 * N2) z[e / N2] = fmaf(wv[j], b[e % N2], z[e / N2]);
+                }
+            }
+            float col[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float u = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) u = fmaf(z[9 * c + k], R.Y[k], u);
+                col[c] = sigmoidf_(u);
+            }
+            const float e = __expf(-sigma * delta);
+            const float w = R.T * (1.0f - e);
+            const float Tn = R.T * e;
+            P0 = fmaf(w, col[0], P0);
+            P1 = fmaf(w, col[1], P1);
+            P2 = fmaf(w, col[2], P2);
+            const float gs = delta * (g0 * (Tn * col[0] - (Cf0 - P0)) + g1 * (Tn * col[1] - (Cf1 - P1)) +
+                                      g2 * (Tn * col[2] - (Cf2 - P2)));
+            const float dsr = sraw > 0.0f ? gs : 0.0f;
+            const float gu[3] = {g0 * w * col[0] * (1.0f - col[0]), g1 * w * col[1] * (1.0f - col[1]),
+                                 g2 * w * col[2] * (1.0f - col[2])};
+            float2 *row = reinterpret_cast<float2 *>(q.dL_dcoeffs + (size_t)p.perm[cb.leaf] * NC);
+#pragma unroll
+            for (int e2 = 0; e2 < NC / 2; ++e2) {
+                float v[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int el = 2 * e2 + h;
+                    if (el < N1) {
+                        v[h] = dsr * b[el];
+                    } else {
+                        const int j = el - N1, c = j / (9 * N2), k = (j / N2) % 9, i = j % N2;
+                        v[h] = gu[c] * R.Y[k] * b[i];
+                    }
+                }
+                atomicAdd(row + e2, make_float2(v[0], v[1]));
+            }
+            R.T = Tn;
+            if (R.T < p.stop_T) return;
+        }
+        int Pn[3];
+        if (!next_cell(R, G, m, lo, csz, tx, Pn)) return;
+        move_to(R, D, Pn, tx);
+        if (step_cap(p, R)) return;
+        cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start, nc);
+    }
+}
+
+template <int N1, int N2>
+__global__ void __maxnreg__(128) backward_kernel(const __grid_constant__ BackwardParams q)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ FrameShared fs;
+    const TraverseParams &p = q.tp;
+    const int stride = blockDim.x;
+    uint32_t *s_nodes = smem;
+    uint32_t *s_stack = smem + p.n_smem_nodes * 8;
+    float *s_bray = reinterpret_cast<float *>(s_stack + STACK_LEVELS * stride);
+    const bool prt = p.fr.mode == FPO_RAYS_EXPLICIT && p.fr.rt != nullptr;
+    frame_prologue(p, s_nodes, fs);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    uint32_t *my_stack = s_stack + threadIdx.x;
+    float *my_b = s_bray + threadIdx.x;
+    const float *bsrc = prt ? my_b : fs.b;
+    const int bstride = prt ? stride : 1;
+    for (;;) {
+        uint32_t tile = 0;
+        if (lane == 0) tile = atomicAdd(p.status + 1, 1u);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= p.n_tiles) break;
+        uint32_t ray;
+        int px = 0, py = 0;
+        if (!tile_ray(p, tile, (uint32_t)lane, ray, px, py)) continue;
+        RayState R;
+        if (!init_ray_geom(p, fs, prt, my_b, stride, my_stack, R, ray, px, py)) continue;
+        NodeCache nc;
+        nc.node = 0xffffffffu;
+        nc.level = -1;
+        backward_ray<N1, N2>(q, bsrc, bstride, s_nodes, my_stack, stride, R, nc);
+    }
+    if (lane == 0) {
+        __threadfence();
+        const uint32_t done = atomicAdd(p.status + 2, 1u);
+        if (done == gridDim.x * (blockDim.x / 32) - 1) {
+            atomicExch(p.status + 1, 0u);
+            atomicExch(p.status + 2, 0u);
+        }
+    }
+}
+
+template <int N1, int N2>
+static int launch_b(const BackwardParams &q, int sm_count, cudaStream_t s)
+{
+    const TraverseParams &p = q.tp;
+    const bool prt = p.fr.mode == FPO_RAYS_EXPLICIT && p.fr.rt != nullptr;
+    const int threads = 256;
+    const int smem = traverse_smem_bytes(p.n_smem_nodes, prt, threads);
+    auto k = backward_kernel<N1, N2>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return (int)e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) per_sm = 1;
+    uint64_t blocks = (uint64_t)sm_count * per_sm;
+    const uint64_t need = (p.n_tiles + (threads / 32) - 1) / (threads / 32);
+    if (need < blocks) blocks = need ? need : 1;
+    k<<<(unsigned)blocks, threads, smem, s>>>(q);
+    return (int)cudaGetLastError();
+}
+
+int launch_backward(const BackwardParams &q, int sm_count, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    const TraverseParams &p = q.tp;
+    if (p.n1 == 31 && p.n2 == 5) return launch_b<31, 5>(q, sm_count, s);
+    if (p.n1 == 11 && p.n2 == 5) return launch_b<11, 5>(q, sm_count, s);
+    if (p.n1 == 21 && p.n2 == 5) return launch_b<21, 5>(q, sm_count, s);
+    if (p.n1 == 31 && p.n2 == 11) return launch_b<31, 11>(q, sm_count, s);
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Canonical coefficients (device, upload order) -> FP32 leaf records.
+// One warp per leaf: lanes stride over the n1 + 27 n2 values (coalesced).
+
+__global__ void __launch_bounds__(256) set_coeffs_kernel(const float *__restrict__ src, const uint32_t *__restrict__ perm,
+                                                         float *sig, float *zc, uint32_t n_leaves, int n1, int n2,
+                                                         int ss, int zs)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    const int nc = n1 + 27 * n2;
+    for (uint32_t leaf = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; leaf < n_leaves; leaf += warps) {
+        const float *row = src + (size_t)perm[leaf] * nc;
+        for (int j = lane; j < nc; j += 32) {
+            const float v = row[j];
+            if (j < n1) sig[(size_t)leaf * ss + j] = v;
+            else zc[(size_t)leaf * zs + (j - n1)] = v;
+        }
+    }
+}
+
+int launch_set_coeffs(const float *src, const uint32_t *perm, float *sig, float *zc, uint32_t n_leaves,
+                      int n1, int n2, int sm_count, void *stream)
+{
+    if (n_leaves == 0) return (int)cudaSuccess;
+    uint64_t blocks = ((uint64_t)n_leaves * 32 + 255) / 256;
+    if (blocks > (uint64_t)sm_count * 16) blocks = (uint64_t)sm_count * 16;
+    set_coeffs_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(src, perm, sig, zc, n_leaves, n1, n2,
+                                                                           sig_stride(n1), z_stride(n2));
+    return (int)cudaGetLastError();
 }
 
 }  // namespace fpo

@@ -30,7 +30,7 @@ FLAG_RECORD_VISITS, FLAG_OUT_T, FLAG_MARK_LEAVES, FLAG_STATS = 1, 2, 4, 8
 # Every symbol include/fpo.h declares.
 EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
            "fpo_render_backward", "fpo_status_sync", "fpo_tree_info_get", "fpo_destroy",
-           "fpo_last_error", "fpo_version", "fpo_render_noalloc"]
+           "fpo_last_error", "fpo_version", "fpo_render_noalloc", "fpo_set_coeffs"]
 
 
 class FPOError(RuntimeError):
@@ -90,6 +90,7 @@ def lib():
         L.fpo_render.argtypes = [P, C.POINTER(Rays), C.POINTER(FrameOpts), P, P]
         L.fpo_render_backward.argtypes = [P, C.POINTER(Rays), C.POINTER(FrameOpts), P, P, P, P]
         L.fpo_render_noalloc.argtypes = [P, C.POINTER(Rays), C.POINTER(FrameOpts), P, P]
+        L.fpo_set_coeffs.argtypes = [P, P, P]
         L.fpo_status_sync.argtypes = [P, P]
         L.fpo_tree_info_get.argtypes = [P, C.POINTER(TreeInfo)]
         L.fpo_destroy.argtypes = [P]
@@ -197,6 +198,16 @@ class Renderer:
         import torch
 
         dev = torch.device("cuda", self.device)
+        r, keep, n = self._rays(camera, t, rays_o, rays_d, t_per_ray)
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        return self._render_into(r, keep, n, out, bg, stop_T, visit_cap, want_T, leaf_mark, stats,
+                                 stream, events)
+
+    def _rays(self, camera, t, rays_o, rays_d, t_per_ray):
+        import torch
+
+        dev = torch.device("cuda", self.device)
         r = Rays()
         keep = []
         if camera is not None:
@@ -220,8 +231,13 @@ class Renderer:
                 keep.append(tp)
                 r.t_per_ray = tp.data_ptr() if n else None
         r.t = float(t)
-        if out is None:
-            out = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        return r, keep, n
+
+    def _render_into(self, r, keep, n, out, bg, stop_T, visit_cap, want_T, leaf_mark, stats,
+                     stream, events):
+        import torch
+
+        dev = torch.device("cuda", self.device)
         res = {"rgb": out}
         opts = FrameOpts()
         opts.bg = (C.c_float * 3)(*bg)
@@ -257,3 +273,66 @@ class Renderer:
                                C.c_void_p(_stream_handle(stream))))
         res["_keep"] = keep
         return res
+
+    def set_coeffs(self, coeffs, stream=None):
+        """Replaces the tree's coefficients from a CUDA float32 tensor [n_leaves, n1 + 27 n2]."""
+        c = coeffs.detach()
+        assert c.is_cuda and c.dtype.is_floating_point and c.is_contiguous()
+        check(lib().fpo_set_coeffs(self.h, C.c_void_p(c.data_ptr()),
+                                   C.c_void_p(_stream_handle(stream))))
+
+    def render_backward(self, out_rgb, dL_drgb, dL_dcoeffs, camera=None, t=0.0, rays_o=None,
+                        rays_d=None, t_per_ray=None, bg=(1.0, 1.0, 1.0), stop_T=1e-4, stream=None):
+        """Accumulates dL/d(coefficients) [n_leaves, n1 + 27 n2] (canonical) into dL_dcoeffs."""
+        r, keep, n = self._rays(camera, t, rays_o, rays_d, t_per_ray)
+        opts = FrameOpts()
+        opts.bg = (C.c_float * 3)(*bg)
+        opts.stop_T = float(stop_T)
+        g = dL_drgb.contiguous()
+        o = out_rgb.contiguous()
+        check(lib().fpo_render_backward(self.h, C.byref(r), C.byref(opts),
+                                        C.c_void_p(o.data_ptr() if n else None),
+                                        C.c_void_p(g.data_ptr() if n else None),
+                                        C.c_void_p(dL_dcoeffs.data_ptr()),
+                                        C.c_void_p(_stream_handle(stream))))
+        del keep
+
+
+def _autograd_function():
+    import torch
+
+    class FPORender(torch.autograd.Function):
+        """Differentiable render of explicit rays with respect to the leaf
+        coefficients (canonical [n_leaves, n1 + 27 n2]): forward sets them and
+        renders through fpo_render, backward calls fpo_render_backward."""
+
+        @staticmethod
+        def forward(ctx, coeffs, renderer, rays_o, rays_d, t_per_ray, bg, stop_T):
+            renderer.set_coeffs(coeffs)
+            rgb = renderer.render(rays_o=rays_o, rays_d=rays_d, t_per_ray=t_per_ray, bg=bg,
+                                  stop_T=stop_T)["rgb"]
+            ctx.renderer, ctx.bg, ctx.stop_T = renderer, bg, stop_T
+            ctx.shape = coeffs.shape
+            ctx.save_for_backward(rays_o, rays_d, t_per_ray, rgb)
+            return rgb
+
+        @staticmethod
+        def backward(ctx, g):
+            rays_o, rays_d, t_per_ray, rgb = ctx.saved_tensors
+            grad = torch.zeros(ctx.shape, dtype=torch.float32, device=g.device)
+            ctx.renderer.render_backward(rgb, g.float(), grad, rays_o=rays_o, rays_d=rays_d,
+                                         t_per_ray=t_per_ray, bg=ctx.bg, stop_T=ctx.stop_T)
+            return grad, None, None, None, None, None, None
+
+    return FPORender
+
+
+_FPORender = None
+
+
+def render_rays(coeffs, renderer, rays_o, rays_d, t_per_ray, bg=(1.0, 1.0, 1.0), stop_T=1e-4):
+    """Differentiable render: rgb [n, 3] of explicit rays, gradients to `coeffs`."""
+    global _FPORender
+    if _FPORender is None:
+        _FPORender = _autograd_function()
+    return _FPORender.apply(coeffs, renderer, rays_o, rays_d, t_per_ray, tuple(bg), float(stop_T))
