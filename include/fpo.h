@@ -221,6 +221,43 @@ int fpo_render_noalloc(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts 
  * Errors: INVALID_ARG, NO_TREE, UNSUPPORTED, CUDA. */
 int fpo_set_coeffs(fpo_ctx *ctx, const float *coeffs, void *cuda_stream);
 
+/* Per-leaf DFT of the Fourier PlenOctree generation (Sec. 4.2, Eq. 10-12):
+ * from the values every leaf of the unified octree takes at frames
+ * t = 1..n_frames (device [n_frames][n_leaves][28]: sigma, then z_{c,k} for
+ * c = 0..2, k = 0..8), computes the coefficients (device [n_leaves][n1 +
+ * 27*n2], canonical order) k_i = sum_t x(t) (w_i / T) {cos(i pi t / T) for
+ * even i, sin((i+1) pi t / T) for odd i} with T = n_frames, w_0 = 1 and
+ * w_i = 2 for i >= 1, so that Eq. 8 inverts it exactly for signals of
+ * frequency below T/2 (the paper prints w_i = 1, under which Eq. 8 would
+ * halve every non-constant term).  Runs on the current device and stream.
+ * Errors: INVALID_ARG (n1 in [1, 32], n2 in [1, 16], n_frames in [1, 256]), CUDA. */
+int fpo_dft_leaves(int32_t n1, int32_t n2, uint32_t n_frames, uint32_t n_leaves,
+                   const float *values, float *coeffs, void *cuda_stream);
+
+/* One frame's octree for fpo_union_trees (host arrays): leaves as in
+ * fpo_tree_desc, values [n_leaves][28] = sigma, then z_{c,k} (c = 0..2,
+ * k = 0..8) of each leaf at that frame. */
+typedef struct {
+    uint32_t n_leaves;
+    const uint8_t *leaf_depth;
+    const uint32_t *leaf_xyz;
+    const float *values;
+} fpo_frame_tree;
+
+/* Union of the frames' octree structures (Sec. 4.2): a cell is divided in the
+ * union if any frame divides it, so every union leaf is as deep as or deeper
+ * than the frame leaves holding it; a frame's value is copied into every
+ * union leaf its (coarser) leaf was divided into, and is zero where that
+ * frame has no leaf.  Host only.  Call with capacity 0 to learn *n_union;
+ * then with host arrays union_depth [capacity], union_xyz [capacity][3] and
+ * union_values [n_frames][capacity][28] (pass capacity = n_union for a dense
+ * array).  Union leaves come in depth-first octant order (x, then y, then z
+ * bit), i.e. Morton order.  Errors: INVALID_ARG, BAD_TREE (a frame's leaves
+ * overlap or leave their grid). */
+int fpo_union_trees(uint32_t n_frames, const fpo_frame_tree *frames, uint32_t max_depth,
+                    uint32_t *n_union, uint8_t *union_depth, uint32_t *union_xyz,
+                    float *union_values, uint32_t capacity);
+
 /* Waits for cuda_stream and returns (then clears) the device status word:
  * FPO_OK, FPO_ERR_TRAVERSAL_LIMIT, FPO_ERR_VISIT_OVERFLOW or
  * FPO_ERR_DEVICE_TIMEOUT. */

@@ -12,6 +12,7 @@ Functions and the passages they follow (Wang et al., CVPR 2022):
                      emission-absorption compositing with early stop   (Sec. 4.1, 3)
   render_grad(...)   dL/d(coefficients) of render for a given dL/d(rgb):
                      the back-propagation of the fine-tuning stage     (Sec. 4.3, Eq. 13)
+  dft(x, n)          per-series DFT of frames t = 1..T                 (Sec. 4.2, Eq. 10-12)
 """
 
 from __future__ import annotations
@@ -78,6 +79,7 @@ def lib():
                                     C.POINTER(Out), C.c_int]
         L.oracle_render_grad.argtypes = [C.c_void_p, C.POINTER(Scene), C.POINTER(Rays),
                                          C.c_void_p, C.c_void_p]
+        L.oracle_dft.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p]
         _lib = L
     return _lib
 
@@ -172,6 +174,18 @@ def render_grad(tree, coeffs, dL_drgb, *, n1=31, n2=5, sh_degree=2, period=60.0,
     if st != 0:
         raise RuntimeError(f"oracle_render_grad failed with status {st}")
     return grad
+
+
+def dft(x, n_coef: int) -> np.ndarray:
+    """Eq. 10-12: x [T, n_series] sampled at frames 1..T -> k [n_series, n_coef] (FP64)."""
+    x = np.ascontiguousarray(x, np.float64)
+    if x.ndim == 1:
+        x = x[:, None]
+    T, ns = x.shape
+    k = np.zeros((ns, n_coef), np.float64)
+    if lib().oracle_dft(T, ns, _ptr(x), n_coef, _ptr(k)) != 0:
+        raise ValueError("bad DFT arguments")
+    return k
 
 
 def _setup(coeffs, n1, n2, sh_degree, period, aabb_min, aabb_size, bg, stop_T, camera, t,

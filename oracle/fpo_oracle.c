@@ -573,3 +573,29 @@ int oracle_render_grad(const void *tree, const oracle_scene *sc, const oracle_ra
     free(del);
     return status;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 10-12 (Sec. 4.2): per-leaf DFT of values sampled at frames t = 1..T,
+ *   k_i = sum_{t=1}^{T} x(t) DFT_i(t),
+ *   DFT_i(t) = (w_i / T) cos(i pi t / T) for even i, (w_i / T) sin((i+1) pi t / T) for odd i.
+ * The paper prints w_i = 1; with it the inverse DFT of Eq. 7-9 would halve
+ * every non-constant term, so this build reads w_0 = 1, w_i = 2 (i >= 1),
+ * which makes Eq. 8 the exact inverse for signals of frequency < T/2.
+ * x: [T][n_series]; k: [n_series][n_coef]. */
+int oracle_dft(int T, int n_series, const double *x, int n_coef, double *k)
+{
+    if (T < 1 || n_series < 0 || n_coef < 1 || (n_series > 0 && (!x || !k))) return ORC_ERR_ARG;
+    for (int s = 0; s < n_series; ++s) {
+        for (int i = 0; i < n_coef; ++i) {
+            double acc = 0.0;
+            for (int t = 1; t <= T; ++t) {
+                double basis = (i % 2 == 0) ? cos((double)i * M_PI * t / T)
+                                            : sin((double)(i + 1) * M_PI * t / T);
+                double w = i == 0 ? 1.0 : 2.0;
+                acc += x[(size_t)(t - 1) * n_series + s] * (w / T) * basis;
+            }
+            k[(size_t)s * n_coef + i] = acc;
+        }
+    }
+    return ORC_OK;
+}

@@ -500,6 +500,22 @@ int fpo_set_coeffs(fpo_ctx *ctx, const float *coeffs, void *cuda_stream)
     return FPO_OK;
 }
 
+int fpo_dft_leaves(int32_t n1, int32_t n2, uint32_t n_frames, uint32_t n_leaves, const float *values,
+                   float *coeffs, void *cuda_stream)
+{
+    if (n1 < 1 || n1 > 32 || n2 < 1 || n2 > 16) return fail(FPO_ERR_INVALID_ARG, "n1 in [1, 32], n2 in [1, 16]");
+    if (n_frames < 1 || n_frames > 256) return fail(FPO_ERR_INVALID_ARG, "n_frames must be in [1, 256]");
+    if (n_leaves == 0) return FPO_OK;
+    if (!values || !coeffs) return fail(FPO_ERR_INVALID_ARG, "NULL array");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    const int ce = launch_dft(values, coeffs, n_leaves, n1, n2, (int)n_frames, sms, cuda_stream);
+    if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "dft launch");
+    return FPO_OK;
+}
+
 int fpo_status_sync(fpo_ctx *ctx, void *cuda_stream)
 {
     if (!ctx) return fail(FPO_ERR_INVALID_ARG, "ctx is NULL");

@@ -171,6 +171,8 @@ struct BackwardParams {
 int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream);
 int materialise_stages(int storage, int n1, int n2);
 int launch_backward(const BackwardParams &q, int sm_count, void *stream);
+int launch_dft(const float *values, float *coeffs, uint32_t n_leaves, int n1, int n2, int T, int sm_count,
+               void *stream);
 int launch_set_coeffs(const float *src, const uint32_t *perm, float *sig, float *zc, uint32_t n_leaves,
                       int n1, int n2, int sm_count, void *stream);
 int launch_traverse(const TraverseParams &p, bool materialised, bool debug, int sm_count,

@@ -1135,4 +1135,53 @@ int launch_set_coeffs(const float *src, const uint32_t *perm, float *sig, float 
     return (int)cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Per-leaf DFT (Sec. 4.2, Eq. 10-12): coefficients from the values a leaf
+// takes at frames t = 1..T (the unified per-frame octrees).  One thread per
+// output coefficient (leaf, j): coalesced stores; the threads of one series
+// read the same per-frame value (L1 broadcast).  The DFT weights
+// (w_i / T) {cos, sin}, w_0 = 1, w_i = 2, come from FP64 into shared memory.
+
+constexpr int DFT_MAX_T = 256;
+
+__global__ void __launch_bounds__(256) dft_kernel(const float *__restrict__ values, float *__restrict__ coeffs,
+                                                  uint32_t n_leaves, int n1, int n2, int T)
+{
+    __shared__ float s_w[32 * DFT_MAX_T];
+    const int nb = n1 > n2 ? n1 : n2;
+    for (int q = threadIdx.x; q < nb * T; q += blockDim.x) {
+        const int i = q / T, t = q % T + 1;
+        const double u = (double)t / (double)T;
+        const double w = (i == 0 ? 1.0 : 2.0) / (double)T;
+        s_w[q] = (float)(w * ((i & 1) ? sinpi((double)(i + 1) * u) : cospi((double)i * u)));
+    }
+    __syncthreads();
+    const int nc = n1 + 27 * n2;
+    const uint64_t total = (uint64_t)n_leaves * nc;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t leaf = (uint32_t)(g / nc);
+        const int j = (int)(g % nc);
+        const int series = j < n1 ? 0 : 1 + (j - n1) / n2;
+        const int i = j < n1 ? j : (j - n1) % n2;
+        const float *x = values + (size_t)leaf * 28 + series;
+        const float *w = s_w + i * T;
+        float acc = 0.0f;
+        for (int t = 0; t < T; ++t) acc = fmaf(__ldg(x + (size_t)t * n_leaves * 28), w[t], acc);
+        coeffs[g] = acc;
+    }
+}
+
+int launch_dft(const float *values, float *coeffs, uint32_t n_leaves, int n1, int n2, int T, int sm_count,
+               void *stream)
+{
+    if (n_leaves == 0) return (int)cudaSuccess;
+    const uint64_t total = (uint64_t)n_leaves * (n1 + 27 * n2);
+    uint64_t blocks = (total + 255) / 256;
+    if (blocks > (uint64_t)sm_count * 32) blocks = (uint64_t)sm_count * 32;
+    dft_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(values, coeffs, n_leaves, n1, n2, T);
+    return (int)cudaGetLastError();
+}
+
 }  // namespace fpo

@@ -30,7 +30,8 @@ FLAG_RECORD_VISITS, FLAG_OUT_T, FLAG_MARK_LEAVES, FLAG_STATS = 1, 2, 4, 8
 # Every symbol include/fpo.h declares.
 EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
            "fpo_render_backward", "fpo_status_sync", "fpo_tree_info_get", "fpo_destroy",
-           "fpo_last_error", "fpo_version", "fpo_render_noalloc", "fpo_set_coeffs"]
+           "fpo_last_error", "fpo_version", "fpo_render_noalloc", "fpo_set_coeffs",
+           "fpo_dft_leaves", "fpo_union_trees"]
 
 
 class FPOError(RuntimeError):
@@ -66,6 +67,11 @@ class FrameOpts(C.Structure):
                 ("events", C.c_void_p * 3)]
 
 
+class FrameTree(C.Structure):
+    _fields_ = [("n_leaves", C.c_uint32), ("leaf_depth", C.c_void_p), ("leaf_xyz", C.c_void_p),
+                ("values", C.c_void_p)]
+
+
 class TreeInfo(C.Structure):
     _fields_ = [("n_leaves", C.c_uint32), ("n_nodes", C.c_uint32), ("max_depth", C.c_uint32),
                 ("n_smem_nodes", C.c_uint32), ("node_bytes", C.c_uint64),
@@ -91,6 +97,9 @@ def lib():
         L.fpo_render_backward.argtypes = [P, C.POINTER(Rays), C.POINTER(FrameOpts), P, P, P, P]
         L.fpo_render_noalloc.argtypes = [P, C.POINTER(Rays), C.POINTER(FrameOpts), P, P]
         L.fpo_set_coeffs.argtypes = [P, P, P]
+        L.fpo_dft_leaves.argtypes = [C.c_int32, C.c_int32, C.c_uint32, C.c_uint32, P, P, P]
+        L.fpo_union_trees.argtypes = [C.c_uint32, P, C.c_uint32, C.POINTER(C.c_uint32), P, P, P,
+                                      C.c_uint32]
         L.fpo_status_sync.argtypes = [P, P]
         L.fpo_tree_info_get.argtypes = [P, C.POINTER(TreeInfo)]
         L.fpo_destroy.argtypes = [P]
@@ -296,6 +305,45 @@ class Renderer:
                                         C.c_void_p(dL_dcoeffs.data_ptr()),
                                         C.c_void_p(_stream_handle(stream))))
         del keep
+
+
+def union_trees(frames, max_depth):
+    """Sec. 4.2 union of per-frame octrees (host).  frames: list of
+    (leaf_depth uint8 [n], leaf_xyz uint32 [n, 3], values float32 [n, 28]).
+    Returns (depth [m], xyz [m, 3], values [n_frames, m, 28])."""
+    keep = []
+    arr = (FrameTree * max(len(frames), 1))()
+    for i, (d, x, v) in enumerate(frames):
+        d = np.ascontiguousarray(d, np.uint8)
+        x = np.ascontiguousarray(x, np.uint32).reshape(-1, 3)
+        v = np.ascontiguousarray(v, np.float32).reshape(-1, 28)
+        keep += [d, x, v]
+        arr[i] = FrameTree(d.shape[0], d.ctypes.data, x.ctypes.data, v.ctypes.data)
+    n = C.c_uint32(0)
+    check(lib().fpo_union_trees(len(frames), arr, int(max_depth), C.byref(n), None, None, None, 0))
+    m = n.value
+    depth = np.zeros(m, np.uint8)
+    xyz = np.zeros((m, 3), np.uint32)
+    vals = np.zeros((len(frames), m, 28), np.float32)
+    if m:
+        check(lib().fpo_union_trees(len(frames), arr, int(max_depth), C.byref(n), depth.ctypes.data,
+                                    xyz.ctypes.data, vals.ctypes.data, m))
+    return depth, xyz, vals
+
+
+def dft_leaves(values, n1=31, n2=5, stream=None):
+    """Eq. 10-12 on the GPU: values [T, n_leaves, 28] (CUDA float32) ->
+    coefficients [n_leaves, n1 + 27 n2] (canonical)."""
+    import torch
+
+    v = values.contiguous()
+    T, n, w = v.shape
+    assert w == 28 and v.is_cuda and v.dtype == torch.float32
+    out = torch.empty((n, n1 + 27 * n2), dtype=torch.float32, device=v.device)
+    check(lib().fpo_dft_leaves(n1, n2, T, n, C.c_void_p(v.data_ptr() if n else None),
+                               C.c_void_p(out.data_ptr() if n else None),
+                               C.c_void_p(_stream_handle(stream))))
+    return out
 
 
 def _autograd_function():

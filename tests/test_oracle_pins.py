@@ -458,3 +458,36 @@ def test_gradient_matches_finite_differences(stop_T):
         assert abs(G[leaf, j] - fd) <= 1e-3 * abs(fd) + 1e-7, (leaf, j, G[leaf, j], fd)
         checked += 1
     assert checked > 100
+
+
+# --------------------------------------------------------------------------
+# Eq. 10-12 (per-leaf DFT) with the 2/T reading
+
+
+def test_dft_round_trip_band_limited():
+    # frequencies 0..15 < T/2: the Eq. 8 series of the DFT coefficients gives
+    # back the samples at every frame t = 1..60 (and matches numpy's FFT)
+    rng = np.random.default_rng(11)
+    T = 60
+    spec = np.zeros(T // 2 + 1, complex)
+    spec[:16] = rng.normal(size=16) + 1j * rng.normal(size=16)
+    spec[0] = spec[0].real
+    x = np.fft.irfft(spec, n=T)  # x[t] for t = 0..59; frame t = 1..60 -> x[t % 60]
+    frames = np.array([x[t % T] for t in range(1, T + 1)])
+    k = oracle.dft(frames, N1)[0]
+    for t in range(1, T + 1):
+        assert abs(oracle.basis(N1, t, T) @ k - frames[t - 1]) < 1e-12
+    X = np.fft.rfft(x)
+    assert abs(k[0] - X[0].real / T) < 1e-12
+    for m in range(1, 16):
+        assert abs(k[2 * m] - 2 * X[m].real / T) < 1e-12
+        assert abs(k[2 * m - 1] + 2 * X[m].imag / T) < 1e-12
+
+
+def test_dft_of_constant_and_single_tone():
+    T = 60
+    k = oracle.dft(np.full(T, 3.5), 5)[0]
+    np.testing.assert_allclose(k, [3.5, 0, 0, 0, 0], atol=1e-13)
+    t = np.arange(1, T + 1)
+    k = oracle.dft(0.7 * np.sin(2 * np.pi * 2 * t / T), 7)[0]  # frequency 2 -> odd index 3
+    np.testing.assert_allclose(k, [0, 0, 0, 0.7, 0, 0, 0], atol=1e-13)
