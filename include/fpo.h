@@ -258,6 +258,34 @@ int fpo_union_trees(uint32_t n_frames, const fpo_frame_tree *frames, uint32_t ma
                     uint32_t *n_union, uint8_t *union_depth, uint32_t *union_xyz,
                     float *union_values, uint32_t capacity);
 
+/* A latent decoder: per leaf a 32-dim FP16 latent, decoded by a shared MLP
+ * 32 -> 64 -> 64 -> n1 + 27*n2 with ReLU after the first two layers (the
+ * learned stand-in for the per-leaf coefficients of Sec. 4.1; the paper's own
+ * network Phi of Eq. 6 maps positions to coefficients).  Device arrays:
+ * weights as BF16 bit patterns, row-major [out][in]; biases FP32. */
+typedef struct {
+    const uint16_t *w1; /* [64][32] */
+    const float *b1;    /* [64] */
+    const uint16_t *w2; /* [64][64] */
+    const float *b2;    /* [64] */
+    const uint16_t *w3; /* [n1 + 27*n2][64] */
+    const float *b3;    /* [n1 + 27*n2] */
+} fpo_decoder;
+
+/* The per-frame table of fpo_render's MATERIALISE mode, decoded from
+ * latents on the tensor cores: for every leaf, [max(0, sigma(t)), z_{c,k}(t)
+ * x 27, 0 x 4] (device [n_leaves][32] FP32) where the coefficients are the
+ * decoder's output and sigma, z follow Eq. 7 and Eq. 9 at time t.  The IDFT
+ * is folded into the last layer (W3' = B(t) W3), so the MLP runs 32 -> 64 ->
+ * 64 -> 28 with FP16 operands and FP32 accumulation (BF16 weights are
+ * converted to FP16 in shared memory).  latents: device FP16 [n_leaves][32].
+ * status: optional device word that receives FPO_ERR_DEVICE_TIMEOUT's bit
+ * when a bounded wait gives up.  Runs on the current device and stream.
+ * Errors: INVALID_ARG, CUDA. */
+int fpo_latent_table(const fpo_decoder *dec, int32_t n1, int32_t n2, double t, double period_T,
+                     uint32_t n_leaves, const uint16_t *latents, float *table, uint32_t *status,
+                     void *cuda_stream);
+
 /* Waits for cuda_stream and returns (then clears) the device status word:
  * FPO_OK, FPO_ERR_TRAVERSAL_LIMIT, FPO_ERR_VISIT_OVERFLOW or
  * FPO_ERR_DEVICE_TIMEOUT. */

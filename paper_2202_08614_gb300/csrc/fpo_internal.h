@@ -160,6 +160,25 @@ CtxView ctx_view(const fpo_ctx *ctx);
 // Records `msg` as the calling thread's last error; returns `code`.
 int set_last_error(int code, const char *msg);
 
+// Latent decoder (per-leaf FP16 latents, MLP 32 -> 64 -> 64 -> n1 + 27 n2,
+// ReLU).  Weights are BF16 bit patterns, row-major [out][in]; biases FP32.
+struct LatentParams {
+    const uint16_t *latents;  // FP16 [n_leaves][32]
+    const uint16_t *w1;       // [64][32]
+    const float *b1;          // [64]
+    const uint16_t *w2;       // [64][64]
+    const float *b2;          // [64]
+    const uint16_t *w3;       // [n1 + 27 n2][64]
+    const float *b3;          // [n1 + 27 n2]
+    int n1, n2;
+    double t, period_T;
+    uint32_t n_leaves;
+    float *table;             // [n_leaves][TABLE_STRIDE]
+    uint32_t *status;
+};
+
+int launch_latent_table(const LatentParams &p, int sm_count, void *stream);
+
 struct BackwardParams {
     TraverseParams tp;          // rays, tree and options as for the fused forward
     const float *out_rgb;       // forward colour [rays][3]

@@ -1,0 +1,355 @@
+// Latent decoder on the 5th-generation tensor cores (tcgen05, TMEM).
+//
+// Each leaf stores a 32-dim FP16 latent; a shared MLP 32 -> 64 -> 64 -> 166
+// (ReLU) decodes the leaf's n1 + 27 n2 Fourier coefficients.  Eq. 7 and 9 are
+// linear in the coefficients, so the frame's IDFT is folded into the last
+// layer: W3'(t) = B(t) W3, b3'(t) = B(t) b3 with B(t) the 28 x 166 map to
+// (sigma_raw, z_{c,k}), and the kernel writes the same per-frame table as the
+// coefficient IDFT pass: [max(0, sigma), 27 z, 0 x 4] per leaf.
+//
+// Per CTA (128 threads = one warpgroup): the weights are staged once in
+// shared memory in the no-swizzle K-major core-matrix layout (8 rows x 16 B
+// blocks), W3'(t) is computed in the prologue; then for each tile of 128
+// leaves the threads lay the latents out as the A operand, one elected
+// thread issues tcgen05.mma (M = 128, K = 16 per instruction, FP16 x FP16 ->
+// FP32 in TMEM), commits to an mbarrier, and the warps read the accumulator
+// rows back with tcgen05.ld (one row per thread), apply bias and ReLU and
+// write the next layer's A operand.  64 TMEM columns hold every layer's
+// accumulator in turn.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fpo_internal.h"
+#include "fpo_ptx.cuh"
+
+namespace fpo {
+namespace {
+
+constexpr int LT_THREADS = 128;
+constexpr int LT_M = 128;          // leaves per tile = MMA M
+constexpr uint32_t LT_TMEM_COLS = 64;
+constexpr uint64_t LT_WAIT_NS = 2000000000ull;
+
+// Shared-memory layout (bytes), all operands no-swizzle K-major.
+constexpr int OFF_W1 = 0;          // 64 x 32  f16:  4 KB
+constexpr int OFF_W2 = 4096;       // 64 x 64  f16:  8 KB
+constexpr int OFF_W3 = 12288;      // 32 x 64  f16:  4 KB
+constexpr int OFF_A1 = 16384;      // 128 x 32 f16:  8 KB
+constexpr int OFF_A2 = 24576;      // 128 x 64 f16: 16 KB
+constexpr int LT_SMEM = 40960 + 16384;  // + padding: caps residency at 4 CTAs per SM
+
+// Byte offset of element (row, k) in a K-major core-matrix layout whose rows
+// hold K elements: core matrix (row / 8, k / 8) at ((row/8) * K/8 + k/8) * 128,
+// inside it row % 8 at 16 B per row.
+__device__ __forceinline__ uint32_t core_off(int row, int k, int K)
+{
+    return (uint32_t)((((row >> 3) * (K >> 3) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: A, B f16, D f32, both K-major, M x N.
+__device__ __forceinline__ uint32_t idesc_f16(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     ptx::smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane; waits for them.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Writes 8 consecutive values of row `row` (K-chunk j) into a core layout.
+__device__ __forceinline__ void put8(unsigned char *base, int row, int j, int K, const float *v)
+{
+    __half2 h[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) h[e] = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
+    *reinterpret_cast<uint4 *>(base + core_off(row, 8 * j, K)) = *reinterpret_cast<const uint4 *>(h);
+}
+
+// Issues the K / 16 MMAs of D[128 x N] = A[128 x K] B[N x K]^T.
+__device__ __forceinline__ void gemm(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, int K, int N)
+{
+    const uint32_t idesc = idesc_f16(LT_M, N);
+    const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+#pragma unroll 1
+    for (int s = 0; s < K / 16; ++s) {
+        const uint64_t a = smem_desc(a_saddr + 256u * s, 128u, sbo);
+        const uint64_t b = smem_desc(b_saddr + 256u * s, 128u, sbo);
+        mma_f16(d_tmem, a, b, idesc, s > 0 ? 1u : 0u);
+    }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_constant__ LatentParams p)
+{
+    extern __shared__ __align__(1024) unsigned char lt_smem[];
+    __shared__ float s_b1[64], s_b2[64], s_b3[32], s_basis[32];
+    __shared__ uint64_t s_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int nc = p.n1 + 27 * p.n2;
+
+    // --- prologue: basis, weights (bf16 -> f16, core layout), folded layer 3
+    const int nb = p.n1 > p.n2 ? p.n1 : p.n2;
+    if (tid < 32) s_basis[tid] = tid < nb ? (float)((tid & 1) ? sinpi((double)(tid + 1) * (p.t / p.period_T))
+                                                             : cospi((double)tid * (p.t / p.period_T)))
+                                         : 0.0f;
+    if (tid < 64) {
+        s_b1[tid] = p.b1[tid];
+        s_b2[tid] = p.b2[tid];
+    }
+    if (tid == 0) {
+        s_fail = 0;
+        ptx::mbar_init(&s_bar, 1);
+        ptx::fence_barrier_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(ptx::smem_u32(&s_tmem)),
+                     "r"(LT_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int q = tid; q < 64 * 4; q += LT_THREADS) {  // W1: 64 rows x 4 chunks
+        const int n = q >> 2, j = q & 3;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = __bfloat162float(__ushort_as_bfloat16(p.w1[n * 32 + 8 * j + e]));
+        put8(lt_smem + OFF_W1, n, j, 32, v);
+    }
+    for (int q = tid; q < 64 * 8; q += LT_THREADS) {  // W2: 64 rows x 8 chunks
+        const int n = q >> 3, j = q & 7;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = __bfloat162float(__ushort_as_bfloat16(p.w2[n * 64 + 8 * j + e]));
+        put8(lt_smem + OFF_W2, n, j, 64, v);
+    }
+    __syncthreads();  // s_basis ready
+    // W3'(t): row 0 = sum_i b_i W3[i], row 1 + q = sum_i b_i W3[n1 + q n2 + i], rows 28..31 = 0
+    for (int q = tid; q < 32 * 8; q += LT_THREADS) {
+        const int r = q >> 3, j = q & 7;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int h = 8 * j + e;
+            float acc = 0.0f;
+            if (r == 0) {
+                for (int i = 0; i < p.n1; ++i) acc = fmaf(s_basis[i], __bfloat162float(__ushort_as_bfloat16(p.w3[i * 64 + h])), acc);
+            } else if (r <= 27) {
+                const int row0 = p.n1 + (r - 1) * p.n2;
+                for (int i = 0; i < p.n2; ++i) acc = fmaf(s_basis[i], __bfloat162float(__ushort_as_bfloat16(p.w3[(row0 + i) * 64 + h])), acc);
+            }
+            v[e] = acc;
+        }
+        put8(lt_smem + OFF_W3, r, j, 64, v);
+    }
+    if (tid < 32) {
+        float acc = 0.0f;
+        if (tid == 0) {
+            for (int i = 0; i < p.n1; ++i) acc = fmaf(s_basis[i], p.b3[i], acc);
+        } else if (tid <= 27) {
+            const int row0 = p.n1 + (tid - 1) * p.n2;
+            for (int i = 0; i < p.n2; ++i) acc = fmaf(s_basis[i], p.b3[row0 + i], acc);
+        }
+        s_b3[tid] = acc;
+    }
+    (void)nc;
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t my_lane = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t sa_w1 = ptx::smem_u32(lt_smem + OFF_W1), sa_w2 = ptx::smem_u32(lt_smem + OFF_W2),
+                   sa_w3 = ptx::smem_u32(lt_smem + OFF_W3), sa_a1 = ptx::smem_u32(lt_smem + OFF_A1),
+                   sa_a2 = ptx::smem_u32(lt_smem + OFF_A2);
+    uint32_t phase = 0;
+    const uint32_t n_tiles = (p.n_leaves + LT_M - 1) / LT_M;
+    const int m = tid;  // this thread's accumulator row (TMEM lane) and leaf in the tile
+
+    // One layer: the elected thread issues the MMAs and commits; everyone
+    // waits on the mbarrier (bounded).  The outcome is made CTA-uniform so
+    // that the collective TMEM loads and barriers below never diverge.
+    auto run_layer = [&](uint32_t a_addr, uint32_t b_addr, int K, int N) -> bool {
+        if (tid == 0) {
+            fence_after();
+            gemm(tmem, a_addr, b_addr, K, N);
+            mma_commit(&s_bar);
+        }
+        if (!ptx::mbar_wait_bounded(&s_bar, phase, LT_WAIT_NS)) s_fail = 1;
+        phase ^= 1u;
+        __syncthreads();
+        fence_after();
+        return s_fail == 0;
+    };
+
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const uint32_t leaf = tile * LT_M + (uint32_t)m;
+        const bool valid = leaf < p.n_leaves;
+        // layer-1 A operand: this thread's latent row (64 B) into the core layout
+        {
+            uint4 q[4] = {};
+            if (valid) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(p.latents + (size_t)leaf * 32);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) q[j] = __ldg(src + j);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4 *>(lt_smem + OFF_A1 + core_off(m, 8 * j, 32)) = q[j];
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (!run_layer(sa_a1, sa_w1, 32, 64)) break;
+        // layer 1 epilogue: bias + ReLU -> layer-2 A operand (MMA 1 is done with A1)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float v[16];
+            tmem_ld16(my_lane + 16 * c, v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e] + s_b1[16 * c + e], 0.0f);
+            put8(lt_smem + OFF_A2, m, 2 * c, 64, v);
+            put8(lt_smem + OFF_A2, m, 2 * c + 1, 64, v + 8);
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (!run_layer(sa_a2, sa_w2, 64, 64)) break;
+        // layer 2 epilogue -> layer-3 A operand, in place (MMA 2 has finished
+        // reading A2, and each thread rewrites only its own row)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float v[16];
+            tmem_ld16(my_lane + 16 * c, v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e] + s_b2[16 * c + e], 0.0f);
+            put8(lt_smem + OFF_A2, m, 2 * c, 64, v);
+            put8(lt_smem + OFF_A2, m, 2 * c + 1, 64, v + 8);
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        if (!run_layer(sa_a2, sa_w3, 64, 32)) break;
+        {
+            float o[32];
+            tmem_ld16(my_lane, o);
+            tmem_ld16(my_lane + 16, o + 16);
+            if (valid) {
+                float4 *dst = reinterpret_cast<float4 *>(p.table + (size_t)leaf * TABLE_STRIDE);
+                float w[32];
+                w[0] = fmaxf(o[0] + s_b3[0], 0.0f);
+#pragma unroll
+                for (int q = 1; q < 28; ++q) w[q] = o[q] + s_b3[q];
+#pragma unroll
+                for (int q = 28; q < 32; ++q) w[q] = 0.0f;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) dst[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+            }
+        }
+        fence_before();
+        __syncthreads();  // the accumulator is free for the next tile's MMA
+    }
+    if (s_fail && tid == 0) {
+        // an MMA that never signalled: wait once more (bounded) before freeing TMEM
+        ptx::mbar_wait_bounded(&s_bar, phase, LT_WAIT_NS);
+        if (p.status) atomicOr(p.status, STATUS_DEVICE_TIMEOUT);
+    }
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(LT_TMEM_COLS) : "memory");
+}
+
+int launch_latent_table(const LatentParams &p, int sm_count, void *stream)
+{
+    if (p.n_leaves == 0) return (int)cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(latent_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, LT_SMEM);
+    if (e != cudaSuccess) return (int)e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, latent_table_kernel, LT_THREADS, LT_SMEM);
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 4) per_sm = 4;  // 4 x 64 TMEM columns <= 512
+    const uint32_t n_tiles = (p.n_leaves + LT_M - 1) / LT_M;
+    uint64_t blocks = (uint64_t)sm_count * per_sm;
+    if (blocks > n_tiles) blocks = n_tiles;
+    latent_table_kernel<<<(unsigned)blocks, LT_THREADS, LT_SMEM, (cudaStream_t)stream>>>(p);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace fpo
+
+using namespace fpo;
+
+extern "C" int fpo_latent_table(const fpo_decoder *dec, int32_t n1, int32_t n2, double t, double period_T,
+                                uint32_t n_leaves, const uint16_t *latents, float *table, uint32_t *status,
+                                void *cuda_stream)
+{
+    if (!dec) return set_last_error(FPO_ERR_INVALID_ARG, "dec is NULL");
+    if (n1 < 1 || n1 > 32 || n2 < 1 || n2 > 16) return set_last_error(FPO_ERR_INVALID_ARG, "n1 in [1, 32], n2 in [1, 16]");
+    if (!(period_T > 0.0)) return set_last_error(FPO_ERR_INVALID_ARG, "period_T must be > 0");
+    if (n_leaves == 0) return FPO_OK;
+    if (!latents || !table || !dec->w1 || !dec->b1 || !dec->w2 || !dec->b2 || !dec->w3 || !dec->b3)
+        return set_last_error(FPO_ERR_INVALID_ARG, "NULL array");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return set_last_error(FPO_ERR_CUDA, cudaGetErrorString(e));
+    LatentParams p{};
+    p.latents = latents;
+    p.w1 = dec->w1;
+    p.b1 = dec->b1;
+    p.w2 = dec->w2;
+    p.b2 = dec->b2;
+    p.w3 = dec->w3;
+    p.b3 = dec->b3;
+    p.n1 = n1;
+    p.n2 = n2;
+    p.t = t;
+    p.period_T = period_T;
+    p.n_leaves = n_leaves;
+    p.table = table;
+    p.status = status;
+    const int ce = launch_latent_table(p, sms, cuda_stream);
+    if (ce != cudaSuccess) return set_last_error(FPO_ERR_CUDA, cudaGetErrorString((cudaError_t)ce));
+    return FPO_OK;
+}

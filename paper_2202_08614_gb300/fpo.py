@@ -31,7 +31,7 @@ FLAG_RECORD_VISITS, FLAG_OUT_T, FLAG_MARK_LEAVES, FLAG_STATS = 1, 2, 4, 8
 EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
            "fpo_render_backward", "fpo_status_sync", "fpo_tree_info_get", "fpo_destroy",
            "fpo_last_error", "fpo_version", "fpo_render_noalloc", "fpo_set_coeffs",
-           "fpo_dft_leaves", "fpo_union_trees"]
+           "fpo_dft_leaves", "fpo_union_trees", "fpo_latent_table"]
 
 
 class FPOError(RuntimeError):
@@ -72,6 +72,11 @@ class FrameTree(C.Structure):
                 ("values", C.c_void_p)]
 
 
+class Decoder(C.Structure):
+    _fields_ = [("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
+                ("w3", C.c_void_p), ("b3", C.c_void_p)]
+
+
 class TreeInfo(C.Structure):
     _fields_ = [("n_leaves", C.c_uint32), ("n_nodes", C.c_uint32), ("max_depth", C.c_uint32),
                 ("n_smem_nodes", C.c_uint32), ("node_bytes", C.c_uint64),
@@ -98,6 +103,8 @@ def lib():
         L.fpo_render_noalloc.argtypes = [P, C.POINTER(Rays), C.POINTER(FrameOpts), P, P]
         L.fpo_set_coeffs.argtypes = [P, P, P]
         L.fpo_dft_leaves.argtypes = [C.c_int32, C.c_int32, C.c_uint32, C.c_uint32, P, P, P]
+        L.fpo_latent_table.argtypes = [C.POINTER(Decoder), C.c_int32, C.c_int32, C.c_double,
+                                       C.c_double, C.c_uint32, P, P, P, P]
         L.fpo_union_trees.argtypes = [C.c_uint32, P, C.c_uint32, C.POINTER(C.c_uint32), P, P, P,
                                       C.c_uint32]
         L.fpo_status_sync.argtypes = [P, P]
@@ -329,6 +336,26 @@ def union_trees(frames, max_depth):
         check(lib().fpo_union_trees(len(frames), arr, int(max_depth), C.byref(n), depth.ctypes.data,
                                     xyz.ctypes.data, vals.ctypes.data, m))
     return depth, xyz, vals
+
+
+def latent_table(latents, w1, b1, w2, b2, w3, b3, t, period_T=60.0, n1=31, n2=5, stream=None):
+    """Per-frame table [n, 32] from FP16 latents [n, 32] and a BF16 MLP (tcgen05)."""
+    import torch
+
+    lat = latents.contiguous()
+    assert lat.dtype == torch.float16 and lat.is_cuda and lat.shape[1] == 32
+    ws = [w.to(torch.bfloat16).contiguous() for w in (w1, w2, w3)]
+    bs = [b.float().contiguous() for b in (b1, b2, b3)]
+    dec = Decoder(ws[0].data_ptr(), bs[0].data_ptr(), ws[1].data_ptr(), bs[1].data_ptr(),
+                  ws[2].data_ptr(), bs[2].data_ptr())
+    n = lat.shape[0]
+    out = torch.empty((n, 32), dtype=torch.float32, device=lat.device)
+    status = torch.zeros(1, dtype=torch.int32, device=lat.device)
+    check(lib().fpo_latent_table(C.byref(dec), n1, n2, float(t), float(period_T), n,
+                                 C.c_void_p(lat.data_ptr() if n else None),
+                                 C.c_void_p(out.data_ptr() if n else None),
+                                 C.c_void_p(status.data_ptr()), C.c_void_p(_stream_handle(stream))))
+    return out, status
 
 
 def dft_leaves(values, n1=31, n2=5, stream=None):
