@@ -53,7 +53,8 @@ typedef enum {
 } fpo_status;
 
 /* Storage precision of the leaf coefficients (the math is FP32 throughout). */
-enum { FPO_STORAGE_F32 = 0, FPO_STORAGE_BF16 = 1, FPO_STORAGE_F16 = 2, FPO_STORAGE_FP8_E4M3 = 3 };
+enum { FPO_STORAGE_F32 = 0, FPO_STORAGE_BF16 = 1, FPO_STORAGE_F16 = 2, FPO_STORAGE_FP8_E4M3 = 3,
+       FPO_STORAGE_LATENT = 4 /* per-leaf FP16 latents + decoder (fpo_set_latents) */ };
 
 /* Where the per-leaf inverse DFT (Eq. 7, Eq. 9) runs:
  *  FUSED        at every ray-leaf visit, from the stored coefficients;
@@ -285,6 +286,41 @@ typedef struct {
 int fpo_latent_table(const fpo_decoder *dec, int32_t n1, int32_t n2, double t, double period_T,
                      uint32_t n_leaves, const uint16_t *latents, float *table, uint32_t *status,
                      void *cuda_stream);
+
+/* FP32 master weights of the latent decoder (device, shapes as fpo_decoder). */
+typedef struct {
+    float *w1, *b1, *w2, *b2, *w3, *b3;
+} fpo_mlp;
+
+/* One gradient evaluation for training the latent decoder: for the leaves
+ * `rows` (device [batch], distinct), decodes y = MLP(latents[row]) in FP32 and
+ * accumulates, for L = sum_rows sum_j coef_weight[j] (y_j - targets[row][j])^2
+ * (+ sum extra_dy . y when extra_dy, device [N][n1+27*n2], is given, e.g. the
+ * render adjoint's dL/d(coefficients)), the weight gradients into `grad`
+ * (the caller zeroes them), writes dL/d(latent) of each batch row to
+ * dlatents (device [batch][32]) and adds L to *loss (device, optional).
+ * latents [N][32] and targets [N][n1+27*n2] are device FP32.
+ * Errors: INVALID_ARG, CUDA. */
+int fpo_decoder_grad(const fpo_mlp *w, int32_t n1, int32_t n2, uint32_t batch, const uint32_t *rows,
+                     const float *latents, const float *targets, const float *coef_weight,
+                     const float *extra_dy, const fpo_mlp *grad, float *dlatents, double *loss,
+                     void *cuda_stream);
+
+/* Adam step (Kingma & Ba 2015) with bias correction, step counted from 1:
+ * dense over n elements (rows NULL), or over the rows of a batch (device
+ * rows [n / dim], distinct; param, m, v [N][dim]; grad [n / dim][dim]).
+ * Errors: INVALID_ARG, CUDA. */
+int fpo_adam(float *param, const float *grad, float *m, float *v, uint64_t n, const uint32_t *rows,
+             uint32_t dim, float lr, float beta1, float beta2, float eps, uint32_t step,
+             void *cuda_stream);
+
+/* LATENT storage: gives the uploaded tree its per-leaf latents (device FP16
+ * [n_leaves][32], upload order) and decoder (device arrays, copied into the
+ * context).  fpo_render then decodes the per-frame table with
+ * fpo_latent_table's tensor-core kernel before the traversal.  The tree is
+ * uploaded with coeffs = NULL for this storage.  Enqueued on the stream.
+ * Errors: INVALID_ARG, NO_TREE, UNSUPPORTED (context storage is not LATENT), OOM, CUDA. */
+int fpo_set_latents(fpo_ctx *ctx, const uint16_t *latents, const fpo_decoder *dec, void *cuda_stream);
 
 /* Waits for cuda_stream and returns (then clears) the device status word:
  * FPO_OK, FPO_ERR_TRAVERSAL_LIMIT, FPO_ERR_VISIT_OVERFLOW or

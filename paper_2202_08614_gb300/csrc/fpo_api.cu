@@ -84,6 +84,10 @@ struct fpo_ctx {
     void *d_sig = nullptr;    // density records (storage precision)
     void *d_z = nullptr;      // SH records (storage precision)
     float *d_scale = nullptr; // FP8: per-leaf scale, padded to a multiple of 4 leaves
+    uint16_t *d_latents = nullptr;  // LATENT: FP16 [n_leaves][32], internal leaf order
+    uint16_t *d_dec_w = nullptr;    // LATENT: w1 | w2 | w3 (BF16 bits)
+    float *d_dec_b = nullptr;       // LATENT: b1 | b2 | b3
+    bool has_latents = false;
     float *d_table = nullptr;
     size_t table_leaves = 0;
 
@@ -94,6 +98,10 @@ struct fpo_ctx {
         dfree(d_sig);
         dfree(d_z);
         dfree(d_scale);
+        dfree(d_latents);
+        dfree(d_dec_w);
+        dfree(d_dec_b);
+        has_latents = false;
         dfree(d_table);
         table_leaves = 0;
         has_tree = false;
@@ -151,7 +159,7 @@ int fpo_create(fpo_ctx **out, const fpo_config *cfg)
     if (cfg->sh_degree != 2) return fail(FPO_ERR_UNSUPPORTED, "only sh_degree 2 is supported");
     if (!(cfg->period_T > 0.0) || !std::isfinite(cfg->period_T))
         return fail(FPO_ERR_INVALID_ARG, "period_T must be finite and > 0");
-    if (cfg->storage < FPO_STORAGE_F32 || cfg->storage > FPO_STORAGE_FP8_E4M3)
+    if (cfg->storage < FPO_STORAGE_F32 || cfg->storage > FPO_STORAGE_LATENT)
         return fail(FPO_ERR_INVALID_ARG, "unknown storage %d", cfg->storage);
     if (cfg->idft_mode < FPO_IDFT_AUTO || cfg->idft_mode > FPO_IDFT_MATERIALISE)
         return fail(FPO_ERR_INVALID_ARG, "unknown idft_mode %d", cfg->idft_mode);
@@ -195,7 +203,8 @@ int fpo_upload_tree(fpo_ctx *ctx, const fpo_tree_desc *tree)
     if (!ctx) return fail(FPO_ERR_INVALID_ARG, "ctx is NULL");
     PackedTree pk;
     std::string err;
-    int st = validate_and_pack(tree, ctx->cfg.n1, ctx->cfg.n2, &pk, &err);
+    const bool latent = ctx->cfg.storage == FPO_STORAGE_LATENT;
+    int st = validate_and_pack(tree, latent ? 0 : ctx->cfg.n1, ctx->cfg.n2, &pk, &err);
     if (st != FPO_OK) return fail(st, "%s", err.c_str());
     DeviceGuard g(ctx->cfg.device);
     if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
@@ -203,8 +212,8 @@ int fpo_upload_tree(fpo_ctx *ctx, const fpo_tree_desc *tree)
 
     const int n1 = ctx->cfg.n1, n2 = ctx->cfg.n2, nc = n1 + 27 * n2;
     const int storage = ctx->cfg.storage;
-    const RecordLayout L = record_layout(storage, n1, n2);
-    const size_t n = tree->n_leaves;
+    const RecordLayout L = record_layout(latent ? FPO_STORAGE_F32 : storage, n1, n2);
+    const size_t n = latent ? 0 : tree->n_leaves;  // latent storage keeps no coefficient records
     // Reorder the coefficients into breadth-first leaf order, split into the
     // density and the SH record arrays (zero padded), encoded in the storage
     // precision; FP8 codes hold coefficient / scale with a per-leaf scale
@@ -251,7 +260,7 @@ int fpo_upload_tree(fpo_ctx *ctx, const fpo_tree_desc *tree)
         ctx->free_tree();
         return st;
     }
-    ctx->n_leaves = (uint32_t)n;
+    ctx->n_leaves = tree->n_leaves;
     ctx->n_nodes = (uint32_t)n_nodes;
     ctx->root_kind = pk.root_kind;
     ctx->depth = pk.depth;
@@ -400,6 +409,8 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
     const bool mat = mode == FPO_IDFT_MATERIALISE && ctx->n_leaves > 0;
     if (!mat && ctx->n_leaves > 0 && ctx->cfg.storage != FPO_STORAGE_F32)
         return fail(FPO_ERR_UNSUPPORTED, "the fused IDFT reads FP32 records only; use the table mode");
+    if (mat && ctx->cfg.storage == FPO_STORAGE_LATENT && !ctx->has_latents)
+        return fail(FPO_ERR_INVALID_ARG, "LATENT storage: call fpo_set_latents before rendering");
     if (!mat && !fused_supported(ctx->cfg.n1, ctx->cfg.n2))
         return fail(FPO_ERR_UNSUPPORTED, "the fused IDFT supports (n1, n2) in {(31,5), (11,5), (21,5), (31,11)}");
 
@@ -421,7 +432,27 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
         if ((e = rec(1)) != cudaSuccess || (e = rec(2)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
         return FPO_OK;
     }
-    if (mat) {
+    if (mat && ctx->cfg.storage == FPO_STORAGE_LATENT) {
+        const int nc = ctx->cfg.n1 + 27 * ctx->cfg.n2;
+        LatentParams lp{};
+        lp.latents = ctx->d_latents;
+        lp.w1 = ctx->d_dec_w;
+        lp.w2 = ctx->d_dec_w + 64 * 32;
+        lp.w3 = ctx->d_dec_w + 64 * 32 + 64 * 64;
+        lp.b1 = ctx->d_dec_b;
+        lp.b2 = ctx->d_dec_b + 64;
+        lp.b3 = ctx->d_dec_b + 128;
+        (void)nc;
+        lp.n1 = ctx->cfg.n1;
+        lp.n2 = ctx->cfg.n2;
+        lp.t = rays->t;
+        lp.period_T = ctx->cfg.period_T;
+        lp.n_leaves = ctx->n_leaves;
+        lp.table = ctx->d_table;
+        lp.status = ctx->d_status;
+        int ce = launch_latent_table(lp, ctx->sm_count, s);
+        if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "latent decode launch");
+    } else if (mat) {
         MaterialiseParams mp{};
         const RecordLayout L = record_layout(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2);
         mp.sig = ctx->d_sig;
@@ -480,6 +511,38 @@ int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts
     q.dL_dcoeffs = dL_dcoeffs;
     const int ce = launch_backward(q, ctx->sm_count, cuda_stream);
     if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "backward launch");
+    return FPO_OK;
+}
+
+int fpo_set_latents(fpo_ctx *ctx, const uint16_t *latents, const fpo_decoder *dec, void *cuda_stream)
+{
+    if (!ctx || !dec) return fail(FPO_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->has_tree) return fail(FPO_ERR_NO_TREE, "set_latents before fpo_upload_tree");
+    if (ctx->cfg.storage != FPO_STORAGE_LATENT) return fail(FPO_ERR_UNSUPPORTED, "context storage is not LATENT");
+    if (!dec->w1 || !dec->b1 || !dec->w2 || !dec->b2 || !dec->w3 || !dec->b3 || (ctx->n_leaves && !latents))
+        return fail(FPO_ERR_INVALID_ARG, "NULL array");
+    DeviceGuard g(ctx->cfg.device);
+    if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
+    const int nc = ctx->cfg.n1 + 27 * ctx->cfg.n2;
+    const size_t nw = 64 * 32 + 64 * 64 + (size_t)nc * 64, nb = 64 + 64 + (size_t)nc;
+    cudaError_t e = cudaSuccess;
+    if (!ctx->d_dec_w) e = cudaMalloc((void **)&ctx->d_dec_w, nw * 2);
+    if (e == cudaSuccess && !ctx->d_dec_b) e = cudaMalloc((void **)&ctx->d_dec_b, nb * 4);
+    if (e == cudaSuccess && !ctx->d_latents && ctx->n_leaves)
+        e = cudaMalloc((void **)&ctx->d_latents, (size_t)ctx->n_leaves * 64);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(latents)");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    struct { void *dst; const void *src; size_t bytes; } cp[6] = {
+        {ctx->d_dec_w, dec->w1, 64 * 32 * 2}, {ctx->d_dec_w + 64 * 32, dec->w2, 64 * 64 * 2},
+        {ctx->d_dec_w + 64 * 32 + 64 * 64, dec->w3, (size_t)nc * 64 * 2}, {ctx->d_dec_b, dec->b1, 64 * 4},
+        {ctx->d_dec_b + 64, dec->b2, 64 * 4}, {ctx->d_dec_b + 128, dec->b3, (size_t)nc * 4}};
+    for (auto &c : cp) {
+        e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "decoder copy");
+    }
+    const int ce = launch_gather_rows(latents, ctx->d_latents, ctx->d_perm, ctx->n_leaves, 64, ctx->sm_count, s);
+    if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "latent gather");
+    ctx->has_latents = true;
     return FPO_OK;
 }
 

@@ -179,6 +179,25 @@ struct LatentParams {
 
 int launch_latent_table(const LatentParams &p, int sm_count, void *stream);
 
+struct DecoderGradParams {
+    fpo_mlp w, g;             // FP32 weights; gradients (accumulated)
+    const uint32_t *rows;     // [batch] leaf rows (distinct)
+    uint32_t batch;
+    const float *latents;     // [N][32]
+    const float *targets;     // [N][nc]
+    const float *coef_weight; // [nc]
+    const float *extra_dy;    // [N][nc] or nullptr
+    float *dlatents;          // [batch][32]
+    double *loss;             // accumulated, or nullptr
+    int nc;
+};
+int launch_decoder_grad(const DecoderGradParams &p, int sm_count, void *stream);
+int launch_gather_rows(const void *src, void *dst, const uint32_t *perm, uint32_t n, uint32_t bytes,
+                       int sm_count, void *stream);
+int decoder_grad_max_coeffs();
+int launch_adam(float *param, const float *grad, float *m, float *v, uint64_t n, const uint32_t *rows, uint32_t dim,
+                float lr, float b1, float b2, float eps, uint32_t step, int sm_count, void *stream);
+
 struct BackwardParams {
     TraverseParams tp;          // rays, tree and options as for the fused forward
     const float *out_rgb;       // forward colour [rays][3]

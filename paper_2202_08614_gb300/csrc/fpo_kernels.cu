@@ -1104,6 +1104,32 @@ int launch_backward(const BackwardParams &q, int sm_count, void *stream)
 }
 
 // ---------------------------------------------------------------------------
+// Rows of `bytes` bytes (a multiple of 16) from upload order to internal
+// leaf order: dst[i] = src[perm[i]].
+
+__global__ void gather_rows_kernel(const uint4 *__restrict__ src, uint4 *__restrict__ dst,
+                                   const uint32_t *__restrict__ perm, uint32_t n, uint32_t words)
+{
+    const uint64_t total = (uint64_t)n * words;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = (uint32_t)(g / words), w = (uint32_t)(g % words);
+        dst[g] = __ldg(src + (size_t)perm[i] * words + w);
+    }
+}
+
+int launch_gather_rows(const void *src, void *dst, const uint32_t *perm, uint32_t n, uint32_t bytes,
+                       int sm_count, void *stream)
+{
+    if (n == 0) return (int)cudaSuccess;
+    const uint32_t words = bytes / 16;
+    uint64_t blocks = ((uint64_t)n * words + 255) / 256;
+    if (blocks > (uint64_t)sm_count * 32) blocks = (uint64_t)sm_count * 32;
+    gather_rows_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+        static_cast<const uint4 *>(src), static_cast<uint4 *>(dst), perm, n, words);
+    return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Canonical coefficients (device, upload order) -> FP32 leaf records.
 // One warp per leaf: lanes stride over the n1 + 27 n2 values (coalesced).
 

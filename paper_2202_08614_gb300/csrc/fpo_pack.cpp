@@ -35,8 +35,7 @@ std::string fmt(const char *f, long long a, long long b = 0, long long c = 0)
 
 int validate_and_pack(const fpo_tree_desc *tree, int n1, int n2, PackedTree *out, std::string *err)
 {
-    (void)n1;
-    (void)n2;
+    (void)n2;  // n1 == 0 marks a tree without coefficients (latent storage)
     if (!tree) { *err = "tree description is NULL"; return FPO_ERR_INVALID_ARG; }
     const uint32_t n = tree->n_leaves;
     if (tree->max_depth > (uint32_t)MAX_DEPTH) {
@@ -49,7 +48,7 @@ int validate_and_pack(const fpo_tree_desc *tree, int n1, int n2, PackedTree *out
         *err = "aabb_size must be finite and > 0, aabb_min finite";
         return FPO_ERR_INVALID_ARG;
     }
-    if (n > 0 && (!tree->leaf_depth || !tree->leaf_xyz || !tree->coeffs)) {
+    if (n > 0 && (!tree->leaf_depth || !tree->leaf_xyz || (!tree->coeffs && n1 > 0))) {
         *err = "leaf_depth, leaf_xyz and coeffs must be non-NULL when n_leaves > 0";
         return FPO_ERR_INVALID_ARG;
     }

@@ -22,7 +22,7 @@ ERRORS = {
     -5: "FPO_ERR_NO_TREE", -6: "FPO_ERR_TRAVERSAL_LIMIT", -7: "FPO_ERR_VISIT_OVERFLOW",
     -8: "FPO_ERR_UNSUPPORTED", -9: "FPO_ERR_DEVICE_TIMEOUT",
 }
-STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "fp8": 3}
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "fp8": 3, "latent": 4}
 IDFT = {"auto": 0, "fused": 1, "materialise": 2}
 RAYS_CAMERA, RAYS_EXPLICIT = 0, 1
 FLAG_RECORD_VISITS, FLAG_OUT_T, FLAG_MARK_LEAVES, FLAG_STATS = 1, 2, 4, 8
@@ -31,7 +31,8 @@ FLAG_RECORD_VISITS, FLAG_OUT_T, FLAG_MARK_LEAVES, FLAG_STATS = 1, 2, 4, 8
 EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
            "fpo_render_backward", "fpo_status_sync", "fpo_tree_info_get", "fpo_destroy",
            "fpo_last_error", "fpo_version", "fpo_render_noalloc", "fpo_set_coeffs",
-           "fpo_dft_leaves", "fpo_union_trees", "fpo_latent_table"]
+           "fpo_dft_leaves", "fpo_union_trees", "fpo_latent_table", "fpo_decoder_grad",
+           "fpo_adam", "fpo_set_latents"]
 
 
 class FPOError(RuntimeError):
@@ -77,6 +78,11 @@ class Decoder(C.Structure):
                 ("w3", C.c_void_p), ("b3", C.c_void_p)]
 
 
+class Mlp(C.Structure):
+    _fields_ = [("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
+                ("w3", C.c_void_p), ("b3", C.c_void_p)]
+
+
 class TreeInfo(C.Structure):
     _fields_ = [("n_leaves", C.c_uint32), ("n_nodes", C.c_uint32), ("max_depth", C.c_uint32),
                 ("n_smem_nodes", C.c_uint32), ("node_bytes", C.c_uint64),
@@ -105,6 +111,11 @@ def lib():
         L.fpo_dft_leaves.argtypes = [C.c_int32, C.c_int32, C.c_uint32, C.c_uint32, P, P, P]
         L.fpo_latent_table.argtypes = [C.POINTER(Decoder), C.c_int32, C.c_int32, C.c_double,
                                        C.c_double, C.c_uint32, P, P, P, P]
+        L.fpo_decoder_grad.argtypes = [C.POINTER(Mlp), C.c_int32, C.c_int32, C.c_uint32, P, P, P, P,
+                                       P, C.POINTER(Mlp), P, P, P]
+        L.fpo_adam.argtypes = [P, P, P, P, C.c_uint64, P, C.c_uint32, C.c_float, C.c_float,
+                               C.c_float, C.c_float, C.c_uint32, P]
+        L.fpo_set_latents.argtypes = [P, P, C.POINTER(Decoder), P]
         L.fpo_union_trees.argtypes = [C.c_uint32, P, C.c_uint32, C.POINTER(C.c_uint32), P, P, P,
                                       C.c_uint32]
         L.fpo_status_sync.argtypes = [P, P]
@@ -296,6 +307,21 @@ class Renderer:
         assert c.is_cuda and c.dtype.is_floating_point and c.is_contiguous()
         check(lib().fpo_set_coeffs(self.h, C.c_void_p(c.data_ptr()),
                                    C.c_void_p(_stream_handle(stream))))
+
+    def set_latents(self, latents_f16, w1, b1, w2, b2, w3, b3, stream=None):
+        """LATENT storage: per-leaf FP16 latents [n_leaves, 32] (CUDA, upload
+        order) and the decoder (weights cast to BF16, biases FP32)."""
+        import torch
+
+        lat = latents_f16.contiguous()
+        assert lat.dtype == torch.float16 and lat.is_cuda
+        ws = [w.detach().to(torch.bfloat16).contiguous() for w in (w1, w2, w3)]
+        bs = [b.detach().float().contiguous() for b in (b1, b2, b3)]
+        dec = Decoder(ws[0].data_ptr(), bs[0].data_ptr(), ws[1].data_ptr(), bs[1].data_ptr(),
+                      ws[2].data_ptr(), bs[2].data_ptr())
+        check(lib().fpo_set_latents(self.h, C.c_void_p(lat.data_ptr()), C.byref(dec),
+                                    C.c_void_p(_stream_handle(stream))))
+        torch.cuda.current_stream().synchronize()  # the copies read ws/bs
 
     def render_backward(self, out_rgb, dL_drgb, dL_dcoeffs, camera=None, t=0.0, rays_o=None,
                         rays_d=None, t_per_ray=None, bg=(1.0, 1.0, 1.0), stop_T=1e-4, stream=None):

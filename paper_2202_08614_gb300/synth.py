@@ -371,3 +371,56 @@ def frame_schedule(n_frames: int, seed: int = 0, n_cams: int = 16, n_t: int = 60
     perm = rng.permutation(n_cams * n_t)
     return [(int(p % n_cams), float(p // n_cams)) for p in perm[:n_frames]] if n_frames <= perm.size \
         else [(int(p % n_cams), float(p // n_cams)) for p in np.resize(perm, n_frames)]
+
+
+# --------------------------------------------------------------------------
+# smooth animated fields (per-frame values of the leaves, for generation)
+
+
+def smooth_frame_values(leaf_depth, leaf_xyz, body, n_frames: int = 60, seed: int = 0,
+                        chunk: int = 1 << 17, device=None):
+    """Per-frame values [n_frames, n, 28] (sigma, z_{c,k}) of the leaves of a
+    union octree under the animated capsule body `body` = (a, b, radii)
+    (from capsule_body): the values a per-frame octree would hold.
+
+    sigma(p, f) = 50 smoothstep(-sdf_f(p) / w), sdf_f the signed distance to
+    the union of capsules at frame f (f = 1..n_frames, frame f uses the body
+    at f mod 60), w = 2 finest cells; z_{c,0} = 1.5 sin(2 pi a_c . p + 2 pi f / T + phi_c),
+    z_{c,k} = 0.3 sin(2 pi a_ck . p + 4 pi f / T + phi_ck) for k >= 1 (at most
+    two temporal cycles, so n2 = 5 Fourier terms hold them exactly).
+    Draw order (default_rng(seed)): a [3, 9, 3] ~ N(0, 1.5), phi [3, 9] ~ U(0, 2 pi).
+    Returns a torch tensor on `device` (default: CUDA if available).
+    """
+    import torch
+
+    dev = torch.device(device or ("cuda" if torch.cuda.is_available() else "cpu"))
+    rng = np.random.default_rng(seed)
+    freq = torch.as_tensor(rng.normal(0.0, 1.5, size=(3, 9, 3)), dtype=torch.float32, device=dev)
+    phase = torch.as_tensor(rng.uniform(0.0, 2 * np.pi, size=(3, 9)), dtype=torch.float32, device=dev)
+    A, B, R = (torch.as_tensor(np.asarray(v), dtype=torch.float32, device=dev) for v in body)
+    depth = int(np.max(leaf_depth)) if len(leaf_depth) else 0
+    w = 2.0 / (1 << max(depth, 1))
+    n = len(leaf_depth)
+    out = torch.empty((n_frames, n, 28), dtype=torch.float32, device=dev)
+    amp = torch.full((9,), 0.3, device=dev)
+    amp[0] = 1.5
+    tcyc = torch.ones(9, device=dev) * 2.0
+    tcyc[0] = 1.0
+    for s0 in range(0, n, chunk):
+        xyz = torch.as_tensor(np.asarray(leaf_xyz[s0:s0 + chunk], np.float64), dtype=torch.float32, device=dev)
+        dd = torch.as_tensor(np.asarray(leaf_depth[s0:s0 + chunk], np.int64), device=dev)
+        p = (xyz + 0.5) / (2.0 ** dd.float())[:, None]  # [m, 3]
+        spatial = 2 * np.pi * torch.einsum("md,ckd->mck", p, freq) + phase  # [m, 3, 9]
+        for f in range(1, n_frames + 1):
+            fi = f % A.shape[1]
+            a, b = A[:, fi], B[:, fi]  # [C, 3]
+            ab = b - a
+            ap = p[:, None, :] - a[None]
+            tt = torch.clamp((ap * ab).sum(-1) / (ab * ab).sum(-1), 0.0, 1.0)
+            dist = torch.linalg.norm(ap - tt[..., None] * ab, dim=-1) - R  # [m, C]
+            sdf = dist.min(dim=1).values
+            u = torch.clamp((-sdf / w + 1.0) * 0.5, 0.0, 1.0)
+            out[f - 1, s0:s0 + chunk, 0] = 50.0 * u * u * (3.0 - 2.0 * u)
+            z = amp * torch.sin(spatial + 2 * np.pi * tcyc * f / n_frames)  # [m, 3, 9]
+            out[f - 1, s0:s0 + chunk, 1:] = z.reshape(-1, 27)
+    return out

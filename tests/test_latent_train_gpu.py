@@ -1,0 +1,160 @@
+"""Training kernels of the latent decoder (fpo_decoder_grad, fpo_adam)
+against the FP64 reference, the LATENT storage render path, and a small
+training run on coefficients produced by the Fourier PlenOctree generation
+(smooth animated fields -> per-leaf DFT)."""
+
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import gpu_util as gu
+from oracle import latent as olat
+from paper_2202_08614_gb300 import fpo, synth
+from paper_2202_08614_gb300.latent import LatentModel
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+N1, N2 = 31, 5
+NC = N1 + 27 * N2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def test_decoder_grad_matches_reference():
+    rng = np.random.default_rng(0)
+    n, b = 2000, 333
+    m = LatentModel(n, seed=1)
+    m.p["b1"].copy_(torch.as_tensor(rng.normal(size=64) * 0.1))
+    m.p["b3"].copy_(torch.as_tensor(rng.normal(size=NC)))
+    tgt = torch.as_tensor(rng.normal(size=(n, NC)), dtype=torch.float32, device="cuda")
+    cw = torch.as_tensor(rng.uniform(0.5, 2, NC), dtype=torch.float32, device="cuda")
+    extra = torch.as_tensor(rng.normal(size=(n, NC)) * 0.01, dtype=torch.float32, device="cuda")
+    rows = torch.as_tensor(rng.permutation(n)[:b], dtype=torch.int32, device="cuda")
+    dl, loss = m.grad(rows, tgt, cw, extra_dy=extra)
+    torch.cuda.synchronize()
+    P = {k: v.double().cpu().numpy() for k, v in m.p.items()}
+    r = rows.cpu().numpy()
+    L, dx, g = olat.loss_grad(P["lat"][r], P["w1"], P["b1"], P["w2"], P["b2"], P["w3"], P["b3"],
+                              tgt.double().cpu().numpy()[r], cw.double().cpu().numpy())
+    # the extra dL/dy enters like the L2 term's 2 cw (y - t)
+    Lx, dxx, gx = olat.loss_grad(P["lat"][r], P["w1"], P["b1"], P["w2"], P["b2"], P["w3"], P["b3"],
+                                 np.zeros((b, NC)), np.ones(NC))
+    y = olat.decode(P["lat"][r], P["w1"], P["b1"], P["w2"], P["b2"], P["w3"], P["b3"])
+    e = extra.double().cpu().numpy()[r]
+    assert abs(loss.item() - L) <= 1e-4 * L
+    # linear term: gradients of sum(e . y) = back-propagate dy = e
+    _, dxe, ge = _backprop_dy(P, r, e)
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel(dl.double().cpu().numpy(), dx + dxe) <= 1e-4
+    for k in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        assert rel(m.g[k].double().cpu().numpy(), g[k] + ge[k]) <= 1e-4, k
+
+
+def _backprop_dy(P, r, dy):
+    x = P["lat"][r]
+    z1 = x @ P["w1"].T + P["b1"]
+    h1 = np.maximum(z1, 0)
+    z2 = h1 @ P["w2"].T + P["b2"]
+    h2 = np.maximum(z2, 0)
+    g = {"w3": dy.T @ h2, "b3": dy.sum(0)}
+    d2 = (dy @ P["w3"]) * (z2 > 0)
+    g["w2"], g["b2"] = d2.T @ h1, d2.sum(0)
+    d1 = (d2 @ P["w2"]) * (z1 > 0)
+    g["w1"], g["b1"] = d1.T @ x, d1.sum(0)
+    return None, d1 @ P["w1"], g
+
+
+def test_adam_dense_and_rows():
+    rng = np.random.default_rng(2)
+    p0 = rng.normal(size=(50, 8)).astype(np.float32)
+    dev = lambda a: torch.as_tensor(np.asarray(a, np.float32), device="cuda")
+    p, m, v = dev(p0), dev(np.zeros_like(p0)), dev(np.zeros_like(p0))
+    pr, mr, vr = p0.astype(np.float64), np.zeros_like(p0, np.float64), np.zeros_like(p0, np.float64)
+    for step in (1, 2, 3):
+        g = rng.normal(size=p0.shape).astype(np.float32)
+        fpo.check(fpo.lib().fpo_adam(C.c_void_p(p.data_ptr()), C.c_void_p(dev(g).data_ptr()),
+                                     C.c_void_p(m.data_ptr()), C.c_void_p(v.data_ptr()), p0.size, None,
+                                     0, 0.01, 0.9, 0.999, 1e-8, step, None))
+        torch.cuda.synchronize()
+        mr = 0.9 * mr + 0.1 * g
+        vr = 0.999 * vr + 0.001 * g * g
+        pr -= 0.01 * (mr / (1 - 0.9 ** step)) / (np.sqrt(vr / (1 - 0.999 ** step)) + 1e-8)
+    np.testing.assert_allclose(p.cpu().numpy(), pr, atol=1e-5)
+    rows = np.array([3, 17, 40], np.int32)
+    q = dev(p0)
+    g = rng.normal(size=(3, 8)).astype(np.float32)
+    mq, vq = dev(np.zeros_like(p0)), dev(np.zeros_like(p0))
+    fpo.check(fpo.lib().fpo_adam(C.c_void_p(q.data_ptr()), C.c_void_p(dev(g).data_ptr()),
+                                 C.c_void_p(mq.data_ptr()), C.c_void_p(vq.data_ptr()), 24,
+                                 C.c_void_p(torch.as_tensor(rows, device="cuda").data_ptr()), 8,
+                                 0.01, 0.9, 0.999, 1e-8, 1, None))
+    qn = q.cpu().numpy()
+    untouched = np.setdiff1d(np.arange(50), rows)
+    assert np.array_equal(qn[untouched], p0[untouched])
+    np.testing.assert_allclose(qn[rows], p0[rows] - 0.01 * np.sign(g), atol=1e-5)
+
+
+def _smooth_tree(depth=6, seed=0):
+    rng = np.random.default_rng(seed)
+    body = synth.capsule_body(rng)
+    xyz = synth.capsule_union_leaves(*body, depth=depth)
+    d = np.full(xyz.shape[0], depth, np.uint8)
+    vals = synth.smooth_frame_values(d, xyz, body)
+    coeffs = fpo.dft_leaves(vals, N1, N2)
+    return d, xyz, coeffs
+
+
+def test_latent_storage_render_matches_decoded_coefficients():
+    d, xyz, _ = _smooth_tree(5)
+    n = d.shape[0]
+    m = LatentModel(n, seed=3)
+    m.p["b3"][0] = 30.0
+    lat, w1, b1, w2, b2, w3, b3 = m.inference_arrays()
+    # what the tensor-core decoder sees: FP16 latents, BF16 weights
+    P = [x.double().cpu().numpy() for x in (lat.float(), w1.bfloat16().float(), b1, w2.bfloat16().float(),
+                                             b2, w3.bfloat16().float(), b3)]
+    co = olat.decode(*P).astype(np.float32)
+    tree = synth.Tree(d, xyz, co, 5)
+    cam = synth.Camera(eye=synth.sphere_eye(60, 15), width=64, height=48)
+    r = fpo.Renderer(storage="latent")
+    r.upload(synth.Tree(d, xyz, np.zeros((0, NC), np.float32), 5))
+    r.set_latents(lat, w1, b1, w2, b2, w3, b3)
+    img = r.render(camera=cam, t=21.0)["rgb"].cpu().numpy()
+    r.status()
+    r.close()
+    ref = gu.oracle.render(gu.oracle_tree(tree), co, camera=cam, t=21.0)["rgb"]
+    assert np.abs(img - ref).max() < 2e-2  # FP16 activations in the decoder
+    assert np.mean((img - ref) ** 2) < 1e-5
+
+
+def test_training_fits_generated_coefficients():
+    d, xyz, coeffs = _smooth_tree(6)
+    n = d.shape[0]
+    m = LatentModel(n, seed=0)
+    m.init_output_bias(coeffs)
+    hist = m.fit(coeffs, steps=1500, batch=8192, lr_w=2e-3, lr_lat=2e-2, log_every=500)
+    print("training loss", hist)
+    assert hist[-1][1] < 0.05 * hist[0][1]
+    lat, *w = m.inference_arrays()
+    r = fpo.Renderer(storage="latent")
+    r.upload(synth.Tree(d, xyz, np.zeros((0, NC), np.float32), 6))
+    r.set_latents(lat, *w)
+    cam = synth.ring_cameras(16, 96, 64)[3]
+    img = r.render(camera=cam, t=17.0)["rgb"].cpu().numpy()
+    r.status()
+    r.close()
+    ref = gu.oracle.render(gu.oracle_tree(synth.Tree(d, xyz, coeffs.cpu().numpy(), 6)),
+                           coeffs.cpu().numpy(), camera=cam, t=17.0)["rgb"]
+    psnr = 10 * np.log10(1.0 / np.mean((img - ref) ** 2))
+    print(f"latent render PSNR vs FP64 oracle of the generated FPO: {psnr:.2f} dB")
+    assert psnr > 25.0

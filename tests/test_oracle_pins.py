@@ -491,3 +491,42 @@ def test_dft_of_constant_and_single_tone():
     t = np.arange(1, T + 1)
     k = oracle.dft(0.7 * np.sin(2 * np.pi * 2 * t / T), 7)[0]  # frequency 2 -> odd index 3
     np.testing.assert_allclose(k, [0, 0, 0, 0.7, 0, 0, 0], atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# latent decoder reference: its gradient against central differences
+
+
+def test_latent_loss_gradient_matches_finite_differences():
+    from oracle import latent as olat
+
+    rng = np.random.default_rng(12)
+    nc = 13
+    w = [rng.normal(size=(64, 32)) / 6, rng.normal(size=64) * 0.1, rng.normal(size=(64, 64)) / 8,
+         rng.normal(size=64) * 0.1, rng.normal(size=(nc, 64)) / 8, rng.normal(size=nc)]
+    x = rng.normal(size=(5, 32))
+    tgt = rng.normal(size=(5, nc))
+    cw = rng.uniform(0.5, 2.0, nc)
+    L, dx, g = olat.loss_grad(x, *w, tgt, cw)
+    names = ["w1", "b1", "w2", "b2", "w3", "b3"]
+
+    def f(ws, xx):
+        return olat.loss_grad(xx, *ws, tgt, cw)[0]
+
+    eps = 1e-6
+    for k, name in enumerate(names):
+        for _ in range(6):
+            idx = tuple(rng.integers(0, s) for s in w[k].shape)
+            wp = [a.copy() for a in w]
+            wm = [a.copy() for a in w]
+            wp[k][idx] += eps
+            wm[k][idx] -= eps
+            fd = (f(wp, x) - f(wm, x)) / (2 * eps)
+            assert abs(g[name][idx] - fd) <= 1e-6 * max(1.0, abs(fd)), name
+    for _ in range(10):
+        idx = tuple(rng.integers(0, s) for s in x.shape)
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += eps
+        xm[idx] -= eps
+        fd = (f(w, xp) - f(w, xm)) / (2 * eps)
+        assert abs(dx[idx] - fd) <= 1e-6 * max(1.0, abs(fd))
