@@ -39,6 +39,17 @@ class LatentModel:
     def _mlp(self, d):
         return fpo.Mlp(*(d[k].data_ptr() for k in ("w1", "b1", "w2", "b2", "w3", "b3")))
 
+    def default_weights(self, device, sigma_weight: float = 0.05):
+        """Squared-error weights by each coefficient's first-order effect on a
+        composited pixel: a density error moves alpha by about delta * d_sigma
+        (delta ~ a fine cell), an SH error moves the colour by about
+        S'(.) Y_00 d_z ~ 0.07 d_z; both scaled by |IDFT_i| <= 1."""
+        import torch
+
+        w = torch.ones(self.nc, device=device)
+        w[: self.n1] = sigma_weight
+        return (w / self.nc).contiguous()
+
     def init_output_bias(self, targets):
         self.p["b3"].copy_(targets.mean(0))
 
@@ -88,8 +99,7 @@ class LatentModel:
 
         dev = targets.device
         if coef_weight is None:
-            coef_weight = 1.0 / (targets.var(0) + 1e-6)
-            coef_weight = (coef_weight / coef_weight.sum()).float().contiguous()
+            coef_weight = self.default_weights(dev)
         g = torch.Generator(device=dev).manual_seed(seed)
         perm = torch.randperm(self.n, generator=g, device=dev).to(torch.int32)
         at, hist = 0, []

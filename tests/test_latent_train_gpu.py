@@ -82,7 +82,8 @@ def test_adam_dense_and_rows():
     pr, mr, vr = p0.astype(np.float64), np.zeros_like(p0, np.float64), np.zeros_like(p0, np.float64)
     for step in (1, 2, 3):
         g = rng.normal(size=p0.shape).astype(np.float32)
-        fpo.check(fpo.lib().fpo_adam(C.c_void_p(p.data_ptr()), C.c_void_p(dev(g).data_ptr()),
+        gd = dev(g)  # kept alive until the kernel has run
+        fpo.check(fpo.lib().fpo_adam(C.c_void_p(p.data_ptr()), C.c_void_p(gd.data_ptr()),
                                      C.c_void_p(m.data_ptr()), C.c_void_p(v.data_ptr()), p0.size, None,
                                      0, 0.01, 0.9, 0.999, 1e-8, step, None))
         torch.cuda.synchronize()
@@ -94,10 +95,11 @@ def test_adam_dense_and_rows():
     q = dev(p0)
     g = rng.normal(size=(3, 8)).astype(np.float32)
     mq, vq = dev(np.zeros_like(p0)), dev(np.zeros_like(p0))
-    fpo.check(fpo.lib().fpo_adam(C.c_void_p(q.data_ptr()), C.c_void_p(dev(g).data_ptr()),
+    gd, rd = dev(g), torch.as_tensor(rows, device="cuda")
+    fpo.check(fpo.lib().fpo_adam(C.c_void_p(q.data_ptr()), C.c_void_p(gd.data_ptr()),
                                  C.c_void_p(mq.data_ptr()), C.c_void_p(vq.data_ptr()), 24,
-                                 C.c_void_p(torch.as_tensor(rows, device="cuda").data_ptr()), 8,
-                                 0.01, 0.9, 0.999, 1e-8, 1, None))
+                                 C.c_void_p(rd.data_ptr()), 8, 0.01, 0.9, 0.999, 1e-8, 1, None))
+    torch.cuda.synchronize()
     qn = q.cpu().numpy()
     untouched = np.setdiff1d(np.arange(50), rows)
     assert np.array_equal(qn[untouched], p0[untouched])
