@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the BF16 and latent-decoder variant measurements")
+    ap.add_argument("--variant-frames", type=int, default=100)
+    ap.add_argument("--latent-steps", type=int, default=20000)
     return ap.parse_args()
 
 
@@ -207,6 +211,96 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def time_frames(r, cams, frames, out, torch):
+    """Mean CUDA-event time (ms) of rendering `frames` (after 3 warm-up frames)."""
+    for k, t in frames[:3]:
+        r.render(camera=cams[k], t=t, out=out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for k, t in frames:
+        r.render(camera=cams[k], t=t, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    r.status()
+    return a.elapsed_time(b) / len(frames)
+
+
+def sampled_psnr(r, ot, coeffs, cams, frames, out, torch, n_px):
+    """PSNR of rendered frames against the FP64 oracle on sampled pixels."""
+    import oracle
+
+    errs = []
+    for i, (k, t) in enumerate(frames):
+        img = r.render(camera=cams[k], t=t, out=out)["rgb"]
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(i)
+        w = cams[k].width
+        sel = np.concatenate([rng.integers(0, n_px, 3000), (cams[k].height // 2) * w + np.arange(0, w, 2)])
+        ref = oracle.render(ot, coeffs, camera=cams[k], t=t, sel=sel)["rgb"]
+        errs.append((img.cpu().numpy()[sel].astype(np.float64) - ref) ** 2)
+    mse = float(np.mean(np.concatenate(errs)))
+    return 10 * np.log10(1.0 / mse) if mse > 0 else float("inf")
+
+
+def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms):
+    """BF16 storage on the same tree, and the latent decoder (trained on
+    coefficients produced by the generation: smooth animated fields -> per-
+    leaf DFT) against the plain FP32 renderer of those coefficients."""
+    import oracle
+    from paper_2202_08614_gb300.latent import LatentModel
+
+    res = {}
+    nf = frames[: args.variant_frames]
+    ot = oracle.OracleTree(tree.leaf_depth, tree.leaf_xyz, tree.max_depth)
+    r = fpo.Renderer(storage="bf16")
+    r.upload(tree)
+    ms = time_frames(r, cams, nf, out, torch)
+    res["bf16"] = {"Mrays_s": n_px / ms / 1e3, "fps": 1e3 / ms, "fp32_Mrays_s": n_px / fp32_ms / 1e3,
+                   "psnr_db_vs_fp64_oracle": sampled_psnr(r, ot, tree.coeffs, cams, nf[:2], out, torch, n_px),
+                   "bytes_per_leaf": r.info()["leaf_record_bytes"]}
+    r.close()
+    # latent decoder on generated coefficients (same leaves)
+    body = synth.capsule_body(np.random.default_rng(0))
+    n = tree.n_leaves
+    coeffs = torch.empty((n, 166), dtype=torch.float32, device="cuda")
+    ch = 1 << 19
+    for s0 in range(0, n, ch):
+        vals = synth.smooth_frame_values(tree.leaf_depth[s0:s0 + ch], tree.leaf_xyz[s0:s0 + ch], body)
+        coeffs[s0:s0 + ch] = fpo.dft_leaves(vals)
+        del vals
+    co_np = coeffs.cpu().numpy()
+    gen = synth.Tree(tree.leaf_depth, tree.leaf_xyz, co_np, tree.max_depth)
+    r = fpo.Renderer()
+    r.upload(gen)
+    ms32 = time_frames(r, cams, nf, out, torch)
+    r.close()
+    m = LatentModel(n, seed=0)
+    m.init_output_bias(coeffs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = m.fit(coeffs, steps=args.latent_steps, batch=65536, lr_w=1e-3, lr_lat=5e-2,
+                 log_every=max(1, args.latent_steps // 4))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    r = fpo.Renderer(storage="latent")
+    r.upload(synth.Tree(tree.leaf_depth, tree.leaf_xyz, np.zeros((0, 166), np.float32), tree.max_depth))
+    r.set_latents(*m.inference_arrays())
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    msl = time_frames(r, cams, nf, out, torch)
+    k, t = nf[0]
+    r.render(camera=cams[k], t=t, out=out, events=ev)
+    torch.cuda.synchronize()
+    res["latent"] = {
+        "Mrays_s": n_px / msl / 1e3, "fps": 1e3 / msl, "fp32_same_tree_Mrays_s": n_px / ms32 / 1e3,
+        "psnr_db_vs_fp64_oracle": sampled_psnr(r, ot, co_np, cams, nf[:2], out, torch, n_px),
+        "decode_ms": ev[0].elapsed_time(ev[1]), "train_steps": args.latent_steps, "train_batch": 65536,
+        "train_s": train_s, "train_loss": hist, "bytes_per_leaf": 64,
+        "coefficients": "per-leaf DFT (Eq. 10-12) of smooth animated fields over the same leaves"}
+    r.close()
+    return res
+
+
 def kernel_source_sha():
     h = hashlib.sha256()
     for f in ("fpo_kernels.cu", "fpo_internal.h"):
@@ -356,6 +450,8 @@ def main():
     res["gpu_launches"] = K * (2 if mat else 1)
     res["clocks"] = clk.summary()
     res["tree"] = info
+    if not args.no_variants and args.storage == "f32" and args.idft == "auto":
+        res["variants"] = variants(args, tree, cams, frames[W:], out, torch, fpo, n_px, t_max / K)
     if rank == 0 and not args.no_cpu_baseline:
         v, rays, secs, thr = oracle_sample_rate(tree, cams, frames[W:], args.cpu_seconds)
         res["cpu_baseline"] = {"value": v, "unit": "Mrays/s", "cores": thr, "kind": "oracle",

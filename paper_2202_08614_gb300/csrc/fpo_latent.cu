@@ -39,7 +39,7 @@ constexpr int OFF_W2 = 4096;       // 64 x 64  f16:  8 KB
 constexpr int OFF_W3 = 12288;      // 32 x 64  f16:  4 KB
 constexpr int OFF_A1 = 16384;      // 128 x 32 f16:  8 KB
 constexpr int OFF_A2 = 24576;      // 128 x 64 f16: 16 KB
-constexpr int LT_SMEM = 40960 + 16384;  // + padding: caps residency at 4 CTAs per SM
+constexpr int LT_SMEM = 40960;           // 5 CTAs per SM by shared memory (5 x 64 TMEM columns)
 
 // Byte offset of element (row, k) in a K-major core-matrix layout whose rows
 // hold K elements: core matrix (row / 8, k / 8) at ((row/8) * K/8 + k/8) * 128,
@@ -222,20 +222,25 @@ __global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_c
         return s_fail == 0;
     };
 
+    // this thread's latent row (64 B) of a tile, loaded one tile ahead
+    auto load_row = [&](uint32_t tile, uint4 q[4]) {
+        const uint32_t leaf = tile * LT_M + (uint32_t)m;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) q[j] = make_uint4(0, 0, 0, 0);
+        if (tile < n_tiles && leaf < p.n_leaves) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(p.latents + (size_t)leaf * 32);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[j] = __ldg(src + j);
+        }
+    };
+    uint4 nextq[4];
+    load_row(blockIdx.x, nextq);
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint32_t leaf = tile * LT_M + (uint32_t)m;
         const bool valid = leaf < p.n_leaves;
-        // layer-1 A operand: this thread's latent row (64 B) into the core layout
-        {
-            uint4 q[4] = {};
-            if (valid) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(p.latents + (size_t)leaf * 32);
+        // layer-1 A operand: the latent row into the core layout
 #pragma unroll
-                for (int j = 0; j < 4; ++j) q[j] = __ldg(src + j);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4 *>(lt_smem + OFF_A1 + core_off(m, 8 * j, 32)) = q[j];
-        }
+        for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4 *>(lt_smem + OFF_A1 + core_off(m, 8 * j, 32)) = nextq[j];
         fence_async_smem();
         fence_before();
         __syncthreads();
@@ -268,6 +273,7 @@ __global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_c
         fence_async_smem();
         fence_before();
         __syncthreads();
+        load_row(tile + gridDim.x, nextq);  // in flight while layer 3 runs
         if (!run_layer(sa_a2, sa_w3, 64, 32)) break;
         {
             float o[32];
@@ -308,7 +314,7 @@ int launch_latent_table(const LatentParams &p, int sm_count, void *stream)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, latent_table_kernel, LT_THREADS, LT_SMEM);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) per_sm = 1;
-    if (per_sm > 4) per_sm = 4;  // 4 x 64 TMEM columns <= 512
+    if (per_sm > 8) per_sm = 8;  // 8 x 64 TMEM columns = 512
     const uint32_t n_tiles = (p.n_leaves + LT_M - 1) / LT_M;
     uint64_t blocks = (uint64_t)sm_count * per_sm;
     if (blocks > n_tiles) blocks = n_tiles;

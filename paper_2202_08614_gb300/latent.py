@@ -93,8 +93,9 @@ class LatentModel:
         return loss
 
     def fit(self, targets, steps, batch=65536, lr_w=1e-3, lr_lat=1e-2, coef_weight=None, seed=0,
-            log_every=0):
-        """Weighted L2 training on `targets` [n, nc]; returns the loss history."""
+            log_every=0, decay=0.01):
+        """Weighted L2 training on `targets` [n, nc]; returns the loss history.
+        Learning rates follow a cosine from their start value to `decay` times it."""
         import torch
 
         dev = targets.device
@@ -110,7 +111,8 @@ class LatentModel:
                 at = 0
             rows = perm[at:at + batch]
             at += batch
-            loss = self.step(rows, targets, coef_weight, lr_w, lr_lat)
+            f = decay + (1.0 - decay) * 0.5 * (1.0 + math.cos(math.pi * s / max(1, steps - 1)))
+            loss = self.step(rows, targets, coef_weight, lr_w * f, lr_lat * f)
             if log_every and (s % log_every == 0 or s == steps - 1):
                 hist.append((s, float(loss.item()) / batch))
         return hist

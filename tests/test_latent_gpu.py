@@ -63,7 +63,7 @@ def _emulate(lat, w1, b1, w2, b2, w3, b3, t):
     return o
 
 
-@pytest.mark.parametrize("n", [1, 128, 129, 1000, 70000])
+@pytest.mark.parametrize("n", [1, 128, 129, 1000, 70000, 2_000_003])
 def test_latent_table_matches_references(n):
     w1, b1, w2, b2, w3, b3 = _net(n)
     rng = np.random.default_rng(100 + n)
