@@ -7,15 +7,16 @@
 // (sigma_raw, z_{c,k}), and the kernel writes the same per-frame table as the
 // coefficient IDFT pass: [max(0, sigma), 27 z, 0 x 4] per leaf.
 //
-// Per CTA (128 threads = one warpgroup): the weights are staged once in
-// shared memory in the no-swizzle K-major core-matrix layout (8 rows x 16 B
-// blocks), W3'(t) is computed in the prologue; then for each tile of 128
-// leaves the threads lay the latents out as the A operand, one elected
-// thread issues tcgen05.mma (M = 128, K = 16 per instruction, FP16 x FP16 ->
-// FP32 in TMEM), commits to an mbarrier, and the warps read the accumulator
-// rows back with tcgen05.ld (one row per thread), apply bias and ReLU and
-// write the next layer's A operand.  64 TMEM columns hold every layer's
-// accumulator in turn.
+// Per CTA the weights are staged once in shared memory in the no-swizzle
+// K-major core-matrix layout (8 rows x 16 B blocks) and W3'(t) is computed
+// in the prologue.  Four warpgroups then run independent tile pipelines
+// (own A buffers, own 64 TMEM columns, own mbarrier and named barrier): for
+// each tile of 128 leaves the threads lay the latents out as the A operand,
+// one elected thread issues tcgen05.mma (M = 128, K = 16 per instruction,
+// FP16 x FP16 -> FP32 in TMEM) and commits to the mbarrier, and the warps
+// read the accumulator rows back with tcgen05.ld (one row per thread, a
+// warp's TMEM lane quarter), apply bias and ReLU and write the next layer's
+// A operand.  The 64 columns hold every layer's accumulator in turn.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -28,18 +29,20 @@
 namespace fpo {
 namespace {
 
-constexpr int LT_THREADS = 128;
+constexpr int LT_GROUPS = 4;       // independent warpgroup pipelines per CTA
+constexpr int LT_THREADS = 128 * LT_GROUPS;
 constexpr int LT_M = 128;          // leaves per tile = MMA M
-constexpr uint32_t LT_TMEM_COLS = 64;
+constexpr uint32_t LT_TMEM_COLS = 64 * LT_GROUPS;  // 64 accumulator columns per warpgroup
 constexpr uint64_t LT_WAIT_NS = 2000000000ull;
 
 // Shared-memory layout (bytes), all operands no-swizzle K-major.
 constexpr int OFF_W1 = 0;          // 64 x 32  f16:  4 KB
 constexpr int OFF_W2 = 4096;       // 64 x 64  f16:  8 KB
 constexpr int OFF_W3 = 12288;      // 32 x 64  f16:  4 KB
-constexpr int OFF_A1 = 16384;      // 128 x 32 f16:  8 KB
-constexpr int OFF_A2 = 24576;      // 128 x 64 f16: 16 KB
-constexpr int LT_SMEM = 40960;           // 5 CTAs per SM by shared memory (5 x 64 TMEM columns)
+constexpr int OFF_A1 = 16384;      // per group: 128 x 32 f16:  8 KB
+constexpr int OFF_A2 = 24576;      // per group: 128 x 64 f16: 16 KB
+constexpr int GROUP_BYTES = 24576; // A1 + A2 of one warpgroup
+constexpr int LT_SMEM = 16384 + LT_GROUPS * GROUP_BYTES;
 
 // Byte offset of element (row, k) in a K-major core-matrix layout whose rows
 // hold K elements: core matrix (row / 8, k / 8) at ((row/8) * K/8 + k/8) * 128,
@@ -119,15 +122,20 @@ __device__ __forceinline__ void gemm(uint32_t d_tmem, uint32_t a_saddr, uint32_t
 
 }  // namespace
 
+__device__ __forceinline__ void group_sync(int group)
+{
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + group) : "memory");
+}
+
 __global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_constant__ LatentParams p)
 {
     extern __shared__ __align__(1024) unsigned char lt_smem[];
     __shared__ float s_b1[64], s_b2[64], s_b3[32], s_basis[32];
-    __shared__ uint64_t s_bar;
+    __shared__ uint64_t s_bar[LT_GROUPS];
     __shared__ uint32_t s_tmem;
-    __shared__ int s_fail;
+    __shared__ int s_fail[LT_GROUPS];
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int nc = p.n1 + 27 * p.n2;
+    const int group = tid >> 7, gt = tid & 127;  // warpgroup and thread within it
 
     // --- prologue: basis, weights (bf16 -> f16, core layout), folded layer 3
     const int nb = p.n1 > p.n2 ? p.n1 : p.n2;
@@ -138,11 +146,11 @@ __global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_c
         s_b1[tid] = p.b1[tid];
         s_b2[tid] = p.b2[tid];
     }
-    if (tid == 0) {
-        s_fail = 0;
-        ptx::mbar_init(&s_bar, 1);
-        ptx::fence_barrier_init();
+    if (tid < LT_GROUPS) {
+        s_fail[tid] = 0;
+        ptx::mbar_init(&s_bar[tid], 1);
     }
+    if (tid == 0) ptx::fence_barrier_init();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(ptx::smem_u32(&s_tmem)),
                      "r"(LT_TMEM_COLS)
@@ -173,10 +181,12 @@ __global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_c
             const int h = 8 * j + e;
             float acc = 0.0f;
             if (r == 0) {
-                for (int i = 0; i < p.n1; ++i) acc = fmaf(s_basis[i], __bfloat162float(__ushort_as_bfloat16(p.w3[i * 64 + h])), acc);
+                for (int i = 0; i < p.n1; ++i)
+                    acc = fmaf(s_basis[i], __bfloat162float(__ushort_as_bfloat16(p.w3[i * 64 + h])), acc);
             } else if (r <= 27) {
                 const int row0 = p.n1 + (r - 1) * p.n2;
-                for (int i = 0; i < p.n2; ++i) acc = fmaf(s_basis[i], __bfloat162float(__ushort_as_bfloat16(p.w3[(row0 + i) * 64 + h])), acc);
+                for (int i = 0; i < p.n2; ++i)
+                    acc = fmaf(s_basis[i], __bfloat162float(__ushort_as_bfloat16(p.w3[(row0 + i) * 64 + h])), acc);
             }
             v[e] = acc;
         }
@@ -192,37 +202,42 @@ __global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_c
         }
         s_b3[tid] = acc;
     }
-    (void)nc;
     fence_async_smem();
     fence_before();
     __syncthreads();
     fence_after();
-    const uint32_t tmem = s_tmem;
-    const uint32_t my_lane = tmem + ((uint32_t)(warp * 32) << 16);
+    // this warpgroup's accumulator columns; this warp's lane quarter
+    const uint32_t tmem = s_tmem + 64u * (uint32_t)group;
+    const uint32_t my_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    unsigned char *ga1 = lt_smem + OFF_A1 + group * GROUP_BYTES;
+    unsigned char *ga2 = lt_smem + OFF_A2 + group * GROUP_BYTES;
     const uint32_t sa_w1 = ptx::smem_u32(lt_smem + OFF_W1), sa_w2 = ptx::smem_u32(lt_smem + OFF_W2),
-                   sa_w3 = ptx::smem_u32(lt_smem + OFF_W3), sa_a1 = ptx::smem_u32(lt_smem + OFF_A1),
-                   sa_a2 = ptx::smem_u32(lt_smem + OFF_A2);
+                   sa_w3 = ptx::smem_u32(lt_smem + OFF_W3), sa_a1 = ptx::smem_u32(ga1), sa_a2 = ptx::smem_u32(ga2);
     uint32_t phase = 0;
     const uint32_t n_tiles = (p.n_leaves + LT_M - 1) / LT_M;
-    const int m = tid;  // this thread's accumulator row (TMEM lane) and leaf in the tile
+    const uint32_t first = blockIdx.x * LT_GROUPS + group, step = gridDim.x * LT_GROUPS;
+    const int m = gt;  // this thread's accumulator row (TMEM lane) and leaf in the tile
 
-    // One layer: the elected thread issues the MMAs and commits; everyone
-    // waits on the mbarrier (bounded).  The outcome is made CTA-uniform so
-    // that the collective TMEM loads and barriers below never diverge.
+    // One layer: the group's elected thread issues the MMAs and commits;
+    // the group waits on its mbarrier (bounded).  The outcome is made
+    // group-uniform so that the collective TMEM loads never diverge.
     auto run_layer = [&](uint32_t a_addr, uint32_t b_addr, int K, int N) -> bool {
-        if (tid == 0) {
+        if (gt == 0) {
             fence_after();
             gemm(tmem, a_addr, b_addr, K, N);
-            mma_commit(&s_bar);
+            mma_commit(&s_bar[group]);
         }
-        if (!ptx::mbar_wait_bounded(&s_bar, phase, LT_WAIT_NS)) s_fail = 1;
+        if (!ptx::mbar_wait_bounded(&s_bar[group], phase, LT_WAIT_NS)) s_fail[group] = 1;
         phase ^= 1u;
-        __syncthreads();
+        group_sync(group);
         fence_after();
-        return s_fail == 0;
+        return s_fail[group] == 0;
     };
-
-    // this thread's latent row (64 B) of a tile, loaded one tile ahead
+    auto hand_off = [&]() {  // generic smem writes and TMEM reads before the next MMA
+        fence_async_smem();
+        fence_before();
+        group_sync(group);
+    };
     auto load_row = [&](uint32_t tile, uint4 q[4]) {
         const uint32_t leaf = tile * LT_M + (uint32_t)m;
 #pragma unroll
@@ -234,16 +249,13 @@ __global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_c
         }
     };
     uint4 nextq[4];
-    load_row(blockIdx.x, nextq);
-    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    load_row(first, nextq);
+    for (uint32_t tile = first; tile < n_tiles; tile += step) {
         const uint32_t leaf = tile * LT_M + (uint32_t)m;
         const bool valid = leaf < p.n_leaves;
-        // layer-1 A operand: the latent row into the core layout
 #pragma unroll
-        for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4 *>(lt_smem + OFF_A1 + core_off(m, 8 * j, 32)) = nextq[j];
-        fence_async_smem();
-        fence_before();
-        __syncthreads();
+        for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4 *>(ga1 + core_off(m, 8 * j, 32)) = nextq[j];
+        hand_off();
         if (!run_layer(sa_a1, sa_w1, 32, 64)) break;
         // layer 1 epilogue: bias + ReLU -> layer-2 A operand (MMA 1 is done with A1)
 #pragma unroll
@@ -252,12 +264,10 @@ __global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_c
             tmem_ld16(my_lane + 16 * c, v);
 #pragma unroll
             for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e] + s_b1[16 * c + e], 0.0f);
-            put8(lt_smem + OFF_A2, m, 2 * c, 64, v);
-            put8(lt_smem + OFF_A2, m, 2 * c + 1, 64, v + 8);
+            put8(ga2, m, 2 * c, 64, v);
+            put8(ga2, m, 2 * c + 1, 64, v + 8);
         }
-        fence_async_smem();
-        fence_before();
-        __syncthreads();
+        hand_off();
         if (!run_layer(sa_a2, sa_w2, 64, 64)) break;
         // layer 2 epilogue -> layer-3 A operand, in place (MMA 2 has finished
         // reading A2, and each thread rewrites only its own row)
@@ -267,13 +277,11 @@ __global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_c
             tmem_ld16(my_lane + 16 * c, v);
 #pragma unroll
             for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e] + s_b2[16 * c + e], 0.0f);
-            put8(lt_smem + OFF_A2, m, 2 * c, 64, v);
-            put8(lt_smem + OFF_A2, m, 2 * c + 1, 64, v + 8);
+            put8(ga2, m, 2 * c, 64, v);
+            put8(ga2, m, 2 * c + 1, 64, v + 8);
         }
-        fence_async_smem();
-        fence_before();
-        __syncthreads();
-        load_row(tile + gridDim.x, nextq);  // in flight while layer 3 runs
+        hand_off();
+        load_row(tile + step, nextq);  // in flight while layer 3 runs
         if (!run_layer(sa_a2, sa_w3, 64, 32)) break;
         {
             float o[32];
@@ -292,17 +300,17 @@ __global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_c
             }
         }
         fence_before();
-        __syncthreads();  // the accumulator is free for the next tile's MMA
+        group_sync(group);  // the accumulator is free for the next tile's MMA
     }
-    if (s_fail && tid == 0) {
+    if (s_fail[group] && gt == 0) {
         // an MMA that never signalled: wait once more (bounded) before freeing TMEM
-        ptx::mbar_wait_bounded(&s_bar, phase, LT_WAIT_NS);
+        ptx::mbar_wait_bounded(&s_bar[group], phase, LT_WAIT_NS);
         if (p.status) atomicOr(p.status, STATUS_DEVICE_TIMEOUT);
     }
     __syncthreads();
     fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(LT_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(LT_TMEM_COLS) : "memory");
 }
 
 int launch_latent_table(const LatentParams &p, int sm_count, void *stream)
@@ -314,10 +322,11 @@ int launch_latent_table(const LatentParams &p, int sm_count, void *stream)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, latent_table_kernel, LT_THREADS, LT_SMEM);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) per_sm = 1;
-    if (per_sm > 8) per_sm = 8;  // 8 x 64 TMEM columns = 512
+    if (per_sm > 2) per_sm = 2;  // 2 x 256 TMEM columns = 512
     const uint32_t n_tiles = (p.n_leaves + LT_M - 1) / LT_M;
     uint64_t blocks = (uint64_t)sm_count * per_sm;
-    if (blocks > n_tiles) blocks = n_tiles;
+    const uint64_t need = (n_tiles + LT_GROUPS - 1) / LT_GROUPS;
+    if (blocks > need) blocks = need;
     latent_table_kernel<<<(unsigned)blocks, LT_THREADS, LT_SMEM, (cudaStream_t)stream>>>(p);
     return (int)cudaGetLastError();
 }

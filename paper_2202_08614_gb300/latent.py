@@ -93,9 +93,10 @@ class LatentModel:
         return loss
 
     def fit(self, targets, steps, batch=65536, lr_w=1e-3, lr_lat=1e-2, coef_weight=None, seed=0,
-            log_every=0, decay=0.01):
+            log_every=0, decay=1.0, decay_from=0.7):
         """Weighted L2 training on `targets` [n, nc]; returns the loss history.
-        Learning rates follow a cosine from their start value to `decay` times it."""
+        Learning rates stay at their start value until `decay_from` of the
+        steps, then follow a cosine down to `decay` times it."""
         import torch
 
         dev = targets.device
@@ -111,7 +112,8 @@ class LatentModel:
                 at = 0
             rows = perm[at:at + batch]
             at += batch
-            f = decay + (1.0 - decay) * 0.5 * (1.0 + math.cos(math.pi * s / max(1, steps - 1)))
+            u = max(0.0, (s / max(1, steps - 1) - decay_from) / max(1e-9, 1.0 - decay_from))
+            f = decay + (1.0 - decay) * 0.5 * (1.0 + math.cos(math.pi * min(1.0, u)))
             loss = self.step(rows, targets, coef_weight, lr_w * f, lr_lat * f)
             if log_every and (s % log_every == 0 or s == steps - 1):
                 hist.append((s, float(loss.item()) / batch))
