@@ -279,7 +279,7 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms):
     m.init_output_bias(coeffs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hist = m.fit(coeffs, steps=args.latent_steps, batch=65536, lr_w=1e-3, lr_lat=5e-2,
+    hist = m.fit(coeffs, steps=args.latent_steps, batch=65536, lr_w=1e-3, lr_lat=1e-1, decay=0.05,
                  log_every=max(1, args.latent_steps // 4))
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
