@@ -385,32 +385,37 @@ def smooth_frame_values(leaf_depth, leaf_xyz, body, n_frames: int = 60, seed: in
 
     sigma(p, f) = 50 smoothstep(-sdf_f(p) / w), sdf_f the signed distance to
     the union of capsules at frame f (f = 1..n_frames, frame f uses the body
-    at f mod 60), w = 2 finest cells; z_{c,0} = 1.5 sin(2 pi a_c . p + 2 pi f / T + phi_c),
-    z_{c,k} = 0.3 sin(2 pi a_ck . p + 4 pi f / T + phi_ck) for k >= 1 (at most
-    two temporal cycles, so n2 = 5 Fourier terms hold them exactly).
-    Draw order (default_rng(seed)): a [3, 9, 3] ~ N(0, 1.5), phi [3, 9] ~ U(0, 2 pi).
+    at f mod 60), w = 2 finest cells.  Colour: four shared travelling waves
+    g_m(p, f) = sin(2 pi a_m . p + 2 pi nu_m f / T + phi_m) (nu = 1, 1, 2, 2)
+    mixed per SH slot, z_{c,k} = s_k sum_m M[c,k,m] g_m with s_0 = 1.5 and
+    s_k = 0.3 for k >= 1: the SH coefficients of a radiance field are
+    correlated across colour channels and SH bands, and at most two temporal
+    cycles keep them exact in n2 = 5 Fourier terms.
+    Draw order (default_rng(seed)): a [4, 3] ~ N(0, 1.5), phi [4] ~ U(0, 2 pi),
+    M [3, 9, 4] ~ N(0, 1/2).
     Returns a torch tensor on `device` (default: CUDA if available).
     """
     import torch
 
     dev = torch.device(device or ("cuda" if torch.cuda.is_available() else "cpu"))
     rng = np.random.default_rng(seed)
-    freq = torch.as_tensor(rng.normal(0.0, 1.5, size=(3, 9, 3)), dtype=torch.float32, device=dev)
-    phase = torch.as_tensor(rng.uniform(0.0, 2 * np.pi, size=(3, 9)), dtype=torch.float32, device=dev)
+    freq = torch.as_tensor(rng.normal(0.0, 1.5, size=(4, 3)), dtype=torch.float32, device=dev)
+    phase = torch.as_tensor(rng.uniform(0.0, 2 * np.pi, size=4), dtype=torch.float32, device=dev)
+    mix = torch.as_tensor(rng.normal(0.0, np.sqrt(0.5), size=(3, 9, 4)), dtype=torch.float32, device=dev)
+    nu = torch.tensor([1.0, 1.0, 2.0, 2.0], device=dev)
+    amp = torch.full((9,), 0.3, device=dev)
+    amp[0] = 1.5
+    mix = mix * amp[None, :, None]
     A, B, R = (torch.as_tensor(np.asarray(v), dtype=torch.float32, device=dev) for v in body)
     depth = int(np.max(leaf_depth)) if len(leaf_depth) else 0
     w = 2.0 / (1 << max(depth, 1))
     n = len(leaf_depth)
     out = torch.empty((n_frames, n, 28), dtype=torch.float32, device=dev)
-    amp = torch.full((9,), 0.3, device=dev)
-    amp[0] = 1.5
-    tcyc = torch.ones(9, device=dev) * 2.0
-    tcyc[0] = 1.0
     for s0 in range(0, n, chunk):
         xyz = torch.as_tensor(np.asarray(leaf_xyz[s0:s0 + chunk], np.float64), dtype=torch.float32, device=dev)
         dd = torch.as_tensor(np.asarray(leaf_depth[s0:s0 + chunk], np.int64), device=dev)
         p = (xyz + 0.5) / (2.0 ** dd.float())[:, None]  # [m, 3]
-        spatial = 2 * np.pi * torch.einsum("md,ckd->mck", p, freq) + phase  # [m, 3, 9]
+        spatial = 2 * np.pi * (p @ freq.T) + phase  # [m, 4]
         for f in range(1, n_frames + 1):
             fi = f % A.shape[1]
             a, b = A[:, fi], B[:, fi]  # [C, 3]
@@ -421,6 +426,6 @@ def smooth_frame_values(leaf_depth, leaf_xyz, body, n_frames: int = 60, seed: in
             sdf = dist.min(dim=1).values
             u = torch.clamp((-sdf / w + 1.0) * 0.5, 0.0, 1.0)
             out[f - 1, s0:s0 + chunk, 0] = 50.0 * u * u * (3.0 - 2.0 * u)
-            z = amp * torch.sin(spatial + 2 * np.pi * tcyc * f / n_frames)  # [m, 3, 9]
-            out[f - 1, s0:s0 + chunk, 1:] = z.reshape(-1, 27)
+            g = torch.sin(spatial + 2 * np.pi * nu * f / n_frames)  # [m, 4]
+            out[f - 1, s0:s0 + chunk, 1:] = torch.einsum("mw,ckw->mck", g, mix).reshape(-1, 27)
     return out
