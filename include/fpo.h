@@ -180,6 +180,19 @@ int fpo_upload_tree(fpo_ctx *ctx, const fpo_tree_desc *tree);
 int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
                float *out_rgb, void *cuda_stream);
 
+/* Renders a sequence of frames (e.g. the frames of a free-viewpoint video)
+ * into out_rgb, device [n_frames][rays][3]; every frame has the same number
+ * of rays (camera or explicit rays without per-ray times) and the same
+ * options, which carry no debug outputs (flags must be 0; events are
+ * ignored).  The result equals n_frames calls of fpo_render.  In the table
+ * mode the work is pipelined: the per-frame table of frame k+1 is computed
+ * on an internal second stream, into a second table, while frame k is
+ * traversed on cuda_stream (the call orders that stream after its own
+ * previous work and before everything it enqueues later).
+ * Errors: as fpo_render. */
+int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames,
+                      const fpo_frame_opts *opts, float *out_rgb, void *cuda_stream);
+
 /* Adjoint of fpo_render (the back-propagation of Sec. 4.3, used to fine-tune
  * the leaf coefficients against the loss of Eq. 13): given dL/d(rgb) (device
  * [rays][3]) it accumulates dL/d(coefficients) into dL_dcoeffs, a device

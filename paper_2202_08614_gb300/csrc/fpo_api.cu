@@ -59,6 +59,14 @@ void dfree(T *&p)
 #ifndef FPO_SUPER_TILE
 #define FPO_SUPER_TILE 0
 #endif
+// CTAs per SM of the two kernels of the frame pipeline (fpo_render_frames),
+// 0 = as many as fit
+#ifndef FPO_PIPE_MAT_CTAS
+#define FPO_PIPE_MAT_CTAS 0
+#endif
+#ifndef FPO_PIPE_TRAV_CTAS
+#define FPO_PIPE_TRAV_CTAS 0
+#endif
 #ifndef FPO_SMEM_NODES
 #define FPO_SMEM_NODES 512
 #endif
@@ -90,6 +98,11 @@ struct fpo_ctx {
     bool has_latents = false;
     float *d_table = nullptr;
     size_t table_leaves = 0;
+    // frame pipeline (fpo_render_frames): second table, aux stream, events
+    float *d_table2 = nullptr;
+    size_t table2_leaves = 0;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_entry = nullptr, ev_mat[2] = {nullptr, nullptr}, ev_trav[2] = {nullptr, nullptr};
 
     void free_tree()
     {
@@ -104,6 +117,8 @@ struct fpo_ctx {
         has_latents = false;
         dfree(d_table);
         table_leaves = 0;
+        dfree(d_table2);
+        table2_leaves = 0;
         has_tree = false;
     }
 };
@@ -384,6 +399,49 @@ static TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, 
     return p;
 }
 
+// The per-frame table for time t into `table` on stream s: the tensor-core
+// decoder for LATENT storage, else the bulk-copy IDFT pass over the stored
+// coefficients (at most max_ctas_per_sm CTAs per SM when > 0).
+static int launch_table_pass(fpo_ctx *ctx, double t, float *table, int max_ctas_per_sm, cudaStream_t s)
+{
+    if (ctx->cfg.storage == FPO_STORAGE_LATENT) {
+        LatentParams lp{};
+        lp.latents = ctx->d_latents;
+        lp.w1 = ctx->d_dec_w;
+        lp.w2 = ctx->d_dec_w + 64 * 32;
+        lp.w3 = ctx->d_dec_w + 64 * 32 + 64 * 64;
+        lp.b1 = ctx->d_dec_b;
+        lp.b2 = ctx->d_dec_b + 64;
+        lp.b3 = ctx->d_dec_b + 128;
+        lp.n1 = ctx->cfg.n1;
+        lp.n2 = ctx->cfg.n2;
+        lp.t = t;
+        lp.period_T = ctx->cfg.period_T;
+        lp.n_leaves = ctx->n_leaves;
+        lp.table = table;
+        lp.status = ctx->d_status;
+        return launch_latent_table(lp, ctx->sm_count, s);
+    }
+    MaterialiseParams mp{};
+    const RecordLayout L = record_layout(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2);
+    mp.sig = ctx->d_sig;
+    mp.zc = ctx->d_z;
+    mp.scale = ctx->d_scale;
+    mp.table = table;
+    mp.n_leaves = ctx->n_leaves;
+    mp.storage = ctx->cfg.storage;
+    mp.n1 = ctx->cfg.n1;
+    mp.n2 = ctx->cfg.n2;
+    mp.sig_stride = L.sig_elems;
+    mp.z_stride = L.z_elems;
+    mp.stages = materialise_stages(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2);
+    mp.max_ctas_per_sm = max_ctas_per_sm;
+    mp.t = t;
+    mp.period_T = ctx->cfg.period_T;
+    mp.status = ctx->d_status;
+    return launch_materialise(mp, ctx->sm_count, s);
+}
+
 int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, float *out_rgb,
                void *cuda_stream)
 {
@@ -432,45 +490,9 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
         if ((e = rec(1)) != cudaSuccess || (e = rec(2)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
         return FPO_OK;
     }
-    if (mat && ctx->cfg.storage == FPO_STORAGE_LATENT) {
-        const int nc = ctx->cfg.n1 + 27 * ctx->cfg.n2;
-        LatentParams lp{};
-        lp.latents = ctx->d_latents;
-        lp.w1 = ctx->d_dec_w;
-        lp.w2 = ctx->d_dec_w + 64 * 32;
-        lp.w3 = ctx->d_dec_w + 64 * 32 + 64 * 64;
-        lp.b1 = ctx->d_dec_b;
-        lp.b2 = ctx->d_dec_b + 64;
-        lp.b3 = ctx->d_dec_b + 128;
-        (void)nc;
-        lp.n1 = ctx->cfg.n1;
-        lp.n2 = ctx->cfg.n2;
-        lp.t = rays->t;
-        lp.period_T = ctx->cfg.period_T;
-        lp.n_leaves = ctx->n_leaves;
-        lp.table = ctx->d_table;
-        lp.status = ctx->d_status;
-        int ce = launch_latent_table(lp, ctx->sm_count, s);
-        if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "latent decode launch");
-    } else if (mat) {
-        MaterialiseParams mp{};
-        const RecordLayout L = record_layout(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2);
-        mp.sig = ctx->d_sig;
-        mp.zc = ctx->d_z;
-        mp.scale = ctx->d_scale;
-        mp.table = ctx->d_table;
-        mp.n_leaves = ctx->n_leaves;
-        mp.storage = ctx->cfg.storage;
-        mp.n1 = ctx->cfg.n1;
-        mp.n2 = ctx->cfg.n2;
-        mp.sig_stride = L.sig_elems;
-        mp.z_stride = L.z_elems;
-        mp.stages = materialise_stages(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2);
-        mp.t = rays->t;
-        mp.period_T = ctx->cfg.period_T;
-        mp.status = ctx->d_status;
-        int ce = launch_materialise(mp, ctx->sm_count, s);
-        if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "materialise launch");
+    if (mat) {
+        const int ce = launch_table_pass(ctx, rays->t, ctx->d_table, 0, s);
+        if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "IDFT table launch");
     }
     if ((e = rec(1)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
 
@@ -480,6 +502,80 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
     int ce = launch_traverse(p, mat, dbg, ctx->sm_count, s);
     if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "traverse launch");
     if ((e = rec(2)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    return FPO_OK;
+}
+
+int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, const fpo_frame_opts *opts,
+                      float *out_rgb, void *cuda_stream)
+{
+    if (!ctx || !opts || (n_frames && !frames)) return fail(FPO_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->has_tree) return fail(FPO_ERR_NO_TREE, "render before fpo_upload_tree");
+    if (opts->flags) return fail(FPO_ERR_INVALID_ARG, "fpo_render_frames takes no debug outputs (flags must be 0)");
+    uint64_t R = 0;
+    for (uint32_t k = 0; k < n_frames; ++k) {
+        uint64_t nr = 0;
+        const int st = check_rays(ctx, &frames[k], &nr);
+        if (st != FPO_OK) return st;
+        if (frames[k].mode == FPO_RAYS_EXPLICIT && frames[k].t_per_ray)
+            return fail(FPO_ERR_INVALID_ARG, "per-ray times need fpo_render (fused IDFT)");
+        if (k == 0) R = nr;
+        else if (nr != R) return fail(FPO_ERR_INVALID_ARG, "every frame must have the same number of rays");
+    }
+    if (n_frames == 0 || R == 0) return FPO_OK;
+    if (!out_rgb) return fail(FPO_ERR_INVALID_ARG, "out_rgb is NULL");
+    if (!(opts->stop_T >= 0.0f)) return fail(FPO_ERR_INVALID_ARG, "stop_T must be >= 0");
+    fpo_frame_opts o1 = *opts;
+    for (int i = 0; i < 3; ++i) o1.events[i] = nullptr;
+    const bool mat = ctx->cfg.idft_mode != FPO_IDFT_FUSED && ctx->n_leaves > 0;
+    if (!mat || n_frames == 1) {
+        for (uint32_t k = 0; k < n_frames; ++k) {
+            const int st = fpo_render(ctx, &frames[k], &o1, out_rgb + (size_t)k * R * 3, cuda_stream);
+            if (st != FPO_OK) return st;
+        }
+        return FPO_OK;
+    }
+    if (ctx->cfg.storage == FPO_STORAGE_LATENT && !ctx->has_latents)
+        return fail(FPO_ERR_INVALID_ARG, "LATENT storage: call fpo_set_latents before rendering");
+    DeviceGuard g(ctx->cfg.device);
+    if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2; ++b) {
+        float *&tb = b ? ctx->d_table2 : ctx->d_table;
+        size_t &tl = b ? ctx->table2_leaves : ctx->table_leaves;
+        if (tl < ctx->n_leaves) {
+            dfree(tb);
+            e = cudaMalloc((void **)&tb, (size_t)ctx->n_leaves * TABLE_STRIDE * 4);
+            if (e != cudaSuccess) { tl = 0; return cuda_fail(e, "cudaMalloc(table)"); }
+            tl = ctx->n_leaves;
+        }
+    }
+    if (!ctx->aux) {
+        e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
+        for (cudaEvent_t *ev : {&ctx->ev_entry, &ctx->ev_mat[0], &ctx->ev_mat[1], &ctx->ev_trav[0], &ctx->ev_trav[1]})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "stream/event creation");
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // The table pass of frame k + 1 runs on the auxiliary stream while frame
+    // k is traversed on the caller's stream; two tables alternate.
+    if ((e = cudaEventRecord(ctx->ev_entry, s)) != cudaSuccess || (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_entry, 0)) != cudaSuccess)
+        return cuda_fail(e, "stream ordering");
+    for (uint32_t k = 0; k < n_frames; ++k) {
+        const int b = (int)(k & 1);
+        float *tbl = b ? ctx->d_table2 : ctx->d_table;
+        if (k >= 2 && (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_trav[b], 0)) != cudaSuccess) return cuda_fail(e, "wait");
+        int ce = launch_table_pass(ctx, frames[k].t, tbl, FPO_PIPE_MAT_CTAS, ctx->aux);
+        if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "IDFT table launch");
+        if ((e = cudaEventRecord(ctx->ev_mat[b], ctx->aux)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, ctx->ev_mat[b], 0)) != cudaSuccess)
+            return cuda_fail(e, "stream ordering");
+        TraverseParams p = traverse_params(ctx, &frames[k], &o1, out_rgb + (size_t)k * R * 3, R);
+        p.table = reinterpret_cast<const float4 *>(tbl);
+        p.max_ctas_per_sm = FPO_PIPE_TRAV_CTAS;
+        ce = launch_traverse(p, true, false, ctx->sm_count, s);
+        if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "traverse launch");
+        if ((e = cudaEventRecord(ctx->ev_trav[b], s)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    }
     return FPO_OK;
 }
 
@@ -607,6 +703,9 @@ void fpo_destroy(fpo_ctx *ctx)
         DeviceGuard g(ctx->cfg.device);
         ctx->free_tree();
         dfree(ctx->d_status);
+        if (ctx->aux) cudaStreamDestroy(ctx->aux);
+        for (cudaEvent_t e : {ctx->ev_entry, ctx->ev_mat[0], ctx->ev_mat[1], ctx->ev_trav[0], ctx->ev_trav[1]})
+            if (e) cudaEventDestroy(e);
     }
     delete ctx;
 }

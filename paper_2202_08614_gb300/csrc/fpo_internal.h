@@ -124,6 +124,7 @@ struct TraverseParams {
     uint32_t refill_min;      // warp refills its idle lanes once this many are idle (32: whole tiles)
     uint32_t inner_steps;     // steps a lane takes between two refill checks
     int block_threads;        // 128 or 256
+    int max_ctas_per_sm;      // 0: as many as fit
     unsigned long long *stats; // FPO_FLAG_STATS: [steps, leaf visits, rays entering the tree]
 };
 
@@ -136,6 +137,7 @@ struct MaterialiseParams {
     int storage;              // FPO_STORAGE_*
     int n1, n2, sig_stride, z_stride;  // strides in elements
     int stages;               // shared-memory pipeline depth (materialise_stages)
+    int max_ctas_per_sm;      // 0: as many as fit
     double t, period_T;
     uint32_t *status;
 };

@@ -241,6 +241,7 @@ int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MAT_THREADS, smem);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) per_sm = 1;
+    if (p.max_ctas_per_sm > 0 && per_sm > p.max_ctas_per_sm) per_sm = p.max_ctas_per_sm;
     const uint32_t n_chunks = (p.n_leaves + MAT_CHUNK - 1) / MAT_CHUNK;
     uint64_t blocks = (uint64_t)sm_count * per_sm;
     if (blocks > n_chunks) blocks = n_chunks;
@@ -878,6 +879,7 @@ static int launch_t(const TraverseParams &p, int sm_count, cudaStream_t s)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) per_sm = 1;
+    if (p.max_ctas_per_sm > 0 && per_sm > p.max_ctas_per_sm) per_sm = p.max_ctas_per_sm;
     uint64_t blocks = (uint64_t)sm_count * per_sm;
     const uint64_t need = (p.n_tiles + (threads / 32) - 1) / (threads / 32);
     if (need < blocks) blocks = need ? need : 1;
@@ -1085,6 +1087,7 @@ static int launch_b(const BackwardParams &q, int sm_count, cudaStream_t s)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) per_sm = 1;
+    if (p.max_ctas_per_sm > 0 && per_sm > p.max_ctas_per_sm) per_sm = p.max_ctas_per_sm;
     uint64_t blocks = (uint64_t)sm_count * per_sm;
     const uint64_t need = (p.n_tiles + (threads / 32) - 1) / (threads / 32);
     if (need < blocks) blocks = need ? need : 1;

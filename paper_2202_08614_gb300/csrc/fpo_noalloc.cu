@@ -140,6 +140,7 @@ extern "C" int fpo_render_noalloc(fpo_ctx *ctx, const fpo_rays *rays, const fpo_
         mp.sig_stride = L.sig_elems;
         mp.z_stride = L.z_elems;
         mp.stages = materialise_stages(c.storage, c.n1, c.n2);
+        mp.max_ctas_per_sm = 0;
         mp.t = rays->t;
         mp.period_T = c.period_T;
         mp.status = c.d_status;

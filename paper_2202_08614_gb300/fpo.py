@@ -32,7 +32,7 @@ EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
            "fpo_render_backward", "fpo_status_sync", "fpo_tree_info_get", "fpo_destroy",
            "fpo_last_error", "fpo_version", "fpo_render_noalloc", "fpo_set_coeffs",
            "fpo_dft_leaves", "fpo_union_trees", "fpo_latent_table", "fpo_decoder_grad",
-           "fpo_adam", "fpo_set_latents"]
+           "fpo_adam", "fpo_set_latents", "fpo_render_frames"]
 
 
 class FPOError(RuntimeError):
@@ -116,6 +116,7 @@ def lib():
         L.fpo_adam.argtypes = [P, P, P, P, C.c_uint64, P, C.c_uint32, C.c_float, C.c_float,
                                C.c_float, C.c_float, C.c_uint32, P]
         L.fpo_set_latents.argtypes = [P, P, C.POINTER(Decoder), P]
+        L.fpo_render_frames.argtypes = [P, P, C.c_uint32, C.POINTER(FrameOpts), P, P]
         L.fpo_union_trees.argtypes = [C.c_uint32, P, C.c_uint32, C.POINTER(C.c_uint32), P, P, P,
                                       C.c_uint32]
         L.fpo_status_sync.argtypes = [P, P]
@@ -300,6 +301,29 @@ class Renderer:
                                C.c_void_p(_stream_handle(stream))))
         res["_keep"] = keep
         return res
+
+    def render_frames(self, cameras, times, bg=(1.0, 1.0, 1.0), stop_T=1e-4, out=None, stream=None):
+        """Renders camera frames (same size) into out [n_frames, W*H, 3] with the
+        pipelined fpo_render_frames."""
+        import torch
+
+        n = len(cameras)
+        arr = (Rays * max(n, 1))()
+        keep = []
+        for i, (cam, t) in enumerate(zip(cameras, times)):
+            r, k, npx = self._rays(cam, t, None, None, None)
+            arr[i] = r
+            keep += k
+        npx = cameras[0].width * cameras[0].height if n else 0
+        if out is None:
+            out = torch.empty((n, npx, 3), dtype=torch.float32, device=torch.device("cuda", self.device))
+        opts = FrameOpts()
+        opts.bg = (C.c_float * 3)(*bg)
+        opts.stop_T = float(stop_T)
+        check(lib().fpo_render_frames(self.h, arr, n, C.byref(opts),
+                                      C.c_void_p(out.data_ptr() if out.numel() else None),
+                                      C.c_void_p(_stream_handle(stream))))
+        return out
 
     def set_coeffs(self, coeffs, stream=None):
         """Replaces the tree's coefficients from a CUDA float32 tensor [n_leaves, n1 + 27 n2]."""
