@@ -51,6 +51,7 @@ def parse():
                     help="skip the BF16 and latent-decoder variant measurements")
     ap.add_argument("--variant-frames", type=int, default=100)
     ap.add_argument("--latent-steps", type=int, default=20000)
+    ap.add_argument("--finetune-steps", type=int, default=200)
     return ap.parse_args()
 
 
@@ -260,6 +261,8 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms):
                    "psnr_db_vs_fp64_oracle": sampled_psnr(r, ot, tree.coeffs, cams, nf[:2], out, torch, n_px),
                    "bytes_per_leaf": r.info()["leaf_record_bytes"]}
     r.close()
+    if args.finetune_steps > 0:
+        res["finetune"] = finetune_variant(args, tree, torch, fpo)
     # latent decoder on generated coefficients (same leaves)
     body = synth.capsule_body(np.random.default_rng(0))
     n = tree.n_leaves
@@ -299,6 +302,90 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms):
         "coefficients": "per-leaf DFT (Eq. 10-12) of smooth animated fields over the same leaves"}
     r.close()
     return res
+
+
+def camera_batch(cams, n, gen, torch, n_frames=60):
+    """n rays drawn uniformly over (camera, integer frame, pixel): origins,
+    unit directions (pixel centres, the pinhole model of fpo.h) and times."""
+    basis = []
+    for c in cams:
+        eye, tgt, up = (np.array(v, np.float64) for v in (c.eye, c.target, c.up))
+        f = (tgt - eye) / np.linalg.norm(tgt - eye)
+        r = np.cross(f, up)
+        r /= np.linalg.norm(r)
+        basis.append(np.concatenate([eye, f, r, np.cross(r, f)]))
+    B = torch.as_tensor(np.stack(basis), dtype=torch.float32, device="cuda")
+    W, H = cams[0].width, cams[0].height
+    th = np.tan(np.radians(cams[0].fov_y_deg) / 2)
+    v = torch.randint(0, len(cams), (n,), device="cuda", generator=gen)
+    p = torch.randint(0, W * H, (n,), device="cuda", generator=gen)
+    t = torch.randint(0, n_frames, (n,), device="cuda", generator=gen).float()
+    sx = ((2 * ((p % W).float() + 0.5) / W - 1) * th * W / H)[:, None]
+    sy = ((1 - 2 * ((p // W).float() + 0.5) / H) * th)[:, None]
+    b = B[v]
+    d = b[:, 3:6] + sx * b[:, 6:9] + sy * b[:, 9:12]
+    return b[:, 0:3].contiguous(), (d / d.norm(dim=1, keepdim=True)).contiguous(), t
+
+
+def finetune_variant(args, tree, torch, fpo):
+    """The fine-tuning stage (Sec. 4.3, Eq. 13) at full scale: coefficients
+    perturbed by N(0, 0.1|k| + 0.05), targets rendered by the FP32 path from
+    the original ones at 800x800 over 16 ring views x 60 frames, batches of
+    65,536 rays, Adam lr 1e-2 (row-sparse, fused with the write-back)."""
+    from paper_2202_08614_gb300.finetune import FineTuner
+
+    B, steps, warm = 65536, args.finetune_steps, 5
+    cams = synth.ring_cameras(16, 800, 800)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    k_true = torch.as_tensor(tree.coeffs, device="cuda")
+    noise = torch.randn(k_true.shape, device="cuda", generator=gen) * (0.1 * k_true.abs() + 0.05)
+    ref = fpo.Renderer(idft_mode="fused")
+    ref.upload(tree)
+    r = fpo.Renderer(idft_mode="fused")
+    r.upload(tree)
+    ft = FineTuner(r, k_true + noise, lr=1e-2)
+    del noise
+    batches = []
+    for _ in range(warm + steps + 1):
+        o, d, t = camera_batch(cams, B, gen, torch)
+        batches.append((o, d, t, ref.render(rays_o=o, rays_d=d, t_per_ray=t)["rgb"].clone()))
+    ref.status()
+    ref.close()
+    del k_true
+    ho = batches.pop()
+    held = lambda: float(((ft.render(*ho[:3]) - ho[3]) ** 2).sum(1).mean())
+    l0 = held()
+    for b in batches[:warm]:
+        ft.step(*b)
+    torch.cuda.synchronize()
+    # rows one batch touches (an untimed count on the next batch's adjoint)
+    o, d, t, y = batches[warm]
+    rgb = ft.render(o, d, t)
+    g = torch.zeros_like(ft.grad)
+    mk = torch.zeros_like(ft.mark)
+    r.render_backward(rgb, rgb - y, g, rays_o=o, rays_d=d, t_per_ray=t, leaf_mark=mk)
+    rows = int(mk.sum())
+    del g, mk
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for i, b in enumerate(batches[warm:]):
+        ft.step(*b, events=ev[i])
+    z.record()
+    torch.cuda.synchronize()
+    r.status()
+    l1 = held()
+    ms = a.elapsed_time(z) / steps
+    phase = lambda j: statistics.mean(e[j].elapsed_time(e[j + 1]) for e in ev)
+    out = {"ms_per_step": ms, "Mrays_s": B / ms / 1e3, "batch_rays": B, "steps": steps,
+           "forward_and_loss_ms": phase(0), "adjoint_ms": phase(1), "adam_writeback_ms": phase(2),
+           "rows_touched_per_batch": rows, "held_out_loss": [l0, l1], "resolution": [800, 800],
+           "optimizer": "Adam lr 1e-2 on the visited rows (sparse-gradient Adam), FP32"}
+    r.close()
+    del ft, batches
+    torch.cuda.empty_cache()
+    return out
 
 
 def kernel_source_sha():

@@ -203,6 +203,9 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames,
  * truncation is part of the function); sigma = max(0, sigma_raw) passes no
  * gradient where sigma_raw <= 0.  Needs FP32 storage and (n1, n2) in
  * {(31,5), (11,5), (21,5), (31,11)}; otherwise FPO_ERR_UNSUPPORTED.
+ * Of the debug flags only FPO_FLAG_MARK_LEAVES is honoured: it sets
+ * leaf_mark[id] = 1 for every leaf the replay visits (the rows that receive
+ * gradient), which fpo_adam_leaves consumes; the others are ignored.
  * Errors: INVALID_ARG, NO_TREE, UNSUPPORTED, CUDA. */
 int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
                         const float *out_rgb, const float *dL_drgb, float *dL_dcoeffs,
@@ -234,6 +237,22 @@ int fpo_render_noalloc(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts 
  * stream.  Needs FP32 storage (else FPO_ERR_UNSUPPORTED).
  * Errors: INVALID_ARG, NO_TREE, UNSUPPORTED, CUDA. */
 int fpo_set_coeffs(fpo_ctx *ctx, const float *coeffs, void *cuda_stream);
+
+/* One optimiser step of the fine-tuning stage (Sec. 4.3, loss of Eq. 13)
+ * on the leaves a batch visited: Adam (Kingma & Ba; lr, beta1, beta2, eps,
+ * step >= 1 for the bias corrections 1 - beta^step) on every row of param
+ * whose leaf_mark is non-zero, using the gradient row of grad (as
+ * accumulated by fpo_render_backward with FPO_FLAG_MARK_LEAVES), with the
+ * moment rows m and v (zero before the first step).  Rows without a mark are
+ * left alone, as in a sparse-gradient Adam.  For each updated leaf the new
+ * coefficients also go into the context's FP32 records (what fpo_set_coeffs
+ * would write), and its grad row and mark are reset to zero, ready for the
+ * next batch.  param, grad, m, v: device [n_leaves][n1 + 27*n2], canonical
+ * order and upload order, caller-owned; leaf_mark: device [n_leaves].
+ * Enqueued on the stream.  Needs FP32 storage (else FPO_ERR_UNSUPPORTED).
+ * Errors: INVALID_ARG, NO_TREE, UNSUPPORTED, CUDA. */
+int fpo_adam_leaves(fpo_ctx *ctx, float *param, float *grad, float *m, float *v, uint8_t *leaf_mark,
+                    float lr, float beta1, float beta2, float eps, uint32_t step, void *cuda_stream);
 
 /* Per-leaf DFT of the Fourier PlenOctree generation (Sec. 4.2, Eq. 10-12):
  * from the values every leaf of the unified octree takes at frames

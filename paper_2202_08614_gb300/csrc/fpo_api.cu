@@ -598,13 +598,16 @@ int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts
     if (n_rays == 0 || ctx->n_leaves == 0) return FPO_OK;
     DeviceGuard g(ctx->cfg.device);
     if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
+    const bool mark = (opts->flags & FPO_FLAG_MARK_LEAVES) != 0;
+    if (mark && !opts->leaf_mark) return fail(FPO_ERR_INVALID_ARG, "FPO_FLAG_MARK_LEAVES needs leaf_mark");
     fpo_frame_opts o = *opts;
-    o.flags = 0;  // debug outputs belong to the forward
+    o.flags = 0;  // the other debug outputs belong to the forward
     BackwardParams q{};
     q.tp = traverse_params(ctx, rays, &o, nullptr, n_rays);
     q.out_rgb = out_rgb;
     q.dL_drgb = dL_drgb;
     q.dL_dcoeffs = dL_dcoeffs;
+    q.leaf_mark = mark ? opts->leaf_mark : nullptr;
     const int ce = launch_backward(q, ctx->sm_count, cuda_stream);
     if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "backward launch");
     return FPO_OK;
@@ -656,6 +659,45 @@ int fpo_set_coeffs(fpo_ctx *ctx, const float *coeffs, void *cuda_stream)
                                      static_cast<float *>(ctx->d_z), ctx->n_leaves, ctx->cfg.n1,
                                      ctx->cfg.n2, ctx->sm_count, cuda_stream);
     if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "set_coeffs launch");
+    return FPO_OK;
+}
+
+int fpo_adam_leaves(fpo_ctx *ctx, float *param, float *grad, float *m, float *v, uint8_t *leaf_mark, float lr,
+                    float beta1, float beta2, float eps, uint32_t step, void *cuda_stream)
+{
+    if (!ctx) return fail(FPO_ERR_INVALID_ARG, "ctx is NULL");
+    if (!ctx->has_tree) return fail(FPO_ERR_NO_TREE, "adam_leaves before fpo_upload_tree");
+    if (ctx->cfg.storage != FPO_STORAGE_F32)
+        return fail(FPO_ERR_UNSUPPORTED, "in-place coefficient updates need FP32 storage");
+    if (ctx->n_leaves == 0) return FPO_OK;
+    if (!param || !grad || !m || !v || !leaf_mark) return fail(FPO_ERR_INVALID_ARG, "NULL array");
+    if (step < 1) return fail(FPO_ERR_INVALID_ARG, "step counts from 1");
+    if (!(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return fail(FPO_ERR_INVALID_ARG, "lr >= 0, beta in [0, 1), eps > 0");
+    DeviceGuard g(ctx->cfg.device);
+    if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
+    LeafAdamParams p{};
+    p.param = param;
+    p.grad = grad;
+    p.m = m;
+    p.v = v;
+    p.leaf_mark = leaf_mark;
+    p.perm = ctx->d_perm;
+    p.sig = static_cast<float *>(ctx->d_sig);
+    p.zc = static_cast<float *>(ctx->d_z);
+    p.n_leaves = ctx->n_leaves;
+    p.n1 = ctx->cfg.n1;
+    p.n2 = ctx->cfg.n2;
+    p.sig_stride = sig_stride(ctx->cfg.n1);
+    p.z_stride = z_stride(ctx->cfg.n2);
+    p.lr = lr;
+    p.beta1 = beta1;
+    p.beta2 = beta2;
+    p.eps = eps;
+    p.bc1 = (float)(1.0 - std::pow((double)beta1, (double)step));
+    p.bc2 = (float)(1.0 - std::pow((double)beta2, (double)step));
+    const int ce = launch_leaf_adam(p, ctx->sm_count, cuda_stream);
+    if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "adam_leaves launch");
     return FPO_OK;
 }
 

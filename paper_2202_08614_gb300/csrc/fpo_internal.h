@@ -205,6 +205,20 @@ struct BackwardParams {
     const float *out_rgb;       // forward colour [rays][3]
     const float *dL_drgb;       // [rays][3]
     float *dL_dcoeffs;          // [n_leaves][n1 + 27 n2], canonical, upload order (accumulated)
+    uint8_t *leaf_mark;         // optional [n_leaves] (upload order): set to 1 for every visited leaf
+};
+
+// Row-sparse Adam over the coefficients of the leaves a batch visited, fused
+// with the write-back into the FP32 records and the reset of their gradient
+// rows and marks.
+struct LeafAdamParams {
+    float *param, *grad, *m, *v;  // [n_leaves][nc], canonical, upload order
+    uint8_t *leaf_mark;           // [n_leaves], upload order
+    const uint32_t *perm;         // internal leaf -> upload id
+    float *sig, *zc;              // FP32 records (internal order)
+    uint32_t n_leaves;
+    int n1, n2, sig_stride, z_stride;
+    float lr, beta1, beta2, eps, bc1, bc2;  // bc = 1 - beta^step
 };
 
 // Launchers (return cudaError_t as int).
@@ -215,6 +229,7 @@ int launch_dft(const float *values, float *coeffs, uint32_t n_leaves, int n1, in
                void *stream);
 int launch_set_coeffs(const float *src, const uint32_t *perm, float *sig, float *zc, uint32_t n_leaves,
                       int n1, int n2, int sm_count, void *stream);
+int launch_leaf_adam(const LeafAdamParams &p, int sm_count, void *stream);
 int launch_traverse(const TraverseParams &p, bool materialised, bool debug, int sm_count,
                     void *stream);
 int traverse_smem_bytes(uint32_t n_smem_nodes, bool per_ray_basis, int threads);

@@ -25,6 +25,12 @@
 #ifndef FPO_FAST_STEP
 #define FPO_FAST_STEP 1
 #endif
+#ifndef FPO_FAST_SIGMOID
+#define FPO_FAST_SIGMOID 1
+#endif
+#ifndef FPO_LDG256
+#define FPO_LDG256 1
+#endif
 #ifndef FPO_PREFETCH
 #define FPO_PREFETCH 1
 #endif
@@ -71,7 +77,48 @@ __device__ __forceinline__ float basis_fp32(int i, float u /* t / T */)
     return (i & 1) ? sinpif(r) : cospif(r);
 }
 
+#if FPO_FAST_SIGMOID
+// approximate reciprocal (2 ulp): 1 / (1 + e^-x) with e^-x = inf gives 0
+__device__ __forceinline__ float sigmoidf_(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
+#else
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + __expf(-x)); }
+#endif
+
+// VW floats from a read-only global address aligned to 4 VW bytes.
+template <int VW>
+__device__ __forceinline__ void load_vec(const float *p, float *v);
+
+// The FP32 coefficient records of (n1, n2) take 32-byte loads when both
+// padded strides are multiples of 8 floats: (31, 5) and (21, 5).
+__host__ __device__ constexpr bool fused_ldg256(int n1, int n2)
+{
+    return ((n1 + 3) & ~3) % 8 == 0 && ((27 * n2 + 3) & ~3) % 8 == 0;
+}
+
+// One 32-byte read-only global load (sm_100+ 256-bit vector load); p is
+// 32-byte aligned.
+__device__ __forceinline__ void ldg256(const float *p, float *v)
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "l"(p));
+}
+
+template <>
+__device__ __forceinline__ void load_vec<8>(const float *p, float *v)
+{
+    ldg256(p, v);
+}
+
+template <>
+__device__ __forceinline__ void load_vec<4>(const float *p, float *v)
+{
+    const float4 w = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = w.x;
+    v[1] = w.y;
+    v[2] = w.z;
+    v[3] = w.w;
+}
 
 }  // namespace
 
@@ -532,7 +579,13 @@ __device__ __forceinline__ bool shade(const TraverseParams &p, const float *bsrc
     float sigma, z[27];
     if constexpr (MAT) {
         const float4 *rec = table_record(p, leaf);
-        float v[28];
+        float v[32];
+#if FPO_LDG256
+        // four 32-byte loads for the 128-byte table line (half the load
+        // instructions, and half the L1 wavefronts, of 16-byte loads)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ldg256(reinterpret_cast<const float *>(rec) + 8 * q, v + 8 * q);
+#else
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
             const float4 w = __ldg(rec + q);
@@ -541,37 +594,60 @@ __device__ __forceinline__ bool shade(const TraverseParams &p, const float *bsrc
             v[4 * q + 2] = w.z;
             v[4 * q + 3] = w.w;
         }
+#endif
         sigma = v[0];
 #pragma unroll
         for (int q = 0; q < 27; ++q) z[q] = v[q + 1];
     } else {
         const float4 *sr = p.sig + (size_t)leaf * p.sig_stride4;
-        float acc = 0.0f;
-#pragma unroll
-        for (int q = 0; q < (N1 + 3) / 4; ++q) {
-            const float4 w = __ldg(sr + q);
-            const float wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (4 * q + j < N1) acc = fmaf(wv[j], bsrc[(4 * q + j) * bstride], acc);
-        }
-        sigma = fmaxf(acc, 0.0f);
+        const float *zr = p.zc + (size_t)leaf * p.z_stride;
         float bz[N2];
 #pragma unroll
         for (int i = 0; i < N2; ++i) bz[i] = bsrc[i * bstride];
-        const float4 *zr = reinterpret_cast<const float4 *>(p.zc + (size_t)leaf * p.z_stride);
 #pragma unroll
         for (int q = 0; q < 27; ++q) z[q] = 0.0f;
+        float acc = 0.0f;
+        if constexpr (FPO_LDG256 && fused_ldg256(N1, N2)) {
+            // 32-byte loads: both record strides are multiples of 8 floats
 #pragma unroll
-        for (int q4 = 0; q4 < (27 * N2 + 3) / 4; ++q4) {
-            const float4 w = __ldg(zr + q4);
-            const float wv[4] = {w.x, w.y, w.z, w.w};
+            for (int q = 0; q < (N1 + 7) / 8; ++q) {
+                float wv[8];
+                ldg256(reinterpret_cast<const float *>(sr) + 8 * q, wv);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int e = 4 * q4 + j;
-                if (e < 27 * N2) z[e / N2] = fmaf(wv[j], bz[e % N2], z[e / N2]);
+                for (int j = 0; j < 8; ++j)
+                    if (8 * q + j < N1) acc = fmaf(wv[j], bsrc[(8 * q + j) * bstride], acc);
+            }
+#pragma unroll
+            for (int q = 0; q < (27 * N2 + 7) / 8; ++q) {
+                float wv[8];
+                ldg256(zr + 8 * q, wv);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int e = 8 * q + j;
+                    if (e < 27 * N2) z[e / N2] = fmaf(wv[j], bz[e % N2], z[e / N2]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < (N1 + 3) / 4; ++q) {
+                const float4 w = __ldg(sr + q);
+                const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (4 * q + j < N1) acc = fmaf(wv[j], bsrc[(4 * q + j) * bstride], acc);
+            }
+#pragma unroll
+            for (int q4 = 0; q4 < (27 * N2 + 3) / 4; ++q4) {
+                const float4 w = __ldg(reinterpret_cast<const float4 *>(zr) + q4);
+                const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int e = 4 * q4 + j;
+                    if (e < 27 * N2) z[e / N2] = fmaf(wv[j], bz[e % N2], z[e / N2]);
+                }
             }
         }
+        sigma = fmaxf(acc, 0.0f);
     }
     float col[3];
 #pragma unroll
@@ -738,10 +814,11 @@ __device__ __forceinline__ bool tile_ray(const TraverseParams &p, uint32_t tile,
 // long rays do not leave most of a warp idle.  Each CTA first stages the top
 // n_smem_nodes nodes of the breadth-first node array and the frame constants
 // in shared memory.  The last CTA to finish resets the counter.
-// Register caps: 80 lets six 128-thread (or three 256-thread) CTAs share an
-// SM in materialised mode; the fused per-visit IDFT needs more.
+// Register caps: 64 lets four 256-thread CTAs share an SM in materialised
+// mode (measured fastest of 48..80 on the 3.5M-leaf body at 1080p); the fused
+// per-visit IDFT needs more.
 #ifndef FPO_TRAV_MAXNREG_MAT
-#define FPO_TRAV_MAXNREG_MAT 80
+#define FPO_TRAV_MAXNREG_MAT 64
 #endif
 #ifndef FPO_TRAV_MAXNREG_FUSED
 #define FPO_TRAV_MAXNREG_FUSED 128
@@ -950,38 +1027,39 @@ __device__ void backward_ray(const BackwardParams &q, const float *bsrc, int bst
     const float Cf0 = q.out_rgb[3 * (size_t)R.ray], Cf1 = q.out_rgb[3 * (size_t)R.ray + 1],
                 Cf2 = q.out_rgb[3 * (size_t)R.ray + 2];
     float P0 = 0.0f, P1 = 0.0f, P2 = 0.0f;  // sum_{k<=j} w_k c_k
-    float b[N1 > N2 ? N1 : N2];
+    float bz[N2];  // the density basis stays in shared memory (bsrc)
 #pragma unroll
-    for (int i = 0; i < (N1 > N2 ? N1 : N2); ++i) b[i] = bsrc[i * bstride];
+    for (int i = 0; i < N2; ++i) bz[i] = bsrc[i * bstride];
     Cube cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start, nc);
     for (;;) {
         int m, lo[3], csz;
         const float tx = cube_exit(R, D, cb.lvl, m, lo, csz);
         if (cb.kind == ROOT_LEAF && tx > R.t) {
             const float delta = tx - R.t;
-            const float4 *sr = p.sig + (size_t)cb.leaf * p.sig_stride4;
+            const float *sr = reinterpret_cast<const float *>(p.sig + (size_t)cb.leaf * p.sig_stride4);
+            const float *zr = p.zc + (size_t)cb.leaf * p.z_stride;
+            constexpr int VW = (FPO_LDG256 && fused_ldg256(N1, N2)) ? 8 : 4;  // floats per load
             float sraw = 0.0f;
 #pragma unroll
-            for (int k4 = 0; k4 < (N1 + 3) / 4; ++k4) {
-                const float4 w = __ldg(sr + k4);
-                const float wv[4] = {w.x, w.y, w.z, w.w};
+            for (int k4 = 0; k4 < (N1 + VW - 1) / VW; ++k4) {
+                float wv[VW];
+                load_vec<VW>(sr + VW * k4, wv);
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (4 * k4 + j < N1) sraw = fmaf(wv[j], b[4 * k4 + j], sraw);
+                for (int j = 0; j < VW; ++j)
+                    if (VW * k4 + j < N1) sraw = fmaf(wv[j], bsrc[(VW * k4 + j) * bstride], sraw);
             }
             const float sigma = fmaxf(sraw, 0.0f);
             float z[27];
 #pragma unroll
             for (int k = 0; k < 27; ++k) z[k] = 0.0f;
-            const float4 *zr = reinterpret_cast<const float4 *>(p.zc + (size_t)cb.leaf * p.z_stride);
 #pragma unroll
-            for (int k4 = 0; k4 < (27 * N2 + 3) / 4; ++k4) {
-                const float4 w = __ldg(zr + k4);
-                const float wv[4] = {w.x, w.y, w.z, w.w};
+            for (int k4 = 0; k4 < (27 * N2 + VW - 1) / VW; ++k4) {
+                float wv[VW];
+                load_vec<VW>(zr + VW * k4, wv);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int e = 4 * k4 + j;
-                    if (e < 27 * N2) z[e / N2] = fmaf(wv[j], b[e % N2], z[e / N2]);
+                for (int j = 0; j < VW; ++j) {
+                    const int e = VW * k4 + j;
+                    if (e < 27 * N2) z[e / N2] = fmaf(wv[j], bz[e % N2], z[e / N2]);
                 }
             }
             float col[3];
@@ -1003,7 +1081,9 @@ __device__ void backward_ray(const BackwardParams &q, const float *bsrc, int bst
             const float dsr = sraw > 0.0f ? gs : 0.0f;
             const float gu[3] = {g0 * w * col[0] * (1.0f - col[0]), g1 * w * col[1] * (1.0f - col[1]),
                                  g2 * w * col[2] * (1.0f - col[2])};
-            float2 *row = reinterpret_cast<float2 *>(q.dL_dcoeffs + (size_t)p.perm[cb.leaf] * NC);
+            const uint32_t id = p.perm[cb.leaf];
+            float2 *row = reinterpret_cast<float2 *>(q.dL_dcoeffs + (size_t)id * NC);
+            if (q.leaf_mark) q.leaf_mark[id] = 1;
 #pragma unroll
             for (int e2 = 0; e2 < NC / 2; ++e2) {
                 float v[2];
@@ -1011,10 +1091,10 @@ __device__ void backward_ray(const BackwardParams &q, const float *bsrc, int bst
                 for (int h = 0; h < 2; ++h) {
                     const int el = 2 * e2 + h;
                     if (el < N1) {
-                        v[h] = dsr * b[el];
+                        v[h] = dsr * bsrc[el * bstride];
                     } else {
                         const int j = el - N1, c = j / (9 * N2), k = (j / N2) % 9, i = j % N2;
-                        v[h] = gu[c] * R.Y[k] * b[i];
+                        v[h] = gu[c] * R.Y[k] * bz[i];
                     }
                 }
                 atomicAdd(row + e2, make_float2(v[0], v[1]));
@@ -1161,6 +1241,69 @@ int launch_set_coeffs(const float *src, const uint32_t *perm, float *sig, float 
     if (blocks > (uint64_t)sm_count * 16) blocks = (uint64_t)sm_count * 16;
     set_coeffs_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(src, perm, sig, zc, n_leaves, n1, n2,
                                                                            sig_stride(n1), z_stride(n2));
+    return (int)cudaGetLastError();
+}
+
+
+// Row-sparse Adam (Kingma & Ba) for the fine-tuning of Sec. 4.3: only the
+// leaves whose mark is set (those the batch visited) are updated, as in a
+// sparse-gradient Adam.  A warp takes 32 internal leaves at a time: one
+// coalesced read of perm and one gather of the marks decide, by ballot, which
+// of them it updates; each marked leaf's row (coalesced over the lanes) gets
+// the Adam step, goes back into the FP32 records at its internal slot, and
+// has its gradient row and mark cleared for the next batch.
+
+constexpr int LEAF_ADAM_CHUNK = 192;  // row elements per unrolled pass (all of n1 + 27 n2 = 166)
+
+__global__ void __launch_bounds__(256) leaf_adam_kernel(const __grid_constant__ LeafAdamParams p)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    const int nc = p.n1 + 27 * p.n2;
+    for (uint32_t base = warp * 32; base < p.n_leaves; base += n_warps * 32) {
+        const uint32_t i = base + lane;
+        uint32_t id = 0;
+        bool marked = false;
+        if (i < p.n_leaves) {
+            id = __ldg(p.perm + i);
+            marked = p.leaf_mark[id] != 0;
+        }
+        uint32_t todo = __ballot_sync(0xffffffffu, marked);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint32_t leaf = base + src;
+            const uint32_t row = __shfl_sync(0xffffffffu, id, src);
+            const size_t at = (size_t)row * nc;
+            for (int j0 = 0; j0 < nc; j0 += LEAF_ADAM_CHUNK)
+#pragma unroll
+            for (int jj = 0; jj < LEAF_ADAM_CHUNK / 32; ++jj) {
+                const int j = j0 + lane + 32 * jj;
+                if (j < nc) {
+                    const float g = p.grad[at + j];
+                    const float mm = p.beta1 * p.m[at + j] + (1.0f - p.beta1) * g;
+                    const float vv = p.beta2 * p.v[at + j] + (1.0f - p.beta2) * g * g;
+                    const float w = p.param[at + j] - p.lr * (mm / p.bc1) / (sqrtf(vv / p.bc2) + p.eps);
+                    p.m[at + j] = mm;
+                    p.v[at + j] = vv;
+                    p.param[at + j] = w;
+                    p.grad[at + j] = 0.0f;
+                    if (j < p.n1) p.sig[(size_t)leaf * p.sig_stride + j] = w;
+                    else p.zc[(size_t)leaf * p.z_stride + (j - p.n1)] = w;
+                }
+            }
+        }
+        if (marked) p.leaf_mark[id] = 0;
+    }
+}
+
+int launch_leaf_adam(const LeafAdamParams &p, int sm_count, void *stream)
+{
+    if (p.n_leaves == 0) return (int)cudaSuccess;
+    uint64_t blocks = ((uint64_t)p.n_leaves + 255) / 256;
+    if (blocks > (uint64_t)sm_count * 8) blocks = (uint64_t)sm_count * 8;
+    leaf_adam_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);
     return (int)cudaGetLastError();
 }
 

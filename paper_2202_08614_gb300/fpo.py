@@ -32,7 +32,7 @@ EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
            "fpo_render_backward", "fpo_status_sync", "fpo_tree_info_get", "fpo_destroy",
            "fpo_last_error", "fpo_version", "fpo_render_noalloc", "fpo_set_coeffs",
            "fpo_dft_leaves", "fpo_union_trees", "fpo_latent_table", "fpo_decoder_grad",
-           "fpo_adam", "fpo_set_latents", "fpo_render_frames"]
+           "fpo_adam", "fpo_set_latents", "fpo_render_frames", "fpo_adam_leaves"]
 
 
 class FPOError(RuntimeError):
@@ -117,6 +117,8 @@ def lib():
                                C.c_float, C.c_float, C.c_uint32, P]
         L.fpo_set_latents.argtypes = [P, P, C.POINTER(Decoder), P]
         L.fpo_render_frames.argtypes = [P, P, C.c_uint32, C.POINTER(FrameOpts), P, P]
+        L.fpo_adam_leaves.argtypes = [P, P, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float,
+                                      C.c_uint32, P]
         L.fpo_union_trees.argtypes = [C.c_uint32, P, C.c_uint32, C.POINTER(C.c_uint32), P, P, P,
                                       C.c_uint32]
         L.fpo_status_sync.argtypes = [P, P]
@@ -348,12 +350,17 @@ class Renderer:
         torch.cuda.current_stream().synchronize()  # the copies read ws/bs
 
     def render_backward(self, out_rgb, dL_drgb, dL_dcoeffs, camera=None, t=0.0, rays_o=None,
-                        rays_d=None, t_per_ray=None, bg=(1.0, 1.0, 1.0), stop_T=1e-4, stream=None):
-        """Accumulates dL/d(coefficients) [n_leaves, n1 + 27 n2] (canonical) into dL_dcoeffs."""
+                        rays_d=None, t_per_ray=None, bg=(1.0, 1.0, 1.0), stop_T=1e-4, leaf_mark=None,
+                        stream=None):
+        """Accumulates dL/d(coefficients) [n_leaves, n1 + 27 n2] (canonical) into
+        dL_dcoeffs; sets leaf_mark[id] = 1 (uint8 CUDA tensor) for visited leaves."""
         r, keep, n = self._rays(camera, t, rays_o, rays_d, t_per_ray)
         opts = FrameOpts()
         opts.bg = (C.c_float * 3)(*bg)
         opts.stop_T = float(stop_T)
+        if leaf_mark is not None:
+            opts.flags = FLAG_MARK_LEAVES
+            opts.leaf_mark = leaf_mark.data_ptr()
         g = dL_drgb.contiguous()
         o = out_rgb.contiguous()
         check(lib().fpo_render_backward(self.h, C.byref(r), C.byref(opts),
@@ -362,6 +369,16 @@ class Renderer:
                                         C.c_void_p(dL_dcoeffs.data_ptr()),
                                         C.c_void_p(_stream_handle(stream))))
         del keep
+
+
+    def adam_leaves(self, param, grad, m, v, leaf_mark, step, lr=1e-2, betas=(0.9, 0.999), eps=1e-8,
+                    stream=None):
+        """Adam step on the marked leaves' rows, written back into the tree (fpo_adam_leaves)."""
+        check(lib().fpo_adam_leaves(self.h, C.c_void_p(param.data_ptr()), C.c_void_p(grad.data_ptr()),
+                                    C.c_void_p(m.data_ptr()), C.c_void_p(v.data_ptr()),
+                                    C.c_void_p(leaf_mark.data_ptr()), float(lr), float(betas[0]),
+                                    float(betas[1]), float(eps), int(step),
+                                    C.c_void_p(_stream_handle(stream))))
 
 
 def union_trees(frames, max_depth):

@@ -166,3 +166,108 @@ def test_finetune_recovers_perturbed_coefficients():
     r.close()
     print(f"held-out loss {l0:.3e} -> {l1:.3e}")
     assert l1 < 0.2 * l0
+
+
+# --------------------------------------------------------------------------
+# Row-sparse fine-tuning step: marks from the adjoint, fused Adam + write-back
+
+
+def _shell_rays(n, seed):
+    cams = synth.ring_cameras(16, 40, 40)
+    rays = [camera_rays(c) for c in cams]
+    rng = np.random.default_rng(seed)
+    v, p = rng.integers(0, 16, n), rng.integers(0, 1600, n)
+    o = torch.as_tensor(np.stack([rays[i][0][j] for i, j in zip(v, p)]), dtype=torch.float32, device="cuda")
+    d = torch.as_tensor(np.stack([rays[i][1][j] for i, j in zip(v, p)]), dtype=torch.float32, device="cuda")
+    t = torch.as_tensor(rng.uniform(0, 60, n), dtype=torch.float32, device="cuda")
+    return o, d, t
+
+
+def test_backward_marks_the_forward_visits():
+    tree = synth.shell_tree()
+    o, d, t = _shell_rays(4000, 1)
+    r = fpo.Renderer(idft_mode="fused")
+    r.upload(tree)
+    fwd = torch.zeros(tree.n_leaves, dtype=torch.uint8, device="cuda")
+    rgb = r.render(rays_o=o, rays_d=d, t_per_ray=t, leaf_mark=fwd)["rgb"]
+    bwd = torch.zeros_like(fwd)
+    g = torch.zeros(tree.coeffs.shape, device="cuda")
+    r.render_backward(rgb, torch.ones_like(rgb), g, rays_o=o, rays_d=d, t_per_ray=t, leaf_mark=bwd)
+    r.status()
+    r.close()
+    assert int(fwd.sum()) > 100
+    assert torch.equal(fwd, bwd)
+    # rows without a mark receive no gradient
+    assert float(g[bwd == 0].abs().max()) == 0.0
+
+
+def test_adam_leaves_matches_adam_on_marked_rows():
+    tree = synth.shell_tree()
+    n, nc = tree.coeffs.shape
+    rng = np.random.default_rng(4)
+    P0 = tree.coeffs.astype(np.float64) + rng.normal(size=(n, nc)) * 0.1
+    G0, M0 = rng.normal(size=(n, nc)), rng.normal(size=(n, nc)) * 0.1
+    V0 = rng.uniform(0, 0.5, (n, nc))
+    mk = (rng.uniform(size=n) < 0.3).astype(np.uint8)
+    dev = lambda a: torch.as_tensor(np.asarray(a, np.float32), device="cuda").contiguous()
+    P, G, M, V = dev(P0), dev(G0), dev(M0), dev(V0)
+    mark = torch.as_tensor(mk, device="cuda")
+    r = fpo.Renderer()
+    r.upload(tree)
+    r.set_coeffs(P)
+    lr, b1, b2, eps, step = 0.01, 0.9, 0.999, 1e-8, 3
+    r.adam_leaves(P, G, M, V, mark, step, lr=lr, betas=(b1, b2), eps=eps)
+    cam = synth.shell_camera(48, 48)
+    img = r.render(camera=cam, t=9.0)["rgb"].clone()
+    r.set_coeffs(P)
+    img2 = r.render(camera=cam, t=9.0)["rgb"]
+    r.status()
+    r.close()
+    # Adam (Kingma & Ba) on the marked rows, from the FP32 inputs in FP64
+    f = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    m_ = b1 * f(M0) + (1 - b1) * f(G0)
+    v_ = b2 * f(V0) + (1 - b2) * f(G0) ** 2
+    p_ = f(P0) - lr * (m_ / (1 - b1 ** step)) / (np.sqrt(v_ / (1 - b2 ** step)) + eps)
+    on = mk.astype(bool)
+    Pn, Gn, Mn, Vn = (x.cpu().numpy() for x in (P, G, M, V))
+    np.testing.assert_allclose(Pn[on], p_[on], atol=1e-6)
+    # FP32 arithmetic: 1 - beta2 = 0.001 itself carries a relative error of
+    # about 2^-24 / 0.001 = 6e-5, so the moments agree to ~1e-6 absolute
+    np.testing.assert_allclose(Mn[on], m_[on], rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(Vn[on], v_[on], rtol=1e-6, atol=1e-6)
+    assert np.array_equal(Pn[~on], np.float32(P0[~on])) and np.array_equal(Mn[~on], np.float32(M0[~on]))
+    assert np.array_equal(Gn[~on], np.float32(G0[~on])) and not Gn[on].any()
+    assert int(mark.sum()) == 0
+    # the records were written with the new rows: same image as set_coeffs(P)
+    assert torch.equal(img, img2)
+
+
+def test_finetuner_recovers_perturbed_coefficients():
+    # Eq. 13 with the library's row-sparse step (marks -> fused Adam + write-back)
+    from paper_2202_08614_gb300.finetune import FineTuner
+
+    tree = synth.shell_tree()
+    rng = np.random.default_rng(3)
+    k_true = torch.as_tensor(tree.coeffs, device="cuda")
+    noise = rng.normal(size=tree.coeffs.shape) * (0.1 * np.abs(tree.coeffs) + 0.05)
+    ref = fpo.Renderer(idft_mode="fused")
+    ref.upload(tree)
+    r = fpo.Renderer(idft_mode="fused")
+    r.upload(tree)
+    ft = FineTuner(r, k_true + torch.as_tensor(noise, dtype=torch.float32, device="cuda"), lr=1e-2)
+    ho = _shell_rays(8192, 99)
+    y_ho = ref.render(rays_o=ho[0], rays_d=ho[1], t_per_ray=ho[2])["rgb"].clone()
+    held = lambda: float(((ft.render(*ho) - y_ho) ** 2).sum(1).mean())
+    l0 = held()
+    for s in range(150):
+        o, d, t = _shell_rays(8192, 1000 + s)
+        y = ref.render(rays_o=o, rays_d=d, t_per_ray=t)["rgb"].clone()
+        ft.step(o, d, t, y)
+    l1 = held()
+    r.status()
+    ref.status()
+    r.close()
+    ref.close()
+    print(f"held-out loss {l0:.3e} -> {l1:.3e}")
+    assert l1 < 0.2 * l0
+    assert int(ft.mark.sum()) == 0
