@@ -197,7 +197,7 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames,
  * the leaf coefficients against the loss of Eq. 13): given dL/d(rgb) (device
  * [rays][3]) it accumulates dL/d(coefficients) into dL_dcoeffs, a device
  * array [n_leaves][n1 + 27*n2] in canonical order and upload order (the
- * caller zeroes it).  out_rgb is the forward colour of the same rays and
+ * caller zeroes it; 16-byte aligned, as cudaMalloc returns it).  out_rgb is the forward colour of the same rays and
  * options.  Each ray is replayed with the per-visit IDFT, so the segments and
  * the early stop are those of a FUSED-mode forward (treated as fixed: the
  * truncation is part of the function); sigma = max(0, sigma_raw) passes no

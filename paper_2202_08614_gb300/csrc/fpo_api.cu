@@ -594,6 +594,8 @@ int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts
         return fail(FPO_ERR_UNSUPPORTED, "the adjoint supports (n1, n2) in {(31,5), (11,5), (21,5), (31,11)}");
     if (n_rays > 0 && (!out_rgb || !dL_drgb)) return fail(FPO_ERR_INVALID_ARG, "out_rgb and dL_drgb must be non-NULL");
     if (ctx->n_leaves > 0 && !dL_dcoeffs) return fail(FPO_ERR_INVALID_ARG, "dL_dcoeffs is NULL");
+    if (reinterpret_cast<uintptr_t>(dL_dcoeffs) % 16 != 0)
+        return fail(FPO_ERR_INVALID_ARG, "dL_dcoeffs must be 16-byte aligned");
     if (!(opts->stop_T >= 0.0f)) return fail(FPO_ERR_INVALID_ARG, "stop_T must be >= 0");
     if (n_rays == 0 || ctx->n_leaves == 0) return FPO_OK;
     DeviceGuard g(ctx->cfg.device);

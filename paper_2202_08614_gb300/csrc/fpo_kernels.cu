@@ -705,6 +705,19 @@ __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const f
     return !step_cap(p, R);
 }
 
+// Fused mode: the coefficient records of the next leaf (672 B at n1 = 31,
+// n2 = 5) are pulled into L2 by two bulk prefetches while the current leaf is
+// shaded, so its 32-byte loads hit L2 instead of HBM.
+__device__ __forceinline__ void prefetch_records(const TraverseParams &p, uint32_t leaf, int n1, int n2)
+{
+    const float4 *sr = p.sig + (size_t)leaf * p.sig_stride4;
+    const float *zr = p.zc + (size_t)leaf * p.z_stride;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sr), "r"((uint32_t)(p.sig_stride4 * 16)));
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(zr), "r"((uint32_t)(p.z_stride * 4)));
+    (void)n1;
+    (void)n2;
+}
+
 // A whole ray (lane-loop schedule).  Software-pipelined: the next cube is
 // located, and its table record prefetched into L1, before the current cube
 // is shaded, so the record's latency hides behind the shading arithmetic.
@@ -725,8 +738,12 @@ __device__ void trace_ray(const TraverseParams &p, const float *bsrc, int bstrid
         if (FPO_PREFETCH && inside) {
             const uint32_t diff = (uint32_t)((R.P[0] ^ Pn[0]) | (R.P[1] ^ Pn[1]) | (R.P[2] ^ Pn[2]));
             nx = locate(p, s_nodes, s_stack, stride, Pn, D - 1 - (31 - __clz(diff)), nc);
-            if (MAT && nx.kind == ROOT_LEAF)
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record(p, nx.leaf)));
+            if (nx.kind == ROOT_LEAF) {
+                if constexpr (MAT)
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record(p, nx.leaf)));
+                else
+                    prefetch_records(p, nx.leaf, N1, N2);
+            }
         }
         if (cb.kind == ROOT_LEAF && tx > R.t)
             if (shade<MAT, DBG, N1, N2>(p, bsrc, bstride, R, cb.leaf, tx - R.t)) return;
@@ -1010,8 +1027,8 @@ int launch_traverse(const TraverseParams &p, bool materialised, bool debug, int 
 //   dL/du_jc    = g_c w_j c_jc (1 - c_jc),   u = sum_k z_ck Y_k,
 //   dL/dk_sigma_i += dL/dsigma_j [sigma_raw > 0] IDFT_i(t),
 //   dL/dk_cki     += dL/du_jc Y_k IDFT_i(t),
-// accumulated with 8-byte vector atomics into the canonical gradient row of
-// the leaf's upload id (rows of n1 + 27 n2 floats are 8-byte aligned).
+// accumulated with 16-byte vector atomics (one 8-byte atomic at an unaligned
+// end) into the canonical gradient row of the leaf's upload id.
 
 template <int N1, int N2>
 __device__ void backward_ray(const BackwardParams &q, const float *bsrc, int bstride,
@@ -1034,6 +1051,17 @@ __device__ void backward_ray(const BackwardParams &q, const float *bsrc, int bst
     for (;;) {
         int m, lo[3], csz;
         const float tx = cube_exit(R, D, cb.lvl, m, lo, csz);
+        // as in the forward: locate the next cube and prefetch its records
+        // before this one is processed
+        int Pn[3];
+        const bool inside = next_cell(R, G, m, lo, csz, tx, Pn);
+        Cube nx;
+        nx.kind = ROOT_EMPTY;
+        if (FPO_PREFETCH && inside) {
+            const uint32_t diff = (uint32_t)((R.P[0] ^ Pn[0]) | (R.P[1] ^ Pn[1]) | (R.P[2] ^ Pn[2]));
+            nx = locate(p, s_nodes, s_stack, stride, Pn, D - 1 - (31 - __clz(diff)), nc);
+            if (nx.kind == ROOT_LEAF) prefetch_records(p, nx.leaf, N1, N2);
+        }
         if (cb.kind == ROOT_LEAF && tx > R.t) {
             const float delta = tx - R.t;
             const float *sr = reinterpret_cast<const float *>(p.sig + (size_t)cb.leaf * p.sig_stride4);
@@ -1082,31 +1110,40 @@ __device__ void backward_ray(const BackwardParams &q, const float *bsrc, int bst
             const float gu[3] = {g0 * w * col[0] * (1.0f - col[0]), g1 * w * col[1] * (1.0f - col[1]),
                                  g2 * w * col[2] * (1.0f - col[2])};
             const uint32_t id = p.perm[cb.leaf];
-            float2 *row = reinterpret_cast<float2 *>(q.dL_dcoeffs + (size_t)id * NC);
+            float *row = q.dL_dcoeffs + (size_t)id * NC;
             if (q.leaf_mark) q.leaf_mark[id] = 1;
+            // dL/dk for element el of the row (compile-time el)
+            auto gval = [&](int el) -> float {
+                if (el < N1) return dsr * bsrc[el * bstride];
+                const int j = el - N1, c = j / (9 * N2), k = (j / N2) % 9, i = j % N2;
+                return gu[c] * R.Y[k] * bz[i];
+            };
+            // 16-byte vector atomics; a row that starts 8 bytes past a 16-byte
+            // boundary (NC = 2 mod 4, odd id) opens with one 8-byte atomic
+            if (NC % 4 == 0 || (id & 1u) == 0u) {
 #pragma unroll
-            for (int e2 = 0; e2 < NC / 2; ++e2) {
-                float v[2];
+                for (int e4 = 0; e4 < NC / 4; ++e4)
+                    atomicAdd(reinterpret_cast<float4 *>(row) + e4,
+                              make_float4(gval(4 * e4), gval(4 * e4 + 1), gval(4 * e4 + 2), gval(4 * e4 + 3)));
+                if constexpr (NC % 4 == 2)
+                    atomicAdd(reinterpret_cast<float2 *>(row + NC - 2), make_float2(gval(NC - 2), gval(NC - 1)));
+            } else {
+                atomicAdd(reinterpret_cast<float2 *>(row), make_float2(gval(0), gval(1)));
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int el = 2 * e2 + h;
-                    if (el < N1) {
-                        v[h] = dsr * bsrc[el * bstride];
-                    } else {
-                        const int j = el - N1, c = j / (9 * N2), k = (j / N2) % 9, i = j % N2;
-                        v[h] = gu[c] * R.Y[k] * bz[i];
-                    }
-                }
-                atomicAdd(row + e2, make_float2(v[0], v[1]));
+                for (int e4 = 0; e4 < NC / 4; ++e4)
+                    atomicAdd(reinterpret_cast<float4 *>(row + 2) + e4,
+                              make_float4(gval(2 + 4 * e4), gval(3 + 4 * e4), gval(4 + 4 * e4), gval(5 + 4 * e4)));
             }
             R.T = Tn;
             if (R.T < p.stop_T) return;
         }
-        int Pn[3];
-        if (!next_cell(R, G, m, lo, csz, tx, Pn)) return;
+        if (!inside) return;
         move_to(R, D, Pn, tx);
         if (step_cap(p, R)) return;
-        cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start, nc);
+        if (FPO_PREFETCH)
+            cb = nx;
+        else
+            cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start, nc);
     }
 }
 
