@@ -311,7 +311,8 @@ typedef struct {
  * decoder's output and sigma, z follow Eq. 7 and Eq. 9 at time t.  The IDFT
  * is folded into the last layer (W3' = B(t) W3), so the MLP runs 32 -> 64 ->
  * 64 -> 28 with FP16 operands and FP32 accumulation (BF16 weights are
- * converted to FP16 in shared memory).  latents: device FP16 [n_leaves][32].
+ * converted to FP16 in shared memory).  latents: device FP16 [n_leaves][32],
+ * 16-byte aligned.
  * status: optional device word that receives FPO_ERR_DEVICE_TIMEOUT's bit
  * when a bounded wait gives up.  Runs on the current device and stream.
  * Errors: INVALID_ARG, CUDA. */

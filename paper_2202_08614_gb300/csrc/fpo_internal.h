@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>  // CUtensorMap (a header type; nothing links the driver library)
 #include <vector_types.h>
 
 #include "fpo.h"
@@ -177,6 +178,7 @@ struct LatentParams {
     uint32_t n_leaves;
     float *table;             // [n_leaves][TABLE_STRIDE]
     uint32_t *status;
+    CUtensorMap table_map;    // set by launch_latent_table: the table as [n_leaves][32] FP32, 128-byte swizzle
 };
 
 int launch_latent_table(const LatentParams &p, int sm_count, void *stream);

@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cstdint>
 
@@ -29,10 +30,14 @@
 namespace fpo {
 namespace {
 
-constexpr int LT_GROUPS = 4;       // independent warpgroup pipelines per CTA
+#ifndef FPO_LT_GROUPS
+#define FPO_LT_GROUPS 4
+#endif
+constexpr int LT_GROUPS = FPO_LT_GROUPS;  // independent warpgroup pipelines per CTA (one CTA per SM)
 constexpr int LT_THREADS = 128 * LT_GROUPS;
 constexpr int LT_M = 128;          // leaves per tile = MMA M
 constexpr uint32_t LT_TMEM_COLS = 64 * LT_GROUPS;  // 64 accumulator columns per warpgroup
+static_assert(LT_TMEM_COLS <= 512 && (LT_TMEM_COLS & (LT_TMEM_COLS - 1)) == 0, "TMEM allocation");
 constexpr uint64_t LT_WAIT_NS = 2000000000ull;
 
 // Shared-memory layout (bytes), all operands no-swizzle K-major.
@@ -42,7 +47,7 @@ constexpr int OFF_W3 = 12288;      // 32 x 64  f16:  4 KB
 constexpr int OFF_A1 = 16384;      // per group: 128 x 32 f16:  8 KB
 constexpr int OFF_A2 = 24576;      // per group: 128 x 64 f16: 16 KB
 constexpr int GROUP_BYTES = 24576; // A1 + A2 of one warpgroup
-constexpr int LT_SMEM = 16384 + LT_GROUPS * GROUP_BYTES;
+constexpr int LT_SMEM = 16384 + LT_GROUPS * GROUP_BYTES + 1024;  // + alignment slack
 
 // Byte offset of element (row, k) in a K-major core-matrix layout whose rows
 // hold K elements: core matrix (row / 8, k / 8) at ((row/8) * K/8 + k/8) * 128,
@@ -83,19 +88,73 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// 16 consecutive FP32 columns of this thread's TMEM lane; waits for them.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+// 64 consecutive FP32 columns of this thread's TMEM lane: two 32-column
+// loads in flight, then one wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float v[64])
 {
-    uint32_t r[16];
+    uint32_t r[64];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr), "r"(taddr + 32)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane; waits for them.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr)
         : "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Tensor store of a 128-row tile of the table (box 32 floats x 128 rows,
+// 128-byte swizzle) from shared memory, committed as its own bulk group.
+__device__ __forceinline__ void tensor_store_rows(const CUtensorMap *map, const void *src, uint32_t row0)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n\t"
+                 "cp.async.bulk.commit_group;" ::"l"(reinterpret_cast<uint64_t>(map)),
+                 "r"(0), "r"(row0), "r"(ptx::smem_u32(src))
+                 : "memory");
+}
+// Waits until every committed bulk store has finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Waits until every committed bulk store has completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Rounds 8 consecutive values to FP16 with ReLU (max(x, 0) after rounding
+// equals rounding after max) and writes them as K-chunk j of row `row` of a
+// core layout.
+__device__ __forceinline__ void put8_relu(unsigned char *base, int row, int j, int K, const float *v)
+{
+    uint32_t h[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)  // the first operand goes to the upper half
+        asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(h[e]) : "f"(v[2 * e + 1]), "f"(v[2 * e]));
+    *reinterpret_cast<uint4 *>(base + core_off(row, 8 * j, K)) = make_uint4(h[0], h[1], h[2], h[3]);
+}
+
+// v[e] += b[e] for 16 values, the biases read as float4.
+__device__ __forceinline__ void add_bias(float v[16], const float *b)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 bb = reinterpret_cast<const float4 *>(b)[q];
+        v[4 * q] += bb.x;
+        v[4 * q + 1] += bb.y;
+        v[4 * q + 2] += bb.z;
+        v[4 * q + 3] += bb.w;
+    }
 }
 
 // Writes 8 consecutive values of row `row` (K-chunk j) into a core layout.
@@ -127,10 +186,12 @@ __device__ __forceinline__ void group_sync(int group)
     asm volatile("bar.sync %0, 128;" ::"r"(1 + group) : "memory");
 }
 
-__global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_constant__ LatentParams p)
+__global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __grid_constant__ LatentParams p)
 {
-    extern __shared__ __align__(1024) unsigned char lt_smem[];
-    __shared__ float s_b1[64], s_b2[64], s_b3[32], s_basis[32];
+    extern __shared__ __align__(1024) unsigned char lt_smem_raw[];
+    // the 128-byte-swizzled output staging needs 1024-byte aligned buffers
+    unsigned char *lt_smem = lt_smem_raw + ((1024u - (ptx::smem_u32(lt_smem_raw) & 1023u)) & 1023u);
+    __shared__ __align__(16) float s_b1[64], s_b2[64], s_b3[32], s_basis[32];
     __shared__ uint64_t s_bar[LT_GROUPS];
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail[LT_GROUPS];
@@ -149,8 +210,8 @@ __global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_c
     if (tid < LT_GROUPS) {
         s_fail[tid] = 0;
         ptx::mbar_init(&s_bar[tid], 1);
+        ptx::fence_barrier_init();
     }
-    if (tid == 0) ptx::fence_barrier_init();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(ptx::smem_u32(&s_tmem)),
                      "r"(LT_TMEM_COLS)
@@ -172,34 +233,24 @@ __global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_c
         put8(lt_smem + OFF_W2, n, j, 64, v);
     }
     __syncthreads();  // s_basis ready
-    // W3'(t): row 0 = sum_i b_i W3[i], row 1 + q = sum_i b_i W3[n1 + q n2 + i], rows 28..31 = 0
-    for (int q = tid; q < 32 * 8; q += LT_THREADS) {
-        const int r = q >> 3, j = q & 7;
-        float v[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int h = 8 * j + e;
-            float acc = 0.0f;
-            if (r == 0) {
-                for (int i = 0; i < p.n1; ++i)
-                    acc = fmaf(s_basis[i], __bfloat162float(__ushort_as_bfloat16(p.w3[i * 64 + h])), acc);
-            } else if (r <= 27) {
-                const int row0 = p.n1 + (r - 1) * p.n2;
-                for (int i = 0; i < p.n2; ++i)
-                    acc = fmaf(s_basis[i], __bfloat162float(__ushort_as_bfloat16(p.w3[(row0 + i) * 64 + h])), acc);
-            }
-            v[e] = acc;
-        }
-        put8(lt_smem + OFF_W3, r, j, 64, v);
+    // W3'(t): row 0 = sum_i b_i W3[i], row 1 + q = sum_i b_i W3[n1 + q n2 + i],
+    // rows 28..31 = 0.  One output element per thread and pass: the loads of a
+    // row are coalesced over h and independent of each other (unrolled), so
+    // the prologue costs a few memory latencies, not one per term.
+    for (int q = tid; q < 32 * 64; q += LT_THREADS) {
+        const int r = q >> 6, h = q & 63;
+        const int row0 = r == 0 ? 0 : p.n1 + (r - 1) * p.n2, terms = r == 0 ? p.n1 : (r <= 27 ? p.n2 : 0);
+        float acc = 0.0f;
+#pragma unroll 8
+        for (int i = 0; i < terms; ++i)
+            acc = fmaf(s_basis[i], __bfloat162float(__ushort_as_bfloat16(p.w3[(row0 + i) * 64 + h])), acc);
+        *reinterpret_cast<__half *>(lt_smem + OFF_W3 + core_off(r, h, 64)) = __float2half_rn(acc);
     }
     if (tid < 32) {
+        const int row0 = tid == 0 ? 0 : p.n1 + (tid - 1) * p.n2, terms = tid == 0 ? p.n1 : (tid <= 27 ? p.n2 : 0);
         float acc = 0.0f;
-        if (tid == 0) {
-            for (int i = 0; i < p.n1; ++i) acc = fmaf(s_basis[i], p.b3[i], acc);
-        } else if (tid <= 27) {
-            const int row0 = p.n1 + (tid - 1) * p.n2;
-            for (int i = 0; i < p.n2; ++i) acc = fmaf(s_basis[i], p.b3[row0 + i], acc);
-        }
+#pragma unroll 8
+        for (int i = 0; i < terms; ++i) acc = fmaf(s_basis[i], p.b3[row0 + i], acc);
         s_b3[tid] = acc;
     }
     fence_async_smem();
@@ -238,70 +289,88 @@ __global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_c
         fence_before();
         group_sync(group);
     };
-    auto load_row = [&](uint32_t tile, uint4 q[4]) {
-        const uint32_t leaf = tile * LT_M + (uint32_t)m;
+    // The tile's latents (128 rows x 64 B, contiguous) in coalesced 16-byte
+    // pieces: thread gt takes pieces gt + 128 i, i.e. row (gt + 128 i) / 4,
+    // K-chunk (gt + 128 i) % 4; rows past the end read as zeros.
+    auto load_tile = [&](uint32_t tile, uint4 q[4]) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(p.latents) + (size_t)tile * LT_M * 4;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) q[j] = make_uint4(0, 0, 0, 0);
-        if (tile < n_tiles && leaf < p.n_leaves) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(p.latents + (size_t)leaf * 32);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) q[j] = __ldg(src + j);
+        for (int i = 0; i < 4; ++i) {
+            const int piece = gt + 128 * i;
+            q[i] = make_uint4(0, 0, 0, 0);
+            if (tile < n_tiles && tile * LT_M + (uint32_t)(piece >> 2) < p.n_leaves) q[i] = __ldg(src + piece);
         }
     };
     uint4 nextq[4];
-    load_row(first, nextq);
+    load_tile(first, nextq);
     for (uint32_t tile = first; tile < n_tiles; tile += step) {
-        const uint32_t leaf = tile * LT_M + (uint32_t)m;
-        const bool valid = leaf < p.n_leaves;
+        if (gt == 0) bulk_wait_read();  // the previous tile's table store has left A2
 #pragma unroll
-        for (int j = 0; j < 4; ++j) *reinterpret_cast<uint4 *>(ga1 + core_off(m, 8 * j, 32)) = nextq[j];
+        for (int i = 0; i < 4; ++i) {
+            const int piece = gt + 128 * i;
+            *reinterpret_cast<uint4 *>(ga1 + core_off(piece >> 2, 8 * (piece & 3), 32)) = nextq[i];
+        }
         hand_off();
         if (!run_layer(sa_a1, sa_w1, 32, 64)) break;
         // layer 1 epilogue: bias + ReLU -> layer-2 A operand (MMA 1 is done with A1)
+        {
+            float v[64];
+            tmem_ld64(my_lane, v);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float v[16];
-            tmem_ld16(my_lane + 16 * c, v);
-#pragma unroll
-            for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e] + s_b1[16 * c + e], 0.0f);
-            put8(ga2, m, 2 * c, 64, v);
-            put8(ga2, m, 2 * c + 1, 64, v + 8);
+            for (int c = 0; c < 4; ++c) {
+                add_bias(v + 16 * c, s_b1 + 16 * c);
+                put8_relu(ga2, m, 2 * c, 64, v + 16 * c);
+                put8_relu(ga2, m, 2 * c + 1, 64, v + 16 * c + 8);
+            }
         }
         hand_off();
         if (!run_layer(sa_a2, sa_w2, 64, 64)) break;
         // layer 2 epilogue -> layer-3 A operand, in place (MMA 2 has finished
         // reading A2, and each thread rewrites only its own row)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float v[16];
-            tmem_ld16(my_lane + 16 * c, v);
-#pragma unroll
-            for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e] + s_b2[16 * c + e], 0.0f);
-            put8(ga2, m, 2 * c, 64, v);
-            put8(ga2, m, 2 * c + 1, 64, v + 8);
-        }
-        hand_off();
-        load_row(tile + step, nextq);  // in flight while layer 3 runs
-        if (!run_layer(sa_a2, sa_w3, 64, 32)) break;
         {
-            float o[32];
-            tmem_ld16(my_lane, o);
-            tmem_ld16(my_lane + 16, o + 16);
-            if (valid) {
-                float4 *dst = reinterpret_cast<float4 *>(p.table + (size_t)leaf * TABLE_STRIDE);
-                float w[32];
-                w[0] = fmaxf(o[0] + s_b3[0], 0.0f);
+            float v[64];
+            tmem_ld64(my_lane, v);
 #pragma unroll
-                for (int q = 1; q < 28; ++q) w[q] = o[q] + s_b3[q];
-#pragma unroll
-                for (int q = 28; q < 32; ++q) w[q] = 0.0f;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) dst[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+            for (int c = 0; c < 4; ++c) {
+                add_bias(v + 16 * c, s_b2 + 16 * c);
+                put8_relu(ga2, m, 2 * c, 64, v + 16 * c);
+                put8_relu(ga2, m, 2 * c + 1, 64, v + 16 * c + 8);
             }
         }
+        hand_off();
+        load_tile(tile + step, nextq);  // in flight while layer 3 runs
+        if (!run_layer(sa_a2, sa_w3, 64, 32)) break;
+        {
+            // output rows [max(0, sigma), 27 z, 0 x 4] into A2 (free since MMA 3
+            // finished), then one bulk copy of the tile's contiguous rows
+            float o[32];
+            tmem_ld32(my_lane, o);
+            float w[32];
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                const float4 bb = reinterpret_cast<const float4 *>(s_b3)[q];
+                w[4 * q] = o[4 * q] + bb.x;
+                w[4 * q + 1] = o[4 * q + 1] + bb.y;
+                w[4 * q + 2] = o[4 * q + 2] + bb.z;
+                w[4 * q + 3] = o[4 * q + 3] + bb.w;
+            }
+            w[0] = fmaxf(w[0], 0.0f);
+#pragma unroll
+            for (int q = 28; q < 32; ++q) w[q] = 0.0f;
+            // 128-byte swizzle (chunk q of row m at chunk q ^ (m % 8)): the 8
+            // lanes of a store phase hit 8 different bank groups, and the
+            // tensor store un-swizzles on the way out
+            float4 *row = reinterpret_cast<float4 *>(ga2 + m * (TABLE_STRIDE * 4));
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                row[q ^ (m & 7)] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        }
+        fence_async_smem();
         fence_before();
-        group_sync(group);  // the accumulator is free for the next tile's MMA
+        group_sync(group);  // the rows are in A2; the accumulator is free for the next tile
+        if (gt == 0) tensor_store_rows(&p.table_map, ga2, tile * LT_M);  // rows past the end are clipped
     }
+    if (gt == 0) bulk_wait_all();  // every table store has completed
     if (s_fail[group] && gt == 0) {
         // an MMA that never signalled: wait once more (bounded) before freeing TMEM
         ptx::mbar_wait_bounded(&s_bar[group], phase, LT_WAIT_NS);
@@ -313,16 +382,43 @@ __global__ void __launch_bounds__(LT_THREADS) latent_table_kernel(const __grid_c
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(LT_TMEM_COLS) : "memory");
 }
 
-int launch_latent_table(const LatentParams &p, int sm_count, void *stream)
+// cuTensorMapEncodeTiled from the driver, looked up once.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
-    if (p.n_leaves == 0) return (int)cudaSuccess;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+int launch_latent_table(const LatentParams &pin, int sm_count, void *stream)
+{
+    if (pin.n_leaves == 0) return (int)cudaSuccess;
+    LatentParams p = pin;
+    // the table as a 2-D tensor [n_leaves][32] FP32 (128-byte rows), stored in
+    // boxes of 128 rows from 128-byte-swizzled shared memory
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return (int)cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {TABLE_STRIDE, p.n_leaves};
+    const cuuint64_t strides[1] = {TABLE_STRIDE * sizeof(float)};
+    const cuuint32_t box[2] = {TABLE_STRIDE, LT_M};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&p.table_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p.table, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return (int)cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(latent_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, LT_SMEM);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, latent_table_kernel, LT_THREADS, LT_SMEM);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) per_sm = 1;
-    if (per_sm > 2) per_sm = 2;  // 2 x 256 TMEM columns = 512
+    if ((uint64_t)per_sm * LT_TMEM_COLS > 512) per_sm = (int)(512 / LT_TMEM_COLS);  // TMEM has 512 columns
     const uint32_t n_tiles = (p.n_leaves + LT_M - 1) / LT_M;
     uint64_t blocks = (uint64_t)sm_count * per_sm;
     const uint64_t need = (n_tiles + LT_GROUPS - 1) / LT_GROUPS;
@@ -345,6 +441,8 @@ extern "C" int fpo_latent_table(const fpo_decoder *dec, int32_t n1, int32_t n2, 
     if (n_leaves == 0) return FPO_OK;
     if (!latents || !table || !dec->w1 || !dec->b1 || !dec->w2 || !dec->b2 || !dec->w3 || !dec->b3)
         return set_last_error(FPO_ERR_INVALID_ARG, "NULL array");
+    if (reinterpret_cast<uintptr_t>(latents) % 16 != 0 || reinterpret_cast<uintptr_t>(table) % 16 != 0)
+        return set_last_error(FPO_ERR_INVALID_ARG, "latents and table must be 16-byte aligned");
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
