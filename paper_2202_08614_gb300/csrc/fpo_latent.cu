@@ -15,8 +15,9 @@
 // one elected thread issues tcgen05.mma (M = 128, K = 16 per instruction,
 // FP16 x FP16 -> FP32 in TMEM) and commits to the mbarrier, and the warps
 // read the accumulator rows back with tcgen05.ld (one row per thread, a
-// warp's TMEM lane quarter), apply bias and ReLU and write the next layer's
-// A operand.  The 64 columns hold every layer's accumulator in turn.
+// warp's TMEM lane quarter), apply ReLU while rounding to FP16 and write the
+// next layer's A operand.  The 64 columns hold every layer's accumulator in
+// turn.  The output tile goes out by one TMA tensor store per tile.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -40,14 +41,22 @@ constexpr uint32_t LT_TMEM_COLS = 64 * LT_GROUPS;  // 64 accumulator columns per
 static_assert(LT_TMEM_COLS <= 512 && (LT_TMEM_COLS & (LT_TMEM_COLS - 1)) == 0, "TMEM allocation");
 constexpr uint64_t LT_WAIT_NS = 2000000000ull;
 
+// Biases ride in the MMAs: every A operand carries two constant-one columns
+// after its data and every B operand the bias split into two FP16 halves
+// (hi = fp16(b), lo = fp16(b - hi), so hi + lo carries b to about 22 bits)
+// in the same two columns; the accumulator then already holds W x + b.  K
+// is padded to a multiple of 16 with zeros: 32 + 16 for layer 1, 64 + 16 for
+// layers 2 and 3.
+constexpr int K1 = 48, K2 = 80;
+
 // Shared-memory layout (bytes), all operands no-swizzle K-major.
-constexpr int OFF_W1 = 0;          // 64 x 32  f16:  4 KB
-constexpr int OFF_W2 = 4096;       // 64 x 64  f16:  8 KB
-constexpr int OFF_W3 = 12288;      // 32 x 64  f16:  4 KB
-constexpr int OFF_A1 = 16384;      // per group: 128 x 32 f16:  8 KB
-constexpr int OFF_A2 = 24576;      // per group: 128 x 64 f16: 16 KB
-constexpr int GROUP_BYTES = 24576; // A1 + A2 of one warpgroup
-constexpr int LT_SMEM = 16384 + LT_GROUPS * GROUP_BYTES + 1024;  // + alignment slack
+constexpr int OFF_W1 = 0;          // 64 x 48  f16:  6 KB
+constexpr int OFF_W2 = 6144;       // 64 x 80  f16: 10 KB
+constexpr int OFF_W3 = 16384;      // 32 x 80  f16:  5 KB
+constexpr int OFF_A1 = 22528;      // per group: 128 x 48 f16: 12 KB
+constexpr int OFF_A2 = 34816;      // per group: 128 x 80 f16: 20 KB (1024-byte aligned: output staging)
+constexpr int GROUP_BYTES = 32768; // A1 + A2 of one warpgroup
+constexpr int LT_SMEM = OFF_A1 + LT_GROUPS * GROUP_BYTES + 1024;  // + alignment slack
 
 // Byte offset of element (row, k) in a K-major core-matrix layout whose rows
 // hold K elements: core matrix (row / 8, k / 8) at ((row/8) * K/8 + k/8) * 128,
@@ -144,19 +153,6 @@ __device__ __forceinline__ void put8_relu(unsigned char *base, int row, int j, i
     *reinterpret_cast<uint4 *>(base + core_off(row, 8 * j, K)) = make_uint4(h[0], h[1], h[2], h[3]);
 }
 
-// v[e] += b[e] for 16 values, the biases read as float4.
-__device__ __forceinline__ void add_bias(float v[16], const float *b)
-{
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float4 bb = reinterpret_cast<const float4 *>(b)[q];
-        v[4 * q] += bb.x;
-        v[4 * q + 1] += bb.y;
-        v[4 * q + 2] += bb.z;
-        v[4 * q + 3] += bb.w;
-    }
-}
-
 // Writes 8 consecutive values of row `row` (K-chunk j) into a core layout.
 __device__ __forceinline__ void put8(unsigned char *base, int row, int j, int K, const float *v)
 {
@@ -164,6 +160,24 @@ __device__ __forceinline__ void put8(unsigned char *base, int row, int j, int K,
 #pragma unroll
     for (int e = 0; e < 4; ++e) h[e] = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
     *reinterpret_cast<uint4 *>(base + core_off(row, 8 * j, K)) = *reinterpret_cast<const uint4 *>(h);
+}
+
+// K-chunk j of row `row` = {hi(b), lo(b), 0 x 6}: the bias columns of a B
+// operand; with `ones`, {1, 1, 0 x 6}: the constant columns of an A operand.
+__device__ __forceinline__ void put_bias_chunk(unsigned char *base, int row, int j, int K, float b, bool ones)
+{
+    const __half hi = ones ? __float2half_rn(1.0f) : __float2half_rn(b);
+    const __half lo = ones ? __float2half_rn(1.0f) : __float2half_rn(b - __half2float(hi));
+    const __half2 h0 = __halves2half2(hi, lo), z = __float2half2_rn(0.0f);
+    uint4 u;
+    u.x = *reinterpret_cast<const uint32_t *>(&h0);
+    u.y = u.z = u.w = *reinterpret_cast<const uint32_t *>(&z);
+    *reinterpret_cast<uint4 *>(base + core_off(row, 8 * j, K)) = u;
+}
+
+__device__ __forceinline__ void put_zero_chunk(unsigned char *base, int row, int j, int K)
+{
+    *reinterpret_cast<uint4 *>(base + core_off(row, 8 * j, K)) = make_uint4(0, 0, 0, 0);
 }
 
 // Issues the K / 16 MMAs of D[128 x N] = A[128 x K] B[N x K]^T.
@@ -191,7 +205,7 @@ __global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __gri
     extern __shared__ __align__(1024) unsigned char lt_smem_raw[];
     // the 128-byte-swizzled output staging needs 1024-byte aligned buffers
     unsigned char *lt_smem = lt_smem_raw + ((1024u - (ptx::smem_u32(lt_smem_raw) & 1023u)) & 1023u);
-    __shared__ __align__(16) float s_b1[64], s_b2[64], s_b3[32], s_basis[32];
+    __shared__ float s_basis[32];
     __shared__ uint64_t s_bar[LT_GROUPS];
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail[LT_GROUPS];
@@ -203,10 +217,6 @@ __global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __gri
     if (tid < 32) s_basis[tid] = tid < nb ? (float)((tid & 1) ? sinpi((double)(tid + 1) * (p.t / p.period_T))
                                                              : cospi((double)tid * (p.t / p.period_T)))
                                          : 0.0f;
-    if (tid < 64) {
-        s_b1[tid] = p.b1[tid];
-        s_b2[tid] = p.b2[tid];
-    }
     if (tid < LT_GROUPS) {
         s_fail[tid] = 0;
         ptx::mbar_init(&s_bar[tid], 1);
@@ -218,19 +228,31 @@ __global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __gri
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int q = tid; q < 64 * 4; q += LT_THREADS) {  // W1: 64 rows x 4 chunks
-        const int n = q >> 2, j = q & 3;
-        float v[8];
+    for (int q = tid; q < 64 * (K1 / 8); q += LT_THREADS) {  // W1 | b1: 64 rows x 6 chunks
+        const int n = q / (K1 / 8), j = q % (K1 / 8);
+        if (j < 4) {
+            float v[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = __bfloat162float(__ushort_as_bfloat16(p.w1[n * 32 + 8 * j + e]));
-        put8(lt_smem + OFF_W1, n, j, 32, v);
+            for (int e = 0; e < 8; ++e) v[e] = __bfloat162float(__ushort_as_bfloat16(p.w1[n * 32 + 8 * j + e]));
+            put8(lt_smem + OFF_W1, n, j, K1, v);
+        } else if (j == 4) {
+            put_bias_chunk(lt_smem + OFF_W1, n, j, K1, p.b1[n], false);
+        } else {
+            put_zero_chunk(lt_smem + OFF_W1, n, j, K1);
+        }
     }
-    for (int q = tid; q < 64 * 8; q += LT_THREADS) {  // W2: 64 rows x 8 chunks
-        const int n = q >> 3, j = q & 7;
-        float v[8];
+    for (int q = tid; q < 64 * (K2 / 8); q += LT_THREADS) {  // W2 | b2: 64 rows x 10 chunks
+        const int n = q / (K2 / 8), j = q % (K2 / 8);
+        if (j < 8) {
+            float v[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = __bfloat162float(__ushort_as_bfloat16(p.w2[n * 64 + 8 * j + e]));
-        put8(lt_smem + OFF_W2, n, j, 64, v);
+            for (int e = 0; e < 8; ++e) v[e] = __bfloat162float(__ushort_as_bfloat16(p.w2[n * 64 + 8 * j + e]));
+            put8(lt_smem + OFF_W2, n, j, K2, v);
+        } else if (j == 8) {
+            put_bias_chunk(lt_smem + OFF_W2, n, j, K2, p.b2[n], false);
+        } else {
+            put_zero_chunk(lt_smem + OFF_W2, n, j, K2);
+        }
     }
     __syncthreads();  // s_basis ready
     // W3'(t): row 0 = sum_i b_i W3[i], row 1 + q = sum_i b_i W3[n1 + q n2 + i],
@@ -244,14 +266,15 @@ __global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __gri
 #pragma unroll 8
         for (int i = 0; i < terms; ++i)
             acc = fmaf(s_basis[i], __bfloat162float(__ushort_as_bfloat16(p.w3[(row0 + i) * 64 + h])), acc);
-        *reinterpret_cast<__half *>(lt_smem + OFF_W3 + core_off(r, h, 64)) = __float2half_rn(acc);
+        *reinterpret_cast<__half *>(lt_smem + OFF_W3 + core_off(r, h, K2)) = __float2half_rn(acc);
     }
     if (tid < 32) {
         const int row0 = tid == 0 ? 0 : p.n1 + (tid - 1) * p.n2, terms = tid == 0 ? p.n1 : (tid <= 27 ? p.n2 : 0);
         float acc = 0.0f;
 #pragma unroll 8
         for (int i = 0; i < terms; ++i) acc = fmaf(s_basis[i], p.b3[row0 + i], acc);
-        s_b3[tid] = acc;
+        put_bias_chunk(lt_smem + OFF_W3, tid, 8, K2, acc, false);  // rows 28..31: b = 0
+        put_zero_chunk(lt_smem + OFF_W3, tid, 9, K2);
     }
     fence_async_smem();
     fence_before();
@@ -268,6 +291,11 @@ __global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __gri
     const uint32_t n_tiles = (p.n_leaves + LT_M - 1) / LT_M;
     const uint32_t first = blockIdx.x * LT_GROUPS + group, step = gridDim.x * LT_GROUPS;
     const int m = gt;  // this thread's accumulator row (TMEM lane) and leaf in the tile
+
+    // the constant-one columns of this thread's row of A1 (A2 gets its own
+    // with every layer-1 epilogue: the output staging overwrites them)
+    put_bias_chunk(ga1, m, 4, K1, 0.0f, true);
+    put_zero_chunk(ga1, m, 5, K1);
 
     // One layer: the group's elected thread issues the MMAs and commits;
     // the group waits on its mbarrier (bounded).  The outcome is made
@@ -308,55 +336,41 @@ __global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __gri
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int piece = gt + 128 * i;
-            *reinterpret_cast<uint4 *>(ga1 + core_off(piece >> 2, 8 * (piece & 3), 32)) = nextq[i];
+            *reinterpret_cast<uint4 *>(ga1 + core_off(piece >> 2, 8 * (piece & 3), K1)) = nextq[i];
         }
         hand_off();
-        if (!run_layer(sa_a1, sa_w1, 32, 64)) break;
+        if (!run_layer(sa_a1, sa_w1, K1, 64)) break;
         // layer 1 epilogue: bias + ReLU -> layer-2 A operand (MMA 1 is done with A1)
         {
             float v[64];
             tmem_ld64(my_lane, v);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                add_bias(v + 16 * c, s_b1 + 16 * c);
-                put8_relu(ga2, m, 2 * c, 64, v + 16 * c);
-                put8_relu(ga2, m, 2 * c + 1, 64, v + 16 * c + 8);
-            }
+            for (int c = 0; c < 8; ++c) put8_relu(ga2, m, c, K2, v + 8 * c);
+            put_bias_chunk(ga2, m, 8, K2, 0.0f, true);
+            put_zero_chunk(ga2, m, 9, K2);
         }
         hand_off();
-        if (!run_layer(sa_a2, sa_w2, 64, 64)) break;
+        if (!run_layer(sa_a2, sa_w2, K2, 64)) break;
         // layer 2 epilogue -> layer-3 A operand, in place (MMA 2 has finished
         // reading A2, and each thread rewrites only its own row)
         {
             float v[64];
             tmem_ld64(my_lane, v);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                add_bias(v + 16 * c, s_b2 + 16 * c);
-                put8_relu(ga2, m, 2 * c, 64, v + 16 * c);
-                put8_relu(ga2, m, 2 * c + 1, 64, v + 16 * c + 8);
-            }
+            for (int c = 0; c < 8; ++c) put8_relu(ga2, m, c, K2, v + 8 * c);
         }
         hand_off();
         load_tile(tile + step, nextq);  // in flight while layer 3 runs
-        if (!run_layer(sa_a2, sa_w3, 64, 32)) break;
+        if (!run_layer(sa_a2, sa_w3, K2, 32)) break;
         {
             // output rows [max(0, sigma), 27 z, 0 x 4] into A2 (free since MMA 3
             // finished), then one bulk copy of the tile's contiguous rows
             float o[32];
             tmem_ld32(my_lane, o);
-            float w[32];
-#pragma unroll
-            for (int q = 0; q < 7; ++q) {
-                const float4 bb = reinterpret_cast<const float4 *>(s_b3)[q];
-                w[4 * q] = o[4 * q] + bb.x;
-                w[4 * q + 1] = o[4 * q + 1] + bb.y;
-                w[4 * q + 2] = o[4 * q + 2] + bb.z;
-                w[4 * q + 3] = o[4 * q + 3] + bb.w;
-            }
+            // the accumulator holds W3'x + b3': sigma gets its clamp, columns
+            // 28..31 are exactly zero
+            float *w = o;
             w[0] = fmaxf(w[0], 0.0f);
-#pragma unroll
-            for (int q = 28; q < 32; ++q) w[q] = 0.0f;
             // 128-byte swizzle (chunk q of row m at chunk q ^ (m % 8)): the 8
             // lanes of a store phase hit 8 different bank groups, and the
             // tensor store un-swizzles on the way out
