@@ -1282,69 +1282,6 @@ int launch_set_coeffs(const float *src, const uint32_t *perm, float *sig, float 
 }
 
 
-// Row-sparse Adam (Kingma & Ba) for the fine-tuning of Sec. 4.3: only the
-// leaves whose mark is set (those the batch visited) are updated, as in a
-// sparse-gradient Adam.  A warp takes 32 internal leaves at a time: one
-// coalesced read of perm and one gather of the marks decide, by ballot, which
-// of them it updates; each marked leaf's row (coalesced over the lanes) gets
-// the Adam step, goes back into the FP32 records at its internal slot, and
-// has its gradient row and mark cleared for the next batch.
-
-constexpr int LEAF_ADAM_CHUNK = 192;  // row elements per unrolled pass (all of n1 + 27 n2 = 166)
-
-__global__ void __launch_bounds__(256) leaf_adam_kernel(const __grid_constant__ LeafAdamParams p)
-{
-    const int lane = threadIdx.x & 31;
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
-    const int nc = p.n1 + 27 * p.n2;
-    for (uint32_t base = warp * 32; base < p.n_leaves; base += n_warps * 32) {
-        const uint32_t i = base + lane;
-        uint32_t id = 0;
-        bool marked = false;
-        if (i < p.n_leaves) {
-            id = __ldg(p.perm + i);
-            marked = p.leaf_mark[id] != 0;
-        }
-        uint32_t todo = __ballot_sync(0xffffffffu, marked);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const uint32_t leaf = base + src;
-            const uint32_t row = __shfl_sync(0xffffffffu, id, src);
-            const size_t at = (size_t)row * nc;
-            for (int j0 = 0; j0 < nc; j0 += LEAF_ADAM_CHUNK)
-#pragma unroll
-            for (int jj = 0; jj < LEAF_ADAM_CHUNK / 32; ++jj) {
-                const int j = j0 + lane + 32 * jj;
-                if (j < nc) {
-                    const float g = p.grad[at + j];
-                    const float mm = p.beta1 * p.m[at + j] + (1.0f - p.beta1) * g;
-                    const float vv = p.beta2 * p.v[at + j] + (1.0f - p.beta2) * g * g;
-                    const float w = p.param[at + j] - p.lr * (mm / p.bc1) / (sqrtf(vv / p.bc2) + p.eps);
-                    p.m[at + j] = mm;
-                    p.v[at + j] = vv;
-                    p.param[at + j] = w;
-                    p.grad[at + j] = 0.0f;
-                    if (j < p.n1) p.sig[(size_t)leaf * p.sig_stride + j] = w;
-                    else p.zc[(size_t)leaf * p.z_stride + (j - p.n1)] = w;
-                }
-            }
-        }
-        if (marked) p.leaf_mark[id] = 0;
-    }
-}
-
-int launch_leaf_adam(const LeafAdamParams &p, int sm_count, void *stream)
-{
-    if (p.n_leaves == 0) return (int)cudaSuccess;
-    uint64_t blocks = ((uint64_t)p.n_leaves + 255) / 256;
-    if (blocks > (uint64_t)sm_count * 8) blocks = (uint64_t)sm_count * 8;
-    leaf_adam_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);
-    return (int)cudaGetLastError();
-}
-
-
 // ---------------------------------------------------------------------------
 // Per-leaf DFT (Sec. 4.2, Eq. 10-12): coefficients from the values a leaf
 // takes at frames t = 1..T (the unified per-frame octrees).  One thread per

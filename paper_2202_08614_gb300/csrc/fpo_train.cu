@@ -10,6 +10,8 @@
 //                       adds its sums to the global gradients once at the end.
 //  adam_kernel          Adam (Kingma & Ba) on a dense array or on the rows of
 //                       a batch (distinct rows).
+//  leaf_adam_kernel     Adam on the marked leaves' coefficient rows, written
+//                       back into the renderer's FP32 records.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -204,6 +206,94 @@ int launch_adam(float *param, const float *grad, float *m, float *v, uint64_t n,
                                                                       b2, eps, (float)bc1, (float)bc2);
     return (int)cudaGetLastError();
 }
+
+// Row-sparse Adam (Kingma & Ba) for the fine-tuning of Sec. 4.3: only the
+// leaves whose mark is set (those the batch visited) are updated, as in a
+// sparse-gradient Adam.  A warp takes 32 internal leaves at a time: one
+// coalesced read of perm and one gather of the marks decide, by ballot, which
+// of them it updates.  Marked rows go LEAF_ADAM_ROWS at a time (all their
+// loads in flight together), lanes across each row's elements; every row gets
+// the Adam step, goes back into the FP32 records at its internal slot, and
+// has its gradient row and mark cleared for the next batch.
+
+constexpr int LEAF_ADAM_CHUNK = 96;   // row elements per unrolled pass
+constexpr int LEAF_ADAM_ROWS = 2;     // marked rows processed together
+
+__global__ void __launch_bounds__(256, 4) leaf_adam_kernel(const __grid_constant__ LeafAdamParams p)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    const int nc = p.n1 + 27 * p.n2;
+    constexpr int PER = LEAF_ADAM_CHUNK / 32;
+    for (uint32_t base = warp * 32; base < p.n_leaves; base += n_warps * 32) {
+        const uint32_t i = base + lane;
+        uint32_t id = 0;
+        bool marked = false;
+        if (i < p.n_leaves) {
+            id = __ldg(p.perm + i);
+            marked = p.leaf_mark[id] != 0;
+        }
+        uint32_t todo = __ballot_sync(0xffffffffu, marked);
+        while (todo) {
+            uint32_t leaf[LEAF_ADAM_ROWS];
+            size_t at[LEAF_ADAM_ROWS];
+            bool have[LEAF_ADAM_ROWS];
+#pragma unroll
+            for (int r = 0; r < LEAF_ADAM_ROWS; ++r) {
+                have[r] = todo != 0;
+                const int src = have[r] ? __ffs(todo) - 1 : 0;
+                todo &= todo - 1;
+                leaf[r] = base + src;
+                at[r] = (size_t)__shfl_sync(0xffffffffu, id, src) * nc;
+            }
+            for (int j0 = 0; j0 < nc; j0 += LEAF_ADAM_CHUNK) {
+                float g[LEAF_ADAM_ROWS][PER], m[LEAF_ADAM_ROWS][PER], v[LEAF_ADAM_ROWS][PER],
+                    w[LEAF_ADAM_ROWS][PER];
+#pragma unroll
+                for (int r = 0; r < LEAF_ADAM_ROWS; ++r)
+#pragma unroll
+                    for (int jj = 0; jj < PER; ++jj) {
+                        const int j = j0 + lane + 32 * jj;
+                        if (have[r] && j < nc) {
+                            g[r][jj] = p.grad[at[r] + j];
+                            m[r][jj] = p.m[at[r] + j];
+                            v[r][jj] = p.v[at[r] + j];
+                            w[r][jj] = p.param[at[r] + j];
+                        }
+                    }
+#pragma unroll
+                for (int r = 0; r < LEAF_ADAM_ROWS; ++r)
+#pragma unroll
+                    for (int jj = 0; jj < PER; ++jj) {
+                        const int j = j0 + lane + 32 * jj;
+                        if (have[r] && j < nc) {
+                            const float mm = p.beta1 * m[r][jj] + (1.0f - p.beta1) * g[r][jj];
+                            const float vv = p.beta2 * v[r][jj] + (1.0f - p.beta2) * g[r][jj] * g[r][jj];
+                            const float ww = w[r][jj] - p.lr * (mm / p.bc1) / (sqrtf(vv / p.bc2) + p.eps);
+                            p.m[at[r] + j] = mm;
+                            p.v[at[r] + j] = vv;
+                            p.param[at[r] + j] = ww;
+                            p.grad[at[r] + j] = 0.0f;
+                            if (j < p.n1) p.sig[(size_t)leaf[r] * p.sig_stride + j] = ww;
+                            else p.zc[(size_t)leaf[r] * p.z_stride + (j - p.n1)] = ww;
+                        }
+                    }
+            }
+        }
+        if (marked) p.leaf_mark[id] = 0;
+    }
+}
+
+int launch_leaf_adam(const LeafAdamParams &p, int sm_count, void *stream)
+{
+    if (p.n_leaves == 0) return (int)cudaSuccess;
+    uint64_t blocks = ((uint64_t)p.n_leaves + 255) / 256;
+    if (blocks > (uint64_t)sm_count * 8) blocks = (uint64_t)sm_count * 8;
+    leaf_adam_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);
+    return (int)cudaGetLastError();
+}
+
 
 }  // namespace fpo
 
