@@ -378,8 +378,8 @@ static TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, 
     p.perm = ctx->d_perm;
     p.status = ctx->d_status;
     if (rays->mode == FPO_RAYS_CAMERA) {
-        p.tiles_x = (rays->width + 7) / 8;
-        const uint32_t tiles_y = (rays->height + 3) / 4;
+        p.tiles_x = (rays->width + TILE_W - 1) / TILE_W;
+        const uint32_t tiles_y = (rays->height + TILE_H - 1) / TILE_H;
         p.super_tile = FPO_SUPER_TILE;
         if (p.super_tile) {
             const uint32_t S = p.super_tile;

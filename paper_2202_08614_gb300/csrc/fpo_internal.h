@@ -65,6 +65,13 @@ uint8_t encode_e4m3(float x);
 // [sigma(t) clamped at 0, z_{c,k}(t) for c = 0..2, k = 0..8 (27 values), 4 zeros].
 constexpr int TABLE_STRIDE = 32;
 
+// Camera rays are scheduled in warp tiles of TILE_W x TILE_H pixels.
+#ifndef FPO_TILE_W
+#define FPO_TILE_W 4
+#endif
+constexpr int TILE_W = FPO_TILE_W, TILE_H = 32 / FPO_TILE_W;
+static_assert(TILE_W * TILE_H == 32, "a tile is one warp of rays");
+
 // Device status word bits.
 constexpr uint32_t STATUS_TRAVERSAL_LIMIT = 1u, STATUS_VISIT_OVERFLOW = 2u, STATUS_DEVICE_TIMEOUT = 4u;
 

@@ -38,7 +38,6 @@
 namespace fpo {
 namespace {
 
-constexpr int TRAV_THREADS = 256;   // 8 warps; each warp traces 8x4-pixel tiles
 constexpr int STACK_LEVELS = MAX_DEPTH + 1;
 constexpr int MAX_BASIS = 64;
 
@@ -331,11 +330,13 @@ struct NodeCache {
     int level;
 };
 
+#if FPO_NODE_CACHE
 __device__ __forceinline__ uint32_t pick_slot(const NodeCache &nc, uint32_t c)
 {
     const uint4 h = (c & 4u) ? nc.hi : nc.lo;
     return (c & 2u) ? ((c & 1u) ? h.w : h.z) : ((c & 1u) ? h.y : h.x);
 }
+#endif
 
 __device__ __forceinline__ void write_result(const TraverseParams &p, const RayState &R, bool dbg)
 {
@@ -796,7 +797,8 @@ __device__ void frame_prologue(const TraverseParams &p, uint32_t *s_nodes, Frame
     }
 }
 
-// Ray k (0..31) of a tile: a camera pixel of an 8x4 block, or an explicit ray.
+// Ray k (0..31) of a tile: a camera pixel of a TILE_W x TILE_H block, or an
+// explicit ray.
 __device__ __forceinline__ bool tile_ray(const TraverseParams &p, uint32_t tile, uint32_t k, uint32_t &ray,
                                          int &px, int &py)
 {
@@ -812,8 +814,8 @@ __device__ __forceinline__ bool tile_ray(const TraverseParams &p, uint32_t tile,
             tx = tile % p.tiles_x;
             ty = tile / p.tiles_x;
         }
-        px = (int)(tx * 8 + (k & 7));
-        py = (int)(ty * 4 + (k >> 3));
+        px = (int)(tx * TILE_W + k % TILE_W);
+        py = (int)(ty * TILE_H + k / TILE_W);
         ray = (uint32_t)py * p.fr.width + (uint32_t)px;
         return px < (int)p.fr.width && py < (int)p.fr.height;
     }
@@ -824,7 +826,7 @@ __device__ __forceinline__ bool tile_ray(const TraverseParams &p, uint32_t tile,
 }  // namespace
 
 // Persistent kernel: a grid of (SM count x resident CTAs) whose warps pull
-// warp-sized tiles (8x4 pixels, or 32 consecutive explicit rays) from one
+// warp-sized tiles (TILE_W x TILE_H pixels, or 32 consecutive explicit rays) from one
 // atomic counter.  Warp-level ray compaction: every lane holds its own ray;
 // when at least REFILL_MIN lanes are idle, the warp hands them the next rays
 // of its current tile (fetching a new tile when that one is used up), so

@@ -189,9 +189,9 @@ extern "C" int fpo_render_noalloc(fpo_ctx *ctx, const fpo_rays *rays, const fpo_
     p.perm = c.d_perm;
     p.status = c.d_status;
     if (rays->mode == FPO_RAYS_CAMERA) {
-        p.tiles_x = (rays->width + 7) / 8;
+        p.tiles_x = (rays->width + TILE_W - 1) / TILE_W;
         p.super_tile = 0;
-        p.n_tiles = p.tiles_x * ((rays->height + 3) / 4);
+        p.n_tiles = p.tiles_x * ((rays->height + TILE_H - 1) / TILE_H);
     } else {
         p.tiles_x = 0;
         p.super_tile = 0;
