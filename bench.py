@@ -268,10 +268,21 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms):
     n = tree.n_leaves
     coeffs = torch.empty((n, 166), dtype=torch.float32, device="cuda")
     ch = 1 << 19
+    dft_ms = 0.0
     for s0 in range(0, n, ch):
         vals = synth.smooth_frame_values(tree.leaf_depth[s0:s0 + ch], tree.leaf_xyz[s0:s0 + ch], body)
-        coeffs[s0:s0 + ch] = fpo.dft_leaves(vals)
-        del vals
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        c = fpo.dft_leaves(vals)
+        e1.record()
+        torch.cuda.synchronize()
+        dft_ms += e0.elapsed_time(e1)
+        coeffs[s0:s0 + ch] = c
+        del vals, c
+    # Eq. 10-12 over the whole tree: 60 frames x 28 values in, 166 coefficients out per leaf
+    dft_bytes = n * (60 * 28 + 166) * 4
+    res["generation_dft"] = {"ms": dft_ms, "leaves": n, "frames": 60, "alg_bytes": dft_bytes,
+                             "GB_s": dft_bytes / (dft_ms * 1e-3) / 1e9}
     co_np = coeffs.cpu().numpy()
     gen = synth.Tree(tree.leaf_depth, tree.leaf_xyz, co_np, tree.max_depth)
     r = fpo.Renderer()
@@ -551,6 +562,25 @@ def main():
     res["gpu_launches"] = K * (2 if mat else 1)
     res["clocks"] = clk.summary()
     res["tree"] = info
+    if not args.no_variants:
+        # the second resolution of the workload: 800x800 from the same ring
+        cams8 = synth.ring_cameras(16, 800, 800)
+        out8 = torch.empty((800 * 800, 3), dtype=torch.float32, device="cuda")
+        ev8 = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in frames[W:]]
+        for k, t in frames[:W]:
+            r.render(camera=cams8[k], t=t, out=out8)
+        torch.cuda.synchronize()
+        for i, (k, t) in enumerate(frames[W:]):
+            ev8[i][0].record(stream)
+            r.render(camera=cams8[k], t=t, out=out8)
+            ev8[i][1].record(stream)
+        torch.cuda.synchronize()
+        r.status()
+        ms8 = [e[0].elapsed_time(e[1]) for e in ev8]
+        res["res_800x800"] = {"Mrays_s": 800 * 800 / statistics.median(ms8) / 1e3,
+                              "fps": 1e3 / statistics.median(ms8),
+                              "frame_ms": {"p10": float(np.percentile(ms8, 10)), "p50": statistics.median(ms8),
+                                           "p90": float(np.percentile(ms8, 90))}}
     if not args.no_variants and args.storage == "f32" and args.idft == "auto":
         res["variants"] = variants(args, tree, cams, frames[W:], out, torch, fpo, n_px, t_max / K)
     if rank == 0 and not args.no_cpu_baseline:
