@@ -1321,10 +1321,134 @@ __global__ void __launch_bounds__(256) dft_kernel(const float *__restrict__ valu
     }
 }
 
+// Tiled version for n2 = 5 (the paper's size; any n1 <= 32): a CTA takes 32
+// leaves at a time.  Frames arrive in chunks of DFT_TC, each chunk's 32 x 28
+// values read with coalesced loads into shared memory; lane l of every warp
+// owns leaf l: warp 0 accumulates the density series (n1 coefficients), warps
+// 1..7 the 27 SH series (series w, w + 7, w + 14, w + 21; 5 coefficients
+// each), with the weights of a frame read as float4 broadcasts.  The sums run
+// over t in the same order as the kernel above, so both give the same bits.
+// The 32 x nc outputs are staged in shared memory and written contiguously.
+constexpr int DFT_TILE = 32, DFT_TC = 8, DFT_XPAD = 29, DFT_N2 = 5;
+
+__global__ void __launch_bounds__(256) dft_tile_kernel(const float *__restrict__ values, float *__restrict__ coeffs,
+                                                       uint32_t n_leaves, int n1, int T)
+{
+    extern __shared__ __align__(16) float dft_smem[];
+    float *s_w = dft_smem;                          // [T][32]: weight of coefficient i at frame t
+    float *s_x = s_w + (size_t)T * 32;              // [DFT_TC][32 leaves][DFT_XPAD]
+    const int nc = n1 + 27 * DFT_N2;
+    float *s_out = s_x + DFT_TC * DFT_TILE * DFT_XPAD;  // [32 leaves][nc]
+    for (int q = threadIdx.x; q < 32 * T; q += blockDim.x) {
+        const int t = q / 32, i = q % 32, nb = n1 > DFT_N2 ? n1 : DFT_N2;
+        const double u = (double)(t + 1) / (double)T;
+        const double w = (i == 0 ? 1.0 : 2.0) / (double)T;
+        s_w[q] = i < nb ? (float)(w * ((i & 1) ? sinpi((double)(i + 1) * u) : cospi((double)i * u))) : 0.0f;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int ser[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ser[q] = warp == 0 ? (q == 0 ? 0 : -1) : (warp + 7 * q <= 27 ? warp + 7 * q : -1);
+    const uint32_t n_tiles = (n_leaves + DFT_TILE - 1) / DFT_TILE;
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const uint32_t leaf0 = tile * DFT_TILE;
+        const int nl = (int)min((uint32_t)DFT_TILE, n_leaves - leaf0);
+        float acc[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
+        for (int t0 = 0; t0 < T; t0 += DFT_TC) {
+            const int tc = min(DFT_TC, T - t0);
+            __syncthreads();  // the previous chunk (and the weights) are done with
+            if (tc == DFT_TC && nl == DFT_TILE && blockDim.x == 256) {
+                // full chunk: 28 coalesced loads per thread, all in flight, then the stores
+                constexpr int PER = DFT_TC * DFT_TILE * 28 / 256;
+                float v[PER];
+#pragma unroll
+                for (int k = 0; k < PER; ++k) {
+                    const int q = threadIdx.x + 256 * k, t = q / (DFT_TILE * 28), r = q % (DFT_TILE * 28);
+                    v[k] = __ldg(values + ((size_t)(t0 + t) * n_leaves + leaf0) * 28 + r);
+                }
+#pragma unroll
+                for (int k = 0; k < PER; ++k) {
+                    const int q = threadIdx.x + 256 * k, t = q / (DFT_TILE * 28), r = q % (DFT_TILE * 28);
+                    s_x[(t * DFT_TILE + r / 28) * DFT_XPAD + r % 28] = v[k];
+                }
+            } else {
+                for (int q = threadIdx.x; q < tc * nl * 28; q += blockDim.x) {
+                    const int t = q / (nl * 28), r = q % (nl * 28);
+                    s_x[(t * DFT_TILE + r / 28) * DFT_XPAD + r % 28] =
+                        __ldg(values + ((size_t)(t0 + t) * n_leaves + leaf0) * 28 + r);
+                }
+            }
+            __syncthreads();
+            if (lane < nl) {
+                for (int t = 0; t < tc; ++t) {
+                    const float *xr = s_x + (t * DFT_TILE + lane) * DFT_XPAD;
+                    const float4 *wr = reinterpret_cast<const float4 *>(s_w + (size_t)(t0 + t) * 32);
+                    if (warp == 0) {
+                        const float x = xr[0];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const float4 w = wr[k];
+                            acc[4 * k] = fmaf(x, w.x, acc[4 * k]);
+                            acc[4 * k + 1] = fmaf(x, w.y, acc[4 * k + 1]);
+                            acc[4 * k + 2] = fmaf(x, w.z, acc[4 * k + 2]);
+                            acc[4 * k + 3] = fmaf(x, w.w, acc[4 * k + 3]);
+                        }
+                    } else {
+                        const float4 w4 = wr[0];
+                        const float w5 = s_w[(size_t)(t0 + t) * 32 + 4];
+                        const float wv[DFT_N2] = {w4.x, w4.y, w4.z, w4.w, w5};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (ser[q] < 0) continue;
+                            const float x = xr[ser[q]];
+#pragma unroll
+                            for (int i = 0; i < DFT_N2; ++i) acc[q * DFT_N2 + i] = fmaf(x, wv[i], acc[q * DFT_N2 + i]);
+                        }
+                    }
+                }
+            }
+        }
+        if (lane < nl) {
+            float *o = s_out + (size_t)lane * nc;
+            if (warp == 0) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    if (i < n1) o[i] = acc[i];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (ser[q] < 0) continue;
+#pragma unroll
+                    for (int i = 0; i < DFT_N2; ++i) o[n1 + (ser[q] - 1) * DFT_N2 + i] = acc[q * DFT_N2 + i];
+                }
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < nl * nc; q += blockDim.x) coeffs[(size_t)leaf0 * nc + q] = s_out[q];
+    }
+}
+
 int launch_dft(const float *values, float *coeffs, uint32_t n_leaves, int n1, int n2, int T, int sm_count,
                void *stream)
 {
     if (n_leaves == 0) return (int)cudaSuccess;
+    if (n2 == DFT_N2 && n1 <= 32) {
+        const int nc = n1 + 27 * DFT_N2;
+        const size_t smem = ((size_t)T * 32 + DFT_TC * DFT_TILE * DFT_XPAD + (size_t)DFT_TILE * nc) * sizeof(float);
+        cudaError_t e = cudaFuncSetAttribute(dft_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dft_tile_kernel, 256, smem);
+        if (e != cudaSuccess) return (int)e;
+        if (per_sm < 1) per_sm = 1;
+        const uint64_t n_tiles = (n_leaves + DFT_TILE - 1) / DFT_TILE;
+        uint64_t blocks = (uint64_t)sm_count * per_sm;
+        if (blocks > n_tiles) blocks = n_tiles;
+        dft_tile_kernel<<<(unsigned)blocks, 256, smem, (cudaStream_t)stream>>>(values, coeffs, n_leaves, n1, T);
+        return (int)cudaGetLastError();
+    }
     const uint64_t total = (uint64_t)n_leaves * (n1 + 27 * n2);
     uint64_t blocks = (total + 255) / 256;
     if (blocks > (uint64_t)sm_count * 32) blocks = (uint64_t)sm_count * 32;
