@@ -103,14 +103,16 @@ def _cuda():
 
 
 @pytest.mark.gpu
-def test_dft_leaves_matches_oracle():
+@pytest.mark.parametrize("n1,n2,T,n", [(31, 5, 60, 3000), (11, 5, 37, 70), (31, 11, 60, 500), (21, 5, 8, 32)])
+def test_dft_leaves_matches_oracle(n1, n2, T, n):
+    # (n1, 5): the tiled kernel (full and partial leaf tiles and frame chunks);
+    # other n2: the one-thread-per-coefficient kernel
     torch = _cuda()
-    rng = np.random.default_rng(0)
-    T, n = 60, 3000
+    rng = np.random.default_rng(n)
     vals = rng.normal(size=(T, n, 28)).astype(np.float32)
-    got = fpo.dft_leaves(torch.as_tensor(vals, device="cuda"), N1, N2).cpu().numpy()
-    k_sig = oracle.dft(vals[:, :, 0].astype(np.float64), N1)  # [n, 31]
-    k_z = oracle.dft(vals[:, :, 1:].reshape(T, -1).astype(np.float64), N2).reshape(n, 27 * N2)
+    got = fpo.dft_leaves(torch.as_tensor(vals, device="cuda"), n1, n2).cpu().numpy()
+    k_sig = oracle.dft(vals[:, :, 0].astype(np.float64), n1)  # [n, n1]
+    k_z = oracle.dft(vals[:, :, 1:].reshape(T, -1).astype(np.float64), n2).reshape(n, 27 * n2)
     ref = np.concatenate([k_sig, k_z], axis=1)
     assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
 
