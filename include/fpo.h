@@ -63,6 +63,12 @@ enum { FPO_STORAGE_F32 = 0, FPO_STORAGE_BF16 = 1, FPO_STORAGE_F16 = 2, FPO_STORA
  *  AUTO         the library's choice (currently MATERIALISE for camera frames,
  *               FUSED for rays with per-ray times). */
 enum { FPO_IDFT_AUTO = 0, FPO_IDFT_FUSED = 1, FPO_IDFT_MATERIALISE = 2 };
+/* Precision of the per-frame table of the MATERIALISE mode (sigma(t) and the
+ * 27 z(t) of every leaf): FP32 (128 bytes per leaf) or FP16 (64 bytes per
+ * leaf, half the table traffic of the traversal).  AUTO: FP32 with FP32
+ * storage, FP16 with the reduced-precision and latent storages, whose
+ * coefficients already carry fewer bits than FP16 keeps of sigma and z. */
+enum { FPO_TABLE_AUTO = 0, FPO_TABLE_F32 = 1, FPO_TABLE_F16 = 2 };
 
 typedef struct {
     int32_t n1;        /* density Fourier coefficients per leaf (paper: 31, Tab. 3) */
@@ -80,6 +86,7 @@ typedef struct {
     int32_t traverse_threads;
     int32_t refill_min;
     int32_t inner_steps;
+    int32_t table_precision; /* FPO_TABLE_* */
 } fpo_config;
 
 /* A union octree given by its leaves (Sec. 4.2): leaf j is the cell
@@ -220,8 +227,9 @@ int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts
  * device memory inside the library: 8 MiB, loaded on every GPU that loads
  * the library and held until the process exits, enough for trees of at most
  * 65536 leaves.  Larger trees, and explicit rays with per-ray times, are
- * rejected with FPO_ERR_INVALID_ARG.  Inputs: ctx (a context whose tree was
- * uploaded beforehand) and rays; output: out_rgb as in fpo_render; opts and
+ * rejected with FPO_ERR_INVALID_ARG; LATENT storage with
+ * FPO_ERR_UNSUPPORTED.  Inputs: ctx (a context whose tree was uploaded
+ * beforehand) and rays; output: out_rgb as in fpo_render; opts and
  * device-side errors as in fpo_render (read them with fpo_status_sync).
  * The array is shared by all calls on a device and keeps the last call's
  * table: calls whose GPU work overlaps (different streams, or different

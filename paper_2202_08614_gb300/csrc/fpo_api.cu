@@ -99,6 +99,7 @@ struct fpo_ctx {
     float *d_table = nullptr;
     size_t table_leaves = 0;
     // frame pipeline (fpo_render_frames): second table, aux stream, events
+    bool half_table = false;  // the per-frame table holds FP16 (64 B per leaf)
     float *d_table2 = nullptr;
     size_t table2_leaves = 0;
     cudaStream_t aux = nullptr;
@@ -125,6 +126,9 @@ struct fpo_ctx {
 
 namespace fpo {
 
+// Bytes of one leaf's row of the per-frame table.
+static size_t table_row_bytes(const fpo_ctx *c) { return c->half_table ? TABLE_STRIDE * 2 : TABLE_STRIDE * 4; }
+
 CtxView ctx_view(const fpo_ctx *c)
 {
     CtxView v{};
@@ -137,6 +141,7 @@ CtxView ctx_view(const fpo_ctx *c)
     v.refill_min = c->cfg.refill_min;
     v.inner_steps = c->cfg.inner_steps;
     v.d_status = c->d_status;
+    v.half_table = c->half_table;
     v.has_tree = c->has_tree;
     v.n_leaves = c->n_leaves;
     v.n_nodes = c->n_nodes;
@@ -183,6 +188,8 @@ int fpo_create(fpo_ctx **out, const fpo_config *cfg)
     if (cfg->refill_min < 0 || cfg->refill_min > 32)
         return fail(FPO_ERR_INVALID_ARG, "refill_min must be in [0, 32]");
     if (cfg->inner_steps < 0) return fail(FPO_ERR_INVALID_ARG, "inner_steps must be >= 0");
+    if (cfg->table_precision < FPO_TABLE_AUTO || cfg->table_precision > FPO_TABLE_F16)
+        return fail(FPO_ERR_INVALID_ARG, "table_precision must be FPO_TABLE_AUTO, _F32 or _F16");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
@@ -193,6 +200,8 @@ int fpo_create(fpo_ctx **out, const fpo_config *cfg)
     fpo_ctx *c = new (std::nothrow) fpo_ctx;
     if (!c) return fail(FPO_ERR_OOM, "host allocation failed");
     c->cfg = *cfg;
+    c->half_table = cfg->table_precision == FPO_TABLE_F16 ||
+                    (cfg->table_precision == FPO_TABLE_AUTO && cfg->storage != FPO_STORAGE_F32);
     e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, cfg->device);
     if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaDeviceGetAttribute"); }
     e = cudaMalloc((void **)&c->d_status, 4 * sizeof(uint32_t));
@@ -300,7 +309,7 @@ int fpo_tree_info_get(const fpo_ctx *ctx, fpo_tree_info *out)
     const RecordLayout L = record_layout(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2);
     out->leaf_record_bytes = (uint64_t)(L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
     out->leaf_bytes = out->leaf_record_bytes * ctx->n_leaves;
-    out->table_bytes = (uint64_t)ctx->table_leaves * TABLE_STRIDE * 4;
+    out->table_bytes = (uint64_t)ctx->table_leaves * table_row_bytes(ctx);
     return FPO_OK;
 }
 
@@ -377,6 +386,7 @@ static TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, 
     p.leaf_mark = opts->leaf_mark;
     p.perm = ctx->d_perm;
     p.status = ctx->d_status;
+    p.half_table = ctx->half_table;
     if (rays->mode == FPO_RAYS_CAMERA) {
         p.tiles_x = (rays->width + TILE_W - 1) / TILE_W;
         const uint32_t tiles_y = (rays->height + TILE_H - 1) / TILE_H;
@@ -419,6 +429,7 @@ static int launch_table_pass(fpo_ctx *ctx, double t, float *table, int max_ctas_
         lp.period_T = ctx->cfg.period_T;
         lp.n_leaves = ctx->n_leaves;
         lp.table = table;
+        lp.half_table = ctx->half_table;
         lp.status = ctx->d_status;
         return launch_latent_table(lp, ctx->sm_count, s);
     }
@@ -436,6 +447,7 @@ static int launch_table_pass(fpo_ctx *ctx, double t, float *table, int max_ctas_
     mp.z_stride = L.z_elems;
     mp.stages = materialise_stages(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2);
     mp.max_ctas_per_sm = max_ctas_per_sm;
+    mp.half_table = ctx->half_table;
     mp.t = t;
     mp.period_T = ctx->cfg.period_T;
     mp.status = ctx->d_status;
@@ -478,7 +490,7 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
     cudaError_t e;
     if (mat && ctx->table_leaves < ctx->n_leaves) {
         dfree(ctx->d_table);
-        e = cudaMalloc((void **)&ctx->d_table, (size_t)ctx->n_leaves * TABLE_STRIDE * 4);
+        e = cudaMalloc((void **)&ctx->d_table, (size_t)ctx->n_leaves * table_row_bytes(ctx));
         if (e != cudaSuccess) { ctx->table_leaves = 0; return cuda_fail(e, "cudaMalloc(table)"); }
         ctx->table_leaves = ctx->n_leaves;
     }
@@ -544,7 +556,7 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
         size_t &tl = b ? ctx->table2_leaves : ctx->table_leaves;
         if (tl < ctx->n_leaves) {
             dfree(tb);
-            e = cudaMalloc((void **)&tb, (size_t)ctx->n_leaves * TABLE_STRIDE * 4);
+            e = cudaMalloc((void **)&tb, (size_t)ctx->n_leaves * table_row_bytes(ctx));
             if (e != cudaSuccess) { tl = 0; return cuda_fail(e, "cudaMalloc(table)"); }
             tl = ctx->n_leaves;
         }

@@ -110,6 +110,7 @@ struct TraverseParams {
     float amin[3];
     // leaf data
     const float4 *table;      // per-frame IDFT table (materialised mode)
+    int half_table;           // the table holds FP16 (64-byte lines) instead of FP32 (128-byte lines)
     const float4 *sig;        // density coefficient records (fused mode)
     const float *zc;          // SH coefficient records (fused mode)
     int n1, n2, sig_stride4, z_stride;
@@ -140,7 +141,8 @@ struct MaterialiseParams {
     const void *sig;          // [n_leaves] records of sig_stride elements
     const void *zc;           // [n_leaves] records of z_stride elements
     const float *scale;       // [n_leaves] (FP8 storage) or nullptr
-    float *table;
+    float *table;             // [n_leaves][32] FP32, or [n_leaves][32] FP16 when half_table
+    int half_table;
     uint32_t n_leaves;
     int storage;              // FPO_STORAGE_*
     int n1, n2, sig_stride, z_stride;  // strides in elements
@@ -157,6 +159,7 @@ struct CtxView {
     double period_T;
     int traverse_threads, refill_min, inner_steps;
     uint32_t *d_status;
+    bool half_table;
     bool has_tree;
     uint32_t n_leaves, n_nodes, root_kind, n_smem_nodes;
     int depth;
@@ -183,9 +186,10 @@ struct LatentParams {
     int n1, n2;
     double t, period_T;
     uint32_t n_leaves;
-    float *table;             // [n_leaves][TABLE_STRIDE]
+    float *table;             // [n_leaves][TABLE_STRIDE] FP32, or FP16 when half_table
+    int half_table;
     uint32_t *status;
-    CUtensorMap table_map;    // set by launch_latent_table: the table as [n_leaves][32] FP32, 128-byte swizzle
+    CUtensorMap table_map;    // set by launch_latent_table: the table as a [n_leaves][32] tensor
 };
 
 int launch_latent_table(const LatentParams &p, int sm_count, void *stream);

@@ -234,7 +234,10 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
             }
             const float zprev = __shfl_up_sync(0xffffffffu, v, 1);
             const float outv = lane == 0 ? fmaxf(part, 0.0f) : (lane <= 27 ? zprev : 0.0f);
-            p.table[((size_t)first + l) * TABLE_STRIDE + lane] = outv;
+            if (p.half_table)
+                reinterpret_cast<__half *>(p.table)[((size_t)first + l) * TABLE_STRIDE + lane] = __float2half_rn(outv);
+            else
+                p.table[((size_t)first + l) * TABLE_STRIDE + lane] = outv;
         }
         __syncthreads();  // every thread is done with stage s
         if (tid == 0) {
@@ -277,6 +280,8 @@ static void *pick_materialise(int storage)
 int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream)
 {
     if (p.n_leaves == 0) return (int)cudaSuccess;
+    if (p.storage < FPO_STORAGE_F32 || p.storage > FPO_STORAGE_FP8_E4M3 || !p.sig || !p.zc)
+        return (int)cudaErrorInvalidValue;  // no coefficient records (e.g. LATENT storage)
     const RecordLayout L = record_layout(p.storage, p.n1, p.n2);
     const int smem = p.stages * MAT_CHUNK * (L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
     const void *kern = p.n2 == 5 ? pick_materialise<5>(p.storage)
@@ -565,20 +570,44 @@ __device__ __forceinline__ void move_to(RayState &R, int D, const int Pn[3], flo
     R.P[2] = Pn[2];
 }
 
+// Table modes of the traversal: the fused per-visit IDFT, or the per-frame
+// table in FP32 (128-byte lines) or FP16 (64-byte lines).
+constexpr int TM_FUSED = 0, TM_TABLE_F32 = 1, TM_TABLE_F16 = 2;
+
 __device__ __forceinline__ const float4 *table_record(const TraverseParams &p, uint32_t leaf)
 {
     return p.table + (size_t)leaf * (TABLE_STRIDE / 4);
 }
 
+__device__ __forceinline__ const __half *table_record_f16(const TraverseParams &p, uint32_t leaf)
+{
+    return reinterpret_cast<const __half *>(p.table) + (size_t)leaf * TABLE_STRIDE;
+}
+
 // Shades one leaf segment of length delta (Eq. 7 and 9 from the table or
 // fused, Eq. 1 colour, emission-absorption update).  Returns true when the
 // transmittance fell below stop_T.
-template <bool MAT, bool DBG, int N1, int N2>
+template <int TM, bool DBG, int N1, int N2>
 __device__ __forceinline__ bool shade(const TraverseParams &p, const float *bsrc, int bstride,
                                       RayState &R, uint32_t leaf, float delta)
 {
     float sigma, z[27];
-    if constexpr (MAT) {
+    if constexpr (TM == TM_TABLE_F16) {
+        // the 64-byte FP16 line: two 32-byte loads, widened to FP32
+        const float *hrec = reinterpret_cast<const float *>(table_record_f16(p, leaf));
+        float raw[16], v[32];
+        ldg256(hrec, raw);
+        ldg256(hrec + 8, raw + 8);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&raw[q]));
+            v[2 * q] = f.x;
+            v[2 * q + 1] = f.y;
+        }
+        sigma = v[0];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) z[q] = v[q + 1];
+    } else if constexpr (TM == TM_TABLE_F32) {
         const float4 *rec = table_record(p, leaf);
         float v[32];
 #if FPO_LDG256
@@ -688,7 +717,7 @@ __device__ __forceinline__ bool step_cap(const TraverseParams &p, RayState &R)
 
 // One traversal step (compaction schedule): locate, shade, move.  Returns
 // false once the ray is finished (left the grid, early stop, or step cap).
-template <bool MAT, bool DBG, int N1, int N2>
+template <int TM, bool DBG, int N1, int N2>
 __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const float *bsrc,
                          int bstride, const uint32_t *__restrict__ s_nodes, uint32_t *s_stack,
                          int stride, RayState &R, NodeCache &nc)
@@ -699,7 +728,7 @@ __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const f
     int m, lo[3], csz;
     const float tx = cube_exit(R, D, cb.lvl, m, lo, csz);
     if (cb.kind == ROOT_LEAF && tx > R.t)
-        if (shade<MAT, DBG, N1, N2>(p, bsrc, bstride, R, cb.leaf, tx - R.t)) return false;
+        if (shade<TM, DBG, N1, N2>(p, bsrc, bstride, R, cb.leaf, tx - R.t)) return false;
     int Pn[3];
     if (!next_cell(R, G, m, lo, csz, tx, Pn)) return false;
     move_to(R, D, Pn, tx);
@@ -722,7 +751,7 @@ __device__ __forceinline__ void prefetch_records(const TraverseParams &p, uint32
 // A whole ray (lane-loop schedule).  Software-pipelined: the next cube is
 // located, and its table record prefetched into L1, before the current cube
 // is shaded, so the record's latency hides behind the shading arithmetic.
-template <bool MAT, bool DBG, int N1, int N2>
+template <int TM, bool DBG, int N1, int N2>
 __device__ void trace_ray(const TraverseParams &p, const float *bsrc, int bstride,
                           const uint32_t *__restrict__ s_nodes, uint32_t *s_stack, int stride,
                           RayState &R, NodeCache &nc)
@@ -740,14 +769,16 @@ __device__ void trace_ray(const TraverseParams &p, const float *bsrc, int bstrid
             const uint32_t diff = (uint32_t)((R.P[0] ^ Pn[0]) | (R.P[1] ^ Pn[1]) | (R.P[2] ^ Pn[2]));
             nx = locate(p, s_nodes, s_stack, stride, Pn, D - 1 - (31 - __clz(diff)), nc);
             if (nx.kind == ROOT_LEAF) {
-                if constexpr (MAT)
+                if constexpr (TM == TM_TABLE_F32)
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record(p, nx.leaf)));
+                else if constexpr (TM == TM_TABLE_F16)
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record_f16(p, nx.leaf)));
                 else
                     prefetch_records(p, nx.leaf, N1, N2);
             }
         }
         if (cb.kind == ROOT_LEAF && tx > R.t)
-            if (shade<MAT, DBG, N1, N2>(p, bsrc, bstride, R, cb.leaf, tx - R.t)) return;
+            if (shade<TM, DBG, N1, N2>(p, bsrc, bstride, R, cb.leaf, tx - R.t)) return;
         if (!inside) return;
         move_to(R, D, Pn, tx);
         if (step_cap(p, R)) return;
@@ -843,8 +874,8 @@ __device__ __forceinline__ bool tile_ray(const TraverseParams &p, uint32_t tile,
 #define FPO_TRAV_MAXNREG_FUSED 128
 #endif
 
-template <bool MAT, bool DBG, int N1, int N2, bool COMPACT>
-__global__ void __maxnreg__(MAT ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED) traverse_kernel(const __grid_constant__ TraverseParams p)
+template <int TM, bool DBG, int N1, int N2, bool COMPACT>
+__global__ void __maxnreg__(TM ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED) traverse_kernel(const __grid_constant__ TraverseParams p)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ FrameShared fs;
@@ -852,7 +883,7 @@ __global__ void __maxnreg__(MAT ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED)
     uint32_t *s_nodes = smem;
     uint32_t *s_stack = smem + p.n_smem_nodes * 8;
     float *s_bray = reinterpret_cast<float *>(s_stack + STACK_LEVELS * stride);
-    const bool prt = !MAT && p.fr.mode == FPO_RAYS_EXPLICIT && p.fr.rt != nullptr;
+    const bool prt = TM == TM_FUSED && p.fr.mode == FPO_RAYS_EXPLICIT && p.fr.rt != nullptr;
 
     frame_prologue(p, s_nodes, fs);
     __syncthreads();
@@ -890,7 +921,7 @@ __global__ void __maxnreg__(MAT ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED)
                     NodeCache nc;
                     nc.node = 0xffffffffu;
                     nc.level = -1;
-                    trace_ray<MAT, DBG, N1, N2>(p, bsrc, bstride, s_nodes, my_stack, stride, R, nc);
+                    trace_ray<TM, DBG, N1, N2>(p, bsrc, bstride, s_nodes, my_stack, stride, R, nc);
                     finish(R);
                 }
             }
@@ -933,7 +964,7 @@ __global__ void __maxnreg__(MAT ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED)
             if (active) {
 #pragma unroll 1
                 for (uint32_t k = 0; k < p.inner_steps; ++k) {
-                    if (!step_ray<MAT, DBG, N1, N2>(p, fs, bsrc, bstride, s_nodes, my_stack, stride, R, nc)) {
+                    if (!step_ray<TM, DBG, N1, N2>(p, fs, bsrc, bstride, s_nodes, my_stack, stride, R, nc)) {
                         finish(R);
                         active = false;
                         break;
@@ -962,13 +993,13 @@ int traverse_smem_bytes(uint32_t n_smem_nodes, bool per_ray_basis, int threads)
 }
 
 
-template <bool MAT, bool DBG, int N1, int N2, bool COMPACT>
+template <int TM, bool DBG, int N1, int N2, bool COMPACT>
 static int launch_t(const TraverseParams &p, int sm_count, cudaStream_t s)
 {
-    const bool prt = !MAT && p.fr.mode == FPO_RAYS_EXPLICIT && p.fr.rt != nullptr;
+    const bool prt = TM == TM_FUSED && p.fr.mode == FPO_RAYS_EXPLICIT && p.fr.rt != nullptr;
     const int threads = p.block_threads;
     const int smem = traverse_smem_bytes(p.n_smem_nodes, prt, threads);
-    auto k = traverse_kernel<MAT, DBG, N1, N2, COMPACT>;
+    auto k = traverse_kernel<TM, DBG, N1, N2, COMPACT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
@@ -984,21 +1015,21 @@ static int launch_t(const TraverseParams &p, int sm_count, cudaStream_t s)
 }
 
 // Debug outputs use the plain schedule (their results do not depend on it).
-template <bool MAT, int N1, int N2>
+template <int TM, int N1, int N2>
 static int launch_sched(const TraverseParams &p, bool debug, int sm_count, cudaStream_t s)
 {
-    if (debug) return launch_t<MAT, true, N1, N2, false>(p, sm_count, s);
-    if (p.refill_min < 32) return launch_t<MAT, false, N1, N2, true>(p, sm_count, s);
-    return launch_t<MAT, false, N1, N2, false>(p, sm_count, s);
+    if (debug) return launch_t<TM, true, N1, N2, false>(p, sm_count, s);
+    if (p.refill_min < 32) return launch_t<TM, false, N1, N2, true>(p, sm_count, s);
+    return launch_t<TM, false, N1, N2, false>(p, sm_count, s);
 }
 
 static int launch_fused(const TraverseParams &p, bool debug, int sm_count, cudaStream_t s)
 {
     // Fused per-visit IDFT: compile-time Fourier sizes (the settings of Tab. 3).
-    if (p.n1 == 31 && p.n2 == 5) return launch_sched<false, 31, 5>(p, debug, sm_count, s);
-    if (p.n1 == 11 && p.n2 == 5) return launch_sched<false, 11, 5>(p, debug, sm_count, s);
-    if (p.n1 == 21 && p.n2 == 5) return launch_sched<false, 21, 5>(p, debug, sm_count, s);
-    if (p.n1 == 31 && p.n2 == 11) return launch_sched<false, 31, 11>(p, debug, sm_count, s);
+    if (p.n1 == 31 && p.n2 == 5) return launch_sched<TM_FUSED, 31, 5>(p, debug, sm_count, s);
+    if (p.n1 == 11 && p.n2 == 5) return launch_sched<TM_FUSED, 11, 5>(p, debug, sm_count, s);
+    if (p.n1 == 21 && p.n2 == 5) return launch_sched<TM_FUSED, 21, 5>(p, debug, sm_count, s);
+    if (p.n1 == 31 && p.n2 == 11) return launch_sched<TM_FUSED, 31, 11>(p, debug, sm_count, s);
     return -1;
 }
 
@@ -1012,7 +1043,9 @@ int launch_traverse(const TraverseParams &p, bool materialised, bool debug, int 
                     void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
-    if (materialised) return launch_sched<true, 0, 0>(p, debug, sm_count, s);
+    if (materialised)
+        return p.half_table ? launch_sched<TM_TABLE_F16, 0, 0>(p, debug, sm_count, s)
+                            : launch_sched<TM_TABLE_F32, 0, 0>(p, debug, sm_count, s);
     return launch_fused(p, debug, sm_count, s);
 }
 

@@ -374,10 +374,26 @@ __global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __gri
             // 128-byte swizzle (chunk q of row m at chunk q ^ (m % 8)): the 8
             // lanes of a store phase hit 8 different bank groups, and the
             // tensor store un-swizzles on the way out
-            float4 *row = reinterpret_cast<float4 *>(ga2 + m * (TABLE_STRIDE * 4));
+            if (p.half_table) {
+                // FP16 rows of 64 B with the 64-byte swizzle (chunk q of row m
+                // at chunk q ^ ((m / 2) % 4)): again no bank conflicts
+                uint4 *row = reinterpret_cast<uint4 *>(ga2 + m * (TABLE_STRIDE * 2));
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                row[q ^ (m & 7)] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t h[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const __half2 hh = __floats2half2_rn(w[8 * q + 2 * e], w[8 * q + 2 * e + 1]);
+                        h[e] = *reinterpret_cast<const uint32_t *>(&hh);
+                    }
+                    row[q ^ ((m >> 1) & 3)] = make_uint4(h[0], h[1], h[2], h[3]);
+                }
+            } else {
+                float4 *row = reinterpret_cast<float4 *>(ga2 + m * (TABLE_STRIDE * 4));
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    row[q ^ (m & 7)] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+            }
         }
         fence_async_smem();
         fence_before();
@@ -414,16 +430,17 @@ int launch_latent_table(const LatentParams &pin, int sm_count, void *stream)
 {
     if (pin.n_leaves == 0) return (int)cudaSuccess;
     LatentParams p = pin;
-    // the table as a 2-D tensor [n_leaves][32] FP32 (128-byte rows), stored in
-    // boxes of 128 rows from 128-byte-swizzled shared memory
+    // the table as a 2-D tensor [n_leaves][32] of FP32 (128-byte rows) or FP16
+    // (64-byte rows), stored in boxes of 128 rows from swizzled shared memory
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return (int)cudaErrorNotSupported;
     const cuuint64_t dims[2] = {TABLE_STRIDE, p.n_leaves};
-    const cuuint64_t strides[1] = {TABLE_STRIDE * sizeof(float)};
+    const cuuint64_t strides[1] = {TABLE_STRIDE * (p.half_table ? 2u : 4u)};
     const cuuint32_t box[2] = {TABLE_STRIDE, LT_M};
     const cuuint32_t estr[2] = {1, 1};
-    if (enc(&p.table_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p.table, dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+    if (enc(&p.table_map, p.half_table ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+            p.table, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            p.half_table ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return (int)cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(latent_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, LT_SMEM);

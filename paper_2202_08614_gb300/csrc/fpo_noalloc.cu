@@ -68,6 +68,8 @@ extern "C" int fpo_render_noalloc(fpo_ctx *ctx, const fpo_rays *rays, const fpo_
     if (!ctx || !rays || !opts) return set_last_error(FPO_ERR_INVALID_ARG, "NULL argument");
     const CtxView c = ctx_view(ctx);
     if (!c.has_tree) return set_last_error(FPO_ERR_NO_TREE, "render before fpo_upload_tree");
+    if (c.storage == FPO_STORAGE_LATENT)
+        return set_last_error(FPO_ERR_UNSUPPORTED, "fpo_render_noalloc renders stored coefficients, not LATENT storage");
     if (c.n_leaves > NOALLOC_MAX_LEAVES) {
         char buf[160];
         std::snprintf(buf, sizeof buf, "tree has %u leaves; fpo_render_noalloc supports at most %u",
@@ -141,6 +143,7 @@ extern "C" int fpo_render_noalloc(fpo_ctx *ctx, const fpo_rays *rays, const fpo_
         mp.z_stride = L.z_elems;
         mp.stages = materialise_stages(c.storage, c.n1, c.n2);
         mp.max_ctas_per_sm = 0;
+        mp.half_table = c.half_table;
         mp.t = rays->t;
         mp.period_T = c.period_T;
         mp.status = c.d_status;
@@ -171,6 +174,7 @@ extern "C" int fpo_render_noalloc(fpo_ctx *ctx, const fpo_rays *rays, const fpo_
     p.grid_scale = (float)((double)(1u << c.depth) / c.aabb_size);
     for (int k = 0; k < 3; ++k) p.amin[k] = (float)c.aabb_min[k];
     p.table = reinterpret_cast<const float4 *>(table);
+    p.half_table = c.half_table;
     p.sig = reinterpret_cast<const float4 *>(c.d_sig);
     p.zc = static_cast<const float *>(c.d_z);
     p.n1 = c.n1;

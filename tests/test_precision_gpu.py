@@ -1,5 +1,6 @@
 """Reduced-precision coefficient storage (BF16, FP16, FP8-E4M3 with a per-leaf
-FP32 scale); the IDFT, SH and compositing stay FP32.
+FP32 scale); the IDFT, SH and compositing stay FP32, the per-frame table is
+FP16 with these storages unless FP32 is asked for.
 
 1. Encoding: storing coefficients in format X must give exactly the image of
    the FP32 renderer fed with the coefficients rounded to X by torch / numpy
@@ -44,8 +45,8 @@ def _round(coeffs: np.ndarray, storage: str) -> np.ndarray:
     return coeffs
 
 
-def _render(tree, storage, cam, t):
-    r = fpo.Renderer(storage=storage, idft_mode="materialise")
+def _render(tree, storage, cam, t, table="auto"):
+    r = fpo.Renderer(storage=storage, idft_mode="materialise", table=table)
     try:
         r.upload(tree)
         out = r.render(camera=cam, t=t)["rgb"].cpu().numpy()
@@ -60,7 +61,7 @@ def _render(tree, storage, cam, t):
 def test_16bit_encoding_matches_library_rounding(storage):
     tree = synth.shell_tree()
     cam = synth.shell_camera(64, 64)
-    a, info = _render(tree, storage, cam, 17.0)
+    a, info = _render(tree, storage, cam, 17.0, table="f32")  # same table precision as the FP32 render
     rounded = synth.Tree(tree.leaf_depth, tree.leaf_xyz, _round(tree.coeffs, storage), tree.max_depth)
     b, _ = _render(rounded, "f32", cam, 17.0)
     assert np.array_equal(a, b)
@@ -70,7 +71,7 @@ def test_16bit_encoding_matches_library_rounding(storage):
 def test_fp8_encoding_matches_library_rounding():
     tree = synth.shell_tree()
     cam = synth.shell_camera(64, 64)
-    a, info = _render(tree, "fp8", cam, 17.0)
+    a, info = _render(tree, "fp8", cam, 17.0, table="f32")
     q, sc = _round(tree.coeffs, "fp8")
     rounded = synth.Tree(tree.leaf_depth, tree.leaf_xyz, (q * sc).astype(np.float32), tree.max_depth)
     b, _ = _render(rounded, "f32", cam, 17.0)
@@ -117,3 +118,21 @@ def test_psnr_body_1080p_sampled(storage, floor):
     sel = np.concatenate([rng.integers(0, 1920 * 1080, 4000), 540 * 1920 + np.arange(0, 1920, 2)])
     ref = gu.oracle.render(ot, tree.coeffs, camera=cam, t=33.0, sel=sel)["rgb"]
     assert _psnr(gpu[sel], ref) >= floor
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "fp8"])
+def test_fp16_table_against_fp32_table(storage):
+    # the FP16 table rounds sigma(t) and z(t) to 11 significant bits: a few
+    # 1e-4 in RGB on the shell (cells 1/32 wide, sigma up to ~60)
+    tree = synth.shell_tree()
+    cam = synth.shell_camera()
+    a, info16 = _render(tree, storage, cam, synth.SHELL_T, table="f16")
+    b, info32 = _render(tree, storage, cam, synth.SHELL_T, table="f32")
+    d = np.abs(a - b)
+    print(f"{storage}: FP16 vs FP32 table max|d| {d.max():.2e}, mean {d.mean():.2e}")
+    assert d.max() <= 5e-3 and d.mean() <= 1e-4
+    assert info16["table_bytes"] * 2 == info32["table_bytes"] == tree.n_leaves * 128
+    ref = gu.oracle.render(gu.oracle_tree(tree), tree.coeffs, camera=cam, t=synth.SHELL_T)["rgb"]
+    pa, pb = _psnr(a, ref), _psnr(b, ref)
+    print(f"{storage}: PSNR vs FP64 oracle {pa:.2f} dB (FP16 table), {pb:.2f} dB (FP32 table)")
+    assert pa >= min(60.0, pb - 1.0)
