@@ -31,7 +31,7 @@ from paper_2202_08614_gb300 import synth  # noqa: E402
 METRIC = "FPO render Mrays/s, 1080p fps; plain FP32 vs BF16/latent at PSNR≥45dB vs FP64"
 ALG_READ_PER_LEAF = 4 * (31 + 135)   # coefficient bytes of one leaf (FP32)
 STORED_PER_LEAF = {"f32": 4 * 166, "bf16": 2 * 166, "f16": 2 * 166, "fp8": 166 + 4}  # + FP8 scale
-TABLE_BYTES_PER_LEAF = 4 * 28        # sigma(t) + 27 z(t)
+TABLE_VALUES_PER_LEAF = 28           # sigma(t) + 27 z(t), FP32 or FP16 (the table precision)
 OUT_BYTES_PER_RAY = 12               # FP32 RGB
 
 
@@ -531,10 +531,13 @@ def main():
     avg_mat = statistics.mean(mat_ms) if mat else 0.0
     avg_trav = statistics.mean(trav_ms)
     mean_vis = statistics.mean(n_vis)
+    # bytes of sigma(t) and z(t) per leaf: FP16 table rows are 64 B, FP32 128 B
+    table_bytes = TABLE_VALUES_PER_LEAF * (2 if r.info()["table_bytes"] == 64 * tree.n_leaves else 4)
+    res["config"]["table"] = ("f16" if table_bytes == 2 * TABLE_VALUES_PER_LEAF else "f32") if mat else None
     if mat:
         kernels = {
-            "materialise_kernel": (avg_mat, tree.n_leaves * (STORED_PER_LEAF[args.storage] + TABLE_BYTES_PER_LEAF)),
-            "traverse_kernel": (avg_trav, mean_vis * TABLE_BYTES_PER_LEAF + n_px * OUT_BYTES_PER_RAY),
+            "materialise_kernel": (avg_mat, tree.n_leaves * (STORED_PER_LEAF[args.storage] + table_bytes)),
+            "traverse_kernel": (avg_trav, mean_vis * table_bytes + n_px * OUT_BYTES_PER_RAY),
         }
     else:
         kernels = {"traverse_kernel": (avg_trav, mean_vis * ALG_READ_PER_LEAF + n_px * OUT_BYTES_PER_RAY)}
