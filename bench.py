@@ -261,6 +261,26 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms):
                    "psnr_db_vs_fp64_oracle": sampled_psnr(r, ot, tree.coeffs, cams, nf[:2], out, torch, n_px),
                    "bytes_per_leaf": r.info()["leaf_record_bytes"]}
     r.close()
+    # multi-view rendering of one frame time: the 16 ring views of each t share
+    # one IDFT pass (FPO_FLAG_REUSE_TABLE)
+    r = fpo.Renderer()
+    r.upload(tree)
+    ts = [float(t) for t in range(0, 60, 6)]
+    for cam in cams[:3]:
+        r.render(camera=cam, t=ts[0], out=out, reuse_table=True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for t in ts:
+        for cam in cams:
+            r.render(camera=cam, t=t, out=out, reuse_table=True)
+    b.record()
+    torch.cuda.synchronize()
+    r.status()
+    r.close()
+    mv = a.elapsed_time(b) / (len(ts) * len(cams))
+    res["multiview_16_views_per_t"] = {"ms_per_view": mv, "Mrays_s": n_px / mv / 1e3, "fps": 1e3 / mv,
+                                       "frame_times": len(ts), "views_per_t": len(cams)}
     if args.finetune_steps > 0:
         res["finetune"] = finetune_variant(args, tree, torch, fpo)
     # latent decoder on generated coefficients (same leaves)

@@ -26,6 +26,8 @@
  *  - Leaf ids at the boundary (visit logs, leaf marks, gradients) are the
  *    upload order of fpo_tree_desc, never internal addresses.
  *  - A context is not thread-safe: calls on one context must not overlap.
+ *    Their GPU work shares the context's buffers (the per-frame table, the
+ *    status word): enqueue it on one stream, or order the streams.
  */
 #ifndef FPO_H
 #define FPO_H
@@ -132,7 +134,15 @@ enum {
     FPO_FLAG_RECORD_VISITS = 1, /* write visit_log / visit_count */
     FPO_FLAG_OUT_T = 2,         /* write the final transmittance to out_T */
     FPO_FLAG_MARK_LEAVES = 4,   /* set leaf_mark[id] = 1 for every visited leaf */
-    FPO_FLAG_STATS = 8          /* add traversal counters to stats[0..2] */
+    FPO_FLAG_STATS = 8,         /* add traversal counters to stats[0..2] */
+    /* Table mode, camera or explicit rays without per-ray times: if the
+     * context's per-frame table was last built by fpo_render for the same t
+     * (bit-equal) and nothing has changed the coefficients or latents since
+     * (fpo_upload_tree, fpo_set_coeffs, fpo_adam_leaves, fpo_set_latents),
+     * skip the IDFT pass and reuse it: several views of one frame time cost
+     * one IDFT pass.  The call must follow the one that built the table on
+     * the same stream (or an ordered one). */
+    FPO_FLAG_REUSE_TABLE = 16
 };
 
 /* Per-call options.  bg: background colour added with the final

@@ -100,6 +100,8 @@ struct fpo_ctx {
     size_t table_leaves = 0;
     // frame pipeline (fpo_render_frames): second table, aux stream, events
     bool half_table = false;  // the per-frame table holds FP16 (64 B per leaf)
+    bool table_ok = false;    // d_table holds the IDFT pass of table_t for the current coefficients
+    double table_t = 0.0;
     float *d_table2 = nullptr;
     size_t table2_leaves = 0;
     cudaStream_t aux = nullptr;
@@ -118,6 +120,7 @@ struct fpo_ctx {
         has_latents = false;
         dfree(d_table);
         table_leaves = 0;
+        table_ok = false;
         dfree(d_table2);
         table2_leaves = 0;
         has_tree = false;
@@ -502,9 +505,12 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
         if ((e = rec(1)) != cudaSuccess || (e = rec(2)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
         return FPO_OK;
     }
-    if (mat) {
+    if (mat && !((fl & FPO_FLAG_REUSE_TABLE) && ctx->table_ok && ctx->table_t == rays->t)) {
+        ctx->table_ok = false;
         const int ce = launch_table_pass(ctx, rays->t, ctx->d_table, 0, s);
         if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "IDFT table launch");
+        ctx->table_ok = true;
+        ctx->table_t = rays->t;
     }
     if ((e = rec(1)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
 
@@ -567,6 +573,7 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(e, "stream/event creation");
     }
+    ctx->table_ok = false;  // the pipeline writes both tables
     cudaStream_t s = (cudaStream_t)cuda_stream;
     // The table pass of frame k + 1 runs on the auxiliary stream while frame
     // k is traversed on the caller's stream; two tables alternate.
@@ -634,6 +641,7 @@ int fpo_set_latents(fpo_ctx *ctx, const uint16_t *latents, const fpo_decoder *de
     if (ctx->cfg.storage != FPO_STORAGE_LATENT) return fail(FPO_ERR_UNSUPPORTED, "context storage is not LATENT");
     if (!dec->w1 || !dec->b1 || !dec->w2 || !dec->b2 || !dec->w3 || !dec->b3 || (ctx->n_leaves && !latents))
         return fail(FPO_ERR_INVALID_ARG, "NULL array");
+    ctx->table_ok = false;  // the coefficients change
     DeviceGuard g(ctx->cfg.device);
     if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
     const int nc = ctx->cfg.n1 + 27 * ctx->cfg.n2;
@@ -667,6 +675,7 @@ int fpo_set_coeffs(fpo_ctx *ctx, const float *coeffs, void *cuda_stream)
         return fail(FPO_ERR_UNSUPPORTED, "in-place coefficient updates need FP32 storage");
     if (ctx->n_leaves == 0) return FPO_OK;
     if (!coeffs) return fail(FPO_ERR_INVALID_ARG, "coeffs is NULL");
+    ctx->table_ok = false;  // the coefficients change
     DeviceGuard g(ctx->cfg.device);
     if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
     const int ce = launch_set_coeffs(coeffs, ctx->d_perm, static_cast<float *>(ctx->d_sig),
@@ -688,6 +697,7 @@ int fpo_adam_leaves(fpo_ctx *ctx, float *param, float *grad, float *m, float *v,
     if (step < 1) return fail(FPO_ERR_INVALID_ARG, "step counts from 1");
     if (!(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
         return fail(FPO_ERR_INVALID_ARG, "lr >= 0, beta in [0, 1), eps > 0");
+    ctx->table_ok = false;  // the coefficients change
     DeviceGuard g(ctx->cfg.device);
     if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
     LeafAdamParams p{};

@@ -26,7 +26,7 @@ STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "fp8": 3, "latent": 4}
 IDFT = {"auto": 0, "fused": 1, "materialise": 2}
 TABLE = {"auto": 0, "f32": 1, "f16": 2}
 RAYS_CAMERA, RAYS_EXPLICIT = 0, 1
-FLAG_RECORD_VISITS, FLAG_OUT_T, FLAG_MARK_LEAVES, FLAG_STATS = 1, 2, 4, 8
+FLAG_RECORD_VISITS, FLAG_OUT_T, FLAG_MARK_LEAVES, FLAG_STATS, FLAG_REUSE_TABLE = 1, 2, 4, 8, 16
 
 # Every symbol include/fpo.h declares.
 EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
@@ -218,7 +218,7 @@ class Renderer:
 
     def render(self, camera=None, t=0.0, rays_o=None, rays_d=None, t_per_ray=None,
                bg=(1.0, 1.0, 1.0), stop_T=1e-4, out=None, visit_cap=None, want_T=False,
-               leaf_mark=None, stats=None, stream=None, events=None):
+               leaf_mark=None, stats=None, stream=None, events=None, reuse_table=False):
         """Renders one frame; returns a dict of device tensors.
 
         camera: an object with eye/target/up/fov_y_deg/width/height (pixel
@@ -226,7 +226,8 @@ class Renderer:
         tensors rays_o, rays_d [n, 3] and optional t_per_ray [n].
         visit_cap: if not None, also returns visit_log [n, cap] and
         visit_count [n] (leaf ids in upload order).  leaf_mark: optional CUDA
-        uint8 tensor [n_leaves] set to 1 for visited leaves.
+        uint8 tensor [n_leaves] set to 1 for visited leaves.  reuse_table:
+        skip the IDFT pass when the last table was built for the same t.
         """
         import torch
 
@@ -235,7 +236,7 @@ class Renderer:
         if out is None:
             out = torch.empty((n, 3), dtype=torch.float32, device=dev)
         return self._render_into(r, keep, n, out, bg, stop_T, visit_cap, want_T, leaf_mark, stats,
-                                 stream, events)
+                                 stream, events, reuse_table)
 
     def _rays(self, camera, t, rays_o, rays_d, t_per_ray):
         import torch
@@ -267,7 +268,7 @@ class Renderer:
         return r, keep, n
 
     def _render_into(self, r, keep, n, out, bg, stop_T, visit_cap, want_T, leaf_mark, stats,
-                     stream, events):
+                     stream, events, reuse_table=False):
         import torch
 
         dev = torch.device("cuda", self.device)
@@ -293,6 +294,8 @@ class Renderer:
         if stats is not None:  # CUDA int64 tensor [3], accumulated
             opts.stats = stats.data_ptr()
             flags |= FLAG_STATS
+        if reuse_table:
+            flags |= FLAG_REUSE_TABLE
         opts.flags = flags
         if events is not None:
             for i, ev in enumerate(events):

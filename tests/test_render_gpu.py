@@ -267,3 +267,28 @@ def test_body_1080p_sampled_pixels(body, mode):
             assert (ref["visit_count"] > 0).sum() > 150  # the sample sees the body
     finally:
         r.close()
+
+
+def test_table_reuse_for_views_of_one_frame_time():
+    # FPO_FLAG_REUSE_TABLE: views of one t share an IDFT pass; a new t, or new
+    # coefficients, rebuild it (the images equal fresh renders bit for bit)
+    tree = synth.random_tree(21, max_depth=5, p_split=0.6, p_empty=0.3)
+    cams = synth.ring_cameras(4, 48, 40)
+    r = fpo.Renderer()
+    fresh = fpo.Renderer()
+    try:
+        r.upload(tree)
+        fresh.upload(tree)
+        ref = lambda cam, t: fresh.render(camera=cam, t=t)["rgb"].clone()
+        r.render(camera=cams[0], t=5.0)
+        assert torch.equal(r.render(camera=cams[1], t=5.0, reuse_table=True)["rgb"], ref(cams[1], 5.0))
+        assert torch.equal(r.render(camera=cams[2], t=6.5, reuse_table=True)["rgb"], ref(cams[2], 6.5))
+        co = torch.as_tensor(tree.coeffs, device="cuda") * 0.5
+        r.set_coeffs(co)
+        fresh.set_coeffs(co)
+        assert torch.equal(r.render(camera=cams[3], t=6.5, reuse_table=True)["rgb"], ref(cams[3], 6.5))
+        r.status()
+        fresh.status()
+    finally:
+        r.close()
+        fresh.close()
