@@ -256,9 +256,202 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
     }
 }
 
+// Reduced-precision storages (BF16, FP16, FP8) with n2 = 5: the pass is
+// bound by instructions, not bytes, in the warp-per-leaf form above (77 warp
+// instructions per leaf, shared-memory bank conflicts on 2-byte elements).
+// Here one thread owns one leaf of a 256-leaf chunk: 16-byte loads of its
+// records from the same bulk-copy ring, unpacked in registers, the density
+// products summed in the same tree order as the warp's butterfly and each z
+// accumulated in the same order as above, so both kernels give the same
+// bits; the row is written with 16-byte stores.
+constexpr int ML_THREADS = 256, ML_CHUNK = 256, ML_N2 = 5;
+
+// The 16 bytes of w as FP32 values (8 for 16-bit storage, 16 for FP8).
+template <int ST>
+__device__ __forceinline__ void unpack16(const uint4 w, float *v)
+{
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if constexpr (ST == FPO_STORAGE_BF16) {
+            v[2 * k] = __uint_as_float(u[k] << 16);
+            v[2 * k + 1] = __uint_as_float(u[k] & 0xffff0000u);
+        } else if constexpr (ST == FPO_STORAGE_F16) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&u[k]));
+            v[2 * k] = f.x;
+            v[2 * k + 1] = f.y;
+        } else {
+            const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u[k] & 0xffffu), __NV_E4M3);
+            const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u[k] >> 16), __NV_E4M3);
+            const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&lo));
+            const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+            v[4 * k] = a.x;
+            v[4 * k + 1] = a.y;
+            v[4 * k + 2] = b.x;
+            v[4 * k + 3] = b.y;
+        }
+    }
+}
+
+template <int ST>
+__global__ void __launch_bounds__(ML_THREADS) materialise_leaf_kernel(const __grid_constant__ MaterialiseParams p)
+{
+    extern __shared__ __align__(128) unsigned char mat_smem[];
+    __shared__ uint64_t bars[MAT_MAX_STAGES];
+    __shared__ float s_b[MAX_BASIS];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x;
+    const int S = p.stages;
+    constexpr uint32_t EB = ST == FPO_STORAGE_FP8_E4M3 ? 1u : 2u;
+    constexpr int PER = 16 / (int)EB;              // elements per 16-byte load
+    constexpr bool SCALED = ST == FPO_STORAGE_FP8_E4M3;
+    constexpr int SIG_ELEMS = 32;                  // n1 <= 32, padded to 16 bytes
+    constexpr int Z_ELEMS = (27 * ML_N2 + PER - 1) / PER * PER;
+    const uint32_t rec_sig = SIG_ELEMS * EB, rec_z = Z_ELEMS * EB;
+    const uint32_t sig_bytes = ML_CHUNK * rec_sig, z_bytes = ML_CHUNK * rec_z;
+    const uint32_t stage_bytes = sig_bytes + z_bytes + (SCALED ? ML_CHUNK * 4u : 0u);
+    const uint32_t n_chunks = (p.n_leaves + ML_CHUNK - 1) / ML_CHUNK;
+    const int nb = p.n1 > ML_N2 ? p.n1 : ML_N2;
+    if (tid < MAX_BASIS) s_b[tid] = tid < nb ? basis_fp64(tid, p.t, p.period_T) : 0.0f;
+    if (tid == 0) {
+        s_fail = 0;
+        for (int s = 0; s < S; ++s) ptx::mbar_init(&bars[s], 1);
+        ptx::fence_barrier_init();
+    }
+    __syncthreads();
+    auto issue = [&](uint32_t c, int s) {
+        const uint32_t first = c * ML_CHUNK;
+        const uint32_t m = min((uint32_t)ML_CHUNK, p.n_leaves - first);
+        unsigned char *dst = mat_smem + (size_t)s * stage_bytes;
+        const uint32_t bsc = SCALED ? ((m + 3u) & ~3u) * 4u : 0u;
+        ptx::mbar_arrive_expect_tx(&bars[s], m * rec_sig + m * rec_z + bsc);
+        ptx::bulk_g2s(dst, static_cast<const unsigned char *>(p.sig) + (size_t)first * rec_sig, m * rec_sig, &bars[s]);
+        ptx::bulk_g2s(dst + sig_bytes, static_cast<const unsigned char *>(p.zc) + (size_t)first * rec_z, m * rec_z,
+                      &bars[s]);
+        if (SCALED) ptx::bulk_g2s(dst + sig_bytes + z_bytes, p.scale + first, bsc, &bars[s]);
+    };
+    if (tid == 0)
+        for (int s = 0; s < S; ++s) {
+            const uint32_t c = blockIdx.x + (uint32_t)s * gridDim.x;
+            if (c < n_chunks) issue(c, s);
+        }
+    float b[SIG_ELEMS], bz[ML_N2];
+#pragma unroll
+    for (int i = 0; i < SIG_ELEMS; ++i) b[i] = i < p.n1 ? s_b[i] : 0.0f;
+#pragma unroll
+    for (int i = 0; i < ML_N2; ++i) bz[i] = s_b[i];
+    uint32_t it = 0;
+    for (;; ++it) {
+        const uint32_t c = blockIdx.x + it * gridDim.x;
+        if (c >= n_chunks) break;
+        const int s = (int)(it % (uint32_t)S);
+        const uint32_t parity = (it / (uint32_t)S) & 1u;
+        if (!ptx::mbar_wait_bounded(&bars[s], parity, WAIT_LIMIT_NS)) s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        const uint32_t first = c * ML_CHUNK;
+        const int m = (int)min((uint32_t)ML_CHUNK, p.n_leaves - first);
+        const unsigned char *stage = mat_smem + (size_t)s * stage_bytes;
+        if (tid < m) {
+            const uint4 *sg = reinterpret_cast<const uint4 *>(stage + tid * rec_sig);
+            const uint4 *zz = reinterpret_cast<const uint4 *>(stage + sig_bytes + tid * rec_z);
+            // density: products k_i b_i, summed as the warp butterfly does
+            // (pairs i, i + 16, then i, i + 8, ... down to i, i + 1)
+            float part[SIG_ELEMS];
+#pragma unroll
+            for (int k = 0; k < SIG_ELEMS / PER; ++k) {
+                float v[PER];
+                unpack16<ST>(sg[k], v);
+#pragma unroll
+                for (int j = 0; j < PER; ++j) part[k * PER + j] = __fmul_rn(v[j], b[k * PER + j]);
+            }
+            // (_rn: no contraction of a product into the sums, as across lanes)
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+                for (int i = 0; i < o; ++i) part[i] = __fadd_rn(part[i], part[i + o]);
+            float z[27];
+#pragma unroll
+            for (int q = 0; q < 27; ++q) z[q] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < Z_ELEMS / PER; ++k) {
+                float v[PER];
+                unpack16<ST>(zz[k], v);
+#pragma unroll
+                for (int j = 0; j < PER; ++j) {
+                    const int e = k * PER + j;
+                    if (e < 27 * ML_N2) z[e / ML_N2] = fmaf(v[j], bz[e % ML_N2], z[e / ML_N2]);
+                }
+            }
+            float sigma = part[0];
+            if (SCALED) {
+                const float sc = reinterpret_cast<const float *>(stage + sig_bytes + z_bytes)[tid];
+                sigma *= sc;
+#pragma unroll
+                for (int q = 0; q < 27; ++q) z[q] *= sc;
+            }
+            sigma = fmaxf(sigma, 0.0f);
+            const size_t leaf = (size_t)first + tid;
+            if (p.half_table) {
+                uint32_t h[16];
+                {
+                    const __half2 hh = __floats2half2_rn(sigma, z[0]);
+                    h[0] = *reinterpret_cast<const uint32_t *>(&hh);
+                }
+#pragma unroll
+                for (int q = 1; q < 14; ++q) {
+                    const __half2 hh = __floats2half2_rn(z[2 * q - 1], z[2 * q]);
+                    h[q] = *reinterpret_cast<const uint32_t *>(&hh);
+                }
+                h[14] = h[15] = 0u;
+                uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__half *>(p.table) + leaf * TABLE_STRIDE);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dst[q] = make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+            } else {
+                float4 *dst = reinterpret_cast<float4 *>(p.table + leaf * TABLE_STRIDE);
+                dst[0] = make_float4(sigma, z[0], z[1], z[2]);
+#pragma unroll
+                for (int q = 1; q < 7; ++q) dst[q] = make_float4(z[4 * q - 1], z[4 * q], z[4 * q + 1], z[4 * q + 2]);
+                dst[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+        }
+        __syncthreads();  // every thread is done with stage s
+        if (tid == 0) {
+            const uint32_t c2 = c + (uint32_t)S * gridDim.x;
+            if (c2 < n_chunks) issue(c2, s);
+        }
+    }
+    if (s_fail && tid == 0) {
+        for (uint32_t k = it; k < it + (uint32_t)S; ++k) {
+            const uint32_t c = blockIdx.x + k * gridDim.x;
+            if (c >= n_chunks) break;
+            ptx::mbar_wait_bounded(&bars[k % (uint32_t)S], (k / (uint32_t)S) & 1u, WAIT_LIMIT_NS);
+        }
+        atomicOr(p.status, STATUS_DEVICE_TIMEOUT);
+    }
+}
+
+// The thread-per-leaf form applies to the reduced-precision storages with
+// n2 = 5 and density records of 32 elements (n1 from 25 or, for FP8, 17 up
+// to 32).
+static bool leaf_form(int storage, int n1, int n2)
+{
+    if (storage < FPO_STORAGE_BF16 || storage > FPO_STORAGE_FP8_E4M3 || n2 != ML_N2 || n1 < 1 || n1 > 32) return false;
+    const RecordLayout L = record_layout(storage, n1, n2);  // the kernel's fixed record strides
+    const int per = 16 / L.elem_bytes;
+    return L.sig_elems == 32 && L.z_elems == (27 * ML_N2 + per - 1) / per * per;
+}
+
 int materialise_stages(int storage, int n1, int n2)
 {
     const RecordLayout L = record_layout(storage, n1, n2);
+    if (leaf_form(storage, n1, n2)) {  // one CTA per SM, 256 leaves per stage
+        const int stage = ML_CHUNK * (L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
+        int s = (200 * 1024) / stage;
+        if (s > MAT_MAX_STAGES) s = MAT_MAX_STAGES;
+        if (s < 2) s = 2;
+        return s;
+    }
     const int stage = MAT_CHUNK * (L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
     int s = (100 * 1024) / stage;  // two CTAs per SM
     if (s > MAT_MAX_STAGES) s = MAT_MAX_STAGES;
@@ -283,21 +476,30 @@ int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream)
     if (p.storage < FPO_STORAGE_F32 || p.storage > FPO_STORAGE_FP8_E4M3 || !p.sig || !p.zc)
         return (int)cudaErrorInvalidValue;  // no coefficient records (e.g. LATENT storage)
     const RecordLayout L = record_layout(p.storage, p.n1, p.n2);
-    const int smem = p.stages * MAT_CHUNK * (L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
-    const void *kern = p.n2 == 5 ? pick_materialise<5>(p.storage)
-                                 : (p.n2 == 11 ? pick_materialise<11>(p.storage) : pick_materialise<0>(p.storage));
+    const bool lf = leaf_form(p.storage, p.n1, p.n2);
+    const int chunk = lf ? ML_CHUNK : MAT_CHUNK;
+    const int smem = p.stages * chunk * (L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
+    const void *kern;
+    if (lf)
+        kern = p.storage == FPO_STORAGE_BF16 ? (const void *)materialise_leaf_kernel<FPO_STORAGE_BF16>
+             : p.storage == FPO_STORAGE_F16  ? (const void *)materialise_leaf_kernel<FPO_STORAGE_F16>
+                                             : (const void *)materialise_leaf_kernel<FPO_STORAGE_FP8_E4M3>;
+    else
+        kern = p.n2 == 5 ? pick_materialise<5>(p.storage)
+                         : (p.n2 == 11 ? pick_materialise<11>(p.storage) : pick_materialise<0>(p.storage));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MAT_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, lf ? ML_THREADS : MAT_THREADS, smem);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) per_sm = 1;
     if (p.max_ctas_per_sm > 0 && per_sm > p.max_ctas_per_sm) per_sm = p.max_ctas_per_sm;
-    const uint32_t n_chunks = (p.n_leaves + MAT_CHUNK - 1) / MAT_CHUNK;
+    const uint32_t n_chunks = (p.n_leaves + chunk - 1) / chunk;
     uint64_t blocks = (uint64_t)sm_count * per_sm;
     if (blocks > n_chunks) blocks = n_chunks;
     void *args[] = {(void *)&p};
-    e = cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(MAT_THREADS), args, smem, (cudaStream_t)stream);
+    e = cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(lf ? ML_THREADS : MAT_THREADS), args, smem,
+                         (cudaStream_t)stream);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }
@@ -611,10 +813,18 @@ __device__ __forceinline__ bool shade(const TraverseParams &p, const float *bsrc
         const float4 *rec = table_record(p, leaf);
         float v[32];
 #if FPO_LDG256
-        // four 32-byte loads for the 128-byte table line (half the load
-        // instructions, and half the L1 wavefronts, of 16-byte loads)
+        // the 112 used bytes of the 128-byte table line: three 32-byte loads
+        // and one 16-byte load (half the load instructions, and half the L1
+        // wavefronts, of 16-byte loads; no registers for the padding)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) ldg256(reinterpret_cast<const float *>(rec) + 8 * q, v + 8 * q);
+        for (int q = 0; q < 3; ++q) ldg256(reinterpret_cast<const float *>(rec) + 8 * q, v + 8 * q);
+        {
+            const float4 w = __ldg(rec + 6);
+            v[24] = w.x;
+            v[25] = w.y;
+            v[26] = w.z;
+            v[27] = w.w;
+        }
 #else
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
