@@ -9,7 +9,8 @@
 //
 // Per CTA the weights are staged once in shared memory in the no-swizzle
 // K-major core-matrix layout (8 rows x 16 B blocks) and W3'(t) is computed
-// in the prologue.  Four warpgroups then run independent tile pipelines
+// in the prologue.  Eight warpgroups (1024 threads, all 512 TMEM columns)
+// then run independent tile pipelines
 // (own A buffers, own 64 TMEM columns, own mbarrier and named barrier): for
 // each tile of 128 leaves the threads lay the latents out as the A operand,
 // one elected thread issues tcgen05.mma (M = 128, K = 16 per instruction,
@@ -32,7 +33,7 @@ namespace fpo {
 namespace {
 
 #ifndef FPO_LT_GROUPS
-#define FPO_LT_GROUPS 4
+#define FPO_LT_GROUPS 8
 #endif
 constexpr int LT_GROUPS = FPO_LT_GROUPS;  // independent warpgroup pipelines per CTA (one CTA per SM)
 constexpr int LT_THREADS = 128 * LT_GROUPS;
@@ -53,9 +54,12 @@ constexpr int K1 = 48, K2 = 80;
 constexpr int OFF_W1 = 0;          // 64 x 48  f16:  6 KB
 constexpr int OFF_W2 = 6144;       // 64 x 80  f16: 10 KB
 constexpr int OFF_W3 = 16384;      // 32 x 80  f16:  5 KB
+// A1 (layer-1 input) and A2 share one region per group: MMA 1 has finished
+// reading A1 before the layer-1 epilogue writes A2, and the next tile's A1 is
+// written only after the tensor store has read the previous output from A2.
 constexpr int OFF_A1 = 22528;      // per group: 128 x 48 f16: 12 KB
-constexpr int OFF_A2 = 34816;      // per group: 128 x 80 f16: 20 KB (1024-byte aligned: output staging)
-constexpr int GROUP_BYTES = 32768; // A1 + A2 of one warpgroup
+constexpr int OFF_A2 = 22528;      // per group: 128 x 80 f16: 20 KB (1024-byte aligned: output staging)
+constexpr int GROUP_BYTES = 20480; // one warpgroup's region
 constexpr int LT_SMEM = OFF_A1 + LT_GROUPS * GROUP_BYTES + 1024;  // + alignment slack
 
 // Byte offset of element (row, k) in a K-major core-matrix layout whose rows
@@ -96,22 +100,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// 64 consecutive FP32 columns of this thread's TMEM lane: two 32-column
-// loads in flight, then one wait.
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float v[64])
-{
-    uint32_t r[64];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-        : "r"(taddr), "r"(taddr + 32)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // 32 consecutive FP32 columns of this thread's TMEM lane; waits for them.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
@@ -292,10 +280,6 @@ __global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __gri
     const uint32_t first = blockIdx.x * LT_GROUPS + group, step = gridDim.x * LT_GROUPS;
     const int m = gt;  // this thread's accumulator row (TMEM lane) and leaf in the tile
 
-    // the constant-one columns of this thread's row of A1 (A2 gets its own
-    // with every layer-1 epilogue: the output staging overwrites them)
-    put_bias_chunk(ga1, m, 4, K1, 0.0f, true);
-    put_zero_chunk(ga1, m, 5, K1);
 
     // One layer: the group's elected thread issues the MMAs and commits;
     // the group waits on its mbarrier (bounded).  The outcome is made
@@ -333,31 +317,37 @@ __global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __gri
     load_tile(first, nextq);
     for (uint32_t tile = first; tile < n_tiles; tile += step) {
         if (gt == 0) bulk_wait_read();  // the previous tile's table store has left A2
+        group_sync(group);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int piece = gt + 128 * i;
             *reinterpret_cast<uint4 *>(ga1 + core_off(piece >> 2, 8 * (piece & 3), K1)) = nextq[i];
         }
+        // the constant-one columns of this thread's row (A2 writes reuse the region)
+        put_bias_chunk(ga1, m, 4, K1, 0.0f, true);
+        put_zero_chunk(ga1, m, 5, K1);
         hand_off();
         if (!run_layer(sa_a1, sa_w1, K1, 64)) break;
         // layer 1 epilogue: bias + ReLU -> layer-2 A operand (MMA 1 is done with A1)
-        {
-            float v[64];
-            tmem_ld64(my_lane, v);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) put8_relu(ga2, m, c, K2, v + 8 * c);
-            put_bias_chunk(ga2, m, 8, K2, 0.0f, true);
-            put_zero_chunk(ga2, m, 9, K2);
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tmem_ld32(my_lane + 32 * h, v);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) put8_relu(ga2, m, 4 * h + c, K2, v + 8 * c);
         }
+        put_bias_chunk(ga2, m, 8, K2, 0.0f, true);
+        put_zero_chunk(ga2, m, 9, K2);
         hand_off();
         if (!run_layer(sa_a2, sa_w2, K2, 64)) break;
         // layer 2 epilogue -> layer-3 A operand, in place (MMA 2 has finished
         // reading A2, and each thread rewrites only its own row)
-        {
-            float v[64];
-            tmem_ld64(my_lane, v);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) put8_relu(ga2, m, c, K2, v + 8 * c);
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tmem_ld32(my_lane + 32 * h, v);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) put8_relu(ga2, m, 4 * h + c, K2, v + 8 * c);
         }
         hand_off();
         load_tile(tile + step, nextq);  // in flight while layer 3 runs
