@@ -25,6 +25,9 @@
 #ifndef FPO_FAST_STEP
 #define FPO_FAST_STEP 1
 #endif
+#ifndef FPO_GENERIC_NODE_LOAD
+#define FPO_GENERIC_NODE_LOAD 1
+#endif
 #ifndef FPO_FAST_SIGMOID
 #define FPO_FAST_SIGMOID 1
 #endif
@@ -691,7 +694,14 @@ __device__ __forceinline__ Cube locate(const TraverseParams &p, const uint32_t *
 #else
         (void)nc;
         const uint32_t idx = node * 8 + c;
+#if FPO_GENERIC_NODE_LOAD
+        // one generic load from shared (top nodes) or global memory: no branch
+        // between two load paths for lanes at different levels
+        const uint32_t *src = node < p.n_smem_nodes ? s_nodes : p.nodes;
+        const uint32_t sl = src[idx];
+#else
         const uint32_t sl = node < p.n_smem_nodes ? s_nodes[idx] : __ldg(p.nodes + idx);
+#endif
 #endif
         ++lvl;
         if (sl == 0u) { cb.kind = ROOT_EMPTY; break; }
