@@ -19,9 +19,6 @@
 #include "fpo_internal.h"
 #include "fpo_ptx.cuh"
 
-#ifndef FPO_NODE_CACHE
-#define FPO_NODE_CACHE 0
-#endif
 #ifndef FPO_FAST_STEP
 #define FPO_FAST_STEP 1
 #endif
@@ -532,21 +529,6 @@ struct RayState {
     uint32_t steps, n_visits, ray;
 };
 
-// The last node read from memory, cached in registers: a step into a sibling
-// cell (the common case at the finest level) needs no load at all.
-struct NodeCache {
-    uint4 lo, hi;  // slots 0..3, 4..7
-    uint32_t node;
-    int level;
-};
-
-#if FPO_NODE_CACHE
-__device__ __forceinline__ uint32_t pick_slot(const NodeCache &nc, uint32_t c)
-{
-    const uint4 h = (c & 4u) ? nc.hi : nc.lo;
-    return (c & 2u) ? ((c & 1u) ? h.w : h.z) : ((c & 1u) ? h.y : h.x);
-}
-#endif
 
 __device__ __forceinline__ void write_result(const TraverseParams &p, const RayState &R, bool dbg)
 {
@@ -659,8 +641,7 @@ struct Cube {
 };
 
 __device__ __forceinline__ Cube locate(const TraverseParams &p, const uint32_t *__restrict__ s_nodes,
-                                       uint32_t *s_stack, int stride, const int P[3], int lvl_start,
-                                       NodeCache &nc)
+                                       uint32_t *s_stack, int stride, const int P[3], int lvl_start)
 {
     Cube cb;
     cb.leaf = 0;
@@ -675,24 +656,6 @@ __device__ __forceinline__ Cube locate(const TraverseParams &p, const uint32_t *
     for (;;) {
         const int sh = D - 1 - lvl;
         const uint32_t c = ((P[0] >> sh) & 1) | (((P[1] >> sh) & 1) << 1) | (((P[2] >> sh) & 1) << 2);
-#if FPO_NODE_CACHE
-        if (!(nc.node == node && nc.level == lvl)) {
-            const uint4 *q = node < p.n_smem_nodes
-                                 ? reinterpret_cast<const uint4 *>(s_nodes) + 2 * node
-                                 : reinterpret_cast<const uint4 *>(p.nodes) + 2 * (size_t)node;
-            if (node < p.n_smem_nodes) {
-                nc.lo = q[0];
-                nc.hi = q[1];
-            } else {
-                nc.lo = __ldg(q);
-                nc.hi = __ldg(q + 1);
-            }
-            nc.node = node;
-            nc.level = lvl;
-        }
-        const uint32_t sl = pick_slot(nc, c);
-#else
-        (void)nc;
         const uint32_t idx = node * 8 + c;
 #if FPO_GENERIC_NODE_LOAD
         // one generic load from shared (top nodes) or global memory: no branch
@@ -701,7 +664,6 @@ __device__ __forceinline__ Cube locate(const TraverseParams &p, const uint32_t *
         const uint32_t sl = src[idx];
 #else
         const uint32_t sl = node < p.n_smem_nodes ? s_nodes[idx] : __ldg(p.nodes + idx);
-#endif
 #endif
         ++lvl;
         if (sl == 0u) { cb.kind = ROOT_EMPTY; break; }
@@ -940,11 +902,11 @@ __device__ __forceinline__ bool step_cap(const TraverseParams &p, RayState &R)
 template <int TM, bool DBG, int N1, int N2>
 __device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const float *bsrc,
                          int bstride, const uint32_t *__restrict__ s_nodes, uint32_t *s_stack,
-                         int stride, RayState &R, NodeCache &nc)
+                         int stride, RayState &R)
 {
     (void)fs;
     const int D = p.depth, G = 1 << D;
-    const Cube cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start, nc);
+    const Cube cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start);
     int m, lo[3], csz;
     const float tx = cube_exit(R, D, cb.lvl, m, lo, csz);
     if (cb.kind == ROOT_LEAF && tx > R.t)
@@ -974,10 +936,10 @@ __device__ __forceinline__ void prefetch_records(const TraverseParams &p, uint32
 template <int TM, bool DBG, int N1, int N2>
 __device__ void trace_ray(const TraverseParams &p, const float *bsrc, int bstride,
                           const uint32_t *__restrict__ s_nodes, uint32_t *s_stack, int stride,
-                          RayState &R, NodeCache &nc)
+                          RayState &R)
 {
     const int D = p.depth, G = 1 << D;
-    Cube cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start, nc);
+    Cube cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start);
     for (;;) {
         int m, lo[3], csz;
         const float tx = cube_exit(R, D, cb.lvl, m, lo, csz);
@@ -987,7 +949,7 @@ __device__ void trace_ray(const TraverseParams &p, const float *bsrc, int bstrid
         nx.kind = ROOT_EMPTY;
         if (FPO_PREFETCH && inside) {
             const uint32_t diff = (uint32_t)((R.P[0] ^ Pn[0]) | (R.P[1] ^ Pn[1]) | (R.P[2] ^ Pn[2]));
-            nx = locate(p, s_nodes, s_stack, stride, Pn, D - 1 - (31 - __clz(diff)), nc);
+            nx = locate(p, s_nodes, s_stack, stride, Pn, D - 1 - (31 - __clz(diff)));
             if (nx.kind == ROOT_LEAF) {
                 if constexpr (TM == TM_TABLE_F32)
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record(p, nx.leaf)));
@@ -1005,7 +967,7 @@ __device__ void trace_ray(const TraverseParams &p, const float *bsrc, int bstrid
         if (FPO_PREFETCH)
             cb = nx;
         else
-            cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start, nc);
+            cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start);
     }
 }
 
@@ -1138,10 +1100,7 @@ __global__ void __maxnreg__(TM ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED) 
             if (tile_ray(p, tile, (uint32_t)lane, ray, px, py)) {
                 RayState R;
                 if (init_ray<DBG>(p, fs, prt, my_b, stride, my_stack, R, ray, px, py)) {
-                    NodeCache nc;
-                    nc.node = 0xffffffffu;
-                    nc.level = -1;
-                    trace_ray<TM, DBG, N1, N2>(p, bsrc, bstride, s_nodes, my_stack, stride, R, nc);
+                    trace_ray<TM, DBG, N1, N2>(p, bsrc, bstride, s_nodes, my_stack, stride, R);
                     finish(R);
                 }
             }
@@ -1155,9 +1114,6 @@ __global__ void __maxnreg__(TM ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED) 
         uint32_t cur_tile = grab_tile();  // warp-uniform cursor: tile and next ray in it
         uint32_t cur_next = 0;
         RayState R;
-        NodeCache nc;
-        nc.node = 0xffffffffu;
-        nc.level = -1;
         bool active = false;
         for (;;) {
             uint32_t idle = __ballot_sync(0xffffffffu, !active);
@@ -1184,7 +1140,7 @@ __global__ void __maxnreg__(TM ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED) 
             if (active) {
 #pragma unroll 1
                 for (uint32_t k = 0; k < p.inner_steps; ++k) {
-                    if (!step_ray<TM, DBG, N1, N2>(p, fs, bsrc, bstride, s_nodes, my_stack, stride, R, nc)) {
+                    if (!step_ray<TM, DBG, N1, N2>(p, fs, bsrc, bstride, s_nodes, my_stack, stride, R)) {
                         finish(R);
                         active = false;
                         break;
@@ -1288,7 +1244,7 @@ int launch_traverse(const TraverseParams &p, bool materialised, bool debug, int 
 template <int N1, int N2>
 __device__ void backward_ray(const BackwardParams &q, const float *bsrc, int bstride,
                              const uint32_t *__restrict__ s_nodes, uint32_t *s_stack, int stride,
-                             RayState &R, NodeCache &nc)
+                             RayState &R)
 {
     constexpr int NC = N1 + 27 * N2;
     static_assert(NC % 2 == 0, "gradient rows are written in pairs");
@@ -1302,7 +1258,7 @@ __device__ void backward_ray(const BackwardParams &q, const float *bsrc, int bst
     float bz[N2];  // the density basis stays in shared memory (bsrc)
 #pragma unroll
     for (int i = 0; i < N2; ++i) bz[i] = bsrc[i * bstride];
-    Cube cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start, nc);
+    Cube cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start);
     for (;;) {
         int m, lo[3], csz;
         const float tx = cube_exit(R, D, cb.lvl, m, lo, csz);
@@ -1314,7 +1270,7 @@ __device__ void backward_ray(const BackwardParams &q, const float *bsrc, int bst
         nx.kind = ROOT_EMPTY;
         if (FPO_PREFETCH && inside) {
             const uint32_t diff = (uint32_t)((R.P[0] ^ Pn[0]) | (R.P[1] ^ Pn[1]) | (R.P[2] ^ Pn[2]));
-            nx = locate(p, s_nodes, s_stack, stride, Pn, D - 1 - (31 - __clz(diff)), nc);
+            nx = locate(p, s_nodes, s_stack, stride, Pn, D - 1 - (31 - __clz(diff)));
             if (nx.kind == ROOT_LEAF) prefetch_records(p, nx.leaf, N1, N2);
         }
         if (cb.kind == ROOT_LEAF && tx > R.t) {
@@ -1398,7 +1354,7 @@ __device__ void backward_ray(const BackwardParams &q, const float *bsrc, int bst
         if (FPO_PREFETCH)
             cb = nx;
         else
-            cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start, nc);
+            cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start);
     }
 }
 
@@ -1430,10 +1386,7 @@ __global__ void __maxnreg__(128) backward_kernel(const __grid_constant__ Backwar
         if (!tile_ray(p, tile, (uint32_t)lane, ray, px, py)) continue;
         RayState R;
         if (!init_ray_geom(p, fs, prt, my_b, stride, my_stack, R, ray, px, py)) continue;
-        NodeCache nc;
-        nc.node = 0xffffffffu;
-        nc.level = -1;
-        backward_ray<N1, N2>(q, bsrc, bstride, s_nodes, my_stack, stride, R, nc);
+        backward_ray<N1, N2>(q, bsrc, bstride, s_nodes, my_stack, stride, R);
     }
     if (lane == 0) {
         __threadfence();
