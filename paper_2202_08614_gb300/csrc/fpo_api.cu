@@ -56,9 +56,6 @@ void dfree(T *&p)
     p = nullptr;
 }
 
-#ifndef FPO_SUPER_TILE
-#define FPO_SUPER_TILE 0
-#endif
 // CTAs per SM of the two kernels of the frame pipeline (fpo_render_frames),
 // 0 = as many as fit
 #ifndef FPO_PIPE_MAT_CTAS
@@ -393,13 +390,7 @@ static TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, 
     if (rays->mode == FPO_RAYS_CAMERA) {
         p.tiles_x = (rays->width + TILE_W - 1) / TILE_W;
         const uint32_t tiles_y = (rays->height + TILE_H - 1) / TILE_H;
-        p.super_tile = FPO_SUPER_TILE;
-        if (p.super_tile) {
-            const uint32_t S = p.super_tile;
-            p.n_tiles = ((p.tiles_x + S - 1) / S) * ((tiles_y + S - 1) / S) * S * S;
-        } else {
-            p.n_tiles = p.tiles_x * tiles_y;
-        }
+        p.n_tiles = p.tiles_x * tiles_y;
     } else {
         p.tiles_x = 0;
         p.n_tiles = (uint32_t)((n_rays + 31) / 32);

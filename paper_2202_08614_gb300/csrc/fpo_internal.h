@@ -128,7 +128,6 @@ struct TraverseParams {
     // scheduling
     uint32_t *status;         // [0] status bits, [1] tile counter, [2] finished CTAs
     uint32_t n_tiles, tiles_x;
-    uint32_t super_tile;      // 0: tiles in row-major order; S: S x S groups of tiles
     uint32_t max_steps;
     uint32_t refill_min;      // warp refills its idle lanes once this many are idle (32: whole tiles)
     uint32_t inner_steps;     // steps a lane takes between two refill checks

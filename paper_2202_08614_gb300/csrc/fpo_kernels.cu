@@ -1016,17 +1016,9 @@ __device__ __forceinline__ bool tile_ray(const TraverseParams &p, uint32_t tile,
                                          int &px, int &py)
 {
     if (p.fr.mode == FPO_RAYS_CAMERA) {
-        uint32_t tx, ty;
-        if (p.super_tile) {  // square groups of super_tile^2 tiles, row-major
-            const uint32_t S = p.super_tile, per = S * S;
-            const uint32_t g = tile / per, w = tile % per, gx = (p.tiles_x + S - 1) / S;
-            tx = (g % gx) * S + w % S;
-            ty = (g / gx) * S + w / S;
-            if (tx >= p.tiles_x) return false;
-        } else {
-            tx = tile % p.tiles_x;
-            ty = tile / p.tiles_x;
-        }
+        // row-major tiles: the tiles in flight form one band of rows, whose
+        // table lines stay in L2
+        const uint32_t tx = tile % p.tiles_x, ty = tile / p.tiles_x;
         px = (int)(tx * TILE_W + k % TILE_W);
         py = (int)(ty * TILE_H + k / TILE_W);
         ray = (uint32_t)py * p.fr.width + (uint32_t)px;

@@ -194,11 +194,9 @@ extern "C" int fpo_render_noalloc(fpo_ctx *ctx, const fpo_rays *rays, const fpo_
     p.status = c.d_status;
     if (rays->mode == FPO_RAYS_CAMERA) {
         p.tiles_x = (rays->width + TILE_W - 1) / TILE_W;
-        p.super_tile = 0;
         p.n_tiles = p.tiles_x * ((rays->height + TILE_H - 1) / TILE_H);
     } else {
         p.tiles_x = 0;
-        p.super_tile = 0;
         p.n_tiles = (uint32_t)((n_rays + 31) / 32);
     }
     p.max_steps = 3u * (1u << c.depth) + 16u;
