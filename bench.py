@@ -2,8 +2,9 @@
 
 Workload: the depth-9 union octree of the animated 14-capsule body (about
 3.5M leaves, n1 = 31, n2 = 5, i.i.d. coefficients, seed 0), rendered at
-1920x1080 from the 16 ring cameras at integer frame times (a seeded order
-over the 16 x 60 grid).  The tree (2.4 GB of coefficient records) is larger
+1920x1080 from the 16 ring cameras at integer frame times: by default the
+960 timed frames are each (camera, t) of the 16 x 60 grid once, in a seeded
+order.  The tree (2.4 GB of coefficient records) is larger
 than L2, so no flush is needed between frames.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
@@ -38,7 +39,7 @@ OUT_BYTES_PER_RAY = 12               # FP32 RGB
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=960)  # every (camera, t) of the 16 x 60 grid once
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fpo", choices=["fpo", "reference"])
     ap.add_argument("--idft", default="auto", choices=["auto", "materialise", "fused"])
