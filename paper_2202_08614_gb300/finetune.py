@@ -39,6 +39,23 @@ class FineTuner:
         self.steps = 0
         self.r.set_coeffs(self.param)
 
+    def state_dict(self):
+        """Coefficients, Adam moments and step count (host tensors)."""
+        return {"param": self.param.cpu(), "m": self.m.cpu(), "v": self.v.cpu(), "steps": self.steps,
+                "lr": self.lr, "betas": tuple(self.betas), "eps": self.eps}
+
+    def load_state_dict(self, st):
+        """Restores a state_dict and writes the coefficients into the renderer."""
+        if tuple(st["param"].shape) != tuple(self.param.shape):
+            raise ValueError(f"state for {tuple(st['param'].shape)} coefficients, tuner has {tuple(self.param.shape)}")
+        for name in ("param", "m", "v"):
+            getattr(self, name).copy_(st[name])
+        self.steps = int(st["steps"])
+        self.lr, self.betas, self.eps = st["lr"], tuple(st["betas"]), st["eps"]
+        self.grad.zero_()
+        self.mark.zero_()
+        self.r.set_coeffs(self.param)
+
     def render(self, rays_o, rays_d, t, out=None):
         return self.r.render(rays_o=rays_o, rays_d=rays_d, t_per_ray=t, bg=self.bg, stop_T=self.stop_T,
                              out=out)["rgb"]

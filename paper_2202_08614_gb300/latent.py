@@ -36,6 +36,20 @@ class LatentModel:
         self.g = {k: torch.zeros_like(v) for k, v in self.p.items() if k != "lat"}
         self.step_count = 0
 
+    def state_dict(self):
+        """Latents, MLP, Adam moments and step count (host tensors)."""
+        return {"n1": self.n1, "n2": self.n2, "step_count": self.step_count,
+                "p": {k: v.cpu() for k, v in self.p.items()}, "m": {k: v.cpu() for k, v in self.m.items()},
+                "v": {k: v.cpu() for k, v in self.v.items()}}
+
+    def load_state_dict(self, st):
+        if (st["n1"], st["n2"]) != (self.n1, self.n2) or tuple(st["p"]["lat"].shape) != tuple(self.p["lat"].shape):
+            raise ValueError("state of a different model size")
+        for part in ("p", "m", "v"):
+            for k, t in getattr(self, part).items():
+                t.copy_(st[part][k])
+        self.step_count = int(st["step_count"])
+
     def _mlp(self, d):
         return fpo.Mlp(*(d[k].data_ptr() for k in ("w1", "b1", "w2", "b2", "w3", "b3")))
 
