@@ -88,13 +88,13 @@ def mrays_per_s(world: int, steps: int, rays_per_frame: int, elapsed_ms: float) 
 # oracle timing (CPU baseline and the reference arm)
 
 
-def oracle_sample_rate(tree, cams, frames, budget_s, stride=61):
+def oracle_sample_rate(tree, cams, frames, budget_s, stride=61, threads=None):
     """Times the FP64 oracle on strided pixel samples of successive frames
     until `budget_s` seconds of wall time; returns (Mrays/s, rays, seconds, threads)."""
     import oracle
 
     ot = oracle.OracleTree(tree.leaf_depth, tree.leaf_xyz, tree.max_depth)
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     rays, spent, i = 0, 0.0, 0
     while spent < budget_s:
         k, t = frames[i % len(frames)]
@@ -612,6 +612,17 @@ def main():
         res["cpu_baseline"] = {"value": v, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
                                "sample": f"{rays} rays: every 61st pixel of successive timed "
                                          f"frames, {secs:.1f} s"}
+        # the same oracle on one core, and the full 128x128 shell frame (the
+        # parity case) on all cores
+        v1, rays1, secs1, _ = oracle_sample_rate(tree, cams, frames[W:], args.cpu_seconds / 4, stride=997, threads=1)
+        res["cpu_baseline"]["one_core"] = {"value": v1, "cores": 1, "sample": f"{rays1} rays, {secs1:.1f} s"}
+        import oracle
+
+        shell = synth.shell_tree()
+        t0 = time.perf_counter()
+        oracle.render(oracle.OracleTree(shell.leaf_depth, shell.leaf_xyz, shell.max_depth), shell.coeffs,
+                      camera=synth.shell_camera(), t=synth.SHELL_T, threads=thr)
+        res["cpu_baseline"]["shell_128_full_frame_s"] = time.perf_counter() - t0
     r.close()
     if rank == 0:
         print(json.dumps(res), flush=True)
