@@ -89,6 +89,11 @@ typedef struct {
     int32_t refill_min;
     int32_t inner_steps;
     int32_t table_precision; /* FPO_TABLE_* */
+    /* Traversal steps a ray may take before it stops and the call reports
+     * FPO_ERR_TRAVERSAL_LIMIT (0 = the library's bound 3 * 2^depth + 16,
+     * which no ray of a valid tree reaches; a small value exercises the
+     * device-side error path). */
+    int32_t max_steps;
 } fpo_config;
 
 /* A union octree given by its leaves (Sec. 4.2): leaf j is the cell

@@ -140,6 +140,7 @@ CtxView ctx_view(const fpo_ctx *c)
     v.traverse_threads = c->cfg.traverse_threads;
     v.refill_min = c->cfg.refill_min;
     v.inner_steps = c->cfg.inner_steps;
+    v.max_steps = c->cfg.max_steps;
     v.d_status = c->d_status;
     v.half_table = c->half_table;
     v.has_tree = c->has_tree;
@@ -188,6 +189,7 @@ int fpo_create(fpo_ctx **out, const fpo_config *cfg)
     if (cfg->refill_min < 0 || cfg->refill_min > 32)
         return fail(FPO_ERR_INVALID_ARG, "refill_min must be in [0, 32]");
     if (cfg->inner_steps < 0) return fail(FPO_ERR_INVALID_ARG, "inner_steps must be >= 0");
+    if (cfg->max_steps < 0) return fail(FPO_ERR_INVALID_ARG, "max_steps must be >= 0");
     if (cfg->table_precision < FPO_TABLE_AUTO || cfg->table_precision > FPO_TABLE_F16)
         return fail(FPO_ERR_INVALID_ARG, "table_precision must be FPO_TABLE_AUTO, _F32 or _F16");
     int ndev = 0;
@@ -395,7 +397,7 @@ static TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, 
         p.tiles_x = 0;
         p.n_tiles = (uint32_t)((n_rays + 31) / 32);
     }
-    p.max_steps = 3u * (1u << ctx->depth) + 16u;
+    p.max_steps = ctx->cfg.max_steps > 0 ? (uint32_t)ctx->cfg.max_steps : 3u * (1u << ctx->depth) + 16u;
     p.block_threads = ctx->cfg.traverse_threads ? ctx->cfg.traverse_threads : DEFAULT_TRAVERSE_THREADS;
     p.refill_min = ctx->cfg.refill_min ? (uint32_t)ctx->cfg.refill_min : DEFAULT_REFILL_MIN;
     p.inner_steps = ctx->cfg.inner_steps ? (uint32_t)ctx->cfg.inner_steps : DEFAULT_INNER_STEPS;

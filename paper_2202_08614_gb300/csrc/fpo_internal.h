@@ -156,7 +156,7 @@ struct CtxView {
     int device, sm_count;
     int n1, n2;
     double period_T;
-    int traverse_threads, refill_min, inner_steps;
+    int traverse_threads, refill_min, inner_steps, max_steps;
     uint32_t *d_status;
     bool half_table;
     bool has_tree;

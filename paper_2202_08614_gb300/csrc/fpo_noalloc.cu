@@ -199,7 +199,7 @@ extern "C" int fpo_render_noalloc(fpo_ctx *ctx, const fpo_rays *rays, const fpo_
         p.tiles_x = 0;
         p.n_tiles = (uint32_t)((n_rays + 31) / 32);
     }
-    p.max_steps = 3u * (1u << c.depth) + 16u;
+    p.max_steps = c.max_steps > 0 ? (uint32_t)c.max_steps : 3u * (1u << c.depth) + 16u;
     p.block_threads = c.traverse_threads ? c.traverse_threads : 256;
     p.refill_min = c.refill_min ? (uint32_t)c.refill_min : 32u;
     p.inner_steps = c.inner_steps ? (uint32_t)c.inner_steps : 0xffffffffu;

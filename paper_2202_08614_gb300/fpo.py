@@ -46,7 +46,7 @@ class Config(C.Structure):
     _fields_ = [("n1", C.c_int32), ("n2", C.c_int32), ("sh_degree", C.c_int32),
                 ("period_T", C.c_double), ("storage", C.c_int32), ("idft_mode", C.c_int32),
                 ("device", C.c_int32), ("traverse_threads", C.c_int32), ("refill_min", C.c_int32),
-                ("inner_steps", C.c_int32), ("table_precision", C.c_int32)]
+                ("inner_steps", C.c_int32), ("table_precision", C.c_int32), ("max_steps", C.c_int32)]
 
 
 class TreeDesc(C.Structure):
@@ -140,9 +140,9 @@ def check(code: int):
 
 
 def make_config(n1=31, n2=5, period_T=60.0, storage="f32", idft_mode="auto", device=0,
-                traverse_threads=0, refill_min=0, inner_steps=0, table="auto"):
+                traverse_threads=0, refill_min=0, inner_steps=0, table="auto", max_steps=0):
     return Config(n1, n2, 2, float(period_T), STORAGE[storage], IDFT[idft_mode], device,
-                  traverse_threads, refill_min, inner_steps, TABLE[table])
+                  traverse_threads, refill_min, inner_steps, TABLE[table], max_steps)
 
 
 def make_tree_desc(leaf_depth, leaf_xyz, coeffs, max_depth, aabb_min=(0.0, 0.0, 0.0),
@@ -177,11 +177,11 @@ class Renderer:
     """One fpo_ctx: a tree resident on one GPU, rendered frame by frame."""
 
     def __init__(self, n1=31, n2=5, period_T=60.0, storage="f32", idft_mode="auto", device=0,
-                 traverse_threads=0, refill_min=0, inner_steps=0, table="auto"):
+                 traverse_threads=0, refill_min=0, inner_steps=0, table="auto", max_steps=0):
         """table: precision of the per-frame table ("auto": FP32 with FP32
         storage, FP16 with the reduced-precision and latent storages)."""
         self.cfg = make_config(n1, n2, period_T, storage, idft_mode, device, traverse_threads,
-                               refill_min, inner_steps, table)
+                               refill_min, inner_steps, table, max_steps)
         self.device = device
         self.n1, self.n2 = n1, n2
         h = C.c_void_p()

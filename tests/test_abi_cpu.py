@@ -119,6 +119,10 @@ def test_null_and_config_errors_without_gpu(L):
         cfg = fpo.make_config()
         cfg.table_precision = tp
         assert L.fpo_create(C.byref(h), C.byref(cfg)) == -1
+    cfg = fpo.make_config()
+    cfg.max_steps = -1
+    assert L.fpo_create(C.byref(h), C.byref(cfg)) == -1
+    assert "max_steps" in L.fpo_last_error().decode()
     assert L.fpo_render(None, None, None, None, None) == -1
     assert L.fpo_status_sync(None, None) == -1
     assert L.fpo_upload_tree(None, None) == -1

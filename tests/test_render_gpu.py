@@ -292,3 +292,33 @@ def test_table_reuse_for_views_of_one_frame_time():
     finally:
         r.close()
         fresh.close()
+
+
+@pytest.mark.parametrize("mode", ["materialise", "fused"])
+def test_step_cap_is_reported_and_the_context_stays_usable(mode):
+    # device-side failure path without a fault: a cap of 4 steps stops the
+    # long rays, the call reports FPO_ERR_TRAVERSAL_LIMIT through the status
+    # word, and the same context then renders normally again
+    tree = synth.shell_tree()
+    cam = synth.shell_camera(64, 64)
+    capped = fpo.Renderer(idft_mode=mode, max_steps=4)
+    normal = fpo.Renderer(idft_mode=mode)
+    try:
+        capped.upload(tree)
+        normal.upload(tree)
+        capped.render(camera=cam, t=3.0)
+        with pytest.raises(fpo.FPOError) as e:
+            capped.status()
+        assert e.value.code == -6
+        capped.status()  # the status word was cleared
+        ref = normal.render(camera=cam, t=3.0)["rgb"].clone()
+        normal.status()
+        # rays that needed at most 4 steps are complete and equal
+        out = capped.render(camera=cam, t=3.0)["rgb"]
+        with pytest.raises(fpo.FPOError):
+            capped.status()
+        same = (out == ref).all(dim=1)
+        assert 0 < int(same.sum()) < same.numel()
+    finally:
+        capped.close()
+        normal.close()

@@ -79,3 +79,19 @@ def test_noalloc_refuses_trees_above_its_limit():
         assert "at most 65536" in fpo.lib().fpo_last_error().decode()
     finally:
         r.close()
+
+
+def test_noalloc_honours_the_step_cap():
+    tree = synth.shell_tree()
+    cam = synth.shell_camera(64, 64)
+    r = fpo.Renderer(idft_mode="materialise", max_steps=4)
+    try:
+        r.upload(tree)
+        out = torch.empty((cam.width * cam.height, 3), device="cuda")
+        assert _noalloc(r, cam, 3.0, out) == fpo.FPO_OK
+        with pytest.raises(fpo.FPOError) as e:
+            r.status()
+        assert e.value.code == -6
+        r.status()
+    finally:
+        r.close()
