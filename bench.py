@@ -84,6 +84,31 @@ def mrays_per_s(world: int, steps: int, rays_per_frame: int, elapsed_ms: float) 
     return world * steps * rays_per_frame / (elapsed_ms * 1e-3) / 1e6
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (context for the measured peak)
+NODE_BYTES = 32
+
+
+def frame_roofline(frame_ms: float, n_leaves: int, n_vis: float, s_leaf: int, table_bytes: int,
+                   n_nodes: int, n_px: int, peak: float) -> dict:
+    """Whole-frame roofline on the bytes the method must move per frame.
+
+    visited: every distinct leaf reached before early stop read once (its
+    stored record), the nodes on the way (counted as all nodes, an upper
+    bound under 1% of the total) and the output.  materialised: the per-frame
+    IDFT pass reads every record and writes every table row, the traversal
+    reads the visited rows.  The smaller of the two is the method's minimum.
+    """
+    out = n_px * OUT_BYTES_PER_RAY
+    nodes = n_nodes * NODE_BYTES
+    b_vis = n_vis * s_leaf + nodes + out
+    b_mat = n_leaves * (s_leaf + table_bytes) + n_vis * table_bytes + nodes + out
+    b_min = min(b_vis, b_mat)
+    achieved = b_min / (frame_ms * 1e-3) / 1e9
+    return {"bytes_visited": b_vis, "bytes_materialised": b_mat, "bytes_min": b_min,
+            "frame_ms": frame_ms, "achieved": achieved, "unit": "GB/s", "peak": peak,
+            "frac": achieved / peak, "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
+
+
 # ---------------------------------------------------------------------------
 # oracle timing (CPU baseline and the reference arm)
 
@@ -245,7 +270,7 @@ def sampled_psnr(r, ot, coeffs, cams, frames, out, torch, n_px):
     return 10 * np.log10(1.0 / mse) if mse > 0 else float("inf")
 
 
-def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms):
+def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, peak):
     """BF16 storage on the same tree, and the latent decoder (trained on
     coefficients produced by the generation: smooth animated fields -> per-
     leaf DFT) against the plain FP32 renderer of those coefficients."""
@@ -261,6 +286,9 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms):
     res["bf16"] = {"Mrays_s": n_px / ms / 1e3, "fps": 1e3 / ms, "fp32_Mrays_s": n_px / fp32_ms / 1e3,
                    "psnr_db_vs_fp64_oracle": sampled_psnr(r, ot, tree.coeffs, cams, nf[:2], out, torch, n_px),
                    "bytes_per_leaf": r.info()["leaf_record_bytes"]}
+    # the FP16 table of reduced-precision storage: 28 values x 2 B per leaf
+    res["bf16"]["frame_roofline"] = frame_roofline(ms, tree.n_leaves, n_vis, STORED_PER_LEAF["bf16"],
+                                                   2 * TABLE_VALUES_PER_LEAF, r.info()["n_nodes"], n_px, peak)
     r.close()
     # multi-view rendering of one frame time: the 16 ring views of each t share
     # one IDFT pass (FPO_FLAG_REUSE_TABLE)
@@ -579,6 +607,9 @@ def main():
                        "launch_ms": ms}
     res["kernels_ms"] = {k: v[0] for k, v in kernels.items()}
     res["visited_leaves_per_frame"] = mean_vis
+    res["frame_roofline"] = frame_roofline(statistics.median(frame_ms), tree.n_leaves, mean_vis,
+                                           STORED_PER_LEAF[args.storage], table_bytes, info["n_nodes"],
+                                           n_px, peak)
     res["e2e"] = {"value": mrays_per_s(world, K, n_px, 1e3 * max_over_ranks(e2e_s, pg, "cuda")),
                   "unit": "Mrays/s",
                   "h2d_bytes_per_step": int(fpo.C.sizeof(fpo.Rays) + fpo.C.sizeof(fpo.FrameOpts)),
@@ -606,7 +637,8 @@ def main():
                               "frame_ms": {"p10": float(np.percentile(ms8, 10)), "p50": statistics.median(ms8),
                                            "p90": float(np.percentile(ms8, 90))}}
     if not args.no_variants and args.storage == "f32" and args.idft == "auto":
-        res["variants"] = variants(args, tree, cams, frames[W:], out, torch, fpo, n_px, t_max / K)
+        res["variants"] = variants(args, tree, cams, frames[W:], out, torch, fpo, n_px, t_max / K,
+                                   mean_vis, peak)
     if rank == 0 and not args.no_cpu_baseline:
         v, rays, secs, thr = oracle_sample_rate(tree, cams, frames[W:], args.cpu_seconds)
         res["cpu_baseline"] = {"value": v, "unit": "Mrays/s", "cores": thr, "kind": "oracle",

@@ -61,3 +61,20 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["unit"] == "Mrays/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["higher_is_better"] is True
+
+
+def test_frame_roofline_bytes():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    # 10 leaves of 664 B, 4 visited, 128 B table rows, 3 nodes, 5 rays, 1 ms
+    fr = bench.frame_roofline(1.0, 10, 4, 664, 128, 3, 5, 1000.0)
+    assert fr["bytes_visited"] == 4 * 664 + 3 * 32 + 5 * 12
+    assert fr["bytes_materialised"] == 10 * (664 + 128) + 4 * 128 + 3 * 32 + 5 * 12
+    assert fr["bytes_min"] == fr["bytes_visited"]
+    assert abs(fr["achieved"] - fr["bytes_min"] / 1e-3 / 1e9) < 1e-12
+    assert abs(fr["frac"] - fr["achieved"] / 1000.0) < 1e-12
+    # distinct visited leaves never outnumber the leaves, so the visited count
+    # is the minimum even when every leaf is reached
+    fr = bench.frame_roofline(1.0, 10, 10, 664, 128, 0, 0, 1000.0)
+    assert fr["bytes_min"] == fr["bytes_visited"] == 6640
