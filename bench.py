@@ -5,7 +5,10 @@ Workload: the depth-9 union octree of the animated 14-capsule body (about
 1920x1080 from the 16 ring cameras at integer frame times: by default the
 960 timed frames are each (camera, t) of the 16 x 60 grid once, in a seeded
 order.  The tree (2.4 GB of coefficient records) is larger
-than L2, so no flush is needed between frames.
+than L2, so no flush is needed between frames.  The timed region renders the
+frames through fpo_render_frames, 32 frames a call (the IDFT pass of frame
+k + 1 overlaps the traversal of frame k); a single-frame pass beforehand
+times each kernel on its own.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
 oracle instead, on a bounded sample of pixels per step.
@@ -51,6 +54,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the BF16 and latent-decoder variant measurements")
     ap.add_argument("--variant-frames", type=int, default=100)
+    ap.add_argument("--frames-per-call", type=int, default=32,
+                    help="frames per fpo_render_frames call in the timed region (1: fpo_render per frame)")
     ap.add_argument("--latent-steps", type=int, default=20000)
     ap.add_argument("--finetune-steps", type=int, default=200)
     return ap.parse_args()
@@ -238,15 +243,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def time_frames(r, cams, frames, out, torch):
-    """Mean CUDA-event time (ms) of rendering `frames` (after 3 warm-up frames)."""
-    for k, t in frames[:3]:
-        r.render(camera=cams[k], t=t, out=out)
+def time_frames(r, cams, frames, out, torch, per_call=1):
+    """Mean CUDA-event time (ms) per frame of rendering `frames` (after
+    warm-up): fpo_render_frames calls of `per_call` frames, or one fpo_render
+    call per frame when per_call is 1."""
+    outb = torch.empty((per_call, out.shape[0], 3), dtype=torch.float32, device=out.device) if per_call > 1 else None
+
+    def run(fr):
+        if per_call <= 1:
+            for k, t in fr:
+                r.render(camera=cams[k], t=t, out=out)
+            return
+        for i in range(0, len(fr), per_call):
+            b = fr[i:i + per_call]
+            r.render_frames([cams[k] for k, _ in b], [t for _, t in b], out=outb[:len(b)])
+
+    run(frames[:max(3, min(per_call, len(frames)))])
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    for k, t in frames:
-        r.render(camera=cams[k], t=t, out=out)
+    run(frames)
     b.record()
     torch.cuda.synchronize()
     r.status()
@@ -282,8 +298,11 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
     ot = oracle.OracleTree(tree.leaf_depth, tree.leaf_xyz, tree.max_depth)
     r = fpo.Renderer(storage="bf16")
     r.upload(tree)
-    ms = time_frames(r, cams, nf, out, torch)
+    B = args.frames_per_call
+    ms = time_frames(r, cams, nf, out, torch, B)
+    ms1 = time_frames(r, cams, nf, out, torch)
     res["bf16"] = {"Mrays_s": n_px / ms / 1e3, "fps": 1e3 / ms, "fp32_Mrays_s": n_px / fp32_ms / 1e3,
+                   "single_frame_Mrays_s": n_px / ms1 / 1e3,
                    "psnr_db_vs_fp64_oracle": sampled_psnr(r, ot, tree.coeffs, cams, nf[:2], out, torch, n_px),
                    "bytes_per_leaf": r.info()["leaf_record_bytes"]}
     # the FP16 table of reduced-precision storage: 28 values x 2 B per leaf
@@ -336,7 +355,7 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
     gen = synth.Tree(tree.leaf_depth, tree.leaf_xyz, co_np, tree.max_depth)
     r = fpo.Renderer()
     r.upload(gen)
-    ms32 = time_frames(r, cams, nf, out, torch)
+    ms32 = time_frames(r, cams, nf, out, torch, B)
     r.close()
     m = LatentModel(n, seed=0)
     m.init_output_bias(coeffs)
@@ -350,12 +369,14 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
     r.upload(synth.Tree(tree.leaf_depth, tree.leaf_xyz, np.zeros((0, 166), np.float32), tree.max_depth))
     r.set_latents(*m.inference_arrays())
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    msl = time_frames(r, cams, nf, out, torch)
+    msl = time_frames(r, cams, nf, out, torch, B)
+    msl1 = time_frames(r, cams, nf, out, torch)
     k, t = nf[0]
     r.render(camera=cams[k], t=t, out=out, events=ev)
     torch.cuda.synchronize()
     res["latent"] = {
         "Mrays_s": n_px / msl / 1e3, "fps": 1e3 / msl, "fp32_same_tree_Mrays_s": n_px / ms32 / 1e3,
+        "single_frame_Mrays_s": n_px / msl1 / 1e3,
         "psnr_db_vs_fp64_oracle": sampled_psnr(r, ot, co_np, cams, nf[:2], out, torch, n_px),
         "decode_ms": ev[0].elapsed_time(ev[1]), "train_steps": args.latent_steps, "train_batch": 65536,
         "train_s": train_s, "train_loss": hist, "bytes_per_leaf": 64,
@@ -500,15 +521,38 @@ def main():
     stream = torch.cuda.current_stream()
     mat = args.idft in ("auto", "materialise")
 
-    # warm-up
+    B = max(1, args.frames_per_call)
+    timed = frames[W:]
+    batches = [timed[i:i + B] for i in range(0, K, B)]
+    outb = torch.empty((min(B, K), n_px, 3), dtype=torch.float32, device="cuda")
+
+    def render_batch(bt, dst):
+        r.render_frames([cams[k] for k, _ in bt], [t for _, t in bt], out=dst[:len(bt)])
+
+    # warm-up: single-frame calls, then pipelined calls (allocates the second table)
     for k, t in frames[:W]:
         r.render(camera=cams[k], t=t, out=out)
+    for i in range(0, W, B):
+        render_batch(frames[i:min(i + B, W)], outb)
     r.status()
 
+    # single-frame calls with events around each kernel: the launch durations
+    # of the IDFT pass and the traversal (the pipelined calls overlap them)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     for e3 in ev:
         for e in e3:
             e.record(stream)
+    torch.cuda.synchronize()
+    for i, (k, t) in enumerate(timed):
+        r.render(camera=cams[k], t=t, out=out, events=ev[i])
+    torch.cuda.synchronize()
+    r.status()
+    frame_ms = [ev[i][0].elapsed_time(ev[i][2]) for i in range(K)]
+    mat_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]
+    trav_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
+
+    # timed region: the K frames through fpo_render_frames, B frames a call
+    bev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in batches]
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
@@ -517,8 +561,10 @@ def main():
     with ClockSampler(local) as clk:
         torch.cuda.nvtx.range_push("timed")
         start.record(stream)
-        for i, (k, t) in enumerate(frames[W:]):
-            r.render(camera=cams[k], t=t, out=out, events=ev[i])
+        for j, bt in enumerate(batches):
+            bev[j][0].record(stream)
+            render_batch(bt, outb)
+            bev[j][1].record(stream)
         stop.record(stream)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
@@ -527,39 +573,38 @@ def main():
     r.status()
     elapsed_ms = start.elapsed_time(stop)
     t_max = max_over_ranks(elapsed_ms, pg, "cuda")
-    frame_ms = [ev[i][0].elapsed_time(ev[i][2]) for i in range(K)]
-    mat_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]
-    trav_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(K)]
+    batch_frame_ms = [bev[j][0].elapsed_time(bev[j][1]) / len(bt) for j, bt in enumerate(batches)]
 
     # visited leaves per timed frame (a marking pass outside the timed region)
     mark = torch.zeros(tree.n_leaves, dtype=torch.uint8, device="cuda")
     n_vis = []
-    for k, t in frames[W:]:
+    for k, t in timed:
         mark.zero_()
         r.render(camera=cams[k], t=t, out=out, leaf_mark=mark)
         n_vis.append(int(mark.sum().item()))
     r.status()
 
-    # end to end through the public API: every frame is read back into pinned host
-    # memory inside the timed region.  Frame i's read-back runs on a copy stream
-    # while frame i + 1 renders (two device and two host buffers); before frame
-    # i + 2 reuses a buffer pair the host waits until frame i is in host memory.
-    outs = [out, torch.empty_like(out)]
-    hosts = [torch.empty((n_px, 3), dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    # end to end through the public API: every frame is read back into pinned
+    # host memory inside the timed region.  Batch j's read-back runs on a copy
+    # stream while batch j + 1 renders (two device and two host buffers);
+    # before batch j + 2 reuses a buffer pair the host waits until batch j is
+    # in host memory.
+    outs = [outb, torch.empty_like(outb)]
+    hosts = [torch.empty(outb.shape, dtype=torch.float32, pin_memory=True) for _ in range(2)]
     copy_stream = torch.cuda.Stream()
     done = [torch.cuda.Event(), torch.cuda.Event()]
     landed = [torch.cuda.Event(), torch.cuda.Event()]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for i, (k, t) in enumerate(frames[W:]):
-        b = i & 1
-        if i >= 2:
+    for j, bt in enumerate(batches):
+        b = j & 1
+        if j >= 2:
             landed[b].synchronize()
-        r.render(camera=cams[k], t=t, out=outs[b])
+        render_batch(bt, outs[b])
         done[b].record(stream)
         copy_stream.wait_event(done[b])
         with torch.cuda.stream(copy_stream):
-            hosts[b].copy_(outs[b], non_blocking=True)
+            hosts[b][:len(bt)].copy_(outs[b][:len(bt)], non_blocking=True)
             landed[b].record(copy_stream)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -573,9 +618,17 @@ def main():
         "config": workload_config(tree, args, "materialise" if mat else "fused"),
     }
     res["config"]["storage"] = args.storage
-    res["fps"] = 1e3 / statistics.median(frame_ms)
-    res["frame_ms"] = {"p10": float(np.percentile(frame_ms, 10)), "p50": statistics.median(frame_ms),
-                       "p90": float(np.percentile(frame_ms, 90))}
+    res["config"]["frames_per_call"] = B
+    res["fps"] = 1e3 * K / t_max
+    res["frame_ms"] = {"p10": float(np.percentile(batch_frame_ms, 10)), "p50": statistics.median(batch_frame_ms),
+                       "p90": float(np.percentile(batch_frame_ms, 90)),
+                       "over": f"{len(batches)} calls of fpo_render_frames (time per call / frames per call)"}
+    res["single_frame"] = {"Mrays_s": n_px / statistics.median(frame_ms) / 1e3,
+                           "fps": 1e3 / statistics.median(frame_ms),
+                           "frame_ms": {"p10": float(np.percentile(frame_ms, 10)),
+                                        "p50": statistics.median(frame_ms),
+                                        "p90": float(np.percentile(frame_ms, 90))},
+                           "over": f"{K} fpo_render calls, events from the IDFT pass to the traversal's end"}
     # roofline of the dominant kernel
     avg_mat = statistics.mean(mat_ms) if mat else 0.0
     avg_trav = statistics.mean(trav_ms)
@@ -604,12 +657,16 @@ def main():
     res["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                        "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                        "traffic": ncu_traffic(dom), "alg_bytes_per_launch": nbytes,
-                       "launch_ms": ms}
+                       "launch_ms": ms,
+                       "launches": "single-frame fpo_render calls (the pipelined calls overlap the two kernels)"}
     res["kernels_ms"] = {k: v[0] for k, v in kernels.items()}
     res["visited_leaves_per_frame"] = mean_vis
-    res["frame_roofline"] = frame_roofline(statistics.median(frame_ms), tree.n_leaves, mean_vis,
+    res["frame_roofline"] = frame_roofline(t_max / K, tree.n_leaves, mean_vis,
                                            STORED_PER_LEAF[args.storage], table_bytes, info["n_nodes"],
                                            n_px, peak)
+    res["single_frame"]["frame_roofline_frac"] = frame_roofline(
+        statistics.median(frame_ms), tree.n_leaves, mean_vis, STORED_PER_LEAF[args.storage], table_bytes,
+        info["n_nodes"], n_px, peak)["frac"]
     res["e2e"] = {"value": mrays_per_s(world, K, n_px, 1e3 * max_over_ranks(e2e_s, pg, "cuda")),
                   "unit": "Mrays/s",
                   "h2d_bytes_per_step": int(fpo.C.sizeof(fpo.Rays) + fpo.C.sizeof(fpo.FrameOpts)),

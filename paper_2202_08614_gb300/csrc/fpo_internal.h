@@ -133,6 +133,7 @@ struct TraverseParams {
     uint32_t inner_steps;     // steps a lane takes between two refill checks
     int block_threads;        // 128 or 256
     int max_ctas_per_sm;      // 0: as many as fit
+    int carveout;             // preferred shared-memory carveout in percent (0: the driver's default)
     unsigned long long *stats; // FPO_FLAG_STATS: [steps, leaf visits, rays entering the tree]
 };
 
@@ -146,7 +147,9 @@ struct MaterialiseParams {
     int storage;              // FPO_STORAGE_*
     int n1, n2, sig_stride, z_stride;  // strides in elements
     int stages;               // shared-memory pipeline depth (materialise_stages)
+    int generic_form;         // 1: the warp-cooperative form even where the thread-per-leaf form applies
     int max_ctas_per_sm;      // 0: as many as fit
+    int carveout;             // preferred shared-memory carveout in percent (0: the driver's default)
     double t, period_T;
     uint32_t *status;
 };
@@ -236,6 +239,9 @@ struct LeafAdamParams {
 // Launchers (return cudaError_t as int).
 int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream);
 int materialise_stages(int storage, int n1, int n2);
+// Stages of the warp-cooperative form that fit in `budget` bytes (at least 2).
+int materialise_generic_stages(int storage, int n1, int n2, int budget);
+int materialise_smem_bytes(const MaterialiseParams &p);  // dynamic shared memory of one CTA
 int launch_backward(const BackwardParams &q, int sm_count, void *stream);
 int launch_dft(const float *values, float *coeffs, uint32_t n_leaves, int n1, int n2, int T, int sm_count,
                void *stream);

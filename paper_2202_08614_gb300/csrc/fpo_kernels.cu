@@ -459,6 +459,23 @@ int materialise_stages(int storage, int n1, int n2)
     return s;
 }
 
+int materialise_generic_stages(int storage, int n1, int n2, int budget)
+{
+    const RecordLayout L = record_layout(storage, n1, n2);
+    const int stage = MAT_CHUNK * (L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
+    int s = budget / stage;
+    if (s > MAT_MAX_STAGES) s = MAT_MAX_STAGES;
+    if (s < 2) s = 2;
+    return s;
+}
+
+int materialise_smem_bytes(const MaterialiseParams &p)
+{
+    const RecordLayout L = record_layout(p.storage, p.n1, p.n2);
+    const int chunk = !p.generic_form && leaf_form(p.storage, p.n1, p.n2) ? ML_CHUNK : MAT_CHUNK;
+    return p.stages * chunk * (L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
+}
+
 template <int N2>
 static void *pick_materialise(int storage)
 {
@@ -475,10 +492,9 @@ int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream)
     if (p.n_leaves == 0) return (int)cudaSuccess;
     if (p.storage < FPO_STORAGE_F32 || p.storage > FPO_STORAGE_FP8_E4M3 || !p.sig || !p.zc)
         return (int)cudaErrorInvalidValue;  // no coefficient records (e.g. LATENT storage)
-    const RecordLayout L = record_layout(p.storage, p.n1, p.n2);
-    const bool lf = leaf_form(p.storage, p.n1, p.n2);
+    const bool lf = !p.generic_form && leaf_form(p.storage, p.n1, p.n2);
     const int chunk = lf ? ML_CHUNK : MAT_CHUNK;
-    const int smem = p.stages * chunk * (L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
+    const int smem = materialise_smem_bytes(p);
     const void *kern;
     if (lf)
         kern = p.storage == FPO_STORAGE_BF16 ? (const void *)materialise_leaf_kernel<FPO_STORAGE_BF16>
@@ -488,6 +504,9 @@ int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream)
         kern = p.n2 == 5 ? pick_materialise<5>(p.storage)
                          : (p.n2 == 11 ? pick_materialise<11>(p.storage) : pick_materialise<0>(p.storage));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 p.carveout > 0 ? p.carveout : (int)cudaSharedmemCarveoutDefault);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, lf ? ML_THREADS : MAT_THREADS, smem);
@@ -1169,6 +1188,9 @@ static int launch_t(const TraverseParams &p, int sm_count, cudaStream_t s)
     const int smem = traverse_smem_bytes(p.n_smem_nodes, prt, threads);
     auto k = traverse_kernel<TM, DBG, N1, N2, COMPACT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 p.carveout > 0 ? p.carveout : (int)cudaSharedmemCarveoutDefault);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
@@ -1399,6 +1421,9 @@ static int launch_b(const BackwardParams &q, int sm_count, cudaStream_t s)
     const int smem = traverse_smem_bytes(p.n_smem_nodes, prt, threads);
     auto k = backward_kernel<N1, N2>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 p.carveout > 0 ? p.carveout : (int)cudaSharedmemCarveoutDefault);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);

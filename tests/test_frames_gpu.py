@@ -1,8 +1,9 @@
 """Pipelined multi-frame rendering (fpo_render_frames): the IDFT table of
-frame k+1 is computed on a second stream while frame k is traversed.  The
-images must equal, bit for bit, those of one fpo_render call per frame (same
-kernels, same per-leaf and per-ray arithmetic), and one of them is checked
-against the FP64 oracle."""
+frame k+1 is computed on a second stream while frame k is traversed, both
+kernels resident on every SM with their own launch shapes (the warp-
+cooperative form of the IDFT pass for every storage).  The images must equal,
+bit for bit, those of one fpo_render call per frame (same per-leaf and per-ray
+arithmetic), and one of them is checked against the FP64 oracle."""
 
 import numpy as np
 import pytest
@@ -29,7 +30,7 @@ def _per_frame(r, cams, times):
     return torch.stack([r.render(camera=c, t=t)["rgb"].clone() for c, t in zip(cams, times)])
 
 
-@pytest.mark.parametrize("storage", ["f32", "fp8"])
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16", "fp8"])
 @pytest.mark.parametrize("n_frames", [1, 2, 7])
 def test_frames_equal_single_renders(storage, n_frames):
     tree = synth.random_tree(11, max_depth=7, p_split=0.6, p_empty=0.3)
