@@ -59,13 +59,14 @@ void dfree(T *&p)
 // Launch shapes of the frame pipeline (fpo_render_frames).  The traversal of
 // frame k and the IDFT pass of frame k + 1 share every SM: two 384-thread
 // traversal CTAs (64 registers a thread) leave a quarter of the register file
-// to two 256-thread IDFT CTAs of the warp-cooperative form, whose stage ring
-// is capped so that the four CTAs' shared memory fits one carveout.
+// to the IDFT pass (materialise_pipeline_shape: one 128-thread CTA of the
+// thread-per-leaf form, or two 256-thread CTAs of the warp-cooperative form),
+// whose stage rings are capped so that all CTAs' shared memory fits one
+// carveout.
 constexpr int PIPE_TRAV_THREADS = 384;
 constexpr int PIPE_TRAV_CTAS = 2;
-constexpr int PIPE_MAT_CTAS = 2;
-constexpr int PIPE_MAT_STAGE_BUDGET = 44 * 1024;  // bytes of coefficient records in flight per IDFT CTA
-constexpr int PIPE_STATIC_SMEM = 512;             // allowance for each kernel's static shared memory
+constexpr int PIPE_MAT_SMEM_BUDGET = 88 * 1024;  // bytes of coefficient records in flight per SM
+constexpr int PIPE_STATIC_SMEM = 512;            // allowance for each kernel's static shared memory
 #ifndef FPO_SMEM_NODES
 #define FPO_SMEM_NODES 512
 #endif
@@ -410,10 +411,10 @@ static TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, 
 // The per-frame table for time t into `table` on stream s: the tensor-core
 // decoder for LATENT storage, else the bulk-copy IDFT pass over the stored
 // coefficients (at most max_ctas_per_sm CTAs per SM when > 0).
-// With generic_stages > 0 the pass takes the warp-cooperative form with that
-// many stages (the shape the frame pipeline co-schedules with the traversal).
+// With pipe_stages > 0 the pass takes the frame-pipeline shape with that many
+// stages (materialise_pipeline_shape), co-scheduled with the traversal.
 static int launch_table_pass(fpo_ctx *ctx, double t, float *table, int max_ctas_per_sm, cudaStream_t s,
-                             int generic_stages = 0, int carveout = 0)
+                             int pipe_stages = 0, int carveout = 0)
 {
     if (ctx->cfg.storage == FPO_STORAGE_LATENT) {
         LatentParams lp{};
@@ -446,8 +447,8 @@ static int launch_table_pass(fpo_ctx *ctx, double t, float *table, int max_ctas_
     mp.n2 = ctx->cfg.n2;
     mp.sig_stride = L.sig_elems;
     mp.z_stride = L.z_elems;
-    mp.stages = generic_stages > 0 ? generic_stages : materialise_stages(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2);
-    mp.generic_form = generic_stages > 0;
+    mp.stages = pipe_stages > 0 ? pipe_stages : materialise_stages(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2);
+    mp.pipeline = pipe_stages > 0;
     mp.max_ctas_per_sm = max_ctas_per_sm;
     mp.carveout = carveout;
     mp.half_table = ctx->half_table;
@@ -576,20 +577,16 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
     // Shapes that let both kernels be resident on an SM at once; the decoder
     // of LATENT storage needs a whole SM, so its frames keep the default shapes.
     bool overlap = ctx->cfg.storage != FPO_STORAGE_LATENT;
-    int mat_stages = 0, carveout = 0;
+    MatShape mshape{};
+    int carveout = 0;
     if (overlap) {
         int max_smem = 0, reserved = 0;
         if ((e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->cfg.device)) != cudaSuccess ||
             (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, ctx->cfg.device)) != cudaSuccess)
             return cuda_fail(e, "cudaDeviceGetAttribute");
-        MaterialiseParams probe{};
-        probe.storage = ctx->cfg.storage;
-        probe.n1 = ctx->cfg.n1;
-        probe.n2 = ctx->cfg.n2;
-        probe.generic_form = 1;
-        probe.stages = mat_stages = materialise_generic_stages(probe.storage, probe.n1, probe.n2, PIPE_MAT_STAGE_BUDGET);
+        mshape = materialise_pipeline_shape(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2, PIPE_MAT_SMEM_BUDGET);
         const long need = (long)PIPE_TRAV_CTAS * (traverse_smem_bytes(ctx->n_smem_nodes, false, PIPE_TRAV_THREADS) + PIPE_STATIC_SMEM + reserved) +
-                          (long)PIPE_MAT_CTAS * (materialise_smem_bytes(probe) + PIPE_STATIC_SMEM + reserved);
+                          (long)mshape.ctas_per_sm * (mshape.smem_per_cta + PIPE_STATIC_SMEM + reserved);
         carveout = max_smem > 0 ? (int)((need * 100 + max_smem - 1) / max_smem) : 101;
         if (carveout > 100) overlap = false;
     }
@@ -603,7 +600,7 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
         const int b = (int)(k & 1);
         float *tbl = b ? ctx->d_table2 : ctx->d_table;
         if (k >= 2 && (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_trav[b], 0)) != cudaSuccess) return cuda_fail(e, "wait");
-        int ce = overlap ? launch_table_pass(ctx, frames[k].t, tbl, PIPE_MAT_CTAS, ctx->aux, mat_stages, carveout)
+        int ce = overlap ? launch_table_pass(ctx, frames[k].t, tbl, mshape.ctas_per_sm, ctx->aux, mshape.stages, carveout)
                          : launch_table_pass(ctx, frames[k].t, tbl, 0, ctx->aux);
         if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "IDFT table launch");
         if ((e = cudaEventRecord(ctx->ev_mat[b], ctx->aux)) != cudaSuccess ||

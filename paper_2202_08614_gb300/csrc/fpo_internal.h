@@ -147,7 +147,7 @@ struct MaterialiseParams {
     int storage;              // FPO_STORAGE_*
     int n1, n2, sig_stride, z_stride;  // strides in elements
     int stages;               // shared-memory pipeline depth (materialise_stages)
-    int generic_form;         // 1: the warp-cooperative form even where the thread-per-leaf form applies
+    int pipeline;             // 1: the frame-pipeline shape (materialise_pipeline_shape)
     int max_ctas_per_sm;      // 0: as many as fit
     int carveout;             // preferred shared-memory carveout in percent (0: the driver's default)
     double t, period_T;
@@ -239,8 +239,13 @@ struct LeafAdamParams {
 // Launchers (return cudaError_t as int).
 int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream);
 int materialise_stages(int storage, int n1, int n2);
-// Stages of the warp-cooperative form that fit in `budget` bytes (at least 2).
-int materialise_generic_stages(int storage, int n1, int n2, int budget);
+// Shape of the IDFT pass when it shares each SM with the traversal (frame
+// pipeline): CTAs per SM and stages such that the CTAs of one SM hold at most
+// smem_budget bytes of records; smem_per_cta is the dynamic shared memory.
+struct MatShape {
+    int ctas_per_sm, stages, smem_per_cta;
+};
+MatShape materialise_pipeline_shape(int storage, int n1, int n2, int smem_budget);
 int materialise_smem_bytes(const MaterialiseParams &p);  // dynamic shared memory of one CTA
 int launch_backward(const BackwardParams &q, int sm_count, void *stream);
 int launch_dft(const float *values, float *coeffs, uint32_t n_leaves, int n1, int n2, int T, int sm_count,

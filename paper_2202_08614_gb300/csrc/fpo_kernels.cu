@@ -264,7 +264,9 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
 // products summed in the same tree order as the warp's butterfly and each z
 // accumulated in the same order as above, so both kernels give the same
 // bits; the row is written with 16-byte stores.
-constexpr int ML_THREADS = 256, ML_CHUNK = 256, ML_N2 = 5;
+// One CTA per SM with 256-leaf stages on its own; 128-leaf stages when it
+// shares the SM with the traversal (frame pipeline).
+constexpr int ML_CHUNK = 256, ML_CHUNK_PIPE = 128, ML_N2 = 5;
 
 // The 16 bytes of w as FP32 values (8 for 16-bit storage, 16 for FP8).
 template <int ST>
@@ -293,8 +295,8 @@ __device__ __forceinline__ void unpack16(const uint4 w, float *v)
     }
 }
 
-template <int ST>
-__global__ void __launch_bounds__(ML_THREADS) materialise_leaf_kernel(const __grid_constant__ MaterialiseParams p)
+template <int ST, int CH>
+__global__ void __launch_bounds__(CH) materialise_leaf_kernel(const __grid_constant__ MaterialiseParams p)
 {
     extern __shared__ __align__(128) unsigned char mat_smem[];
     __shared__ uint64_t bars[MAT_MAX_STAGES];
@@ -308,9 +310,9 @@ __global__ void __launch_bounds__(ML_THREADS) materialise_leaf_kernel(const __gr
     constexpr int SIG_ELEMS = 32;                  // n1 <= 32, padded to 16 bytes
     constexpr int Z_ELEMS = (27 * ML_N2 + PER - 1) / PER * PER;
     const uint32_t rec_sig = SIG_ELEMS * EB, rec_z = Z_ELEMS * EB;
-    const uint32_t sig_bytes = ML_CHUNK * rec_sig, z_bytes = ML_CHUNK * rec_z;
-    const uint32_t stage_bytes = sig_bytes + z_bytes + (SCALED ? ML_CHUNK * 4u : 0u);
-    const uint32_t n_chunks = (p.n_leaves + ML_CHUNK - 1) / ML_CHUNK;
+    const uint32_t sig_bytes = CH * rec_sig, z_bytes = CH * rec_z;
+    const uint32_t stage_bytes = sig_bytes + z_bytes + (SCALED ? CH * 4u : 0u);
+    const uint32_t n_chunks = (p.n_leaves + CH - 1) / CH;
     const int nb = p.n1 > ML_N2 ? p.n1 : ML_N2;
     if (tid < MAX_BASIS) s_b[tid] = tid < nb ? basis_fp64(tid, p.t, p.period_T) : 0.0f;
     if (tid == 0) {
@@ -320,8 +322,8 @@ __global__ void __launch_bounds__(ML_THREADS) materialise_leaf_kernel(const __gr
     }
     __syncthreads();
     auto issue = [&](uint32_t c, int s) {
-        const uint32_t first = c * ML_CHUNK;
-        const uint32_t m = min((uint32_t)ML_CHUNK, p.n_leaves - first);
+        const uint32_t first = c * CH;
+        const uint32_t m = min((uint32_t)CH, p.n_leaves - first);
         unsigned char *dst = mat_smem + (size_t)s * stage_bytes;
         const uint32_t bsc = SCALED ? ((m + 3u) & ~3u) * 4u : 0u;
         ptx::mbar_arrive_expect_tx(&bars[s], m * rec_sig + m * rec_z + bsc);
@@ -349,8 +351,8 @@ __global__ void __launch_bounds__(ML_THREADS) materialise_leaf_kernel(const __gr
         if (!ptx::mbar_wait_bounded(&bars[s], parity, WAIT_LIMIT_NS)) s_fail = 1;
         __syncthreads();
         if (s_fail) break;
-        const uint32_t first = c * ML_CHUNK;
-        const int m = (int)min((uint32_t)ML_CHUNK, p.n_leaves - first);
+        const uint32_t first = c * CH;
+        const int m = (int)min((uint32_t)CH, p.n_leaves - first);
         const unsigned char *stage = mat_smem + (size_t)s * stage_bytes;
         if (tid < m) {
             const uint4 *sg = reinterpret_cast<const uint4 *>(stage + tid * rec_sig);
@@ -459,21 +461,56 @@ int materialise_stages(int storage, int n1, int n2)
     return s;
 }
 
-int materialise_generic_stages(int storage, int n1, int n2, int budget)
+static int record_bytes(int storage, int n1, int n2)
 {
     const RecordLayout L = record_layout(storage, n1, n2);
-    const int stage = MAT_CHUNK * (L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
-    int s = budget / stage;
-    if (s > MAT_MAX_STAGES) s = MAT_MAX_STAGES;
-    if (s < 2) s = 2;
-    return s;
+    return L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0);
+}
+
+static int clamp_stages(int s)
+{
+    return s > MAT_MAX_STAGES ? MAT_MAX_STAGES : (s < 2 ? 2 : s);
+}
+
+MatShape materialise_pipeline_shape(int storage, int n1, int n2, int smem_budget)
+{
+    MatShape m{};
+    if (leaf_form(storage, n1, n2)) {  // one CTA of ML_CHUNK_PIPE threads
+        const int stage = ML_CHUNK_PIPE * record_bytes(storage, n1, n2);
+        m.ctas_per_sm = 1;
+        m.stages = clamp_stages(smem_budget / stage);
+        m.smem_per_cta = m.stages * stage;
+    } else {  // two CTAs of the warp-cooperative form
+        const int stage = MAT_CHUNK * record_bytes(storage, n1, n2);
+        m.ctas_per_sm = 2;
+        m.stages = clamp_stages(smem_budget / 2 / stage);
+        m.smem_per_cta = m.stages * stage;
+    }
+    return m;
+}
+
+// Leaves per stage (= threads of the thread-per-leaf form); 0 for the
+// warp-cooperative form.
+static int leaf_chunk(const MaterialiseParams &p)
+{
+    if (!leaf_form(p.storage, p.n1, p.n2)) return 0;
+    return p.pipeline ? ML_CHUNK_PIPE : ML_CHUNK;
 }
 
 int materialise_smem_bytes(const MaterialiseParams &p)
 {
-    const RecordLayout L = record_layout(p.storage, p.n1, p.n2);
-    const int chunk = !p.generic_form && leaf_form(p.storage, p.n1, p.n2) ? ML_CHUNK : MAT_CHUNK;
-    return p.stages * chunk * (L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
+    const int lc = leaf_chunk(p);
+    return p.stages * (lc ? lc : MAT_CHUNK) * record_bytes(p.storage, p.n1, p.n2);
+}
+
+template <int CH>
+static void *pick_leaf(int storage)
+{
+    switch (storage) {
+    case FPO_STORAGE_BF16: return (void *)materialise_leaf_kernel<FPO_STORAGE_BF16, CH>;
+    case FPO_STORAGE_F16: return (void *)materialise_leaf_kernel<FPO_STORAGE_F16, CH>;
+    default: return (void *)materialise_leaf_kernel<FPO_STORAGE_FP8_E4M3, CH>;
+    }
 }
 
 template <int N2>
@@ -492,14 +529,14 @@ int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream)
     if (p.n_leaves == 0) return (int)cudaSuccess;
     if (p.storage < FPO_STORAGE_F32 || p.storage > FPO_STORAGE_FP8_E4M3 || !p.sig || !p.zc)
         return (int)cudaErrorInvalidValue;  // no coefficient records (e.g. LATENT storage)
-    const bool lf = !p.generic_form && leaf_form(p.storage, p.n1, p.n2);
-    const int chunk = lf ? ML_CHUNK : MAT_CHUNK;
+    const int lc = leaf_chunk(p);
+    const bool lf = lc > 0;
+    const int chunk = lf ? lc : MAT_CHUNK;
+    const int threads = lf ? lc : MAT_THREADS;
     const int smem = materialise_smem_bytes(p);
     const void *kern;
     if (lf)
-        kern = p.storage == FPO_STORAGE_BF16 ? (const void *)materialise_leaf_kernel<FPO_STORAGE_BF16>
-             : p.storage == FPO_STORAGE_F16  ? (const void *)materialise_leaf_kernel<FPO_STORAGE_F16>
-                                             : (const void *)materialise_leaf_kernel<FPO_STORAGE_FP8_E4M3>;
+        kern = lc == ML_CHUNK ? pick_leaf<ML_CHUNK>(p.storage) : pick_leaf<ML_CHUNK_PIPE>(p.storage);
     else
         kern = p.n2 == 5 ? pick_materialise<5>(p.storage)
                          : (p.n2 == 11 ? pick_materialise<11>(p.storage) : pick_materialise<0>(p.storage));
@@ -509,7 +546,7 @@ int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream)
                                  p.carveout > 0 ? p.carveout : (int)cudaSharedmemCarveoutDefault);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, lf ? ML_THREADS : MAT_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return (int)e;
     if (per_sm < 1) per_sm = 1;
     if (p.max_ctas_per_sm > 0 && per_sm > p.max_ctas_per_sm) per_sm = p.max_ctas_per_sm;
@@ -517,7 +554,7 @@ int launch_materialise(const MaterialiseParams &p, int sm_count, void *stream)
     uint64_t blocks = (uint64_t)sm_count * per_sm;
     if (blocks > n_chunks) blocks = n_chunks;
     void *args[] = {(void *)&p};
-    e = cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(lf ? ML_THREADS : MAT_THREADS), args, smem,
+    e = cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(threads), args, smem,
                          (cudaStream_t)stream);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
