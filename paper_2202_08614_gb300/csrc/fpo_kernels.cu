@@ -321,16 +321,25 @@ __global__ void __launch_bounds__(CH) materialise_leaf_kernel(const __grid_const
         ptx::fence_barrier_init();
     }
     __syncthreads();
+    // Beside the traversal (frame pipeline) the records, read once, are
+    // marked for early eviction from L2, which leaves more of it to the
+    // traversal's nodes and table lines (measured: 0.580 against 0.588 ms per
+    // BF16 frame; the FP32 pass, in the warp-cooperative form, gains nothing).
+    const bool hint_ld = p.pipeline != 0;
+    const uint64_t pol = ptx::l2_evict_first();
+    auto copy = [&](void *d, const void *src, uint32_t n, uint64_t *b) {
+        if (hint_ld) ptx::bulk_g2s_hint(d, src, n, b, pol);
+        else ptx::bulk_g2s(d, src, n, b);
+    };
     auto issue = [&](uint32_t c, int s) {
         const uint32_t first = c * CH;
         const uint32_t m = min((uint32_t)CH, p.n_leaves - first);
         unsigned char *dst = mat_smem + (size_t)s * stage_bytes;
         const uint32_t bsc = SCALED ? ((m + 3u) & ~3u) * 4u : 0u;
         ptx::mbar_arrive_expect_tx(&bars[s], m * rec_sig + m * rec_z + bsc);
-        ptx::bulk_g2s(dst, static_cast<const unsigned char *>(p.sig) + (size_t)first * rec_sig, m * rec_sig, &bars[s]);
-        ptx::bulk_g2s(dst + sig_bytes, static_cast<const unsigned char *>(p.zc) + (size_t)first * rec_z, m * rec_z,
-                      &bars[s]);
-        if (SCALED) ptx::bulk_g2s(dst + sig_bytes + z_bytes, p.scale + first, bsc, &bars[s]);
+        copy(dst, static_cast<const unsigned char *>(p.sig) + (size_t)first * rec_sig, m * rec_sig, &bars[s]);
+        copy(dst + sig_bytes, static_cast<const unsigned char *>(p.zc) + (size_t)first * rec_z, m * rec_z, &bars[s]);
+        if (SCALED) copy(dst + sig_bytes + z_bytes, p.scale + first, bsc, &bars[s]);
     };
     if (tid == 0)
         for (int s = 0; s < S; ++s) {
