@@ -711,6 +711,20 @@ def main():
         res["cpu_baseline"]["one_core"] = {"value": v1, "cores": 1, "sample": f"{rays1} rays, {secs1:.1f} s"}
         import oracle
 
+        # four whole frames per resolution (seeded picks from the timed frames)
+        ot = oracle.OracleTree(tree.leaf_depth, tree.leaf_xyz, tree.max_depth)
+        picks = [frames[W:][i] for i in np.random.default_rng(7).choice(K, size=min(4, K), replace=False)]
+        res["cpu_baseline"]["full_frames"] = {}
+        for w, h in ((args.width, args.height), (800, 800)):
+            cams_r = synth.ring_cameras(16, w, h)
+            secs = []
+            for k, t in picks:
+                t0 = time.perf_counter()
+                oracle.render(ot, tree.coeffs, camera=cams_r[k], t=t, threads=thr)
+                secs.append(time.perf_counter() - t0)
+            res["cpu_baseline"]["full_frames"][f"{w}x{h}"] = {
+                "frames": len(picks), "s_per_frame": statistics.mean(secs),
+                "Mrays_s": w * h * len(secs) / sum(secs) / 1e6, "cores": thr}
         shell = synth.shell_tree()
         t0 = time.perf_counter()
         oracle.render(oracle.OracleTree(shell.leaf_depth, shell.leaf_xyz, shell.max_depth), shell.coeffs,
