@@ -67,6 +67,7 @@ constexpr int PIPE_TRAV_THREADS = 384;
 constexpr int PIPE_TRAV_CTAS = 2;
 constexpr int PIPE_MAT_SMEM_BUDGET = 88 * 1024;  // bytes of coefficient records in flight per SM
 constexpr int PIPE_STATIC_SMEM = 512;            // allowance for each kernel's static shared memory
+constexpr int SMEM_CONFIGS_KB[] = {0, 8, 16, 32, 64, 100, 132, 164, 196, 228};  // per SM, sm_100 family
 #ifndef FPO_SMEM_NODES
 #define FPO_SMEM_NODES 512
 #endif
@@ -587,8 +588,13 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
         mshape = materialise_pipeline_shape(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2, PIPE_MAT_SMEM_BUDGET);
         const long need = (long)PIPE_TRAV_CTAS * (traverse_smem_bytes(ctx->n_smem_nodes, false, PIPE_TRAV_THREADS) + PIPE_STATIC_SMEM + reserved) +
                           (long)mshape.ctas_per_sm * (mshape.smem_per_cta + PIPE_STATIC_SMEM + reserved);
-        carveout = max_smem > 0 ? (int)((need * 100 + max_smem - 1) / max_smem) : 101;
-        if (carveout > 100) overlap = false;
+        // The driver rounds a carveout request up to one of the SM's shared-
+        // memory configurations: ask for the smallest one that holds `need`.
+        long config = -1;
+        for (const int kb : SMEM_CONFIGS_KB)
+            if ((long)kb * 1024 >= need) { config = (long)kb * 1024; break; }
+        if (config < 0 || config > max_smem) overlap = false;
+        else carveout = (int)(config * 100 / max_smem);
     }
     ctx->table_ok = false;  // the pipeline writes both tables
     cudaStream_t s = (cudaStream_t)cuda_stream;
