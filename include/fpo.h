@@ -212,9 +212,9 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
  * traversed on cuda_stream (the call orders that stream after its own
  * previous work and before everything it enqueues later).  Both kernels
  * share every SM: the call picks their launch shapes itself (two 384-thread
- * traversal CTAs and two IDFT CTAs per SM, with a shared-memory carveout that
- * holds all four), whatever traverse_threads says; LATENT storage keeps the
- * single-frame shapes.  Errors: as fpo_render. */
+ * traversal CTAs and one or two IDFT CTAs per SM, with a shared-memory
+ * carveout that holds them all), whatever traverse_threads says; LATENT
+ * storage keeps the single-frame shapes.  Errors: as fpo_render. */
 int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames,
                       const fpo_frame_opts *opts, float *out_rgb, void *cuda_stream);
 
