@@ -78,3 +78,21 @@ def test_frame_roofline_bytes():
     # is the minimum even when every leaf is reached
     fr = bench.frame_roofline(1.0, 10, 10, 664, 128, 0, 0, 1000.0)
     assert fr["bytes_min"] == fr["bytes_visited"] == 6640
+
+
+def test_clock_sampler_summary_flags_throttling():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    c = bench.ClockSampler(0)
+    # index, sm, max sm, power, active reasons, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap
+    c.out = ("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+             "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+             "0, 2070, 2070, 1100.5, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    c.out = "0, 1500, 2070, 700.0, 0x8, Active, Not Active, Not Active, Not Active\n"
+    assert c.summary()["reasons"] == ["hw_slowdown"]
+    c.out = ""
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
