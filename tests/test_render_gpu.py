@@ -269,6 +269,35 @@ def test_body_1080p_sampled_pixels(body, mode):
         r.close()
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_body_1080p_pipelined_frames(body, storage):
+    # the timed launch configuration: fpo_render_frames, the IDFT pass of the
+    # next frame beside the traversal on every SM.  Bit-equal to single-frame
+    # renders; FP32 sampled pixels within the parity bounds of the oracle.
+    tree, ot = body
+    cams = synth.ring_cameras(16, 1920, 1080)
+    picks = [(3, 5.0), (8, 31.0), (14, 58.0), (1, 17.0)]
+    r = fpo.Renderer(storage=storage)
+    r.upload(tree)
+    try:
+        import oracle
+
+        imgs = r.render_frames([cams[k] for k, _ in picks], [t for _, t in picks])
+        r.status()
+        for i, (k, t) in enumerate(picks):
+            single = r.render(camera=cams[k], t=t)["rgb"]
+            r.status()
+            assert torch.equal(imgs[i], single)
+        if storage == "f32":
+            for i, (k, t) in enumerate(picks[:2]):
+                rng = np.random.default_rng(100 + k)
+                sel = rng.integers(0, 1920 * 1080, 3000)
+                ref = oracle.render(ot, tree.coeffs, camera=cams[k], t=t, sel=sel)
+                gu.compare({"rgb": imgs[i].cpu().numpy()[sel]}, ref)
+    finally:
+        r.close()
+
+
 def test_table_reuse_for_views_of_one_frame_time():
     # FPO_FLAG_REUSE_TABLE: views of one t share an IDFT pass; a new t, or new
     # coefficients, rebuild it (the images equal fresh renders bit for bit)
