@@ -169,7 +169,7 @@ def run_reference(args, rank, world):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / max(len(times), 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(tree, args, "oracle"),
+        "config": workload_config(tree, args),
         "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -180,14 +180,19 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 
 
-def workload_config(tree, args, idft):
+def workload_config(tree, args):
+    """The workload, derived from the arguments alone, so that the oracle arm
+    and the GPU arm name the same one."""
     return {
         "workload": (f"body union octree (14 animated capsules, 60 frames), depth 9, "
                      f"{tree.n_leaves} leaves, n1=31 n2=5 SH deg 2, {args.width}x{args.height}, "
                      f"16 ring cameras x 60 integer t"),
         "leaves": tree.n_leaves,
         "resolution": [args.width, args.height],
-        "idft": idft,
+        "idft": "fused" if args.idft == "fused" else "materialise",
+        "storage": args.storage,
+        "table": None if args.idft == "fused" else ("f32" if args.storage == "f32" else "f16"),
+        "frames_per_call": max(1, args.frames_per_call),
         "l2": "inputs larger than L2 (2.4 GB of leaf records)",
         "early_stop_T": 1e-4,
     }
@@ -276,21 +281,26 @@ def time_frames(r, cams, frames, out, torch, per_call=1):
     return a.elapsed_time(b) / len(frames)
 
 
-def sampled_psnr(r, ot, coeffs, cams, frames, out, torch, n_px):
-    """PSNR of rendered frames against the FP64 oracle on sampled pixels."""
+PSNR_FRAMES = [(k, 3.75 * k) for k in range(16)]  # one frame per ring camera, t = 3.75 k
+
+
+def frame_psnr(r, ot, coeffs, cams, out, torch, refs=None):
+    """Per-frame PSNR (and max |dRGB|) of whole rendered frames against the
+    FP64 oracle over the 16 frames of PSNR_FRAMES.  `refs` caches the oracle
+    images of one coefficient set."""
     import oracle
 
-    errs = []
-    for i, (k, t) in enumerate(frames):
-        img = r.render(camera=cams[k], t=t, out=out)["rgb"]
-        torch.cuda.synchronize()
-        rng = np.random.default_rng(i)
-        w = cams[k].width
-        sel = np.concatenate([rng.integers(0, n_px, 3000), (cams[k].height // 2) * w + np.arange(0, w, 2)])
-        ref = oracle.render(ot, coeffs, camera=cams[k], t=t, sel=sel)["rgb"]
-        errs.append((img.cpu().numpy()[sel].astype(np.float64) - ref) ** 2)
-    mse = float(np.mean(np.concatenate(errs)))
-    return 10 * np.log10(1.0 / mse) if mse > 0 else float("inf")
+    if refs is None:
+        refs = [oracle.render(ot, coeffs, camera=cams[k], t=t)["rgb"] for k, t in PSNR_FRAMES]
+    db, mx = [], []
+    for (k, t), ref in zip(PSNR_FRAMES, refs):
+        img = r.render(camera=cams[k], t=t, out=out)["rgb"].cpu().numpy().astype(np.float64)
+        mse = float(np.mean((img - ref) ** 2))
+        db.append(10 * np.log10(1.0 / mse) if mse > 0 else float("inf"))
+        mx.append(float(np.abs(img - ref).max()))
+    r.status()
+    return {"min_db": min(db), "mean_db": float(np.mean(db)), "per_frame_db": db, "max_abs_rgb": max(mx),
+            "frames": "camera k at t = 3.75 k, k = 0..15, whole frames"}, refs
 
 
 def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, peak):
@@ -310,7 +320,7 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
     ms1 = time_frames(r, cams, nf, out, torch)
     res["bf16"] = {"Mrays_s": n_px / ms / 1e3, "fps": 1e3 / ms, "fp32_Mrays_s": n_px / fp32_ms / 1e3,
                    "single_frame_Mrays_s": n_px / ms1 / 1e3,
-                   "psnr_db_vs_fp64_oracle": sampled_psnr(r, ot, tree.coeffs, cams, nf[:2], out, torch, n_px),
+                   "psnr_vs_fp64_oracle": frame_psnr(r, ot, tree.coeffs, cams, out, torch)[0],
                    "bytes_per_leaf": r.info()["leaf_record_bytes"]}
     # the FP16 table of reduced-precision storage: 28 values x 2 B per leaf
     res["bf16"]["frame_roofline"] = frame_roofline(ms, tree.n_leaves, n_vis, STORED_PER_LEAF["bf16"],
@@ -384,7 +394,7 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
     res["latent"] = {
         "Mrays_s": n_px / msl / 1e3, "fps": 1e3 / msl, "fp32_same_tree_Mrays_s": n_px / ms32 / 1e3,
         "single_frame_Mrays_s": n_px / msl1 / 1e3,
-        "psnr_db_vs_fp64_oracle": sampled_psnr(r, ot, co_np, cams, nf[:2], out, torch, n_px),
+        "psnr_vs_fp64_oracle": frame_psnr(r, ot, co_np, cams, out, torch)[0],
         "decode_ms": ev[0].elapsed_time(ev[1]), "train_steps": args.latent_steps, "train_batch": 65536,
         "train_s": train_s, "train_loss": hist, "bytes_per_leaf": 64,
         "coefficients": "per-leaf DFT (Eq. 10-12) of smooth animated fields over the same leaves"}
@@ -502,6 +512,11 @@ def ncu_traffic(kernel: str):
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.gpus != world:
+        # one process per GPU: N > 1 needs a launcher (torchrun) that starts N ranks
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world}; launch N ranks with "
+              f"torch.distributed.run --nproc-per-node {args.gpus}", file=sys.stderr)
+        sys.exit(2)
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
@@ -536,6 +551,10 @@ def main():
     def render_batch(bt, dst):
         r.render_frames([cams[k] for k, _ in bt], [t for _, t in bt], out=dst[:len(bt)])
 
+    # clocks and throttle reasons are sampled over the whole GPU phase (warm-up,
+    # the per-kernel pass, the timed region and the end-to-end pass): the
+    # timed region alone can be shorter than the sampling period
+    clk = ClockSampler(local).__enter__()
     # warm-up: single-frame calls, then pipelined calls (allocates the second table)
     for k, t in frames[:W]:
         r.render(camera=cams[k], t=t, out=out)
@@ -565,16 +584,15 @@ def main():
         pg.barrier()
     torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        torch.cuda.nvtx.range_push("timed")
-        start.record(stream)
-        for j, bt in enumerate(batches):
-            bev[j][0].record(stream)
-            render_batch(bt, outb)
-            bev[j][1].record(stream)
-        stop.record(stream)
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_push("timed")
+    start.record(stream)
+    for j, bt in enumerate(batches):
+        bev[j][0].record(stream)
+        render_batch(bt, outb)
+        bev[j][1].record(stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     if pg:
         pg.barrier()
     r.status()
@@ -624,16 +642,15 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     r.status()
+    clk.__exit__(None, None, None)
 
     value = mrays_per_s(world, K, n_px, t_max)
     res = {
         "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(tree, args, "materialise" if mat else "fused"),
+        "config": workload_config(tree, args),
     }
-    res["config"]["storage"] = args.storage
-    res["config"]["frames_per_call"] = B
     res["fps"] = 1e3 * K / t_max
     res["frame_ms"] = {"p10": float(np.percentile(batch_frame_ms, 10)), "p50": statistics.median(batch_frame_ms),
                        "p90": float(np.percentile(batch_frame_ms, 90)),
@@ -650,7 +667,7 @@ def main():
     mean_vis = statistics.mean(n_vis)
     # bytes of sigma(t) and z(t) per leaf: FP16 table rows are 64 B, FP32 128 B
     table_bytes = TABLE_VALUES_PER_LEAF * (2 if r.info()["table_bytes"] == 64 * tree.n_leaves else 4)
-    res["config"]["table"] = ("f16" if table_bytes == 2 * TABLE_VALUES_PER_LEAF else "f32") if mat else None
+    assert res["config"]["table"] == (("f16" if table_bytes == 2 * TABLE_VALUES_PER_LEAF else "f32") if mat else None)
     if mat:
         kernels = {
             "materialise_kernel": (avg_mat, tree.n_leaves * (STORED_PER_LEAF[args.storage] + table_bytes)),
@@ -688,6 +705,7 @@ def main():
                   "d2h_bytes_per_step": int(n_px * 3 * 4)}
     res["gpu_launches"] = K * (2 if mat else 1)
     res["clocks"] = clk.summary()
+    res["clocks"]["window"] = "the whole GPU phase: warm-up, per-kernel pass, timed region, end-to-end pass"
     res["tree"] = info
     if not args.no_variants:
         # the second resolution of the workload: 800x800 from the same ring

@@ -319,7 +319,11 @@ int fpo_tree_info_get(const fpo_ctx *ctx, fpo_tree_info *out)
     return FPO_OK;
 }
 
-static int check_rays(const fpo_ctx *ctx, const fpo_rays *r, uint64_t *n_rays)
+}  // extern "C"
+
+namespace fpo {
+
+int check_rays(const fpo_rays *r, uint64_t *n_rays)
 {
     if (r->mode == FPO_RAYS_CAMERA) {
         const double fov = r->fov_y_deg;
@@ -337,19 +341,33 @@ static int check_rays(const fpo_ctx *ctx, const fpo_rays *r, uint64_t *n_rays)
         *n_rays = (uint64_t)r->width * r->height;
     } else if (r->mode == FPO_RAYS_EXPLICIT) {
         if (r->n > 0 && (!r->o || !r->d)) return fail(FPO_ERR_INVALID_ARG, "o and d must be non-NULL");
+        if (!r->t_per_ray && !std::isfinite(r->t)) return fail(FPO_ERR_INVALID_ARG, "t must be finite");
         *n_rays = r->n;
     } else {
         return fail(FPO_ERR_INVALID_ARG, "unknown ray mode %d", r->mode);
     }
     if (*n_rays >= (1ull << 31)) return fail(FPO_ERR_INVALID_ARG, "too many rays");
-    (void)ctx;
+    return FPO_OK;
+}
+
+int check_render_opts(const fpo_ctx *ctx, const fpo_frame_opts *opts, uint64_t n_rays, const float *out_rgb)
+{
+    if (n_rays > 0 && !out_rgb) return fail(FPO_ERR_INVALID_ARG, "out_rgb is NULL");
+    const uint32_t fl = opts->flags;
+    if ((fl & FPO_FLAG_RECORD_VISITS) && (!opts->visit_count || (opts->visit_cap && !opts->visit_log)))
+        return fail(FPO_ERR_INVALID_ARG, "RECORD_VISITS needs visit_count (and visit_log if visit_cap > 0)");
+    if ((fl & FPO_FLAG_OUT_T) && !opts->out_T) return fail(FPO_ERR_INVALID_ARG, "OUT_T needs out_T");
+    if ((fl & FPO_FLAG_STATS) && !opts->stats) return fail(FPO_ERR_INVALID_ARG, "STATS needs stats");
+    if ((fl & FPO_FLAG_MARK_LEAVES) && !opts->leaf_mark && ctx->n_leaves)
+        return fail(FPO_ERR_INVALID_ARG, "MARK_LEAVES needs leaf_mark");
+    if (!(opts->stop_T >= 0.0f)) return fail(FPO_ERR_INVALID_ARG, "stop_T must be >= 0");
     return FPO_OK;
 }
 
 // Kernel parameters of one render (or adjoint) call from the context, rays
 // and options.
-static TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
-                                      float *out_rgb, uint64_t n_rays)
+TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
+                               float *out_rgb, uint64_t n_rays)
 {
     const uint32_t fl = opts->flags;
     TraverseParams p{};
@@ -414,9 +432,10 @@ static TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, 
 // coefficients (at most max_ctas_per_sm CTAs per SM when > 0).
 // With pipe_stages > 0 the pass takes the frame-pipeline shape with that many
 // stages (materialise_pipeline_shape), co-scheduled with the traversal.
-static int launch_table_pass(fpo_ctx *ctx, double t, float *table, int max_ctas_per_sm, cudaStream_t s,
-                             int pipe_stages = 0, int carveout = 0)
+int launch_table_pass(const fpo_ctx *ctx, double t, float *table, int max_ctas_per_sm, void *stream,
+                      int pipe_stages, int carveout)
 {
+    const cudaStream_t s = (cudaStream_t)stream;
     if (ctx->cfg.storage == FPO_STORAGE_LATENT) {
         LatentParams lp{};
         lp.latents = ctx->d_latents;
@@ -459,23 +478,20 @@ static int launch_table_pass(fpo_ctx *ctx, double t, float *table, int max_ctas_
     return launch_materialise(mp, ctx->sm_count, s);
 }
 
+}  // namespace fpo
+
+extern "C" {
+
 int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, float *out_rgb,
                void *cuda_stream)
 {
     if (!ctx || !rays || !opts) return fail(FPO_ERR_INVALID_ARG, "NULL argument");
     if (!ctx->has_tree) return fail(FPO_ERR_NO_TREE, "render before fpo_upload_tree");
     uint64_t n_rays = 0;
-    int st = check_rays(ctx, rays, &n_rays);
+    int st = check_rays(rays, &n_rays);
     if (st != FPO_OK) return st;
-    if (n_rays > 0 && !out_rgb) return fail(FPO_ERR_INVALID_ARG, "out_rgb is NULL");
+    if ((st = check_render_opts(ctx, opts, n_rays, out_rgb)) != FPO_OK) return st;
     const uint32_t fl = opts->flags;
-    if ((fl & FPO_FLAG_RECORD_VISITS) && (!opts->visit_count || (opts->visit_cap && !opts->visit_log)))
-        return fail(FPO_ERR_INVALID_ARG, "RECORD_VISITS needs visit_count (and visit_log if visit_cap > 0)");
-    if ((fl & FPO_FLAG_OUT_T) && !opts->out_T) return fail(FPO_ERR_INVALID_ARG, "OUT_T needs out_T");
-    if ((fl & FPO_FLAG_STATS) && !opts->stats) return fail(FPO_ERR_INVALID_ARG, "STATS needs stats");
-    if ((fl & FPO_FLAG_MARK_LEAVES) && !opts->leaf_mark && ctx->n_leaves)
-        return fail(FPO_ERR_INVALID_ARG, "MARK_LEAVES needs leaf_mark");
-    if (!(opts->stop_T >= 0.0f)) return fail(FPO_ERR_INVALID_ARG, "stop_T must be >= 0");
     const bool per_ray_t = rays->mode == FPO_RAYS_EXPLICIT && rays->t_per_ray;
     int mode = ctx->cfg.idft_mode;
     if (mode == FPO_IDFT_AUTO) mode = per_ray_t ? FPO_IDFT_FUSED : FPO_IDFT_MATERIALISE;
@@ -509,7 +525,7 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
     }
     if (mat && !((fl & FPO_FLAG_REUSE_TABLE) && ctx->table_ok && ctx->table_t == rays->t)) {
         ctx->table_ok = false;
-        const int ce = launch_table_pass(ctx, rays->t, ctx->d_table, 0, s);
+        const int ce = launch_table_pass(ctx, rays->t, ctx->d_table, 0, s, 0, 0);
         if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "IDFT table launch");
         ctx->table_ok = true;
         ctx->table_t = rays->t;
@@ -534,7 +550,7 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
     uint64_t R = 0;
     for (uint32_t k = 0; k < n_frames; ++k) {
         uint64_t nr = 0;
-        const int st = check_rays(ctx, &frames[k], &nr);
+        const int st = check_rays(&frames[k], &nr);
         if (st != FPO_OK) return st;
         if (frames[k].mode == FPO_RAYS_EXPLICIT && frames[k].t_per_ray)
             return fail(FPO_ERR_INVALID_ARG, "per-ray times need fpo_render (fused IDFT)");
@@ -607,7 +623,7 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
         float *tbl = b ? ctx->d_table2 : ctx->d_table;
         if (k >= 2 && (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_trav[b], 0)) != cudaSuccess) return cuda_fail(e, "wait");
         int ce = overlap ? launch_table_pass(ctx, frames[k].t, tbl, mshape.ctas_per_sm, ctx->aux, mshape.stages, carveout)
-                         : launch_table_pass(ctx, frames[k].t, tbl, 0, ctx->aux);
+                         : launch_table_pass(ctx, frames[k].t, tbl, 0, ctx->aux, 0, 0);
         if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "IDFT table launch");
         if ((e = cudaEventRecord(ctx->ev_mat[b], ctx->aux)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(s, ctx->ev_mat[b], 0)) != cudaSuccess)
@@ -633,7 +649,7 @@ int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts
     if (!ctx || !rays || !opts) return fail(FPO_ERR_INVALID_ARG, "NULL argument");
     if (!ctx->has_tree) return fail(FPO_ERR_NO_TREE, "backward before fpo_upload_tree");
     uint64_t n_rays = 0;
-    int st = check_rays(ctx, rays, &n_rays);
+    int st = check_rays(rays, &n_rays);
     if (st != FPO_OK) return st;
     if (ctx->cfg.storage != FPO_STORAGE_F32)
         return fail(FPO_ERR_UNSUPPORTED, "gradients are taken with respect to FP32 records only");

@@ -175,6 +175,23 @@ CtxView ctx_view(const fpo_ctx *ctx);
 // Records `msg` as the calling thread's last error; returns `code`.
 int set_last_error(int code, const char *msg);
 
+// Argument checks shared by the render entry points (FPO_OK or the status
+// they recorded): the rays (camera validity, finite t, ray count), and the
+// options and output of one render.
+int check_rays(const fpo_rays *r, uint64_t *n_rays);
+int check_render_opts(const fpo_ctx *ctx, const fpo_frame_opts *opts, uint64_t n_rays, const float *out_rgb);
+// Kernel parameters of one render (or adjoint) call; p.table is the context's
+// own per-frame table, which a caller may point elsewhere.
+TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
+                               float *out_rgb, uint64_t n_rays);
+// The per-frame table for time t into `table` on `stream`: the tensor-core
+// decoder for LATENT storage, else the IDFT pass over the stored coefficients
+// (at most max_ctas_per_sm CTAs per SM when > 0; with pipe_stages > 0 the
+// frame-pipeline shape with that many stages and the given carveout).
+// Returns a cudaError_t.
+int launch_table_pass(const fpo_ctx *ctx, double t, float *table, int max_ctas_per_sm, void *stream,
+                      int pipe_stages, int carveout);
+
 // Latent decoder (per-leaf FP16 latents, MLP 32 -> 64 -> 64 -> n1 + 27 n2,
 // ReLU).  Weights are BF16 bit patterns, row-major [out][in]; biases FP32.
 struct LatentParams {

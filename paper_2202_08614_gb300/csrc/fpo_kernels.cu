@@ -1250,13 +1250,14 @@ static int launch_t(const TraverseParams &p, int sm_count, cudaStream_t s)
     return (int)cudaGetLastError();
 }
 
-// Debug outputs use the plain schedule (their results do not depend on it).
+// The compaction schedule (refill_min < 32) or the plain one, each with or
+// without the debug outputs (visit logs, final T, leaf marks, counters).
 template <int TM, int N1, int N2>
 static int launch_sched(const TraverseParams &p, bool debug, int sm_count, cudaStream_t s)
 {
-    if (debug) return launch_t<TM, true, N1, N2, false>(p, sm_count, s);
-    if (p.refill_min < 32) return launch_t<TM, false, N1, N2, true>(p, sm_count, s);
-    return launch_t<TM, false, N1, N2, false>(p, sm_count, s);
+    if (p.refill_min < 32)
+        return debug ? launch_t<TM, true, N1, N2, true>(p, sm_count, s) : launch_t<TM, false, N1, N2, true>(p, sm_count, s);
+    return debug ? launch_t<TM, true, N1, N2, false>(p, sm_count, s) : launch_t<TM, false, N1, N2, false>(p, sm_count, s);
 }
 
 static int launch_fused(const TraverseParams &p, bool debug, int sm_count, cudaStream_t s)

@@ -61,6 +61,9 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["unit"] == "Mrays/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["higher_is_better"] is True
+    # the GPU arm's default workload
+    assert line["config"]["idft"] == "materialise" and line["config"]["table"] == "f32"
+    assert line["config"]["storage"] == "f32" and line["config"]["frames_per_call"] == 32
 
 
 def test_frame_roofline_bytes():
@@ -96,3 +99,31 @@ def test_clock_sampler_summary_flags_throttling():
     assert c.summary()["reasons"] == ["hw_slowdown"]
     c.out = ""
     assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_gpus_flag_must_match_the_launched_ranks():
+    # --gpus 2 without a launcher would silently time one GPU: refused
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2", "--steps", "1"],
+                         capture_output=True, text=True, timeout=120, cwd=ROOT, env=env)
+    assert out.returncode != 0
+    assert "WORLD_SIZE=1" in out.stderr
+
+
+def test_both_arms_name_the_same_workload():
+    sys.path.insert(0, ROOT)
+    import argparse
+
+    import bench
+
+    class T:
+        n_leaves = 3506408
+
+    args = argparse.Namespace(width=1920, height=1080, idft="auto", storage="f32", frames_per_call=32)
+    cfg = bench.workload_config(T(), args)
+    assert cfg["idft"] == "materialise" and cfg["table"] == "f32" and cfg["storage"] == "f32"
+    assert cfg["frames_per_call"] == 32 and cfg["resolution"] == [1920, 1080]
+    args.storage = "bf16"
+    assert bench.workload_config(T(), args)["table"] == "f16"
+    args.idft = "fused"
+    assert bench.workload_config(T(), args)["table"] is None

@@ -530,3 +530,91 @@ def test_latent_loss_gradient_matches_finite_differences():
         xm[idx] -= eps
         fd = (f(w, xp) - f(w, xm)) / (2 * eps)
         assert abs(dx[idx] - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+def _one_hot_net(nc=NCOEF):
+    """A decoder whose outputs are known ReLU chains of single latent entries:
+    h1 = [relu(x + 0.25), relu(0.25 - x)], h2 = relu(h1[perm] - 0.5) with a
+    permutation that is not its own inverse, y_o = (o + 1) h2[o % 64] + o."""
+    w1 = np.zeros((64, 32))
+    for j in range(32):
+        w1[j, j] = 1.0
+        w1[32 + j, j] = -1.0
+    perm = (np.arange(64) * 5 + 3) % 64
+    w2 = np.zeros((64, 64))
+    w2[np.arange(64), perm] = 1.0
+    w3 = np.zeros((nc, 64))
+    w3[np.arange(nc), np.arange(nc) % 64] = np.arange(nc) + 1.0
+    return w1, np.full(64, 0.25), w2, np.full(64, -0.5), w3, np.arange(nc, dtype=float), perm
+
+
+def test_latent_decode_of_a_one_hot_network():
+    # decode() against the ReLU chains written out by hand: catches a missing
+    # ReLU (the -0.5 bias makes h2 negative without the second one, and
+    # relu(-x) without the first), a transposed weight (W1 is 64 x 32 and the
+    # permutation in W2 is not symmetric) and a dropped bias.
+    from oracle import latent as olat
+
+    w1, b1, w2, b2, w3, b3, perm = _one_hot_net()
+    x = np.random.default_rng(3).normal(size=(7, 32)) * 2.0
+    y = olat.decode(x, w1, b1, w2, b2, w3, b3)
+    for r in range(x.shape[0]):
+        h1 = [max(x[r, j] + 0.25, 0.0) for j in range(32)] + [max(0.25 - x[r, j], 0.0) for j in range(32)]
+        h2 = [max(h1[perm[i]] - 0.5, 0.0) for i in range(64)]
+        want = [(o + 1) * h2[o % 64] + o for o in range(NCOEF)]
+        np.testing.assert_allclose(y[r], want, rtol=0, atol=1e-12)
+    # a latent of -1 everywhere drives the first half of h1 to 0 and the
+    # second half to 1.25
+    yn = olat.decode(-np.ones((1, 32)), w1, b1, w2, b2, w3, b3)[0]
+    h2n = np.where(perm >= 32, 0.75, 0.0)
+    np.testing.assert_allclose(yn, [(o + 1) * h2n[o % 64] + o for o in range(NCOEF)], atol=1e-12)
+
+
+def test_latent_loss_forward_is_decode():
+    # loss_grad's own forward must be decode(): L = sum_j cw_j (decode - target)^2
+    from oracle import latent as olat
+
+    rng = np.random.default_rng(21)
+    nc = 17
+    w = [rng.normal(size=(64, 32)) / 6, rng.normal(size=64) * 0.1, rng.normal(size=(64, 64)) / 8,
+         rng.normal(size=64) * 0.1, rng.normal(size=(nc, 64)) / 8, rng.normal(size=nc)]
+    x = rng.normal(size=(9, 32))
+    tgt = rng.normal(size=(9, nc))
+    cw = rng.uniform(0.5, 2.0, nc)
+    L = olat.loss_grad(x, *w, tgt, cw)[0]
+    y = olat.decode(x, *w)
+    assert abs(L - float(np.sum(cw * (y - tgt) ** 2))) <= 1e-12 * max(1.0, abs(L))
+    w1, b1, w2, b2, w3, b3, _ = _one_hot_net(nc)
+    L1 = olat.loss_grad(x, w1, b1, w2, b2, w3, b3, tgt, cw)[0]
+    y1 = olat.decode(x, w1, b1, w2, b2, w3, b3)
+    assert abs(L1 - float(np.sum(cw * (y1 - tgt) ** 2))) <= 1e-12 * max(1.0, abs(L1))
+
+
+def test_latent_table_against_the_oracle_render():
+    # table() holds [max(0, sigma(t)), z_{c,k}(t)] of Eq. 7 and Eq. 9; the
+    # pinned C oracle renders a one-leaf tree from the same coefficients, and
+    # along a ray of length L through the leaf the pixel is
+    # (1 - e^{-sigma L}) S(sum_k z_{c,k} Y_k(d)) + e^{-sigma L} bg.  A
+    # transposed (n2, 27) reshape or a wrong density row fails it.
+    from oracle import latent as olat
+
+    rng = np.random.default_rng(8)
+    co = synth.draw_coefficients(rng, 3)  # i.i.d. draws of the parity recipe
+    co[2, :N1] *= -1.0                    # a leaf whose density clamps at 0
+    tree = _one_leaf()
+    bg = np.array([0.2, 0.5, 0.9])
+    for t in (0.0, 13.37, 44.0):
+        tab = olat.table(co, t)
+        assert np.all(tab[:, 28:] == 0.0)
+        for j in range(co.shape[0]):
+            sigma, z = tab[j, 0], tab[j, 1:28].reshape(3, 9)
+            assert sigma >= 0.0
+            for d in ((1.0, 0.0, 0.0), (0.6, -0.48, 0.64), (-0.36, 0.8, 0.48)):
+                dn = np.array(d) / np.linalg.norm(d)
+                o = np.array([0.375, 0.375, 0.375]) - 2.0 * dn
+                r = _render_ray(tree, co[j:j + 1], o, dn, bg=tuple(bg), stop_T=0.0, t=t)
+                L = r["visit_delta"][0, 0]
+                Y = oracle.sh(dn, 2)
+                col = 1.0 / (1.0 + np.exp(-(z @ Y)))
+                a = 1.0 - math.exp(-sigma * L)
+                np.testing.assert_allclose(r["rgb"][0], a * col + (1 - a) * bg, rtol=0, atol=1e-12)
