@@ -402,35 +402,12 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
     return res
 
 
-def camera_batch(cams, n, gen, torch, n_frames=60):
-    """n rays drawn uniformly over (camera, integer frame, pixel): origins,
-    unit directions (pixel centres, the pinhole model of fpo.h) and times."""
-    basis = []
-    for c in cams:
-        eye, tgt, up = (np.array(v, np.float64) for v in (c.eye, c.target, c.up))
-        f = (tgt - eye) / np.linalg.norm(tgt - eye)
-        r = np.cross(f, up)
-        r /= np.linalg.norm(r)
-        basis.append(np.concatenate([eye, f, r, np.cross(r, f)]))
-    B = torch.as_tensor(np.stack(basis), dtype=torch.float32, device="cuda")
-    W, H = cams[0].width, cams[0].height
-    th = np.tan(np.radians(cams[0].fov_y_deg) / 2)
-    v = torch.randint(0, len(cams), (n,), device="cuda", generator=gen)
-    p = torch.randint(0, W * H, (n,), device="cuda", generator=gen)
-    t = torch.randint(0, n_frames, (n,), device="cuda", generator=gen).float()
-    sx = ((2 * ((p % W).float() + 0.5) / W - 1) * th * W / H)[:, None]
-    sy = ((1 - 2 * ((p // W).float() + 0.5) / H) * th)[:, None]
-    b = B[v]
-    d = b[:, 3:6] + sx * b[:, 6:9] + sy * b[:, 9:12]
-    return b[:, 0:3].contiguous(), (d / d.norm(dim=1, keepdim=True)).contiguous(), t
-
-
 def finetune_variant(args, tree, torch, fpo):
     """The fine-tuning stage (Sec. 4.3, Eq. 13) at full scale: coefficients
     perturbed by N(0, 0.1|k| + 0.05), targets rendered by the FP32 path from
     the original ones at 800x800 over 16 ring views x 60 frames, batches of
     65,536 rays, Adam lr 1e-2 (row-sparse, fused with the write-back)."""
-    from paper_2202_08614_gb300.finetune import FineTuner
+    from paper_2202_08614_gb300.finetune import FineTuner, camera_ray_batch
 
     B, steps, warm = 65536, args.finetune_steps, 5
     cams = synth.ring_cameras(16, 800, 800)
@@ -445,7 +422,7 @@ def finetune_variant(args, tree, torch, fpo):
     del noise
     batches = []
     for _ in range(warm + steps + 1):
-        o, d, t = camera_batch(cams, B, gen, torch)
+        o, d, t = camera_ray_batch(cams, B, gen)
         batches.append((o, d, t, ref.render(rays_o=o, rays_d=d, t_per_ray=t)["rgb"].clone()))
     ref.status()
     ref.close()
@@ -548,8 +525,8 @@ def main():
     batches = [timed[i:i + B] for i in range(0, K, B)]
     outb = torch.empty((min(B, K), n_px, 3), dtype=torch.float32, device="cuda")
 
-    def render_batch(bt, dst):
-        r.render_frames([cams[k] for k, _ in bt], [t for _, t in bt], out=dst[:len(bt)])
+    def render_batch(bt, dst, events=None):
+        r.render_frames([cams[k] for k, _ in bt], [t for _, t in bt], out=dst[:len(bt)], frame_events=events)
 
     # clocks and throttle reasons are sampled over the whole GPU phase (warm-up,
     # the per-kernel pass, the timed region and the end-to-end pass): the
@@ -610,35 +587,34 @@ def main():
     r.status()
 
     # end to end through the public API: every frame is read back into pinned
-    # host memory inside the timed region.  Batch j's read-back runs on a copy
-    # stream while batch j + 1 renders (two device and two host buffers);
-    # before batch j + 2 reuses a buffer pair the host waits until batch j is
-    # in host memory.
+    # host memory inside the timed region.  Frame i of a call is copied on a
+    # copy stream as soon as its pixels are written (the call's per-frame
+    # events), while the later frames render; two device and two host buffers
+    # alternate between calls, and before a call reuses a pair the host waits
+    # until the pair's previous frames are in host memory.
     outs = [outb, torch.empty_like(outb)]
     hosts = [torch.empty(outb.shape, dtype=torch.float32, pin_memory=True) for _ in range(2)]
     copy_stream = torch.cuda.Stream()
-    done = [torch.cuda.Event(), torch.cuda.Event()]
+    fev = [[torch.cuda.Event() for _ in range(outb.shape[0])] for _ in range(2)]
     landed = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def e2e_batch(b, bt):
+        render_batch(bt, outs[b], fev[b][:len(bt)])
+        with torch.cuda.stream(copy_stream):
+            for i in range(len(bt)):
+                copy_stream.wait_event(fev[b][i])
+                hosts[b][i].copy_(outs[b][i], non_blocking=True)
+            landed[b].record(copy_stream)
+
     # warm-up of this path (first copies into the pinned buffers, events)
     for b in range(2):
-        render_batch(frames[:min(B, W)], outs[b])
-        done[b].record(stream)
-        copy_stream.wait_event(done[b])
-        with torch.cuda.stream(copy_stream):
-            hosts[b].copy_(outs[b], non_blocking=True)
-            landed[b].record(copy_stream)
+        e2e_batch(b, frames[:min(B, W)])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for j, bt in enumerate(batches):
-        b = j & 1
         if j >= 2:
-            landed[b].synchronize()
-        render_batch(bt, outs[b])
-        done[b].record(stream)
-        copy_stream.wait_event(done[b])
-        with torch.cuda.stream(copy_stream):
-            hosts[b][:len(bt)].copy_(outs[b][:len(bt)], non_blocking=True)
-            landed[b].record(copy_stream)
+            landed[j & 1].synchronize()
+        e2e_batch(j & 1, bt)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     r.status()

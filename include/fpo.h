@@ -147,7 +147,25 @@ enum {
      * skip the IDFT pass and reuse it: several views of one frame time cost
      * one IDFT pass.  The call must follow the one that built the table on
      * the same stream (or an ordered one). */
-    FPO_FLAG_REUSE_TABLE = 16
+    FPO_FLAG_REUSE_TABLE = 16,
+    /* fpo_render_backward only: the gradient-check replay.  The FP32 stepping
+     * still decides which leaves a ray visits, in which order and where it
+     * stops (as in the forward); each visited leaf's segment is then measured
+     * by an FP64 slab test of its box, and the IDFT, SH, sigmoid,
+     * transmittance products and S_j run in FP64 over two replays of the ray
+     * (the first accumulates the FP64 colour, so out_rgb is not used).
+     * dL_dcoeffs then points to FP64 values (double [n_leaves][n1 + 27*n2],
+     * 8-byte aligned).  Slow: for checking gradients, not for training. */
+    FPO_FLAG_FP64_GRADCHECK = 32,
+    /* Test of the device-side failure path (fpo_render in the table mode):
+     * the first wait of every CTA of the table pass (the IDFT pass's wait
+     * for its first bulk copies, or the latent decoder's wait for its first
+     * MMAs) is made on a barrier that nothing signals, with a 1 ms limit.
+     * The pass stops, waits (with its normal limit) for the copies or MMAs it
+     * has in flight, and the call then reports FPO_ERR_DEVICE_TIMEOUT through
+     * fpo_status_sync; the frame's pixels are undefined, and the context
+     * renders normally afterwards. */
+    FPO_FLAG_TEST_DEVICE_TIMEOUT = 64
 };
 
 /* Per-call options.  bg: background colour added with the final
@@ -205,8 +223,11 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
 /* Renders a sequence of frames (e.g. the frames of a free-viewpoint video)
  * into out_rgb, device [n_frames][rays][3]; every frame has the same number
  * of rays (camera or explicit rays without per-ray times) and the same
- * options, which carry no debug outputs (flags must be 0; events are
- * ignored).  The result equals n_frames calls of fpo_render.  In the table
+ * options, which carry no debug outputs (flags must be 0; opts->events are
+ * ignored).  frame_done: NULL, or host array [n_frames] of cudaEvent_t
+ * handles (NULL entries allowed); event k is recorded on cuda_stream once
+ * frame k's pixels are written, so a caller can read frame k back while
+ * later frames render.  The result equals n_frames calls of fpo_render.  In the table
  * mode the work is pipelined: the per-frame table of frame k+1 is computed
  * on an internal second stream, into a second table, while frame k is
  * traversed on cuda_stream (the call orders that stream after its own
@@ -216,7 +237,8 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
  * carveout that holds them all), whatever traverse_threads says; LATENT
  * storage keeps the single-frame shapes.  Errors: as fpo_render. */
 int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames,
-                      const fpo_frame_opts *opts, float *out_rgb, void *cuda_stream);
+                      const fpo_frame_opts *opts, float *out_rgb, void *const *frame_done,
+                      void *cuda_stream);
 
 /* Adjoint of fpo_render (the back-propagation of Sec. 4.3, used to fine-tune
  * the leaf coefficients against the loss of Eq. 13): given dL/d(rgb) (device
@@ -231,6 +253,7 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames,
  * Of the debug flags only FPO_FLAG_MARK_LEAVES is honoured: it sets
  * leaf_mark[id] = 1 for every leaf the replay visits (the rows that receive
  * gradient), which fpo_adam_leaves consumes; the others are ignored.
+ * FPO_FLAG_FP64_GRADCHECK selects the FP64 replay (see the flag).
  * Errors: INVALID_ARG, NO_TREE, UNSUPPORTED, CUDA. */
 int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
                         const float *out_rgb, const float *dL_drgb, float *dL_dcoeffs,
@@ -365,6 +388,15 @@ int fpo_decoder_grad(const fpo_mlp *w, int32_t n1, int32_t n2, uint32_t batch, c
                      const float *extra_dy, const fpo_mlp *grad, float *dlatents, double *loss,
                      void *cuda_stream);
 
+/* The decoded coefficients of n leaves in FP32: coeffs[i] = MLP(latents[i])
+ * (device [n][32] in, device [n][n1 + 27*n2] out, canonical order), with the
+ * FP32 master weights.  Used to put the decoder's current coefficients into
+ * an FP32 context (fpo_set_coeffs), e.g. for the render adjoint of a pixel
+ * loss while the decoder trains.  Runs on the current device and stream.
+ * Errors: INVALID_ARG, CUDA. */
+int fpo_decoder_forward(const fpo_mlp *w, int32_t n1, int32_t n2, uint32_t n, const float *latents,
+                        float *coeffs, void *cuda_stream);
+
 /* Adam step (Kingma & Ba 2015) with bias correction, step counted from 1:
  * dense over n elements (rows NULL), or over the rows of a batch (device
  * rows [n / dim], distinct; param, m, v [N][dim]; grad [n / dim][dim]).
@@ -395,7 +427,7 @@ void fpo_destroy(fpo_ctx *ctx);
 /* Message of the last failure on the calling thread ("" if none). */
 const char *fpo_last_error(void);
 
-/* ABI version: 100 * major + minor. */
+/* ABI version: 100 * major + minor (1.1: fpo_render_frames takes frame_done). */
 int fpo_version(void);
 
 #ifdef __cplusplus

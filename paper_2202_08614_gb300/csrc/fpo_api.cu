@@ -172,7 +172,7 @@ extern "C" {
 
 const char *fpo_last_error(void) { return g_err.c_str(); }
 
-int fpo_version(void) { return 100; }
+int fpo_version(void) { return 101; }
 
 int fpo_create(fpo_ctx **out, const fpo_config *cfg)
 {
@@ -390,8 +390,12 @@ TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, const f
     p.root_kind = ctx->root_kind;
     p.depth = ctx->depth;
     p.n_smem_nodes = ctx->n_smem_nodes;
-    p.grid_scale = (float)((double)(1u << ctx->depth) / ctx->aabb_size);
-    for (int k = 0; k < 3; ++k) p.amin[k] = (float)ctx->aabb_min[k];
+    p.grid_scale64 = (double)(1u << ctx->depth) / ctx->aabb_size;
+    p.grid_scale = (float)p.grid_scale64;
+    for (int k = 0; k < 3; ++k) {
+        p.amin64[k] = ctx->aabb_min[k];
+        p.amin[k] = (float)ctx->aabb_min[k];
+    }
     p.table = reinterpret_cast<const float4 *>(ctx->d_table);
     p.sig = reinterpret_cast<const float4 *>(ctx->d_sig);
     p.zc = static_cast<const float *>(ctx->d_z);
@@ -433,7 +437,7 @@ TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, const f
 // With pipe_stages > 0 the pass takes the frame-pipeline shape with that many
 // stages (materialise_pipeline_shape), co-scheduled with the traversal.
 int launch_table_pass(const fpo_ctx *ctx, double t, float *table, int max_ctas_per_sm, void *stream,
-                      int pipe_stages, int carveout)
+                      int pipe_stages, int carveout, bool test_timeout)
 {
     const cudaStream_t s = (cudaStream_t)stream;
     if (ctx->cfg.storage == FPO_STORAGE_LATENT) {
@@ -453,6 +457,7 @@ int launch_table_pass(const fpo_ctx *ctx, double t, float *table, int max_ctas_p
         lp.table = table;
         lp.half_table = ctx->half_table;
         lp.status = ctx->d_status;
+        lp.test_timeout = test_timeout;
         return launch_latent_table(lp, ctx->sm_count, s);
     }
     MaterialiseParams mp{};
@@ -475,6 +480,7 @@ int launch_table_pass(const fpo_ctx *ctx, double t, float *table, int max_ctas_p
     mp.t = t;
     mp.period_T = ctx->cfg.period_T;
     mp.status = ctx->d_status;
+    mp.test_timeout = test_timeout;
     return launch_materialise(mp, ctx->sm_count, s);
 }
 
@@ -525,9 +531,10 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
     }
     if (mat && !((fl & FPO_FLAG_REUSE_TABLE) && ctx->table_ok && ctx->table_t == rays->t)) {
         ctx->table_ok = false;
-        const int ce = launch_table_pass(ctx, rays->t, ctx->d_table, 0, s, 0, 0);
+        const int ce = launch_table_pass(ctx, rays->t, ctx->d_table, 0, s, 0, 0,
+                                         (fl & FPO_FLAG_TEST_DEVICE_TIMEOUT) != 0);
         if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "IDFT table launch");
-        ctx->table_ok = true;
+        ctx->table_ok = (fl & FPO_FLAG_TEST_DEVICE_TIMEOUT) == 0;
         ctx->table_t = rays->t;
     }
     if ((e = rec(1)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
@@ -542,7 +549,7 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
 }
 
 int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, const fpo_frame_opts *opts,
-                      float *out_rgb, void *cuda_stream)
+                      float *out_rgb, void *const *frame_done, void *cuda_stream)
 {
     if (!ctx || !opts || (n_frames && !frames)) return fail(FPO_ERR_INVALID_ARG, "NULL argument");
     if (!ctx->has_tree) return fail(FPO_ERR_NO_TREE, "render before fpo_upload_tree");
@@ -567,6 +574,10 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
         for (uint32_t k = 0; k < n_frames; ++k) {
             const int st = fpo_render(ctx, &frames[k], &o1, out_rgb + (size_t)k * R * 3, cuda_stream);
             if (st != FPO_OK) return st;
+            if (frame_done && frame_done[k]) {
+                const cudaError_t e = cudaEventRecord((cudaEvent_t)frame_done[k], (cudaStream_t)cuda_stream);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(frame_done)");
+            }
         }
         return FPO_OK;
     }
@@ -622,8 +633,8 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
         const int b = (int)(k & 1);
         float *tbl = b ? ctx->d_table2 : ctx->d_table;
         if (k >= 2 && (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_trav[b], 0)) != cudaSuccess) return cuda_fail(e, "wait");
-        int ce = overlap ? launch_table_pass(ctx, frames[k].t, tbl, mshape.ctas_per_sm, ctx->aux, mshape.stages, carveout)
-                         : launch_table_pass(ctx, frames[k].t, tbl, 0, ctx->aux, 0, 0);
+        int ce = overlap ? launch_table_pass(ctx, frames[k].t, tbl, mshape.ctas_per_sm, ctx->aux, mshape.stages, carveout, false)
+                         : launch_table_pass(ctx, frames[k].t, tbl, 0, ctx->aux, 0, 0, false);
         if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "IDFT table launch");
         if ((e = cudaEventRecord(ctx->ev_mat[b], ctx->aux)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(s, ctx->ev_mat[b], 0)) != cudaSuccess)
@@ -638,6 +649,8 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
         ce = launch_traverse(p, true, false, ctx->sm_count, s);
         if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "traverse launch");
         if ((e = cudaEventRecord(ctx->ev_trav[b], s)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        if (frame_done && frame_done[k] && (e = cudaEventRecord((cudaEvent_t)frame_done[k], s)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventRecord(frame_done)");
     }
     return FPO_OK;
 }
@@ -657,8 +670,9 @@ int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts
         return fail(FPO_ERR_UNSUPPORTED, "the adjoint supports (n1, n2) in {(31,5), (11,5), (21,5), (31,11)}");
     if (n_rays > 0 && (!out_rgb || !dL_drgb)) return fail(FPO_ERR_INVALID_ARG, "out_rgb and dL_drgb must be non-NULL");
     if (ctx->n_leaves > 0 && !dL_dcoeffs) return fail(FPO_ERR_INVALID_ARG, "dL_dcoeffs is NULL");
-    if (reinterpret_cast<uintptr_t>(dL_dcoeffs) % 16 != 0)
-        return fail(FPO_ERR_INVALID_ARG, "dL_dcoeffs must be 16-byte aligned");
+    const bool fp64 = (opts->flags & FPO_FLAG_FP64_GRADCHECK) != 0;
+    if (reinterpret_cast<uintptr_t>(dL_dcoeffs) % (fp64 ? 8 : 16) != 0)
+        return fail(FPO_ERR_INVALID_ARG, fp64 ? "dL_dcoeffs must be 8-byte aligned" : "dL_dcoeffs must be 16-byte aligned");
     if (!(opts->stop_T >= 0.0f)) return fail(FPO_ERR_INVALID_ARG, "stop_T must be >= 0");
     if (n_rays == 0 || ctx->n_leaves == 0) return FPO_OK;
     DeviceGuard g(ctx->cfg.device);
@@ -671,7 +685,8 @@ int fpo_render_backward(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts
     q.tp = traverse_params(ctx, rays, &o, nullptr, n_rays);
     q.out_rgb = out_rgb;
     q.dL_drgb = dL_drgb;
-    q.dL_dcoeffs = dL_dcoeffs;
+    q.dL_dcoeffs = fp64 ? nullptr : dL_dcoeffs;
+    q.dL_dcoeffs64 = fp64 ? reinterpret_cast<double *>(dL_dcoeffs) : nullptr;
     q.leaf_mark = mark ? opts->leaf_mark : nullptr;
     const int ce = launch_backward(q, ctx->sm_count, cuda_stream);
     if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "backward launch");

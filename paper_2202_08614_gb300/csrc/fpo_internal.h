@@ -74,6 +74,8 @@ static_assert(TILE_W * TILE_H == 32, "a tile is one warp of rays");
 
 // Device status word bits.
 constexpr uint32_t STATUS_TRAVERSAL_LIMIT = 1u, STATUS_VISIT_OVERFLOW = 2u, STATUS_DEVICE_TIMEOUT = 4u;
+// Limit of the waits that FPO_FLAG_TEST_DEVICE_TIMEOUT makes run out: 1 ms.
+constexpr uint64_t TEST_WAIT_LIMIT_NS = 1000000ull;
 
 struct PackedTree {
     uint32_t root_kind = ROOT_EMPTY;
@@ -108,6 +110,7 @@ struct TraverseParams {
     uint32_t n_smem_nodes;
     float grid_scale;         // 2^D / aabb_size
     float amin[3];
+    double grid_scale64, amin64[3];  // the same in FP64 (gradient-check replay)
     // leaf data
     const float4 *table;      // per-frame IDFT table (materialised mode)
     int half_table;           // the table holds FP16 (64-byte lines) instead of FP32 (128-byte lines)
@@ -152,6 +155,7 @@ struct MaterialiseParams {
     int carveout;             // preferred shared-memory carveout in percent (0: the driver's default)
     double t, period_T;
     uint32_t *status;
+    int test_timeout;         // 1: the first wait of each CTA gives up (failure-path test)
 };
 
 // Read-only view of a context's uploaded tree and launch settings.
@@ -189,8 +193,9 @@ TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, const f
 // (at most max_ctas_per_sm CTAs per SM when > 0; with pipe_stages > 0 the
 // frame-pipeline shape with that many stages and the given carveout).
 // Returns a cudaError_t.
+// test_timeout: the failure-path test of FPO_FLAG_TEST_DEVICE_TIMEOUT.
 int launch_table_pass(const fpo_ctx *ctx, double t, float *table, int max_ctas_per_sm, void *stream,
-                      int pipe_stages, int carveout);
+                      int pipe_stages, int carveout, bool test_timeout);
 
 // Latent decoder (per-leaf FP16 latents, MLP 32 -> 64 -> 64 -> n1 + 27 n2,
 // ReLU).  Weights are BF16 bit patterns, row-major [out][in]; biases FP32.
@@ -208,6 +213,7 @@ struct LatentParams {
     float *table;             // [n_leaves][TABLE_STRIDE] FP32, or FP16 when half_table
     int half_table;
     uint32_t *status;
+    int test_timeout;         // 1: each warpgroup's first wait gives up (failure-path test)
     CUtensorMap table_map;    // set by launch_latent_table: the table as a [n_leaves][32] tensor
 };
 
@@ -229,6 +235,8 @@ int launch_decoder_grad(const DecoderGradParams &p, int sm_count, void *stream);
 int launch_gather_rows(const void *src, void *dst, const uint32_t *perm, uint32_t n, uint32_t bytes,
                        int sm_count, void *stream);
 int decoder_grad_max_coeffs();
+int launch_decoder_forward(const fpo_mlp &w, int nc, uint32_t n, const float *latents, float *out, int sm_count,
+                           void *stream);
 int launch_adam(float *param, const float *grad, float *m, float *v, uint64_t n, const uint32_t *rows, uint32_t dim,
                 float lr, float b1, float b2, float eps, uint32_t step, int sm_count, void *stream);
 
@@ -237,6 +245,7 @@ struct BackwardParams {
     const float *out_rgb;       // forward colour [rays][3]
     const float *dL_drgb;       // [rays][3]
     float *dL_dcoeffs;          // [n_leaves][n1 + 27 n2], canonical, upload order (accumulated)
+    double *dL_dcoeffs64;       // the same in FP64 (gradient-check replay), else nullptr
     uint8_t *leaf_mark;         // optional [n_leaves] (upload order): set to 1 for every visited leaf
 };
 

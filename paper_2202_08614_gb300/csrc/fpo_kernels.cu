@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
 {
     extern __shared__ __align__(128) unsigned char mat_smem[];
     __shared__ uint64_t bars[MAT_MAX_STAGES];
+    __shared__ uint64_t never;  // FPO_FLAG_TEST_DEVICE_TIMEOUT: a barrier nothing signals
     __shared__ float s_b[MAX_BASIS];
     __shared__ int s_fail;
     const int tid = threadIdx.x;
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
     if (tid == 0) {
         s_fail = 0;
         for (int s = 0; s < S; ++s) ptx::mbar_init(&bars[s], 1);
+        ptx::mbar_init(&never, 1);
         ptx::fence_barrier_init();
     }
     __syncthreads();
@@ -201,7 +203,11 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
         if (c >= n_chunks) break;
         const int s = (int)(it % (uint32_t)S);
         const uint32_t parity = (it / (uint32_t)S) & 1u;
-        if (!ptx::mbar_wait_bounded(&bars[s], parity, WAIT_LIMIT_NS)) s_fail = 1;
+        // (the failure-path test makes the first wait run out; the drain below
+        // still waits for every copy in flight)
+        const bool ok = p.test_timeout && it == 0 ? ptx::mbar_wait_bounded(&never, 0, TEST_WAIT_LIMIT_NS)
+                                                  : ptx::mbar_wait_bounded(&bars[s], parity, WAIT_LIMIT_NS);
+        if (!ok) s_fail = 1;
         __syncthreads();
         if (s_fail) break;
         const uint32_t first = c * MAT_CHUNK;
@@ -300,6 +306,7 @@ __global__ void __launch_bounds__(CH) materialise_leaf_kernel(const __grid_const
 {
     extern __shared__ __align__(128) unsigned char mat_smem[];
     __shared__ uint64_t bars[MAT_MAX_STAGES];
+    __shared__ uint64_t never;  // FPO_FLAG_TEST_DEVICE_TIMEOUT: a barrier nothing signals
     __shared__ float s_b[MAX_BASIS];
     __shared__ int s_fail;
     const int tid = threadIdx.x;
@@ -318,6 +325,7 @@ __global__ void __launch_bounds__(CH) materialise_leaf_kernel(const __grid_const
     if (tid == 0) {
         s_fail = 0;
         for (int s = 0; s < S; ++s) ptx::mbar_init(&bars[s], 1);
+        ptx::mbar_init(&never, 1);
         ptx::fence_barrier_init();
     }
     __syncthreads();
@@ -357,7 +365,11 @@ __global__ void __launch_bounds__(CH) materialise_leaf_kernel(const __grid_const
         if (c >= n_chunks) break;
         const int s = (int)(it % (uint32_t)S);
         const uint32_t parity = (it / (uint32_t)S) & 1u;
-        if (!ptx::mbar_wait_bounded(&bars[s], parity, WAIT_LIMIT_NS)) s_fail = 1;
+        // (the failure-path test makes the first wait run out; the drain below
+        // still waits for every copy in flight)
+        const bool ok = p.test_timeout && it == 0 ? ptx::mbar_wait_bounded(&never, 0, TEST_WAIT_LIMIT_NS)
+                                                  : ptx::mbar_wait_bounded(&bars[s], parity, WAIT_LIMIT_NS);
+        if (!ok) s_fail = 1;
         __syncthreads();
         if (s_fail) break;
         const uint32_t first = c * CH;
@@ -1484,14 +1496,224 @@ static int launch_b(const BackwardParams &q, int sm_count, cudaStream_t s)
     return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Gradient-check replay (FPO_FLAG_FP64_GRADCHECK).  The FP32 stepping above
+// decides which leaves the ray visits and in which order (as the forward
+// does); each visited leaf's segment is re-measured by an FP64 slab test of
+// its box along the FP64-normalised ray, and the IDFT (Eq. 7, 9), the SH
+// colour (Eq. 1), the transmittance products and S_j are FP64.  Two replays
+// per ray: the first composites the FP64 colour C (with T_end bg), the second
+// forms S_j = C - sum_{k<=j} w_k c_k and the gradients, accumulated with FP64
+// atomics.
+
+struct Ray64 {
+    double go[3], gd[3];  // origin and unit direction, in grid units
+    double Y[9];          // real SH of the unit direction
+    double b[MAX_BASIS];  // Eq. 8 at the ray's time
+};
+
+__device__ __forceinline__ void sh_basis64(double x, double y, double z, double Y[9])
+{
+    const double c0 = 0.28209479177387814, c1 = 0.48860251190291992, c2 = 1.09254843059207907,
+                 c3 = 0.31539156525252005, c4 = 0.54627421529603959;
+    Y[0] = c0;
+    Y[1] = -c1 * y;
+    Y[2] = c1 * z;
+    Y[3] = -c1 * x;
+    Y[4] = c2 * x * y;
+    Y[5] = -c2 * y * z;
+    Y[6] = c3 * (3.0 * z * z - 1.0);
+    Y[7] = -c2 * x * z;
+    Y[8] = c4 * (x * x - y * y);
+}
+
+// The FP64 ray of ray index `ray` (camera pixel or explicit ray), as the
+// oracle forms it: camera frame and pixel direction in FP64, or the FP32
+// inputs widened, then normalised in FP64.
+__device__ void ray64_setup(const TraverseParams &p, uint32_t ray, int px, int py, Ray64 &r)
+{
+    double o[3], d[3], t = p.fr.t;
+    if (p.fr.mode == FPO_RAYS_CAMERA) {
+        double f[3], rt[3], u[3];
+        for (int k = 0; k < 3; ++k) f[k] = p.fr.target[k] - p.fr.eye[k];
+        const double fl = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        for (int k = 0; k < 3; ++k) f[k] /= fl;
+        rt[0] = f[1] * p.fr.up[2] - f[2] * p.fr.up[1];
+        rt[1] = f[2] * p.fr.up[0] - f[0] * p.fr.up[2];
+        rt[2] = f[0] * p.fr.up[1] - f[1] * p.fr.up[0];
+        const double rl = sqrt(rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2]);
+        for (int k = 0; k < 3; ++k) rt[k] /= rl;
+        u[0] = rt[1] * f[2] - rt[2] * f[1];
+        u[1] = rt[2] * f[0] - rt[0] * f[2];
+        u[2] = rt[0] * f[1] - rt[1] * f[0];
+        const double th = tan(0.5 * p.fr.fov_y_deg * 3.14159265358979323846 / 180.0);
+        const double sx = (2.0 * ((double)px + 0.5) / (double)p.fr.width - 1.0) * th * ((double)p.fr.width / (double)p.fr.height);
+        const double sy = (1.0 - 2.0 * ((double)py + 0.5) / (double)p.fr.height) * th;
+        for (int k = 0; k < 3; ++k) {
+            o[k] = p.fr.eye[k];
+            d[k] = f[k] + sx * rt[k] + sy * u[k];
+        }
+    } else {
+        for (int k = 0; k < 3; ++k) {
+            o[k] = (double)p.fr.ro[3 * (size_t)ray + k];
+            d[k] = (double)p.fr.rd[3 * (size_t)ray + k];
+        }
+        if (p.fr.rt) t = (double)p.fr.rt[ray];
+    }
+    const double dl = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int k = 0; k < 3; ++k) {
+        d[k] /= dl;
+        r.go[k] = (o[k] - p.amin64[k]) * p.grid_scale64;
+        r.gd[k] = d[k] * p.grid_scale64;
+    }
+    sh_basis64(d[0], d[1], d[2], r.Y);
+    const int nb = p.n1 > p.n2 ? p.n1 : p.n2;
+    const double u = t / p.fr.period_T;
+    for (int i = 0; i < nb; ++i) r.b[i] = (i & 1) ? sinpi((double)(i + 1) * u) : cospi((double)i * u);
+}
+
+// Length (along the unit ray, t >= 0) of the ray inside the box
+// [lo, lo + csz]^3 (grid units): the FP64 slab test.
+__device__ __forceinline__ double segment64(const Ray64 &r, const int lo[3], int csz)
+{
+    double t0 = 0.0, t1 = 1.0e300;
+    for (int a = 0; a < 3; ++a) {
+        if (r.gd[a] == 0.0) continue;
+        const double ta = ((double)lo[a] - r.go[a]) / r.gd[a], tb = ((double)(lo[a] + csz) - r.go[a]) / r.gd[a];
+        t0 = fmax(t0, fmin(ta, tb));
+        t1 = fmin(t1, fmax(ta, tb));
+    }
+    return t1 - t0;
+}
+
+// One replay of a ray: pass 0 composites C (returned with T_end bg added);
+// pass 1 accumulates the gradients with C from pass 0.
+template <int N1, int N2>
+__device__ void replay_fp64(const BackwardParams &q, RayState R, const Ray64 &r, int pass, double C[3],
+                            const uint32_t *__restrict__ s_nodes, uint32_t *s_stack, int stride)
+{
+    constexpr int NC = N1 + 27 * N2;
+    const TraverseParams &p = q.tp;
+    const int D = p.depth, G = 1 << D;
+    double g[3] = {0.0, 0.0, 0.0};
+    if (pass == 1)
+        for (int c = 0; c < 3; ++c) g[c] = (double)q.dL_drgb[3 * (size_t)R.ray + c];
+    double T = 1.0, P[3] = {0.0, 0.0, 0.0};
+    for (;;) {
+        const Cube cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start);
+        int m, lo[3], csz;
+        const float tx = cube_exit(R, D, cb.lvl, m, lo, csz);
+        if (cb.kind == ROOT_LEAF && tx > R.t) {
+            const double delta = segment64(r, lo, csz);
+            const float *sr = reinterpret_cast<const float *>(p.sig + (size_t)cb.leaf * p.sig_stride4);
+            const float *zr = p.zc + (size_t)cb.leaf * p.z_stride;
+            double sraw = 0.0;
+            for (int i = 0; i < N1; ++i) sraw += (double)sr[i] * r.b[i];
+            const double sigma = sraw > 0.0 ? sraw : 0.0;
+            double col[3];
+            for (int c = 0; c < 3; ++c) {
+                double u = 0.0;
+                for (int k = 0; k < 9; ++k) {
+                    double z = 0.0;
+                    for (int i = 0; i < N2; ++i) z += (double)zr[(c * 9 + k) * N2 + i] * r.b[i];
+                    u += z * r.Y[k];
+                }
+                col[c] = 1.0 / (1.0 + exp(-u));
+            }
+            const double e = exp(-sigma * delta);
+            const double w = T * (1.0 - e), Tn = T * e;
+            for (int c = 0; c < 3; ++c) P[c] += w * col[c];
+            if (pass == 1) {
+                double gs = 0.0;
+                for (int c = 0; c < 3; ++c) gs += g[c] * delta * (Tn * col[c] - (C[c] - P[c]));
+                double *row = q.dL_dcoeffs64 + (size_t)p.perm[cb.leaf] * NC;
+                if (sraw > 0.0)
+                    for (int i = 0; i < N1; ++i) atomicAdd(row + i, gs * r.b[i]);
+                for (int c = 0; c < 3; ++c) {
+                    const double du = g[c] * w * col[c] * (1.0 - col[c]);
+                    for (int k = 0; k < 9; ++k)
+                        for (int i = 0; i < N2; ++i) atomicAdd(row + N1 + (c * 9 + k) * N2 + i, du * r.Y[k] * r.b[i]);
+                }
+                if (q.leaf_mark) q.leaf_mark[p.perm[cb.leaf]] = 1;
+            }
+            T = Tn;
+            if (T < (double)p.stop_T) break;
+        }
+        int Pn[3];
+        if (!next_cell(R, G, m, lo, csz, tx, Pn)) break;
+        move_to(R, D, Pn, tx);
+        if (step_cap(p, R)) break;
+    }
+    if (pass == 0)
+        for (int c = 0; c < 3; ++c) C[c] = P[c] + T * (double)p.bg[c];
+}
+
+template <int N1, int N2>
+__global__ void __launch_bounds__(128) backward_fp64_kernel(const __grid_constant__ BackwardParams q)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ FrameShared fs;
+    const TraverseParams &p = q.tp;
+    const int stride = blockDim.x;
+    uint32_t *s_nodes = smem;
+    uint32_t *s_stack = smem + p.n_smem_nodes * 8;
+    float *s_bray = reinterpret_cast<float *>(s_stack + STACK_LEVELS * stride);
+    frame_prologue(p, s_nodes, fs);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    uint32_t *my_stack = s_stack + threadIdx.x;
+    for (;;) {
+        uint32_t tile = 0;
+        if (lane == 0) tile = atomicAdd(p.status + 1, 1u);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= p.n_tiles) break;
+        uint32_t ray;
+        int px = 0, py = 0;
+        if (!tile_ray(p, tile, (uint32_t)lane, ray, px, py)) continue;
+        RayState R0;
+        // the FP32 ray as the forward sets it up (it decides the stepping)
+        if (!init_ray_geom(p, fs, false, s_bray + threadIdx.x, stride, my_stack, R0, ray, px, py)) continue;
+        Ray64 r;
+        ray64_setup(p, ray, px, py, r);
+        double C[3];
+        replay_fp64<N1, N2>(q, R0, r, 0, C, s_nodes, my_stack, stride);
+        replay_fp64<N1, N2>(q, R0, r, 1, C, s_nodes, my_stack, stride);
+    }
+    if (lane == 0) {
+        __threadfence();
+        const uint32_t done = atomicAdd(p.status + 2, 1u);
+        if (done == gridDim.x * (blockDim.x / 32) - 1) {
+            atomicExch(p.status + 1, 0u);
+            atomicExch(p.status + 2, 0u);
+        }
+    }
+}
+
+template <int N1, int N2>
+static int launch_b64(const BackwardParams &q, int sm_count, cudaStream_t s)
+{
+    const TraverseParams &p = q.tp;
+    const int threads = 128;
+    const int smem = traverse_smem_bytes(p.n_smem_nodes, false, threads);
+    auto k = backward_fp64_kernel<N1, N2>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return (int)e;
+    const uint64_t need = (p.n_tiles + (threads / 32) - 1) / (threads / 32);
+    uint64_t blocks = (uint64_t)sm_count * 4;
+    if (need < blocks) blocks = need ? need : 1;
+    k<<<(unsigned)blocks, threads, smem, s>>>(q);
+    return (int)cudaGetLastError();
+}
+
 int launch_backward(const BackwardParams &q, int sm_count, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
     const TraverseParams &p = q.tp;
-    if (p.n1 == 31 && p.n2 == 5) return launch_b<31, 5>(q, sm_count, s);
-    if (p.n1 == 11 && p.n2 == 5) return launch_b<11, 5>(q, sm_count, s);
-    if (p.n1 == 21 && p.n2 == 5) return launch_b<21, 5>(q, sm_count, s);
-    if (p.n1 == 31 && p.n2 == 11) return launch_b<31, 11>(q, sm_count, s);
+    const bool fp64 = q.dL_dcoeffs64 != nullptr;
+    if (p.n1 == 31 && p.n2 == 5) return fp64 ? launch_b64<31, 5>(q, sm_count, s) : launch_b<31, 5>(q, sm_count, s);
+    if (p.n1 == 11 && p.n2 == 5) return fp64 ? launch_b64<11, 5>(q, sm_count, s) : launch_b<11, 5>(q, sm_count, s);
+    if (p.n1 == 21 && p.n2 == 5) return fp64 ? launch_b64<21, 5>(q, sm_count, s) : launch_b<21, 5>(q, sm_count, s);
+    if (p.n1 == 31 && p.n2 == 11) return fp64 ? launch_b64<31, 11>(q, sm_count, s) : launch_b<31, 11>(q, sm_count, s);
     return -1;
 }
 

@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __gri
     unsigned char *lt_smem = lt_smem_raw + ((1024u - (ptx::smem_u32(lt_smem_raw) & 1023u)) & 1023u);
     __shared__ float s_basis[32];
     __shared__ uint64_t s_bar[LT_GROUPS];
+    __shared__ uint64_t s_never;  // FPO_FLAG_TEST_DEVICE_TIMEOUT: a barrier nothing signals
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail[LT_GROUPS];
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -208,6 +209,7 @@ __global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __gri
     if (tid < LT_GROUPS) {
         s_fail[tid] = 0;
         ptx::mbar_init(&s_bar[tid], 1);
+        if (tid == 0) ptx::mbar_init(&s_never, 1);
         ptx::fence_barrier_init();
     }
     if (warp == 0) {
@@ -283,18 +285,26 @@ __global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __gri
 
     // One layer: the group's elected thread issues the MMAs and commits;
     // the group waits on its mbarrier (bounded).  The outcome is made
-    // group-uniform so that the collective TMEM loads never diverge.
+    // group-uniform so that the collective TMEM loads never diverge.  On a
+    // time-out `phase` stays at the pending commit, which the drain after
+    // the loop waits for before TMEM is freed.  The failure-path test makes
+    // the group's first wait (on a barrier nothing signals) run out.
+    bool first_wait = p.test_timeout != 0;
     auto run_layer = [&](uint32_t a_addr, uint32_t b_addr, int K, int N) -> bool {
         if (gt == 0) {
             fence_after();
             gemm(tmem, a_addr, b_addr, K, N);
             mma_commit(&s_bar[group]);
         }
-        if (!ptx::mbar_wait_bounded(&s_bar[group], phase, LT_WAIT_NS)) s_fail[group] = 1;
-        phase ^= 1u;
+        const bool ok = first_wait ? ptx::mbar_wait_bounded(&s_never, 0, TEST_WAIT_LIMIT_NS)
+                                   : ptx::mbar_wait_bounded(&s_bar[group], phase, LT_WAIT_NS);
+        first_wait = false;
+        if (!ok) s_fail[group] = 1;
         group_sync(group);
         fence_after();
-        return s_fail[group] == 0;
+        if (s_fail[group]) return false;
+        phase ^= 1u;
+        return true;
     };
     auto hand_off = [&]() {  // generic smem writes and TMEM reads before the next MMA
         fence_async_smem();
@@ -392,7 +402,8 @@ __global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __gri
     }
     if (gt == 0) bulk_wait_all();  // every table store has completed
     if (s_fail[group] && gt == 0) {
-        // an MMA that never signalled: wait once more (bounded) before freeing TMEM
+        // the commit whose wait gave up: wait for it once more (bounded)
+        // before TMEM is freed
         ptx::mbar_wait_bounded(&s_bar[group], phase, LT_WAIT_NS);
         if (p.status) atomicOr(p.status, STATUS_DEVICE_TIMEOUT);
     }

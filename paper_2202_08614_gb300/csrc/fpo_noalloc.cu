@@ -108,7 +108,7 @@ extern "C" int fpo_render_noalloc(fpo_ctx *ctx, const fpo_rays *rays, const fpo_
     const bool mat = c.n_leaves > 0;
     if (mat) {
         // Every table entry the traversal reads is written first: nothing to clear.
-        const int ce = launch_table_pass(ctx, rays->t, table, 0, s, 0, 0);
+        const int ce = launch_table_pass(ctx, rays->t, table, 0, s, 0, 0, (fl & FPO_FLAG_TEST_DEVICE_TIMEOUT) != 0);
         if (ce != cudaSuccess) return cuda_err((cudaError_t)ce, "IDFT table launch");
     }
     if ((e = rec(1)) != cudaSuccess) return cuda_err(e, "cudaEventRecord");

@@ -179,6 +179,141 @@ int launch_decoder_grad(const DecoderGradParams &p, int sm_count, void *stream)
 
 int decoder_grad_max_coeffs() { return TG_MAXC; }
 
+// FP32 decode of every leaf: y = W3 relu(W2 relu(W1 x + b1) + b2) + b3.  A CTA
+// keeps the transposed weights in shared memory and walks tiles of 64 leaves;
+// each thread owns 4 rows x (outputs tc, tc + 16, ...) of a layer, so a warp
+// reads weight rows without bank conflicts and activations as broadcasts.
+constexpr int DF_ROWS = 64, DF_THREADS = 256, DF_MAXC = 176;
+
+struct DecodeSmem {
+    float w1t[32 * 64], w2t[64 * 64], w3t[64 * DF_MAXC], b1[64], b2[64], b3[DF_MAXC];
+    float x[DF_ROWS * 33], h1[DF_ROWS * 65], h2[DF_ROWS * 65];
+};
+
+__global__ void __launch_bounds__(DF_THREADS) decoder_forward_kernel(const fpo_mlp w, int nc, uint32_t n,
+                                                                      const float *__restrict__ latents,
+                                                                      float *__restrict__ out)
+{
+    extern __shared__ __align__(16) unsigned char df_raw[];
+    DecodeSmem &S = *reinterpret_cast<DecodeSmem *>(df_raw);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 64 * 32; i += DF_THREADS) S.w1t[(i & 31) * 64 + (i >> 5)] = w.w1[i];
+    for (int i = tid; i < 64 * 64; i += DF_THREADS) S.w2t[(i & 63) * 64 + (i >> 6)] = w.w2[i];
+    for (int i = tid; i < DF_MAXC * 64; i += DF_THREADS) {
+        const int c = i >> 6, k = i & 63;
+        S.w3t[k * DF_MAXC + c] = c < nc ? w.w3[c * 64 + k] : 0.0f;
+    }
+    for (int i = tid; i < 64; i += DF_THREADS) { S.b1[i] = w.b1[i]; S.b2[i] = w.b2[i]; }
+    for (int i = tid; i < DF_MAXC; i += DF_THREADS) S.b3[i] = i < nc ? w.b3[i] : 0.0f;
+    const int tr = tid >> 4, tc = tid & 15;  // rows 4 tr .. 4 tr + 3; outputs tc + 16 j
+    const uint32_t n_tiles = (n + DF_ROWS - 1) / DF_ROWS;
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const uint32_t r0 = tile * DF_ROWS;
+        const int nr = (int)min((uint32_t)DF_ROWS, n - r0);
+        __syncthreads();  // weights staged; the previous tile is done with x, h1, h2
+        for (int i = tid; i < DF_ROWS * 32; i += DF_THREADS) {
+            const int r = i >> 5;
+            S.x[r * 33 + (i & 31)] = r < nr ? latents[(size_t)(r0 + r) * 32 + (i & 31)] : 0.0f;
+        }
+        __syncthreads();
+        {
+            float a[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a[i][j] = S.b1[tc + 16 * j];
+#pragma unroll 4
+            for (int k = 0; k < 32; ++k) {
+                float xv[4], wv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) xv[i] = S.x[(4 * tr + i) * 33 + k];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) wv[j] = S.w1t[k * 64 + tc + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) a[i][j] = fmaf(xv[i], wv[j], a[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) S.h1[(4 * tr + i) * 65 + tc + 16 * j] = fmaxf(a[i][j], 0.0f);
+        }
+        __syncthreads();
+        {
+            float a[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a[i][j] = S.b2[tc + 16 * j];
+#pragma unroll 4
+            for (int k = 0; k < 64; ++k) {
+                float xv[4], wv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) xv[i] = S.h1[(4 * tr + i) * 65 + k];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) wv[j] = S.w2t[k * 64 + tc + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) a[i][j] = fmaf(xv[i], wv[j], a[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) S.h2[(4 * tr + i) * 65 + tc + 16 * j] = fmaxf(a[i][j], 0.0f);
+        }
+        __syncthreads();
+        {
+            constexpr int J = DF_MAXC / 16;
+            float a[4][J];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < J; ++j) a[i][j] = S.b3[tc + 16 * j];
+#pragma unroll 2
+            for (int k = 0; k < 64; ++k) {
+                float xv[4], wv[J];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) xv[i] = S.h2[(4 * tr + i) * 65 + k];
+#pragma unroll
+                for (int j = 0; j < J; ++j) wv[j] = S.w3t[k * DF_MAXC + tc + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < J; ++j) a[i][j] = fmaf(xv[i], wv[j], a[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = 4 * tr + i;
+                if (r < nr) {
+#pragma unroll
+                    for (int j = 0; j < J; ++j)
+                        if (tc + 16 * j < nc) out[(size_t)(r0 + r) * nc + tc + 16 * j] = a[i][j];
+                }
+            }
+        }
+    }
+}
+
+int launch_decoder_forward(const fpo_mlp &w, int nc, uint32_t n, const float *latents, float *out, int sm_count,
+                           void *stream)
+{
+    if (n == 0) return (int)cudaSuccess;
+    const int smem = (int)sizeof(DecodeSmem);
+    cudaError_t e = cudaFuncSetAttribute(decoder_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return (int)e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decoder_forward_kernel, DF_THREADS, smem);
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) per_sm = 1;
+    const uint32_t n_tiles = (n + DF_ROWS - 1) / DF_ROWS;
+    uint64_t blocks = (uint64_t)sm_count * per_sm;
+    if (blocks > n_tiles) blocks = n_tiles;
+    decoder_forward_kernel<<<(unsigned)blocks, DF_THREADS, smem, (cudaStream_t)stream>>>(w, nc, n, latents, out);
+    return (int)cudaGetLastError();
+}
+
 // Adam: m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
 // p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
 __global__ void adam_kernel(float *param, const float *grad, float *m, float *v, uint64_t n, const uint32_t *rows,
@@ -327,6 +462,23 @@ extern "C" int fpo_decoder_grad(const fpo_mlp *w, int32_t n1, int32_t n2, uint32
     p.loss = loss;
     p.nc = n1 + 27 * n2;
     const int ce = launch_decoder_grad(p, sms, cuda_stream);
+    if (ce != cudaSuccess) return set_last_error(FPO_ERR_CUDA, cudaGetErrorString((cudaError_t)ce));
+    return FPO_OK;
+}
+
+extern "C" int fpo_decoder_forward(const fpo_mlp *w, int32_t n1, int32_t n2, uint32_t n, const float *latents,
+                                   float *coeffs, void *cuda_stream)
+{
+    if (!w || !w->w1 || !w->b1 || !w->w2 || !w->b2 || !w->w3 || !w->b3)
+        return set_last_error(FPO_ERR_INVALID_ARG, "NULL weights");
+    if (n1 < 1 || n2 < 1 || n1 + 27 * n2 > DF_MAXC) return set_last_error(FPO_ERR_INVALID_ARG, "n1 + 27 n2 must be in [28, 176]");
+    if (n == 0) return FPO_OK;
+    if (!latents || !coeffs) return set_last_error(FPO_ERR_INVALID_ARG, "NULL array");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return set_last_error(FPO_ERR_CUDA, cudaGetErrorString(e));
+    const int ce = launch_decoder_forward(*w, n1 + 27 * n2, n, latents, coeffs, sms, cuda_stream);
     if (ce != cudaSuccess) return set_last_error(FPO_ERR_CUDA, cudaGetErrorString((cudaError_t)ce));
     return FPO_OK;
 }

@@ -17,7 +17,35 @@ of them (16 GB per step) to change a few.
 
 from __future__ import annotations
 
+import numpy as np
+
 from . import fpo
+
+
+def camera_ray_batch(cams, n, gen, n_frames=60):
+    """n training rays drawn uniformly over (camera, integer frame, pixel):
+    origins, unit directions (pixel centres of the pinhole model documented
+    in fpo.h) and frame times, as CUDA tensors.  `gen`: a CUDA torch.Generator."""
+    import torch
+
+    basis = []
+    for c in cams:
+        eye, tgt, up = (np.array(v, np.float64) for v in (c.eye, c.target, c.up))
+        f = (tgt - eye) / np.linalg.norm(tgt - eye)
+        r = np.cross(f, up)
+        r /= np.linalg.norm(r)
+        basis.append(np.concatenate([eye, f, r, np.cross(r, f)]))
+    B = torch.as_tensor(np.stack(basis), dtype=torch.float32, device="cuda")
+    W, H = cams[0].width, cams[0].height
+    th = np.tan(np.radians(cams[0].fov_y_deg) / 2)
+    v = torch.randint(0, len(cams), (n,), device="cuda", generator=gen)
+    p = torch.randint(0, W * H, (n,), device="cuda", generator=gen)
+    t = torch.randint(0, n_frames, (n,), device="cuda", generator=gen).float()
+    sx = ((2 * ((p % W).float() + 0.5) / W - 1) * th * W / H)[:, None]
+    sy = ((1 - 2 * ((p // W).float() + 0.5) / H) * th)[:, None]
+    b = B[v]
+    d = b[:, 3:6] + sx * b[:, 6:9] + sy * b[:, 9:12]
+    return b[:, 0:3].contiguous(), (d / d.norm(dim=1, keepdim=True)).contiguous(), t
 
 
 class FineTuner:

@@ -27,13 +27,15 @@ IDFT = {"auto": 0, "fused": 1, "materialise": 2}
 TABLE = {"auto": 0, "f32": 1, "f16": 2}
 RAYS_CAMERA, RAYS_EXPLICIT = 0, 1
 FLAG_RECORD_VISITS, FLAG_OUT_T, FLAG_MARK_LEAVES, FLAG_STATS, FLAG_REUSE_TABLE = 1, 2, 4, 8, 16
+FLAG_FP64_GRADCHECK, FLAG_TEST_DEVICE_TIMEOUT = 32, 64
 
 # Every symbol include/fpo.h declares.
 EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
            "fpo_render_backward", "fpo_status_sync", "fpo_tree_info_get", "fpo_destroy",
            "fpo_last_error", "fpo_version", "fpo_render_noalloc", "fpo_set_coeffs",
            "fpo_dft_leaves", "fpo_union_trees", "fpo_latent_table", "fpo_decoder_grad",
-           "fpo_adam", "fpo_set_latents", "fpo_render_frames", "fpo_adam_leaves"]
+           "fpo_adam", "fpo_set_latents", "fpo_render_frames", "fpo_adam_leaves",
+           "fpo_decoder_forward"]
 
 
 class FPOError(RuntimeError):
@@ -114,10 +116,11 @@ def lib():
                                        C.c_double, C.c_uint32, P, P, P, P]
         L.fpo_decoder_grad.argtypes = [C.POINTER(Mlp), C.c_int32, C.c_int32, C.c_uint32, P, P, P, P,
                                        P, C.POINTER(Mlp), P, P, P]
+        L.fpo_decoder_forward.argtypes = [C.POINTER(Mlp), C.c_int32, C.c_int32, C.c_uint32, P, P, P]
         L.fpo_adam.argtypes = [P, P, P, P, C.c_uint64, P, C.c_uint32, C.c_float, C.c_float,
                                C.c_float, C.c_float, C.c_uint32, P]
         L.fpo_set_latents.argtypes = [P, P, C.POINTER(Decoder), P]
-        L.fpo_render_frames.argtypes = [P, P, C.c_uint32, C.POINTER(FrameOpts), P, P]
+        L.fpo_render_frames.argtypes = [P, P, C.c_uint32, C.POINTER(FrameOpts), P, P, P]
         L.fpo_adam_leaves.argtypes = [P, P, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float,
                                       C.c_uint32, P]
         L.fpo_union_trees.argtypes = [C.c_uint32, P, C.c_uint32, C.POINTER(C.c_uint32), P, P, P,
@@ -218,7 +221,8 @@ class Renderer:
 
     def render(self, camera=None, t=0.0, rays_o=None, rays_d=None, t_per_ray=None,
                bg=(1.0, 1.0, 1.0), stop_T=1e-4, out=None, visit_cap=None, want_T=False,
-               leaf_mark=None, stats=None, stream=None, events=None, reuse_table=False):
+               leaf_mark=None, stats=None, stream=None, events=None, reuse_table=False,
+               test_timeout=False):
         """Renders one frame; returns a dict of device tensors.
 
         camera: an object with eye/target/up/fov_y_deg/width/height (pixel
@@ -228,6 +232,7 @@ class Renderer:
         visit_count [n] (leaf ids in upload order).  leaf_mark: optional CUDA
         uint8 tensor [n_leaves] set to 1 for visited leaves.  reuse_table:
         skip the IDFT pass when the last table was built for the same t.
+        test_timeout: the failure-path test (FPO_FLAG_TEST_DEVICE_TIMEOUT).
         """
         import torch
 
@@ -236,7 +241,7 @@ class Renderer:
         if out is None:
             out = torch.empty((n, 3), dtype=torch.float32, device=dev)
         return self._render_into(r, keep, n, out, bg, stop_T, visit_cap, want_T, leaf_mark, stats,
-                                 stream, events, reuse_table)
+                                 stream, events, reuse_table, test_timeout)
 
     def _rays(self, camera, t, rays_o, rays_d, t_per_ray):
         import torch
@@ -268,7 +273,7 @@ class Renderer:
         return r, keep, n
 
     def _render_into(self, r, keep, n, out, bg, stop_T, visit_cap, want_T, leaf_mark, stats,
-                     stream, events, reuse_table=False):
+                     stream, events, reuse_table=False, test_timeout=False):
         import torch
 
         dev = torch.device("cuda", self.device)
@@ -296,6 +301,8 @@ class Renderer:
             flags |= FLAG_STATS
         if reuse_table:
             flags |= FLAG_REUSE_TABLE
+        if test_timeout:
+            flags |= FLAG_TEST_DEVICE_TIMEOUT
         opts.flags = flags
         if events is not None:
             for i, ev in enumerate(events):
@@ -310,9 +317,11 @@ class Renderer:
         res["_keep"] = keep
         return res
 
-    def render_frames(self, cameras, times, bg=(1.0, 1.0, 1.0), stop_T=1e-4, out=None, stream=None):
+    def render_frames(self, cameras, times, bg=(1.0, 1.0, 1.0), stop_T=1e-4, out=None, stream=None,
+                      frame_events=None):
         """Renders camera frames (same size) into out [n_frames, W*H, 3] with the
-        pipelined fpo_render_frames."""
+        pipelined fpo_render_frames.  frame_events: optional torch.cuda.Event
+        per frame, recorded once that frame's pixels are written."""
         import torch
 
         n = len(cameras)
@@ -328,9 +337,19 @@ class Renderer:
         opts = FrameOpts()
         opts.bg = (C.c_float * 3)(*bg)
         opts.stop_T = float(stop_T)
+        done = None
+        if frame_events is not None:
+            assert len(frame_events) == n
+            done = (C.c_void_p * max(n, 1))()
+            for i, ev in enumerate(frame_events):
+                if ev is None:
+                    continue
+                if not ev.cuda_event:  # torch creates the CUDA event at its first record
+                    ev.record(stream)
+                done[i] = ev.cuda_event
         check(lib().fpo_render_frames(self.h, arr, n, C.byref(opts),
                                       C.c_void_p(out.data_ptr() if out.numel() else None),
-                                      C.c_void_p(_stream_handle(stream))))
+                                      done, C.c_void_p(_stream_handle(stream))))
         return out
 
     def set_coeffs(self, coeffs, stream=None):
@@ -357,16 +376,26 @@ class Renderer:
 
     def render_backward(self, out_rgb, dL_drgb, dL_dcoeffs, camera=None, t=0.0, rays_o=None,
                         rays_d=None, t_per_ray=None, bg=(1.0, 1.0, 1.0), stop_T=1e-4, leaf_mark=None,
-                        stream=None):
+                        stream=None, fp64=False):
         """Accumulates dL/d(coefficients) [n_leaves, n1 + 27 n2] (canonical) into
-        dL_dcoeffs; sets leaf_mark[id] = 1 (uint8 CUDA tensor) for visited leaves."""
+        dL_dcoeffs; sets leaf_mark[id] = 1 (uint8 CUDA tensor) for visited leaves.
+        fp64: the gradient-check replay (dL_dcoeffs is then a float64 tensor)."""
+        import torch
+
         r, keep, n = self._rays(camera, t, rays_o, rays_d, t_per_ray)
         opts = FrameOpts()
         opts.bg = (C.c_float * 3)(*bg)
         opts.stop_T = float(stop_T)
+        flags = 0
+        if fp64:
+            assert dL_dcoeffs.dtype == torch.float64
+            flags |= FLAG_FP64_GRADCHECK
+        else:
+            assert dL_dcoeffs.dtype == torch.float32
         if leaf_mark is not None:
-            opts.flags = FLAG_MARK_LEAVES
+            flags |= FLAG_MARK_LEAVES
             opts.leaf_mark = leaf_mark.data_ptr()
+        opts.flags = flags
         g = dL_drgb.contiguous()
         o = out_rgb.contiguous()
         check(lib().fpo_render_backward(self.h, C.byref(r), C.byref(opts),

@@ -3,10 +3,14 @@
 Each leaf gets a 32-dim latent; a shared MLP 32 -> 64 -> 64 -> n1 + 27 n2
 (ReLU) decodes its Fourier coefficients.  Training minimises the per-
 coefficient weighted squared error to target coefficients (those the Fourier
-PlenOctree generation produces); every gradient and update runs in libfpo
-(fpo_decoder_grad, fpo_adam).  PyTorch holds the arrays and draws the batches.
-Inference casts the latents to FP16 and the weights to BF16 for the
-tensor-core decoder (fpo_latent_table / LATENT storage).
+PlenOctree generation produces) plus, optionally, the rendered-pixel loss
+(PixelLoss): the squared error of rays rendered from the decoded coefficients
+against rays rendered from the targets, back-propagated through the render
+adjoint (the back-propagation of the fine-tuning stage, Sec. 4.3, Eq. 13) into
+the decoder.  Every gradient and update runs in libfpo (fpo_decoder_forward,
+fpo_render, fpo_render_backward, fpo_decoder_grad, fpo_adam); PyTorch holds the
+arrays and draws the batches.  Inference casts the latents to FP16 and the
+weights to BF16 for the tensor-core decoder (fpo_latent_table / LATENT storage).
 """
 
 from __future__ import annotations
@@ -67,12 +71,14 @@ class LatentModel:
     def init_output_bias(self, targets):
         self.p["b3"].copy_(targets.mean(0))
 
-    def grad(self, rows, targets, coef_weight, extra_dy=None, stream=None):
-        """Accumulates weight gradients into self.g; returns (dlatents, loss tensor)."""
+    def grad(self, rows, targets, coef_weight, extra_dy=None, stream=None, accumulate=False):
+        """Weight gradients into self.g (zeroed first unless `accumulate`);
+        returns (dlatents of the batch rows, loss tensor)."""
         import torch
 
-        for t in self.g.values():
-            t.zero_()
+        if not accumulate:
+            for t in self.g.values():
+                t.zero_()
         b = rows.shape[0]
         dl = torch.empty((b, 32), device=rows.device)
         loss = torch.zeros(1, dtype=torch.float64, device=rows.device)
@@ -86,6 +92,17 @@ class LatentModel:
             C.c_void_p(fpo._stream_handle(stream))))
         return dl, loss
 
+    def decode(self, out=None, stream=None):
+        """FP32 coefficients of every leaf [n, nc] (fpo_decoder_forward)."""
+        import torch
+
+        if out is None:
+            out = torch.empty((self.n, self.nc), device=self.p["lat"].device)
+        fpo.check(fpo.lib().fpo_decoder_forward(C.byref(self._mlp(self.p)), self.n1, self.n2, self.n,
+                                                C.c_void_p(self.p["lat"].data_ptr()), C.c_void_p(out.data_ptr()),
+                                                C.c_void_p(fpo._stream_handle(stream))))
+        return out
+
     def _adam(self, key, grad, lr, rows=None, dim=0, stream=None):
         p, m, v = self.p[key], self.m[key], self.v[key]
         n = grad.numel()
@@ -94,23 +111,44 @@ class LatentModel:
             C.c_void_p(v.data_ptr()), n, C.c_void_p(rows.data_ptr() if rows is not None else None),
             dim, lr, 0.9, 0.999, 1e-8, self.step_count, C.c_void_p(fpo._stream_handle(stream))))
 
-    def step(self, rows, targets, coef_weight, lr_w=1e-3, lr_lat=1e-2, extra_dy=None):
-        dl, loss = self.grad(rows, targets, coef_weight, extra_dy)
+    def step(self, rows, targets, coef_weight, lr_w=1e-3, lr_lat=1e-2, pixel=None):
+        """One Adam step on the batch `rows` (mean weighted L2 to `targets`).
+        pixel: optional (rows_px, dy) from PixelLoss.gradient: dL/d(decoded
+        coefficients) of the pixel loss for the leaves rows_px (dy is indexed
+        by leaf, [n, nc], already a mean over rays), added to the gradients."""
+        dl, loss = self.grad(rows, targets, coef_weight)
         self.step_count += 1
         scale = 1.0 / rows.shape[0]
         for k in self.g:
             self.g[k].mul_(scale)
         dl.mul_(scale)
+        dl_px = None
+        if pixel is not None:
+            rows_px, dy = pixel
+            if rows_px.shape[0]:
+                dl_px, _ = self.grad(rows_px, targets, self._zero_weight(targets.device), extra_dy=dy,
+                                     accumulate=True)
         for k in ("w1", "b1", "w2", "b2", "w3", "b3"):
             self._adam(k, self.g[k], lr_w)
         self._adam("lat", dl, lr_lat, rows=rows, dim=32)
+        if dl_px is not None:
+            self._adam("lat", dl_px, lr_lat, rows=pixel[0], dim=32)
         return loss
 
+    def _zero_weight(self, device):
+        import torch
+
+        if getattr(self, "_zw", None) is None:
+            self._zw = torch.zeros(self.nc, device=device)
+        return self._zw
+
     def fit(self, targets, steps, batch=65536, lr_w=1e-3, lr_lat=1e-2, coef_weight=None, seed=0,
-            log_every=0, decay=1.0, decay_from=0.7):
+            log_every=0, decay=1.0, decay_from=0.7, pixel=None):
         """Weighted L2 training on `targets` [n, nc]; returns the loss history.
         Learning rates stay at their start value until `decay_from` of the
-        steps, then follow a cosine down to `decay` times it."""
+        steps, then follow a cosine down to `decay` times it.  pixel: an
+        optional PixelLoss, applied every pixel.every steps from
+        pixel.start * steps on."""
         import torch
 
         dev = targets.device
@@ -128,7 +166,10 @@ class LatentModel:
             at += batch
             u = max(0.0, (s / max(1, steps - 1) - decay_from) / max(1e-9, 1.0 - decay_from))
             f = decay + (1.0 - decay) * 0.5 * (1.0 + math.cos(math.pi * min(1.0, u)))
-            loss = self.step(rows, targets, coef_weight, lr_w * f, lr_lat * f)
+            px = None
+            if pixel is not None and s >= pixel.start * steps and (s % pixel.every) == 0:
+                px = pixel.gradient(self)
+            loss = self.step(rows, targets, coef_weight, lr_w * f, lr_lat * f, pixel=px)
             if log_every and (s % log_every == 0 or s == steps - 1):
                 hist.append((s, float(loss.item()) / batch))
         return hist
@@ -139,3 +180,57 @@ class LatentModel:
 
         return (self.p["lat"].to(torch.float16), self.p["w1"], self.p["b1"], self.p["w2"],
                 self.p["b2"], self.p["w3"], self.p["b3"])
+
+
+class PixelLoss:
+    """The rendered-pixel term of the decoder's loss: rays drawn over the
+    training views and frames are rendered from the decoder's current
+    coefficients and from the target coefficients (both FP32 contexts with the
+    per-visit IDFT, since every ray has its own frame time); the mean squared
+    RGB error, times `weight`, is back-propagated by fpo_render_backward to
+    dL/d(coefficients) of the leaves the rays visit, which the decoder's
+    gradient takes as its extra dL/dy."""
+
+    def __init__(self, tree, cams, rays=8192, weight=1.0, every=4, start=0.0, seed=0, n_frames=60,
+                 bg=(1.0, 1.0, 1.0), stop_T=1e-4):
+        """tree: the target Fourier PlenOctree (leaf structure and target
+        coefficients, host arrays); cams: the training cameras."""
+        import torch
+
+        self.cams, self.rays, self.weight, self.every, self.start = cams, rays, weight, every, start
+        self.n_frames, self.bg, self.stop_T = n_frames, tuple(bg), float(stop_T)
+        self.ref = fpo.Renderer(n1=tree.n1, n2=tree.n2, idft_mode="fused")
+        self.ref.upload(tree)
+        self.work = fpo.Renderer(n1=tree.n1, n2=tree.n2, idft_mode="fused")
+        self.work.upload(tree)
+        n, nc = tree.coeffs.shape
+        self.dec = torch.empty((n, nc), device="cuda")
+        self.dy = torch.zeros((n, nc), device="cuda")
+        self.mark = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        self.gen = torch.Generator(device="cuda").manual_seed(seed)
+        self.last_loss = None
+
+    def gradient(self, model):
+        """(rows, dy): the visited leaves and dL/d(coefficients) [n, nc] of
+        the pixel loss at the model's current parameters."""
+        import torch
+
+        from .finetune import camera_ray_batch
+
+        model.decode(out=self.dec)
+        self.work.set_coeffs(self.dec)
+        o, d, t = camera_ray_batch(self.cams, self.rays, self.gen, self.n_frames)
+        kw = dict(rays_o=o, rays_d=d, t_per_ray=t, bg=self.bg, stop_T=self.stop_T)
+        y = self.ref.render(**kw)["rgb"]
+        rgb = self.work.render(**kw)["rgb"]
+        diff = rgb - y
+        self.last_loss = (diff * diff).sum(1).mean()
+        self.dy.zero_()
+        self.mark.zero_()
+        self.work.render_backward(rgb, diff * (2.0 * self.weight / self.rays), self.dy, leaf_mark=self.mark, **kw)
+        rows = torch.nonzero(self.mark).flatten().to(torch.int32)
+        return rows, self.dy
+
+    def close(self):
+        self.ref.close()
+        self.work.close()

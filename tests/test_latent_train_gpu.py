@@ -160,3 +160,47 @@ def test_training_fits_generated_coefficients():
     psnr = 10 * np.log10(1.0 / np.mean((img - ref) ** 2))
     print(f"latent render PSNR vs FP64 oracle of the generated FPO: {psnr:.2f} dB")
     assert psnr > 25.0
+
+
+def test_decoder_timeout_is_reported_and_the_context_stays_usable():
+    # the tensor-core decoder's failure path: each warpgroup's first wait for
+    # its MMAs (on a barrier nothing signals) runs out after 1 ms; the group
+    # waits for the MMAs it committed before TMEM is freed, the call reports
+    # FPO_ERR_DEVICE_TIMEOUT, and the context then renders normally
+    d, xyz, _ = _smooth_tree(5)
+    n = d.shape[0]
+    m = LatentModel(n, seed=3)
+    m.p["b3"][0] = 30.0
+    cam = synth.Camera(eye=synth.sphere_eye(60, 15), width=64, height=48)
+    r = fpo.Renderer(storage="latent")
+    try:
+        r.upload(synth.Tree(d, xyz, np.zeros((0, NC), np.float32), 5))
+        r.set_latents(*m.inference_arrays())
+        ref = r.render(camera=cam, t=21.0)["rgb"].clone()
+        r.status()
+        r.render(camera=cam, t=21.0, test_timeout=True)
+        with pytest.raises(fpo.FPOError) as e:
+            r.status()
+        assert e.value.code == -9
+        r.status()
+        again = r.render(camera=cam, t=21.0)["rgb"]
+        r.status()
+        assert torch.equal(again, ref)
+    finally:
+        r.close()
+
+
+def test_decoder_forward_matches_reference():
+    # fpo_decoder_forward (FP32 SIMT decode of every leaf) against the FP64
+    # reference, element by element; 3001 leaves: a ragged last tile
+    rng = np.random.default_rng(4)
+    n = 3001
+    m = LatentModel(n, seed=9)
+    m.p["b1"].copy_(torch.as_tensor(rng.normal(size=64) * 0.1))
+    m.p["b2"].copy_(torch.as_tensor(rng.normal(size=64) * 0.1))
+    m.p["b3"].copy_(torch.as_tensor(rng.normal(size=NC)))
+    y = m.decode().double().cpu().numpy()
+    P = {k: v.double().cpu().numpy() for k, v in m.p.items()}
+    ref = olat.decode(P["lat"], P["w1"], P["b1"], P["w2"], P["b2"], P["w3"], P["b3"])
+    # FP32 sums of at most 64 products: a few ulp of the largest partial sums
+    np.testing.assert_allclose(y, ref, rtol=0, atol=2e-5 * max(1.0, np.abs(ref).max()))

@@ -351,3 +351,29 @@ def test_step_cap_is_reported_and_the_context_stays_usable(mode):
     finally:
         capped.close()
         normal.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "fp8"])
+def test_bounded_wait_timeout_is_reported_and_the_context_stays_usable(storage):
+    # device-side failure path without a fault: FPO_FLAG_TEST_DEVICE_TIMEOUT
+    # makes the IDFT pass's first wait (on a barrier nothing signals) run out
+    # after 1 ms; the pass drains its bulk copies in flight, the call reports
+    # FPO_ERR_DEVICE_TIMEOUT, and the same context then renders normally
+    tree = synth.shell_tree()
+    cam = synth.shell_camera(64, 64)
+    r = fpo.Renderer(storage=storage)
+    try:
+        r.upload(tree)
+        ref = r.render(camera=cam, t=3.0)["rgb"].clone()
+        r.status()
+        r.render(camera=cam, t=3.0, test_timeout=True)
+        with pytest.raises(fpo.FPOError) as e:
+            r.status()
+        assert e.value.code == -9
+        r.status()  # cleared
+        # the failed pass left no valid table behind: REUSE_TABLE rebuilds it
+        again = r.render(camera=cam, t=3.0, reuse_table=True)["rgb"]
+        r.status()
+        assert torch.equal(again, ref)
+    finally:
+        r.close()
