@@ -308,7 +308,7 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
     coefficients produced by the generation: smooth animated fields -> per-
     leaf DFT) against the plain FP32 renderer of those coefficients."""
     import oracle
-    from paper_2202_08614_gb300.latent import LatentModel
+    from paper_2202_08614_gb300.latent import LatentModel, PixelLoss
 
     res = {}
     nf = frames[: args.variant_frames]
@@ -374,14 +374,22 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
     r.upload(gen)
     ms32 = time_frames(r, cams, nf, out, torch, B)
     r.close()
+    # training: coefficient L2 (density weight 0.2) plus the rendered-pixel
+    # loss every 4th step (8192 rays over the 16 ring views x 60 frames,
+    # weight 10) through the render adjoint
     m = LatentModel(n, seed=0)
     m.init_output_bias(coeffs)
+    pixel_cfg = dict(rays=8192, weight=10.0, every=4, start=0.1)
+    pixel = PixelLoss(gen, cams, **pixel_cfg)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     hist = m.fit(coeffs, steps=args.latent_steps, batch=65536, lr_w=1e-3, lr_lat=1e-1, decay=0.05,
-                 log_every=max(1, args.latent_steps // 4))
+                 coef_weight=m.default_weights(coeffs.device, sigma_weight=0.2),
+                 log_every=max(1, args.latent_steps // 4), pixel=pixel)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    pixel_loss = float(pixel.last_loss)
+    pixel.close()
     r = fpo.Renderer(storage="latent")
     r.upload(synth.Tree(tree.leaf_depth, tree.leaf_xyz, np.zeros((0, 166), np.float32), tree.max_depth))
     r.set_latents(*m.inference_arrays())
@@ -396,7 +404,8 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
         "single_frame_Mrays_s": n_px / msl1 / 1e3,
         "psnr_vs_fp64_oracle": frame_psnr(r, ot, co_np, cams, out, torch)[0],
         "decode_ms": ev[0].elapsed_time(ev[1]), "train_steps": args.latent_steps, "train_batch": 65536,
-        "train_s": train_s, "train_loss": hist, "bytes_per_leaf": 64,
+        "train_s": train_s, "train_loss": hist, "bytes_per_leaf": r.info()["leaf_record_bytes"],
+        "fp32_bytes_per_leaf": 672, "pixel_loss": dict(pixel_cfg, last_batch_mse=pixel_loss),
         "coefficients": "per-leaf DFT (Eq. 10-12) of smooth animated fields over the same leaves"}
     r.close()
     return res

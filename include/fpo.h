@@ -194,8 +194,8 @@ typedef struct {
 typedef struct {
     uint32_t n_leaves, n_nodes, max_depth, n_smem_nodes;
     uint64_t node_bytes;      /* device bytes of the node array */
-    uint64_t leaf_bytes;      /* device bytes of the stored coefficients */
-    uint64_t leaf_record_bytes; /* stored bytes per leaf (padded) */
+    uint64_t leaf_bytes;      /* device bytes of the stored coefficients (or latents) */
+    uint64_t leaf_record_bytes; /* stored bytes per leaf (padded); 64 for LATENT storage */
     uint64_t table_bytes;     /* device bytes of the per-frame IDFT table (0 until used) */
 } fpo_tree_info;
 
@@ -233,9 +233,9 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
  * traversed on cuda_stream (the call orders that stream after its own
  * previous work and before everything it enqueues later).  Both kernels
  * share every SM: the call picks their launch shapes itself (two 384-thread
- * traversal CTAs and one or two IDFT CTAs per SM, with a shared-memory
- * carveout that holds them all), whatever traverse_threads says; LATENT
- * storage keeps the single-frame shapes.  Errors: as fpo_render. */
+ * traversal CTAs and one or two IDFT CTAs per SM, or for LATENT storage one
+ * 256-thread decoder CTA, with a shared-memory carveout that holds them
+ * all), whatever traverse_threads says.  Errors: as fpo_render. */
 int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames,
                       const fpo_frame_opts *opts, float *out_rgb, void *const *frame_done,
                       void *cuda_stream);

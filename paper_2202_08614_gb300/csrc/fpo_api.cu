@@ -63,9 +63,18 @@ void dfree(T *&p)
 // thread-per-leaf form, or two 256-thread CTAs of the warp-cooperative form),
 // whose stage rings are capped so that all CTAs' shared memory fits one
 // carveout.
-constexpr int PIPE_TRAV_THREADS = 384;
-constexpr int PIPE_TRAV_CTAS = 2;
-constexpr int PIPE_MAT_SMEM_BUDGET = 88 * 1024;  // bytes of coefficient records in flight per SM
+#ifndef FPO_PIPE_TRAV_THREADS
+#define FPO_PIPE_TRAV_THREADS 384
+#endif
+#ifndef FPO_PIPE_TRAV_CTAS
+#define FPO_PIPE_TRAV_CTAS 2
+#endif
+#ifndef FPO_PIPE_MAT_SMEM_KB
+#define FPO_PIPE_MAT_SMEM_KB 88
+#endif
+constexpr int PIPE_TRAV_THREADS = FPO_PIPE_TRAV_THREADS;
+constexpr int PIPE_TRAV_CTAS = FPO_PIPE_TRAV_CTAS;
+constexpr int PIPE_MAT_SMEM_BUDGET = FPO_PIPE_MAT_SMEM_KB * 1024;  // bytes of coefficient records in flight per SM
 constexpr int PIPE_STATIC_SMEM = 512;            // allowance for each kernel's static shared memory
 constexpr int SMEM_CONFIGS_KB[] = {0, 8, 16, 32, 64, 100, 132, 164, 196, 228};  // per SM, sm_100 family
 #ifndef FPO_SMEM_NODES
@@ -312,8 +321,12 @@ int fpo_tree_info_get(const fpo_ctx *ctx, fpo_tree_info *out)
     out->max_depth = ctx->max_depth;
     out->n_smem_nodes = ctx->n_smem_nodes;
     out->node_bytes = (uint64_t)ctx->n_nodes * 32;
-    const RecordLayout L = record_layout(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2);
-    out->leaf_record_bytes = (uint64_t)(L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
+    if (ctx->cfg.storage == FPO_STORAGE_LATENT) {
+        out->leaf_record_bytes = 64;  // one FP16 latent of 32 values (the decoder is shared)
+    } else {
+        const RecordLayout L = record_layout(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2);
+        out->leaf_record_bytes = (uint64_t)(L.sig_bytes() + L.z_bytes() + (L.scaled ? 4 : 0));
+    }
     out->leaf_bytes = out->leaf_record_bytes * ctx->n_leaves;
     out->table_bytes = (uint64_t)ctx->table_leaves * table_row_bytes(ctx);
     return FPO_OK;
@@ -458,6 +471,8 @@ int launch_table_pass(const fpo_ctx *ctx, double t, float *table, int max_ctas_p
         lp.half_table = ctx->half_table;
         lp.status = ctx->d_status;
         lp.test_timeout = test_timeout;
+        lp.pipeline = pipe_stages > 0;
+        lp.carveout = carveout;
         return launch_latent_table(lp, ctx->sm_count, s);
     }
     MaterialiseParams mp{};
@@ -602,9 +617,10 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(e, "stream/event creation");
     }
-    // Shapes that let both kernels be resident on an SM at once; the decoder
-    // of LATENT storage needs a whole SM, so its frames keep the default shapes.
-    bool overlap = ctx->cfg.storage != FPO_STORAGE_LATENT;
+    // Shapes that let both kernels be resident on an SM at once: the IDFT
+    // pass in materialise_pipeline_shape, or for LATENT storage one 256-thread
+    // decoder CTA (two warpgroup pipelines, 128 TMEM columns) per SM.
+    bool overlap = true;
     MatShape mshape{};
     int carveout = 0;
     if (overlap) {
@@ -612,7 +628,13 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
         if ((e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->cfg.device)) != cudaSuccess ||
             (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, ctx->cfg.device)) != cudaSuccess)
             return cuda_fail(e, "cudaDeviceGetAttribute");
-        mshape = materialise_pipeline_shape(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2, PIPE_MAT_SMEM_BUDGET);
+        if (ctx->cfg.storage == FPO_STORAGE_LATENT) {
+            mshape.ctas_per_sm = 1;
+            mshape.stages = 1;  // (a positive value selects the pipeline shape)
+            mshape.smem_per_cta = latent_pipeline_smem_bytes();
+        } else {
+            mshape = materialise_pipeline_shape(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2, PIPE_MAT_SMEM_BUDGET);
+        }
         const long need = (long)PIPE_TRAV_CTAS * (traverse_smem_bytes(ctx->n_smem_nodes, false, PIPE_TRAV_THREADS) + PIPE_STATIC_SMEM + reserved) +
                           (long)mshape.ctas_per_sm * (mshape.smem_per_cta + PIPE_STATIC_SMEM + reserved);
         // The driver rounds a carveout request up to one of the SM's shared-

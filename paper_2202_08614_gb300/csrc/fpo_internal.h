@@ -214,10 +214,13 @@ struct LatentParams {
     int half_table;
     uint32_t *status;
     int test_timeout;         // 1: each warpgroup's first wait gives up (failure-path test)
+    int pipeline;             // 1: the frame-pipeline shape (one 256-thread CTA per SM)
+    int carveout;             // preferred shared-memory carveout in percent (0: the driver's default)
     CUtensorMap table_map;    // set by launch_latent_table: the table as a [n_leaves][32] tensor
 };
 
 int launch_latent_table(const LatentParams &p, int sm_count, void *stream);
+int latent_pipeline_smem_bytes();  // dynamic shared memory of the pipeline-shape decoder CTA
 
 struct DecoderGradParams {
     fpo_mlp w, g;             // FP32 weights; gradients (accumulated)

@@ -32,14 +32,15 @@
 namespace fpo {
 namespace {
 
-#ifndef FPO_LT_GROUPS
-#define FPO_LT_GROUPS 8
-#endif
-constexpr int LT_GROUPS = FPO_LT_GROUPS;  // independent warpgroup pipelines per CTA (one CTA per SM)
-constexpr int LT_THREADS = 128 * LT_GROUPS;
+// Independent warpgroup pipelines per CTA (one CTA per SM): 8 (1024 threads,
+// all 512 TMEM columns) when the decoder has the SM to itself, 2 (256
+// threads, 128 columns) beside the traversal in the frame pipeline.
+constexpr int LT_GROUPS_FULL = 8, LT_GROUPS_PIPE = 2;
 constexpr int LT_M = 128;          // leaves per tile = MMA M
-constexpr uint32_t LT_TMEM_COLS = 64 * LT_GROUPS;  // 64 accumulator columns per warpgroup
-static_assert(LT_TMEM_COLS <= 512 && (LT_TMEM_COLS & (LT_TMEM_COLS - 1)) == 0, "TMEM allocation");
+// 64 accumulator columns per warpgroup
+template <int G>
+__host__ __device__ constexpr uint32_t lt_tmem_cols() { return 64u * G; }
+static_assert(lt_tmem_cols<LT_GROUPS_FULL>() <= 512 && lt_tmem_cols<LT_GROUPS_PIPE>() >= 32, "TMEM allocation");
 constexpr uint64_t LT_WAIT_NS = 2000000000ull;
 
 // Biases ride in the MMAs: every A operand carries two constant-one columns
@@ -60,7 +61,8 @@ constexpr int OFF_W3 = 16384;      // 32 x 80  f16:  5 KB
 constexpr int OFF_A1 = 22528;      // per group: 128 x 48 f16: 12 KB
 constexpr int OFF_A2 = 22528;      // per group: 128 x 80 f16: 20 KB (1024-byte aligned: output staging)
 constexpr int GROUP_BYTES = 20480; // one warpgroup's region
-constexpr int LT_SMEM = OFF_A1 + LT_GROUPS * GROUP_BYTES + 1024;  // + alignment slack
+template <int G>
+__host__ __device__ constexpr int lt_smem() { return OFF_A1 + G * GROUP_BYTES + 1024; }  // + alignment slack
 
 // Byte offset of element (row, k) in a K-major core-matrix layout whose rows
 // hold K elements: core matrix (row / 8, k / 8) at ((row/8) * K/8 + k/8) * 128,
@@ -188,8 +190,11 @@ __device__ __forceinline__ void group_sync(int group)
     asm volatile("bar.sync %0, 128;" ::"r"(1 + group) : "memory");
 }
 
-__global__ void __launch_bounds__(LT_THREADS, 1) latent_table_kernel(const __grid_constant__ LatentParams p)
+template <int G>
+__global__ void __launch_bounds__(128 * G, 8 / G) latent_table_kernel(const __grid_constant__ LatentParams p)
 {
+    constexpr int LT_GROUPS = G, LT_THREADS = 128 * G;
+    constexpr uint32_t LT_TMEM_COLS = lt_tmem_cols<G>();
     extern __shared__ __align__(1024) unsigned char lt_smem_raw[];
     // the 128-byte-swizzled output staging needs 1024-byte aligned buffers
     unsigned char *lt_smem = lt_smem_raw + ((1024u - (ptx::smem_u32(lt_smem_raw) & 1023u)) & 1023u);
@@ -444,20 +449,32 @@ int launch_latent_table(const LatentParams &pin, int sm_count, void *stream)
             p.half_table ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return (int)cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(latent_table_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, LT_SMEM);
-    if (e != cudaSuccess) return (int)e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, latent_table_kernel, LT_THREADS, LT_SMEM);
-    if (e != cudaSuccess) return (int)e;
-    if (per_sm < 1) per_sm = 1;
-    if ((uint64_t)per_sm * LT_TMEM_COLS > 512) per_sm = (int)(512 / LT_TMEM_COLS);  // TMEM has 512 columns
-    const uint32_t n_tiles = (p.n_leaves + LT_M - 1) / LT_M;
-    uint64_t blocks = (uint64_t)sm_count * per_sm;
-    const uint64_t need = (n_tiles + LT_GROUPS - 1) / LT_GROUPS;
-    if (blocks > need) blocks = need;
-    latent_table_kernel<<<(unsigned)blocks, LT_THREADS, LT_SMEM, (cudaStream_t)stream>>>(p);
-    return (int)cudaGetLastError();
+    auto launch = [&](auto kern, int G, int smem, int ctas_per_sm) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     p.carveout > 0 ? p.carveout : (int)cudaSharedmemCarveoutDefault);
+        if (e != cudaSuccess) return e;
+        int per_sm = ctas_per_sm;
+        if (per_sm <= 0) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128 * G, smem);
+            if (e != cudaSuccess) return e;
+            if (per_sm < 1) per_sm = 1;
+        }
+        if (per_sm * 64 * G > 512) per_sm = 512 / (64 * G);  // TMEM has 512 columns
+        const uint32_t n_tiles = (p.n_leaves + LT_M - 1) / LT_M;
+        uint64_t blocks = (uint64_t)sm_count * per_sm;
+        const uint64_t need = (n_tiles + G - 1) / G;
+        if (blocks > need) blocks = need;
+        kern<<<(unsigned)blocks, 128 * G, smem, (cudaStream_t)stream>>>(p);
+        return cudaGetLastError();
+    };
+    if (p.pipeline)
+        return (int)launch(latent_table_kernel<LT_GROUPS_PIPE>, LT_GROUPS_PIPE, lt_smem<LT_GROUPS_PIPE>(), 1);
+    return (int)launch(latent_table_kernel<LT_GROUPS_FULL>, LT_GROUPS_FULL, lt_smem<LT_GROUPS_FULL>(), 0);
 }
+
+int latent_pipeline_smem_bytes() { return lt_smem<LT_GROUPS_PIPE>(); }
 
 }  // namespace fpo
 

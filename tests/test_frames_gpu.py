@@ -56,16 +56,20 @@ def test_frames_equal_single_renders(storage, n_frames):
         assert d.mean() <= 1e-5
 
 
-def test_frames_latent_storage():
-    xyz = synth.shell_leaves(5)
+@pytest.mark.parametrize("depth", [5, 7])
+def test_frames_latent_storage(depth):
+    # LATENT frames in the pipeline: the two-warpgroup decoder CTA beside the
+    # traversal gives the same table, bit for bit, as the eight-warpgroup one
+    # of single-frame renders (depth 7: 325k leaves, many tiles per group)
+    xyz = synth.shell_leaves(depth)
     n = xyz.shape[0]
-    d = np.full(n, 5, np.uint8)
+    d = np.full(n, depth, np.uint8)
     m = LatentModel(n, seed=4)
     m.p["b3"][0] = 20.0
     lat, *w = m.inference_arrays()
     r = fpo.Renderer(storage="latent")
     try:
-        r.upload(synth.Tree(d, xyz, np.zeros((0, 166), np.float32), 5))
+        r.upload(synth.Tree(d, xyz, np.zeros((0, 166), np.float32), depth))
         r.set_latents(lat, *w)
         cams = synth.ring_cameras(4, 64, 48)
         times = [1.0, 30.5, 59.0, 12.25]

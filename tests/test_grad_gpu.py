@@ -91,6 +91,12 @@ def test_gradient_matches_oracle(stop_T):
     rows, err = _row_errors(gpu, ref)
     print(f"stop_T={stop_T}: norm-wise {rel:.2e}; {rows.size} rows, worst row {err.max():.2e}, "
           f"median {np.median(err):.2e}; flagged rays dropped {(flags != 0).sum()}")
+    nr = np.linalg.norm(ref, axis=1)
+    for q in np.argsort(err)[-8:]:
+        print(f"  row {rows[q]}: rel {err[q]:.2e}, norm / max {nr[rows[q]] / nr.max():.2e}")
+    for fl in (1e-2, 3e-2, 1e-1):
+        rr, ee = _row_errors(gpu, ref, floor=fl)
+        print(f"  floor {fl}: {rr.size} rows, worst {ee.max():.2e}")
     assert rows.size > 100
     # rows untouched by the oracle get nothing on the GPU either
     assert np.all(gpu[np.linalg.norm(ref, axis=1) == 0] == 0)
