@@ -51,7 +51,8 @@ typedef enum {
     FPO_ERR_TRAVERSAL_LIMIT = -6, /* device: a ray exceeded its step cap */
     FPO_ERR_VISIT_OVERFLOW = -7,  /* device: a ray had more visits than visit_cap */
     FPO_ERR_UNSUPPORTED = -8,     /* a valid request this build does not implement */
-    FPO_ERR_DEVICE_TIMEOUT = -9   /* device: a bounded wait on an async copy gave up */
+    FPO_ERR_DEVICE_TIMEOUT = -9,  /* device: a bounded wait on an async copy gave up */
+    FPO_ERR_RANGE = -10           /* device: a latent decoder operand exceeded the FP16 range */
 } fpo_status;
 
 /* Storage precision of the leaf coefficients (the math is FP32 throughout). */
@@ -360,10 +361,13 @@ typedef struct {
  * decoder's output and sigma, z follow Eq. 7 and Eq. 9 at time t.  The IDFT
  * is folded into the last layer (W3' = B(t) W3), so the MLP runs 32 -> 64 ->
  * 64 -> 28 with FP16 operands and FP32 accumulation (BF16 weights are
- * converted to FP16 in shared memory).  latents: device FP16 [n_leaves][32],
+ * converted to FP16 in shared memory: FP16 keeps 3 more significant bits
+ * than BF16, in a range of +-65504).  latents: device FP16 [n_leaves][32],
  * 16-byte aligned.
- * status: optional device word that receives FPO_ERR_DEVICE_TIMEOUT's bit
- * when a bounded wait gives up.  Runs on the current device and stream.
+ * status: optional device word that receives the bit of
+ * FPO_ERR_DEVICE_TIMEOUT when a bounded wait gives up, and that of
+ * FPO_ERR_RANGE when a weight, bias or hidden activation is beyond the FP16
+ * range (the table is then wrong).  Runs on the current device and stream.
  * Errors: INVALID_ARG, CUDA. */
 int fpo_latent_table(const fpo_decoder *dec, int32_t n1, int32_t n2, double t, double period_T,
                      uint32_t n_leaves, const uint16_t *latents, float *table, uint32_t *status,
@@ -414,8 +418,8 @@ int fpo_adam(float *param, const float *grad, float *m, float *v, uint64_t n, co
 int fpo_set_latents(fpo_ctx *ctx, const uint16_t *latents, const fpo_decoder *dec, void *cuda_stream);
 
 /* Waits for cuda_stream and returns (then clears) the device status word:
- * FPO_OK, FPO_ERR_TRAVERSAL_LIMIT, FPO_ERR_VISIT_OVERFLOW or
- * FPO_ERR_DEVICE_TIMEOUT. */
+ * FPO_OK, FPO_ERR_TRAVERSAL_LIMIT, FPO_ERR_VISIT_OVERFLOW,
+ * FPO_ERR_DEVICE_TIMEOUT or FPO_ERR_RANGE. */
 int fpo_status_sync(fpo_ctx *ctx, void *cuda_stream);
 
 /* Sizes of the uploaded tree.  Errors: INVALID_ARG, NO_TREE. */

@@ -840,6 +840,8 @@ int fpo_status_sync(fpo_ctx *ctx, void *cuda_stream)
     if (st & STATUS_TRAVERSAL_LIMIT) return fail(FPO_ERR_TRAVERSAL_LIMIT, "a ray exceeded its step cap");
     if (st & STATUS_VISIT_OVERFLOW) return fail(FPO_ERR_VISIT_OVERFLOW, "a ray had more visits than visit_cap");
     if (st & STATUS_DEVICE_TIMEOUT) return fail(FPO_ERR_DEVICE_TIMEOUT, "a device-side wait gave up after its time limit");
+    if (st & STATUS_FP16_RANGE)
+        return fail(FPO_ERR_RANGE, "a latent decoder weight, bias or hidden activation exceeded the FP16 range (65504)");
     return FPO_OK;
 }
 

@@ -73,7 +73,8 @@ constexpr int TILE_W = FPO_TILE_W, TILE_H = 32 / FPO_TILE_W;
 static_assert(TILE_W * TILE_H == 32, "a tile is one warp of rays");
 
 // Device status word bits.
-constexpr uint32_t STATUS_TRAVERSAL_LIMIT = 1u, STATUS_VISIT_OVERFLOW = 2u, STATUS_DEVICE_TIMEOUT = 4u;
+constexpr uint32_t STATUS_TRAVERSAL_LIMIT = 1u, STATUS_VISIT_OVERFLOW = 2u, STATUS_DEVICE_TIMEOUT = 4u,
+                   STATUS_FP16_RANGE = 8u;
 // Limit of the waits that FPO_FLAG_TEST_DEVICE_TIMEOUT makes run out: 1 ms.
 constexpr uint64_t TEST_WAIT_LIMIT_NS = 1000000ull;
 

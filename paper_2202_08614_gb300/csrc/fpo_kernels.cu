@@ -974,26 +974,6 @@ __device__ __forceinline__ bool step_cap(const TraverseParams &p, RayState &R)
     return false;
 }
 
-// One traversal step (compaction schedule): locate, shade, move.  Returns
-// false once the ray is finished (left the grid, early stop, or step cap).
-template <int TM, bool DBG, int N1, int N2>
-__device__ bool step_ray(const TraverseParams &p, const FrameShared &fs, const float *bsrc,
-                         int bstride, const uint32_t *__restrict__ s_nodes, uint32_t *s_stack,
-                         int stride, RayState &R)
-{
-    (void)fs;
-    const int D = p.depth, G = 1 << D;
-    const Cube cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start);
-    int m, lo[3], csz;
-    const float tx = cube_exit(R, D, cb.lvl, m, lo, csz);
-    if (cb.kind == ROOT_LEAF && tx > R.t)
-        if (shade<TM, DBG, N1, N2>(p, bsrc, bstride, R, cb.leaf, tx - R.t)) return false;
-    int Pn[3];
-    if (!next_cell(R, G, m, lo, csz, tx, Pn)) return false;
-    move_to(R, D, Pn, tx);
-    return !step_cap(p, R);
-}
-
 // Fused mode: the coefficient records of the next leaf (672 B at n1 = 31,
 // n2 = 5) are pulled into L2 by two bulk prefetches while the current leaf is
 // shaded, so its 32-byte loads hit L2 instead of HBM.
@@ -1007,44 +987,56 @@ __device__ __forceinline__ void prefetch_records(const TraverseParams &p, uint32
     (void)n2;
 }
 
-// A whole ray (lane-loop schedule).  Software-pipelined: the next cube is
-// located, and its table record prefetched into L1, before the current cube
-// is shaded, so the record's latency hides behind the shading arithmetic.
+// One step of the software-pipelined walk: the exit of cube `cb` (which
+// holds R.P), the next cube located and its table record (or coefficient
+// records) prefetched before `cb` is shaded, so the record's latency hides
+// behind the shading arithmetic; then the move.  `cb` becomes the next cube.
+// Returns false once the ray is finished (left the grid, early stop, or
+// step cap).
+template <int TM, bool DBG, int N1, int N2>
+__device__ __forceinline__ bool pipelined_step(const TraverseParams &p, const float *bsrc, int bstride,
+                                               const uint32_t *__restrict__ s_nodes, uint32_t *s_stack,
+                                               int stride, RayState &R, Cube &cb)
+{
+    const int D = p.depth, G = 1 << D;
+    int m, lo[3], csz;
+    const float tx = cube_exit(R, D, cb.lvl, m, lo, csz);
+    int Pn[3];
+    const bool inside = next_cell(R, G, m, lo, csz, tx, Pn);
+    Cube nx;
+    nx.kind = ROOT_EMPTY;
+    if (FPO_PREFETCH && inside) {
+        const uint32_t diff = (uint32_t)((R.P[0] ^ Pn[0]) | (R.P[1] ^ Pn[1]) | (R.P[2] ^ Pn[2]));
+        nx = locate(p, s_nodes, s_stack, stride, Pn, D - 1 - (31 - __clz(diff)));
+        if (nx.kind == ROOT_LEAF) {
+            if constexpr (TM == TM_TABLE_F32)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record(p, nx.leaf)));
+            else if constexpr (TM == TM_TABLE_F16)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record_f16(p, nx.leaf)));
+            else
+                prefetch_records(p, nx.leaf, N1, N2);
+        }
+    }
+    if (cb.kind == ROOT_LEAF && tx > R.t)
+        if (shade<TM, DBG, N1, N2>(p, bsrc, bstride, R, cb.leaf, tx - R.t)) return false;
+    if (!inside) return false;
+    move_to(R, D, Pn, tx);
+    if (step_cap(p, R)) return false;
+    if (FPO_PREFETCH)
+        cb = nx;
+    else
+        cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start);
+    return true;
+}
+
+// A whole ray (lane-loop schedule).
 template <int TM, bool DBG, int N1, int N2>
 __device__ void trace_ray(const TraverseParams &p, const float *bsrc, int bstride,
                           const uint32_t *__restrict__ s_nodes, uint32_t *s_stack, int stride,
                           RayState &R)
 {
-    const int D = p.depth, G = 1 << D;
     Cube cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start);
-    for (;;) {
-        int m, lo[3], csz;
-        const float tx = cube_exit(R, D, cb.lvl, m, lo, csz);
-        int Pn[3];
-        const bool inside = next_cell(R, G, m, lo, csz, tx, Pn);
-        Cube nx;
-        nx.kind = ROOT_EMPTY;
-        if (FPO_PREFETCH && inside) {
-            const uint32_t diff = (uint32_t)((R.P[0] ^ Pn[0]) | (R.P[1] ^ Pn[1]) | (R.P[2] ^ Pn[2]));
-            nx = locate(p, s_nodes, s_stack, stride, Pn, D - 1 - (31 - __clz(diff)));
-            if (nx.kind == ROOT_LEAF) {
-                if constexpr (TM == TM_TABLE_F32)
-                    asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record(p, nx.leaf)));
-                else if constexpr (TM == TM_TABLE_F16)
-                    asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record_f16(p, nx.leaf)));
-                else
-                    prefetch_records(p, nx.leaf, N1, N2);
-            }
-        }
-        if (cb.kind == ROOT_LEAF && tx > R.t)
-            if (shade<TM, DBG, N1, N2>(p, bsrc, bstride, R, cb.leaf, tx - R.t)) return;
-        if (!inside) return;
-        move_to(R, D, Pn, tx);
-        if (step_cap(p, R)) return;
-        if (FPO_PREFETCH)
-            cb = nx;
-        else
-            cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start);
+    while (pipelined_step<TM, DBG, N1, N2>(p, bsrc, bstride, s_nodes, s_stack, stride, R, cb)) {
     }
 }
 
@@ -1183,6 +1175,10 @@ __global__ void __maxnreg__(TM ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED) 
         uint32_t cur_tile = grab_tile();  // warp-uniform cursor: tile and next ray in it
         uint32_t cur_next = 0;
         RayState R;
+        Cube cb;  // the cube holding R.P, located ahead (pipelined step)
+        cb.kind = ROOT_EMPTY;
+        cb.leaf = 0;
+        cb.lvl = 0;
         bool active = false;
         for (;;) {
             uint32_t idle = __ballot_sync(0xffffffffu, !active);
@@ -1193,8 +1189,10 @@ __global__ void __maxnreg__(TM ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED) 
                     if (((idle >> lane) & 1u) && rank < take) {
                         uint32_t ray;
                         int px = 0, py = 0;
-                        if (tile_ray(p, cur_tile, cur_next + rank, ray, px, py))
+                        if (tile_ray(p, cur_tile, cur_next + rank, ray, px, py)) {
                             active = init_ray<DBG>(p, fs, prt, my_b, stride, my_stack, R, ray, px, py);
+                            if (active) cb = locate(p, s_nodes, my_stack, stride, R.P, R.lvl_start);
+                        }
                     }
                     cur_next += take;
                     if (cur_next >= 32) {
@@ -1209,7 +1207,7 @@ __global__ void __maxnreg__(TM ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED) 
             if (active) {
 #pragma unroll 1
                 for (uint32_t k = 0; k < p.inner_steps; ++k) {
-                    if (!step_ray<TM, DBG, N1, N2>(p, fs, bsrc, bstride, s_nodes, my_stack, stride, R)) {
+                    if (!pipelined_step<TM, DBG, N1, N2>(p, bsrc, bstride, s_nodes, my_stack, stride, R, cb)) {
                         finish(R);
                         active = false;
                         break;

@@ -133,15 +133,20 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 
 // Rounds 8 consecutive values to FP16 with ReLU (max(x, 0) after rounding
 // equals rounding after max) and writes them as K-chunk j of row `row` of a
-// core layout.
-__device__ __forceinline__ void put8_relu(unsigned char *base, int row, int j, int K, const float *v)
+// core layout.  `hmax` keeps the packed running maximum of what was written:
+// a value beyond the FP16 range rounds to +inf, which the maximum keeps.
+__device__ __forceinline__ void put8_relu(unsigned char *base, int row, int j, int K, const float *v, __half2 &hmax)
 {
     uint32_t h[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e)  // the first operand goes to the upper half
+    for (int e = 0; e < 4; ++e) {  // the first operand goes to the upper half
         asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(h[e]) : "f"(v[2 * e + 1]), "f"(v[2 * e]));
+        hmax = __hmax2(hmax, *reinterpret_cast<const __half2 *>(&h[e]));
+    }
     *reinterpret_cast<uint4 *>(base + core_off(row, 8 * j, K)) = make_uint4(h[0], h[1], h[2], h[3]);
 }
+
+constexpr float F16_MAX = 65504.0f;  // the largest finite FP16 value
 
 // Writes 8 consecutive values of row `row` (K-chunk j) into a core layout.
 __device__ __forceinline__ void put8(unsigned char *base, int row, int j, int K, const float *v)
@@ -203,6 +208,7 @@ __global__ void __launch_bounds__(128 * G, 8 / G) latent_table_kernel(const __gr
     __shared__ uint64_t s_never;  // FPO_FLAG_TEST_DEVICE_TIMEOUT: a barrier nothing signals
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail[LT_GROUPS];
+    __shared__ int s_range;  // a weight or bias beyond the FP16 range
     const int tid = threadIdx.x, warp = tid >> 5;
     const int group = tid >> 7, gt = tid & 127;  // warpgroup and thread within it
 
@@ -211,6 +217,7 @@ __global__ void __launch_bounds__(128 * G, 8 / G) latent_table_kernel(const __gr
     if (tid < 32) s_basis[tid] = tid < nb ? (float)((tid & 1) ? sinpi((double)(tid + 1) * (p.t / p.period_T))
                                                              : cospi((double)tid * (p.t / p.period_T)))
                                          : 0.0f;
+    if (tid == 0) s_range = 0;
     if (tid < LT_GROUPS) {
         s_fail[tid] = 0;
         ptx::mbar_init(&s_bar[tid], 1);
@@ -229,8 +236,11 @@ __global__ void __launch_bounds__(128 * G, 8 / G) latent_table_kernel(const __gr
             float v[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) v[e] = __bfloat162float(__ushort_as_bfloat16(p.w1[n * 32 + 8 * j + e]));
+            for (int e = 0; e < 8; ++e)
+                if (!(fabsf(v[e]) <= F16_MAX)) s_range = 1;
             put8(lt_smem + OFF_W1, n, j, K1, v);
         } else if (j == 4) {
+            if (!(fabsf(p.b1[n]) <= F16_MAX)) s_range = 1;
             put_bias_chunk(lt_smem + OFF_W1, n, j, K1, p.b1[n], false);
         } else {
             put_zero_chunk(lt_smem + OFF_W1, n, j, K1);
@@ -242,8 +252,11 @@ __global__ void __launch_bounds__(128 * G, 8 / G) latent_table_kernel(const __gr
             float v[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) v[e] = __bfloat162float(__ushort_as_bfloat16(p.w2[n * 64 + 8 * j + e]));
+            for (int e = 0; e < 8; ++e)
+                if (!(fabsf(v[e]) <= F16_MAX)) s_range = 1;
             put8(lt_smem + OFF_W2, n, j, K2, v);
         } else if (j == 8) {
+            if (!(fabsf(p.b2[n]) <= F16_MAX)) s_range = 1;
             put_bias_chunk(lt_smem + OFF_W2, n, j, K2, p.b2[n], false);
         } else {
             put_zero_chunk(lt_smem + OFF_W2, n, j, K2);
@@ -261,6 +274,7 @@ __global__ void __launch_bounds__(128 * G, 8 / G) latent_table_kernel(const __gr
 #pragma unroll 8
         for (int i = 0; i < terms; ++i)
             acc = fmaf(s_basis[i], __bfloat162float(__ushort_as_bfloat16(p.w3[(row0 + i) * 64 + h])), acc);
+        if (!(fabsf(acc) <= F16_MAX)) s_range = 1;
         *reinterpret_cast<__half *>(lt_smem + OFF_W3 + core_off(r, h, K2)) = __float2half_rn(acc);
     }
     if (tid < 32) {
@@ -268,6 +282,7 @@ __global__ void __launch_bounds__(128 * G, 8 / G) latent_table_kernel(const __gr
         float acc = 0.0f;
 #pragma unroll 8
         for (int i = 0; i < terms; ++i) acc = fmaf(s_basis[i], p.b3[row0 + i], acc);
+        if (!(fabsf(acc) <= F16_MAX)) s_range = 1;
         put_bias_chunk(lt_smem + OFF_W3, tid, 8, K2, acc, false);  // rows 28..31: b = 0
         put_zero_chunk(lt_smem + OFF_W3, tid, 9, K2);
     }
@@ -283,6 +298,7 @@ __global__ void __launch_bounds__(128 * G, 8 / G) latent_table_kernel(const __gr
     const uint32_t sa_w1 = ptx::smem_u32(lt_smem + OFF_W1), sa_w2 = ptx::smem_u32(lt_smem + OFF_W2),
                    sa_w3 = ptx::smem_u32(lt_smem + OFF_W3), sa_a1 = ptx::smem_u32(ga1), sa_a2 = ptx::smem_u32(ga2);
     uint32_t phase = 0;
+    __half2 hmax = __float2half2_rn(0.0f);  // packed maximum of the FP16 activations written
     const uint32_t n_tiles = (p.n_leaves + LT_M - 1) / LT_M;
     const uint32_t first = blockIdx.x * LT_GROUPS + group, step = gridDim.x * LT_GROUPS;
     const int m = gt;  // this thread's accumulator row (TMEM lane) and leaf in the tile
@@ -349,7 +365,7 @@ __global__ void __launch_bounds__(128 * G, 8 / G) latent_table_kernel(const __gr
             float v[32];
             tmem_ld32(my_lane + 32 * h, v);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) put8_relu(ga2, m, 4 * h + c, K2, v + 8 * c);
+            for (int c = 0; c < 4; ++c) put8_relu(ga2, m, 4 * h + c, K2, v + 8 * c, hmax);
         }
         put_bias_chunk(ga2, m, 8, K2, 0.0f, true);
         put_zero_chunk(ga2, m, 9, K2);
@@ -362,7 +378,7 @@ __global__ void __launch_bounds__(128 * G, 8 / G) latent_table_kernel(const __gr
             float v[32];
             tmem_ld32(my_lane + 32 * h, v);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) put8_relu(ga2, m, 4 * h + c, K2, v + 8 * c);
+            for (int c = 0; c < 4; ++c) put8_relu(ga2, m, 4 * h + c, K2, v + 8 * c, hmax);
         }
         hand_off();
         load_tile(tile + step, nextq);  // in flight while layer 3 runs
@@ -406,6 +422,10 @@ __global__ void __launch_bounds__(128 * G, 8 / G) latent_table_kernel(const __gr
         if (gt == 0) tensor_store_rows(&p.table_map, ga2, tile * LT_M);  // rows past the end are clipped
     }
     if (gt == 0) bulk_wait_all();  // every table store has completed
+    // FP16 operands: a hidden activation, weight or bias beyond the FP16
+    // range (it became +inf) makes the table wrong; report it
+    if (p.status && (!(__low2float(hmax) <= F16_MAX) || !(__high2float(hmax) <= F16_MAX) || (tid == 0 && s_range)))
+        atomicOr(p.status, STATUS_FP16_RANGE);
     if (s_fail[group] && gt == 0) {
         // the commit whose wait gave up: wait for it once more (bounded)
         // before TMEM is freed

@@ -20,7 +20,7 @@ FPO_OK = 0
 ERRORS = {
     -1: "FPO_ERR_INVALID_ARG", -2: "FPO_ERR_OOM", -3: "FPO_ERR_CUDA", -4: "FPO_ERR_BAD_TREE",
     -5: "FPO_ERR_NO_TREE", -6: "FPO_ERR_TRAVERSAL_LIMIT", -7: "FPO_ERR_VISIT_OVERFLOW",
-    -8: "FPO_ERR_UNSUPPORTED", -9: "FPO_ERR_DEVICE_TIMEOUT",
+    -8: "FPO_ERR_UNSUPPORTED", -9: "FPO_ERR_DEVICE_TIMEOUT", -10: "FPO_ERR_RANGE",
 }
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "fp8": 3, "latent": 4}
 IDFT = {"auto": 0, "fused": 1, "materialise": 2}

@@ -63,6 +63,28 @@ def _emulate(lat, w1, b1, w2, b2, w3, b3, t):
     return o
 
 
+def _fp16_bound(lat, w1, b1, w2, b2, w3, b3, t):
+    """Element-wise bound on |kernel table - FP64 table| from the FP16
+    operands: W3'(t) and each hidden activation are rounded to FP16 (relative
+    error <= 2^-11), the first hidden layer's error passes through |W2| and
+    |W3'(t)|; twice the first-order sum, plus a few FP32 ulps of the terms."""
+    import oracle
+
+    x = np.asarray(lat, np.float64)
+    a1 = np.maximum(x @ w1.T + b1, 0)
+    a2 = np.maximum(a1 @ w2.T + b2, 0)
+    b = oracle.basis(N1, t, 60.0)
+    w3f = np.zeros((28, 64))
+    w3f[0] = b[:N1] @ w3[:N1]
+    w3f[1:28] = np.einsum("i,qih->qh", b[:N2], w3[N1:].reshape(27, N2, 64))
+    u = 2.0 ** -11
+    terms = np.abs(a2) @ np.abs(w3f).T
+    first = u * (2 * terms + (np.abs(a1) @ np.abs(w2).T) @ np.abs(w3f).T)
+    out = np.zeros((x.shape[0], 32))
+    out[:, :28] = 2 * first + 1e-6 * (terms + 1.0)
+    return out
+
+
 @pytest.mark.parametrize("n", [1, 128, 129, 1000, 70000, 2_000_003])
 def test_latent_table_matches_references(n):
     w1, b1, w2, b2, w3, b3 = _net(n)
@@ -77,6 +99,34 @@ def test_latent_table_matches_references(n):
     emu = _emulate(lat.astype(np.float64), w1, b1, w2, b2, w3, b3, t)
     err = np.abs(got - emu)
     assert err.max() <= 2e-3 * max(1.0, np.abs(emu).max()), err.max()
-    exact = olat.table(olat.decode(lat.astype(np.float64), w1, b1, w2, b2, w3, b3), t)
-    rel = np.linalg.norm(got - exact) / np.linalg.norm(exact)
-    assert rel <= 1e-2, rel
+    # element by element against the plain FP64 table, within the FP16
+    # operand bound (rows sampled for the largest case)
+    rows = np.arange(n) if n <= 70000 else np.random.default_rng(n).choice(n, 70000, replace=False)
+    exact = olat.table(olat.decode(lat[rows].astype(np.float64), w1, b1, w2, b2, w3, b3), t)
+    bound = _fp16_bound(lat[rows], w1, b1, w2, b2, w3, b3, t)
+    d = np.abs(got[rows] - exact)
+    worst = (d / np.maximum(bound, 1e-30))[:, :28].max()
+    print(f"n={n}: max |table - FP64| {d.max():.2e}, worst / bound {worst:.3f}")
+    assert np.all(d <= bound)
+
+
+def test_latent_table_reports_fp16_range():
+    # a hidden activation beyond 65504 rounds to +inf in the FP16 operands:
+    # the table is wrong, and the status word says so
+    w1, b1, w2, b2, w3, b3 = _net(3)
+    lat = np.full((300, 32), 30.0, np.float16)
+    dev = lambda a: torch.as_tensor(np.asarray(a), device="cuda")
+    big = w1 * 0 + np.float32(100.0)  # every first-layer output is 32 * 30 * 100 = 96000
+    _, status = fpo.latent_table(dev(lat), dev(big), dev(b1), dev(w2), dev(b2), dev(w3), dev(b3), 5.0)
+    torch.cuda.synchronize()
+    assert int(status.item()) & 8
+    # a weight beyond the range (BF16 holds it, FP16 does not)
+    w2b = w2.copy()
+    w2b[3, 7] = 1.0e5
+    _, status = fpo.latent_table(dev(lat * 0), dev(w1), dev(b1), dev(w2b), dev(b2), dev(w3), dev(b3), 5.0)
+    torch.cuda.synchronize()
+    assert int(status.item()) & 8
+    # in range: nothing reported
+    _, status = fpo.latent_table(dev(lat * 0), dev(w1), dev(b1), dev(w2), dev(b2), dev(w3), dev(b3), 5.0)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
