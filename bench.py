@@ -58,6 +58,10 @@ def parse():
                     help="frames per fpo_render_frames call in the timed region (1: fpo_render per frame)")
     ap.add_argument("--latent-steps", type=int, default=20000)
     ap.add_argument("--finetune-steps", type=int, default=200)
+    ap.add_argument("--refill-min", type=int, default=0,
+                    help="traversal schedule: warp-level ray compaction once this many lanes are idle (0: plain)")
+    ap.add_argument("--inner-steps", type=int, default=0,
+                    help="steps a lane takes between two compaction checks (0: to the end of its ray)")
     return ap.parse_args()
 
 
@@ -195,6 +199,8 @@ def workload_config(tree, args):
         "frames_per_call": max(1, args.frames_per_call),
         "l2": "inputs larger than L2 (2.4 GB of leaf records)",
         "early_stop_T": 1e-4,
+        "schedule": ("plain" if args.refill_min in (0, 32) else
+                     f"compaction: refill_min {args.refill_min}, inner_steps {args.inner_steps or 'to the end'}"),
     }
 
 
@@ -521,7 +527,8 @@ def main():
     cams = synth.ring_cameras(16, args.width, args.height)
     K, W = args.steps, args.warmup
     frames = frames_for_rank(rank, K + W)
-    r = fpo.Renderer(idft_mode=args.idft, storage=args.storage, device=local)
+    r = fpo.Renderer(idft_mode=args.idft, storage=args.storage, device=local, refill_min=args.refill_min,
+                     inner_steps=args.inner_steps)
     r.upload(tree)
     info = r.info()
     n_px = args.width * args.height

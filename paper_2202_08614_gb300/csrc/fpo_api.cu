@@ -141,6 +141,10 @@ namespace fpo {
 
 // Bytes of one leaf's row of the per-frame table.
 static size_t table_row_bytes(const fpo_ctx *c) { return c->half_table ? TABLE_STRIDE * 2 : TABLE_STRIDE * 4; }
+// Bytes of a per-frame table: rows rounded up to a multiple of 8 leaves, so
+// that a prefetch of the aligned 512-byte group of rows holding any leaf
+// stays inside the allocation.
+static size_t table_alloc_bytes(const fpo_ctx *c) { return (((size_t)c->n_leaves + 7) & ~(size_t)7) * table_row_bytes(c); }
 
 CtxView ctx_view(const fpo_ctx *c)
 {
@@ -532,7 +536,7 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts, f
     cudaError_t e;
     if (mat && ctx->table_leaves < ctx->n_leaves) {
         dfree(ctx->d_table);
-        e = cudaMalloc((void **)&ctx->d_table, (size_t)ctx->n_leaves * table_row_bytes(ctx));
+        e = cudaMalloc((void **)&ctx->d_table, table_alloc_bytes(ctx));
         if (e != cudaSuccess) { ctx->table_leaves = 0; return cuda_fail(e, "cudaMalloc(table)"); }
         ctx->table_leaves = ctx->n_leaves;
     }
@@ -606,7 +610,7 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
         size_t &tl = b ? ctx->table2_leaves : ctx->table_leaves;
         if (tl < ctx->n_leaves) {
             dfree(tb);
-            e = cudaMalloc((void **)&tb, (size_t)ctx->n_leaves * table_row_bytes(ctx));
+            e = cudaMalloc((void **)&tb, table_alloc_bytes(ctx));
             if (e != cudaSuccess) { tl = 0; return cuda_fail(e, "cudaMalloc(table)"); }
             tl = ctx->n_leaves;
         }

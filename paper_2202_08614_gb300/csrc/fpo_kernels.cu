@@ -34,6 +34,12 @@
 #ifndef FPO_PREFETCH
 #define FPO_PREFETCH 1
 #endif
+#ifndef FPO_FAST_EXIT
+#define FPO_FAST_EXIT 0
+#endif
+#ifndef FPO_PREFETCH_SIBLINGS
+#define FPO_PREFETCH_SIBLINGS 0
+#endif
 
 namespace fpo {
 namespace {
@@ -757,14 +763,24 @@ __device__ __forceinline__ Cube locate(const TraverseParams &p, const uint32_t *
 // the cube's lower corner lo.
 __device__ __forceinline__ float cube_exit(const RayState &R, int D, int lvl, int &m, int lo[3], int &csz)
 {
-    csz = 1 << (D - lvl);
     float te[3];
+    if (FPO_FAST_EXIT && lvl == D) {
+        // a finest cell: the same planes as below with csz = 1, lo = P
+        csz = 1;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        lo[a] = R.P[a] & ~(csz - 1);
-        // (plane - go) is exact for nearby planes (Sterbenz), so te carries
-        // one rounding of the product
-        te[a] = (R.zmask >> a) & 1 ? FLT_MAX : ((float)(lo[a] + R.pos[a] * csz) - R.go[a]) * R.inv[a];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = R.P[a];
+            te[a] = (R.zmask >> a) & 1 ? FLT_MAX : ((float)(R.P[a] + R.pos[a]) - R.go[a]) * R.inv[a];
+        }
+    } else {
+        csz = 1 << (D - lvl);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = R.P[a] & ~(csz - 1);
+            // (plane - go) is exact for nearby planes (Sterbenz), so te carries
+            // one rounding of the product
+            te[a] = (R.zmask >> a) & 1 ? FLT_MAX : ((float)(lo[a] + R.pos[a] * csz) - R.go[a]) * R.inv[a];
+        }
     }
     m = 0;
     float tx = te[0];
@@ -1009,12 +1025,17 @@ __device__ __forceinline__ bool pipelined_step(const TraverseParams &p, const fl
         const uint32_t diff = (uint32_t)((R.P[0] ^ Pn[0]) | (R.P[1] ^ Pn[1]) | (R.P[2] ^ Pn[2]));
         nx = locate(p, s_nodes, s_stack, stride, Pn, D - 1 - (31 - __clz(diff)));
         if (nx.kind == ROOT_LEAF) {
-            if constexpr (TM == TM_TABLE_F32)
+            if constexpr (TM == TM_TABLE_F32) {
                 asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record(p, nx.leaf)));
-            else if constexpr (TM == TM_TABLE_F16)
+                if (FPO_PREFETCH_SIBLINGS)  // the aligned group of 4 lines holding it (siblings are adjacent)
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], 512;" ::"l"(table_record(p, nx.leaf & ~3u)));
+            } else if constexpr (TM == TM_TABLE_F16) {
                 asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record_f16(p, nx.leaf)));
-            else
+                if (FPO_PREFETCH_SIBLINGS)
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], 512;" ::"l"(table_record_f16(p, nx.leaf & ~7u)));
+            } else {
                 prefetch_records(p, nx.leaf, N1, N2);
+            }
         }
     }
     if (cb.kind == ROOT_LEAF && tx > R.t)

@@ -119,10 +119,11 @@ def test_both_arms_name_the_same_workload():
     class T:
         n_leaves = 3506408
 
-    args = argparse.Namespace(width=1920, height=1080, idft="auto", storage="f32", frames_per_call=32)
+    args = argparse.Namespace(width=1920, height=1080, idft="auto", storage="f32", frames_per_call=32,
+                              refill_min=0, inner_steps=0)
     cfg = bench.workload_config(T(), args)
     assert cfg["idft"] == "materialise" and cfg["table"] == "f32" and cfg["storage"] == "f32"
-    assert cfg["frames_per_call"] == 32 and cfg["resolution"] == [1920, 1080]
+    assert cfg["frames_per_call"] == 32 and cfg["resolution"] == [1920, 1080] and cfg["schedule"] == "plain"
     args.storage = "bf16"
     assert bench.workload_config(T(), args)["table"] == "f16"
     args.idft = "fused"
