@@ -84,9 +84,8 @@ typedef struct {
     /* Launch tuning of the traversal (0 = library default): threads per CTA
      * (128 or 256); the number of idle lanes at which a warp refills them
      * with new rays (1..32; 32 refills only a fully idle warp); the number of
-     * steps a lane takes between two such checks (a step: one cube of the
-     * octree, or one 4 x 4 x 4-cell brick below level depth - 2; default:
-     * to the end of its ray). */
+     * steps a lane takes between two such checks (default: to the end of its
+     * ray). */
     int32_t traverse_threads;
     int32_t refill_min;
     int32_t inner_steps;

@@ -99,8 +99,6 @@ struct fpo_ctx {
     double aabb_min[3] = {0, 0, 0}, aabb_size = 1.0;
     uint32_t *d_nodes = nullptr;
     uint32_t *d_perm = nullptr;
-    uint32_t *d_bricks = nullptr;  // bricks of the level D - 2 nodes (depth >= 3)
-    uint32_t brick_node0 = 0;
     void *d_sig = nullptr;    // density records (storage precision)
     void *d_z = nullptr;      // SH records (storage precision)
     float *d_scale = nullptr; // FP8: per-leaf scale, padded to a multiple of 4 leaves
@@ -123,7 +121,6 @@ struct fpo_ctx {
     {
         dfree(d_nodes);
         dfree(d_perm);
-        dfree(d_bricks);
         dfree(d_sig);
         dfree(d_z);
         dfree(d_scale);
@@ -300,7 +297,6 @@ int fpo_upload_tree(fpo_ctx *ctx, const fpo_tree_desc *tree)
     };
     if ((st = up((void **)&ctx->d_nodes, pk.nodes.data(), pk.nodes.size() * 4, "nodes")) ||
         (st = up((void **)&ctx->d_perm, pk.perm.data(), pk.perm.size() * 4, "perm")) ||
-        (st = up((void **)&ctx->d_bricks, pk.bricks.data(), pk.bricks.size() * 4, "bricks")) ||
         (st = up((void **)&ctx->d_sig, sig.data(), sig.size(), "sigma records")) ||
         (st = up((void **)&ctx->d_z, zc.data(), zc.size(), "SH records")) ||
         (st = up((void **)&ctx->d_scale, scale.data(), scale.size() * 4, "FP8 scales"))) {
@@ -309,7 +305,6 @@ int fpo_upload_tree(fpo_ctx *ctx, const fpo_tree_desc *tree)
     }
     ctx->n_leaves = tree->n_leaves;
     ctx->n_nodes = (uint32_t)n_nodes;
-    ctx->brick_node0 = pk.brick_node0;
     ctx->root_kind = pk.root_kind;
     ctx->depth = pk.depth;
     ctx->max_depth = tree->max_depth;
@@ -412,8 +407,6 @@ TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, const f
     p.root_kind = ctx->root_kind;
     p.depth = ctx->depth;
     p.n_smem_nodes = ctx->n_smem_nodes;
-    p.bricks = ctx->d_bricks;
-    p.brick_node0 = ctx->brick_node0;
     p.grid_scale64 = (double)(1u << ctx->depth) / ctx->aabb_size;
     p.grid_scale = (float)p.grid_scale64;
     for (int k = 0; k < 3; ++k) {

@@ -78,25 +78,11 @@ constexpr uint32_t STATUS_TRAVERSAL_LIMIT = 1u, STATUS_VISIT_OVERFLOW = 2u, STAT
 // Limit of the waits that FPO_FLAG_TEST_DEVICE_TIMEOUT makes run out: 1 ms.
 constexpr uint64_t TEST_WAIT_LIMIT_NS = 1000000ull;
 
-// Bricks: every node at level D - 2 (a cube of 4 x 4 x 4 finest cells) also
-// gets a brick of 64 slots, one per finest cell of its cube (index x + 4 y +
-// 16 z in local cell coordinates), telling what covers the cell: a leaf
-// (LEAF_BIT | leaf index) or empty space (0), with BRICK_COARSE set when that
-// leaf or empty cube is the level D - 1 cube (8 cells, replicated) rather
-// than the cell itself.  Breadth-first numbering puts the nodes of one level
-// in a contiguous range, so the brick of node n is brick n - brick_node0.
-// Trees of depth < 3 have none.
-constexpr int BRICK_CELLS = 64;
-constexpr uint32_t BRICK_COARSE = 0x40000000u;
-constexpr uint32_t BRICK_LEAF_MASK = 0x3FFFFFFFu;
-
 struct PackedTree {
     uint32_t root_kind = ROOT_EMPTY;
     int depth = 0;                 // grid depth D: finest cell = 1 / 2^D of the cube
     std::vector<uint32_t> nodes;   // [n_nodes * 8]
     std::vector<uint32_t> perm;    // internal leaf index -> upload index
-    std::vector<uint32_t> bricks;  // [n_bricks * BRICK_CELLS]
-    uint32_t brick_node0 = 0;      // first node at level D - 2
 };
 
 // Validates a tree description (and packs it when `out` is non-null).
@@ -123,8 +109,6 @@ struct TraverseParams {
     uint32_t root_kind;
     int depth;
     uint32_t n_smem_nodes;
-    const uint32_t *bricks;   // the bricks of the level D - 2 nodes, or nullptr
-    uint32_t brick_node0;     // node index of brick 0
     float grid_scale;         // 2^D / aabb_size
     float amin[3];
     double grid_scale64, amin64[3];  // the same in FP64 (gradient-check replay)

@@ -40,12 +40,6 @@
 #ifndef FPO_PREFETCH_SIBLINGS
 #define FPO_PREFETCH_SIBLINGS 0
 #endif
-#ifndef FPO_BRICKS
-#define FPO_BRICKS 0
-#endif
-#ifndef FPO_BRICK_LOCATE
-#define FPO_BRICK_LOCATE 0
-#endif
 
 namespace fpo {
 namespace {
@@ -740,17 +734,6 @@ __device__ __forceinline__ Cube locate(const TraverseParams &p, const uint32_t *
         return cb;
     }
     const int D = p.depth;
-    if (FPO_BRICK_LOCATE && p.bricks && lvl_start >= D - 2) {
-        // P shares its level D - 2 ancestor (on the stack) with the previous
-        // cell: its cube is in that node's brick, one slot per finest cell
-        const uint32_t nb = s_stack[(D - 2) * stride];
-        const uint32_t sl = __ldg(p.bricks + (size_t)(nb - p.brick_node0) * BRICK_CELLS +
-                                  ((P[0] & 3) | ((P[1] & 3) << 2) | ((P[2] & 3) << 4)));
-        cb.lvl = (sl & BRICK_COARSE) ? D - 1 : D;
-        cb.kind = (sl & LEAF_BIT) ? ROOT_LEAF : ROOT_EMPTY;
-        cb.leaf = sl & BRICK_LEAF_MASK;
-        return cb;
-    }
     int lvl = lvl_start;
     uint32_t node = s_stack[lvl * stride];
     for (;;) {
@@ -1067,115 +1050,14 @@ __device__ __forceinline__ bool pipelined_step(const TraverseParams &p, const fl
     return true;
 }
 
-// Prefetch of a leaf's table line (or, fused, its coefficient records).
-template <int TM, int N1, int N2>
-__device__ __forceinline__ void prefetch_leaf(const TraverseParams &p, uint32_t leaf)
-{
-    if constexpr (TM == TM_TABLE_F32)
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record(p, leaf)));
-    else if constexpr (TM == TM_TABLE_F16)
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record_f16(p, leaf)));
-    else
-        prefetch_records(p, leaf, N1, N2);
-}
-
-// The finest cells of the level D - 2 cube holding R.P, walked from its
-// brick (64 slots, one per finest cell) one plane crossing at a time, with
-// no descent per cell.  A run of cells with the same slot (one leaf, or empty
-// space) is one segment: it ends at the first plane crossing into a cell with
-// another slot, and that crossing's distance is computed as cube_exit
-// computes the exit of the run's cube ((plane - go) inv, ties x < y < z), so
-// the segments, their order and their lengths are those of the cube-by-cube
-// walk.  cur_slot is the slot of R.P's cell.  Returns false once the ray is
-// finished (early stop, step cap, or it left the grid); true when it left
-// the brick, with R at the first cell outside it (R.t and R.lvl_start as
-// move_to sets them).
-template <int TM, bool DBG, int N1, int N2>
-__device__ __forceinline__ bool brick_walk(const TraverseParams &p, const float *bsrc, int bstride,
-                                           const uint32_t *__restrict__ brick, RayState &R, uint32_t cur_slot)
-{
-    const int D = p.depth, G = 1 << D;
-    float te[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        te[a] = (R.zmask >> a) & 1 ? FLT_MAX : ((float)(R.P[a] + R.pos[a]) - R.go[a]) * R.inv[a];
-    int idx = (R.P[0] & 3) | ((R.P[1] & 3) << 2) | ((R.P[2] & 3) << 4);
-    for (;;) {
-        int m = 0;
-        float tx = te[0];
-        if (te[1] < tx) { tx = te[1]; m = 1; }
-        if (te[2] < tx) { tx = te[2]; m = 2; }
-        // the cell across plane m: its coordinate, brick index and slot
-        int pm = 0, dir = 0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (a == m) {
-                dir = 2 * R.pos[a] - 1;
-                pm = R.P[a] + dir;
-            }
-        const bool leaving = ((pm ^ (pm - dir)) & ~3) != 0;  // crossed a multiple of 4: out of the brick
-        const int nidx = idx + dir * (1 << (2 * m));
-        uint32_t nslot = leaving ? 0u : __ldg(brick + nidx);
-        nslot = (nslot & LEAF_BIT) ? (nslot & ~BRICK_COARSE) : 0u;
-        if (leaving || nslot != cur_slot) {
-            if (nslot & LEAF_BIT) prefetch_leaf<TM, N1, N2>(p, nslot & ~LEAF_BIT);
-            if ((cur_slot & LEAF_BIT) && tx > R.t)
-                if (shade<TM, DBG, N1, N2>(p, bsrc, bstride, R, cur_slot & ~LEAF_BIT, tx - R.t)) return false;
-            R.t = fmaxf(R.t, tx);
-            if (step_cap(p, R)) return false;
-            cur_slot = nslot;
-        }
-        if (leaving) {
-            if ((unsigned)pm >= (unsigned)G) return false;  // left the grid
-            const int old = pm - dir;
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-                if (a == m) R.P[a] = pm;
-            R.lvl_start = D - 1 - (31 - __clz((uint32_t)(old ^ pm)));
-            return true;
-        }
-        idx = nidx;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (a == m) {
-                R.P[a] = pm;
-                te[a] = ((float)(pm + R.pos[a]) - R.go[a]) * R.inv[a];
-            }
-    }
-}
-
-// One unit of the walk from cube cb (which holds R.P): the whole brick when
-// cb lies inside a level D - 2 node (brick_walk, then the first cube after
-// it is located), else one pipelined cube step.  Returns false once the ray
-// is finished.
-template <int TM, bool DBG, int N1, int N2>
-__device__ __forceinline__ bool advance(const TraverseParams &p, const float *bsrc, int bstride,
-                                        const uint32_t *__restrict__ s_nodes, uint32_t *s_stack, int stride,
-                                        RayState &R, Cube &cb)
-{
-    if (FPO_BRICKS && p.bricks && cb.lvl >= p.depth - 1) {
-        // the level D - 2 ancestor is on the stack (the descent passed it)
-        const uint32_t nb = s_stack[(p.depth - 2) * stride];
-        const uint32_t *brick = p.bricks + (size_t)(nb - p.brick_node0) * BRICK_CELLS;
-        if (!brick_walk<TM, DBG, N1, N2>(p, bsrc, bstride, brick, R,
-                                        cb.kind == ROOT_LEAF ? (LEAF_BIT | cb.leaf) : 0u))
-            return false;
-        cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start);
-        if (cb.kind == ROOT_LEAF) prefetch_leaf<TM, N1, N2>(p, cb.leaf);
-        return true;
-    }
-    return pipelined_step<TM, DBG, N1, N2>(p, bsrc, bstride, s_nodes, s_stack, stride, R, cb);
-}
-
-// A whole ray (lane-loop schedule): cube by cube through the octree, and
-// brick by brick below level D - 2.
+// A whole ray (lane-loop schedule).
 template <int TM, bool DBG, int N1, int N2>
 __device__ void trace_ray(const TraverseParams &p, const float *bsrc, int bstride,
                           const uint32_t *__restrict__ s_nodes, uint32_t *s_stack, int stride,
                           RayState &R)
 {
     Cube cb = locate(p, s_nodes, s_stack, stride, R.P, R.lvl_start);
-    while (advance<TM, DBG, N1, N2>(p, bsrc, bstride, s_nodes, s_stack, stride, R, cb)) {
+    while (pipelined_step<TM, DBG, N1, N2>(p, bsrc, bstride, s_nodes, s_stack, stride, R, cb)) {
     }
 }
 
@@ -1346,7 +1228,7 @@ __global__ void __maxnreg__(TM ? FPO_TRAV_MAXNREG_MAT : FPO_TRAV_MAXNREG_FUSED) 
             if (active) {
 #pragma unroll 1
                 for (uint32_t k = 0; k < p.inner_steps; ++k) {
-                    if (!advance<TM, DBG, N1, N2>(p, bsrc, bstride, s_nodes, my_stack, stride, R, cb)) {
+                    if (!pipelined_step<TM, DBG, N1, N2>(p, bsrc, bstride, s_nodes, my_stack, stride, R, cb)) {
                         finish(R);
                         active = false;
                         break;

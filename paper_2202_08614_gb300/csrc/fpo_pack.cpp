@@ -131,11 +131,8 @@ int validate_and_pack(const fpo_tree_desc *tree, int n1, int n2, PackedTree *out
     out->nodes.resize(tn.size() * 8);
     out->perm.reserve(n);
     std::vector<int32_t> queue;
-    std::vector<int> level;  // level of each node in queue order
     queue.reserve(tn.size());
-    level.reserve(tn.size());
     queue.push_back(0);
-    level.push_back(0);
     for (size_t qi = 0; qi < queue.size(); ++qi) {
         const TNode &t = tn[queue[qi]];
         for (int c = 0; c < 8; ++c) {
@@ -143,37 +140,11 @@ int validate_and_pack(const fpo_tree_desc *tree, int n1, int n2, PackedTree *out
             if (t.c[c] >= 0) {
                 slot = (uint32_t)queue.size();
                 queue.push_back(t.c[c]);
-                level.push_back(level[qi] + 1);
             } else if (t.c[c] <= -2) {
                 slot = LEAF_BIT | (uint32_t)out->perm.size();
                 out->perm.push_back((uint32_t)(-(t.c[c] + 2)));
             }
             out->nodes[qi * 8 + c] = slot;
-        }
-    }
-    // Bricks of the level D - 2 nodes (contiguous in breadth-first order).
-    if (dmax >= 3 && n <= BRICK_LEAF_MASK) {
-        const int lb = dmax - 2;
-        size_t first = 0;
-        while (first < level.size() && level[first] < lb) ++first;
-        size_t last = first;
-        while (last < level.size() && level[last] == lb) ++last;
-        out->brick_node0 = (uint32_t)first;
-        out->bricks.assign((last - first) * BRICK_CELLS, 0u);
-        for (size_t b = first; b < last; ++b) {
-            uint32_t *brick = &out->bricks[(b - first) * BRICK_CELLS];
-            for (int c1 = 0; c1 < 8; ++c1) {
-                const uint32_t s1 = out->nodes[b * 8 + c1];
-                for (int c2 = 0; c2 < 8; ++c2) {
-                    // a level D - 1 leaf or empty cube covers all 8 cells; a
-                    // level D - 1 node holds each cell's own leaf or emptiness
-                    uint32_t s2 = s1 | BRICK_COARSE;
-                    if (s1 != 0u && !(s1 & LEAF_BIT)) s2 = out->nodes[(size_t)s1 * 8 + c2];
-                    const int x = ((c1 & 1) << 1) | (c2 & 1), y = (c1 & 2) | ((c2 >> 1) & 1),
-                              z = ((c1 >> 1) & 2) | ((c2 >> 2) & 1);
-                    brick[x + 4 * y + 16 * z] = s2;
-                }
-            }
         }
     }
     return FPO_OK;
