@@ -25,6 +25,9 @@
 #ifndef FPO_GENERIC_NODE_LOAD
 #define FPO_GENERIC_NODE_LOAD 1
 #endif
+#ifndef FPO_NODE_SMEM
+#define FPO_NODE_SMEM 1
+#endif
 #ifndef FPO_FAST_SIGMOID
 #define FPO_FAST_SIGMOID 1
 #endif
@@ -740,7 +743,11 @@ __device__ __forceinline__ Cube locate(const TraverseParams &p, const uint32_t *
         const int sh = D - 1 - lvl;
         const uint32_t c = ((P[0] >> sh) & 1) | (((P[1] >> sh) & 1) << 1) | (((P[2] >> sh) & 1) << 2);
         const uint32_t idx = node * 8 + c;
-#if FPO_GENERIC_NODE_LOAD
+#if FPO_NODE_SMEM == 0
+        // every node slot from global memory (read-only path)
+        const uint32_t sl = __ldg(p.nodes + idx);
+        (void)s_nodes;
+#elif FPO_GENERIC_NODE_LOAD
         // one generic load from shared (top nodes) or global memory: no branch
         // between two load paths for lanes at different levels
         const uint32_t *src = node < p.n_smem_nodes ? s_nodes : p.nodes;
