@@ -230,9 +230,11 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
  * frame k's pixels are written, so a caller can read frame k back while
  * later frames render.  The result equals n_frames calls of fpo_render.  In the table
  * mode the work is pipelined: the per-frame table of frame k+1 is computed
- * on an internal second stream, into a second table, while frame k is
- * traversed on cuda_stream (the call orders that stream after its own
- * previous work and before everything it enqueues later).  Both kernels
+ * on an internal stream, into a second table, while frame k is traversed;
+ * even frames are traversed on cuda_stream and odd frames on another
+ * internal stream, so that consecutive traversals may overlap (the call
+ * orders all of it after cuda_stream's previous work and before everything
+ * enqueued on cuda_stream after the call).  Both kernels
  * share every SM: the call picks their launch shapes itself (two 384-thread
  * traversal CTAs and one or two IDFT CTAs per SM, or for LATENT storage one
  * 256-thread decoder CTA, with a shared-memory carveout that holds them

@@ -69,6 +69,9 @@ void dfree(T *&p)
 #ifndef FPO_PIPE_TRAV_CTAS
 #define FPO_PIPE_TRAV_CTAS 2
 #endif
+#ifndef FPO_PIPE_TWO_STREAMS
+#define FPO_PIPE_TWO_STREAMS 1  // odd frames' traversals on a second stream
+#endif
 #ifndef FPO_PIPE_MAT_SMEM_KB
 #define FPO_PIPE_MAT_SMEM_KB 88
 #endif
@@ -77,10 +80,13 @@ constexpr int PIPE_TRAV_CTAS = FPO_PIPE_TRAV_CTAS;
 constexpr int PIPE_MAT_SMEM_BUDGET = FPO_PIPE_MAT_SMEM_KB * 1024;  // bytes of coefficient records in flight per SM
 constexpr int PIPE_STATIC_SMEM = 512;            // allowance for each kernel's static shared memory
 constexpr int SMEM_CONFIGS_KB[] = {0, 8, 16, 32, 64, 100, 132, 164, 196, 228};  // per SM, sm_100 family
+// Top-level nodes staged in shared memory per traversal CTA (32 B each); 0
+// with the kernels' default FPO_NODE_SMEM 0, which reads every node slot
+// from global memory.
 #ifndef FPO_SMEM_NODES
-#define FPO_SMEM_NODES 512
+#define FPO_SMEM_NODES 0
 #endif
-constexpr uint32_t SMEM_NODE_BUDGET = FPO_SMEM_NODES;  // top-level nodes staged per CTA (32 B each)
+constexpr uint32_t SMEM_NODE_BUDGET = FPO_SMEM_NODES;
 constexpr int DEFAULT_TRAVERSE_THREADS = 256;
 constexpr uint32_t DEFAULT_REFILL_MIN = 32;
 constexpr uint32_t DEFAULT_INNER_STEPS = 0xffffffffu;  // a lane runs its ray to the end
@@ -90,7 +96,10 @@ constexpr uint32_t DEFAULT_INNER_STEPS = 0xffffffffu;  // a lane runs its ray to
 struct fpo_ctx {
     fpo_config cfg{};
     int sm_count = 0;
-    uint32_t *d_status = nullptr;  // [0] status bits, [1] tile counter, [2] finished CTAs, [3] pad
+    // [0] status bits; [1], [2] tile counter and finished warps of a traversal;
+    // [5], [6] the same for the odd frames of fpo_render_frames, whose
+    // traversals run on a second stream and may overlap the even ones
+    uint32_t *d_status = nullptr;
     // tree
     bool has_tree = false;
     uint32_t n_leaves = 0, n_nodes = 0, root_kind = ROOT_EMPTY, n_smem_nodes = 0;
@@ -114,7 +123,8 @@ struct fpo_ctx {
     double table_t = 0.0;
     float *d_table2 = nullptr;
     size_t table2_leaves = 0;
-    cudaStream_t aux = nullptr;
+    cudaStream_t aux = nullptr;   // IDFT passes / decodes
+    cudaStream_t aux2 = nullptr;  // traversals of the odd frames
     cudaEvent_t ev_entry = nullptr, ev_mat[2] = {nullptr, nullptr}, ev_trav[2] = {nullptr, nullptr};
 
     void free_tree()
@@ -223,9 +233,9 @@ int fpo_create(fpo_ctx **out, const fpo_config *cfg)
                     (cfg->table_precision == FPO_TABLE_AUTO && cfg->storage != FPO_STORAGE_F32);
     e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, cfg->device);
     if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaDeviceGetAttribute"); }
-    e = cudaMalloc((void **)&c->d_status, 4 * sizeof(uint32_t));
+    e = cudaMalloc((void **)&c->d_status, 8 * sizeof(uint32_t));
     if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(status)"); }
-    e = cudaMemset(c->d_status, 0, 4 * sizeof(uint32_t));
+    e = cudaMemset(c->d_status, 0, 8 * sizeof(uint32_t));
     if (e != cudaSuccess) { cudaFree(c->d_status); delete c; return cuda_fail(e, "cudaMemset"); }
     *out = c;
     g_err.clear();
@@ -431,6 +441,7 @@ TraverseParams traverse_params(const fpo_ctx *ctx, const fpo_rays *rays, const f
     p.leaf_mark = opts->leaf_mark;
     p.perm = ctx->d_perm;
     p.status = ctx->d_status;
+    p.tiles = ctx->d_status + 1;
     p.half_table = ctx->half_table;
     if (rays->mode == FPO_RAYS_CAMERA) {
         p.tiles_x = (rays->width + TILE_W - 1) / TILE_W;
@@ -617,6 +628,7 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
     }
     if (!ctx->aux) {
         e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux2, cudaStreamNonBlocking);
         for (cudaEvent_t *ev : {&ctx->ev_entry, &ctx->ev_mat[0], &ctx->ev_mat[1], &ctx->ev_trav[0], &ctx->ev_trav[1]})
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(e, "stream/event creation");
@@ -652,32 +664,43 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
     ctx->table_ok = false;  // the pipeline writes both tables
     cudaStream_t s = (cudaStream_t)cuda_stream;
     // The table pass of frame k + 1 runs on the auxiliary stream while frame
-    // k is traversed on the caller's stream; two tables alternate.
-    if ((e = cudaEventRecord(ctx->ev_entry, s)) != cudaSuccess || (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_entry, 0)) != cudaSuccess)
+    // k is traversed; two tables alternate.  The traversals of even frames
+    // run on the caller's stream and those of odd frames on a second stream
+    // (with their own tile counters), so that one traversal can fill the SMs
+    // that the last warps of the previous one leave idle.  Table b is
+    // rewritten only after the traversal that read it (event ev_trav[b]),
+    // and the caller's stream waits for the last odd traversal at the end.
+    if ((e = cudaEventRecord(ctx->ev_entry, s)) != cudaSuccess || (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_entry, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(ctx->aux2, ctx->ev_entry, 0)) != cudaSuccess)
         return cuda_fail(e, "stream ordering");
     for (uint32_t k = 0; k < n_frames; ++k) {
         const int b = (int)(k & 1);
         float *tbl = b ? ctx->d_table2 : ctx->d_table;
+        cudaStream_t ts = (FPO_PIPE_TWO_STREAMS && b) ? ctx->aux2 : s;
         if (k >= 2 && (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_trav[b], 0)) != cudaSuccess) return cuda_fail(e, "wait");
         int ce = overlap ? launch_table_pass(ctx, frames[k].t, tbl, mshape.ctas_per_sm, ctx->aux, mshape.stages, carveout, false)
                          : launch_table_pass(ctx, frames[k].t, tbl, 0, ctx->aux, 0, 0, false);
         if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "IDFT table launch");
         if ((e = cudaEventRecord(ctx->ev_mat[b], ctx->aux)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(s, ctx->ev_mat[b], 0)) != cudaSuccess)
+            (e = cudaStreamWaitEvent(ts, ctx->ev_mat[b], 0)) != cudaSuccess)
             return cuda_fail(e, "stream ordering");
         TraverseParams p = traverse_params(ctx, &frames[k], &o1, out_rgb + (size_t)k * R * 3, R);
         p.table = reinterpret_cast<const float4 *>(tbl);
+        p.tiles = ctx->d_status + ((FPO_PIPE_TWO_STREAMS && b) ? 5 : 1);
         if (overlap) {
             p.block_threads = PIPE_TRAV_THREADS;
             p.max_ctas_per_sm = PIPE_TRAV_CTAS;
             p.carveout = carveout;
         }
-        ce = launch_traverse(p, true, false, ctx->sm_count, s);
+        ce = launch_traverse(p, true, false, ctx->sm_count, ts);
         if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "traverse launch");
-        if ((e = cudaEventRecord(ctx->ev_trav[b], s)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-        if (frame_done && frame_done[k] && (e = cudaEventRecord((cudaEvent_t)frame_done[k], s)) != cudaSuccess)
+        if ((e = cudaEventRecord(ctx->ev_trav[b], ts)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        if (frame_done && frame_done[k] && (e = cudaEventRecord((cudaEvent_t)frame_done[k], ts)) != cudaSuccess)
             return cuda_fail(e, "cudaEventRecord(frame_done)");
     }
+    // everything above is ordered before the caller's later work
+    if (n_frames >= 2 && (e = cudaStreamWaitEvent(s, ctx->ev_trav[1], 0)) != cudaSuccess)
+        return cuda_fail(e, "stream ordering");
     return FPO_OK;
 }
 
@@ -857,6 +880,7 @@ void fpo_destroy(fpo_ctx *ctx)
         ctx->free_tree();
         dfree(ctx->d_status);
         if (ctx->aux) cudaStreamDestroy(ctx->aux);
+        if (ctx->aux2) cudaStreamDestroy(ctx->aux2);
         for (cudaEvent_t e : {ctx->ev_entry, ctx->ev_mat[0], ctx->ev_mat[1], ctx->ev_trav[0], ctx->ev_trav[1]})
             if (e) cudaEventDestroy(e);
     }

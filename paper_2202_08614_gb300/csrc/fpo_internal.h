@@ -130,7 +130,8 @@ struct TraverseParams {
     uint8_t *leaf_mark;
     const uint32_t *perm;
     // scheduling
-    uint32_t *status;         // [0] status bits, [1] tile counter, [2] finished CTAs
+    uint32_t *status;         // status bits (atomicOr)
+    uint32_t *tiles;          // [0] tile counter, [1] finished warps (reset by the last warp)
     uint32_t n_tiles, tiles_x;
     uint32_t max_steps;
     uint32_t refill_min;      // warp refills its idle lanes once this many are idle (32: whole tiles)
