@@ -69,6 +69,9 @@ void dfree(T *&p)
 #ifndef FPO_PIPE_TRAV_CTAS
 #define FPO_PIPE_TRAV_CTAS 2
 #endif
+#ifndef FPO_PIPE_MAT_CTAS
+#define FPO_PIPE_MAT_CTAS 0  // IDFT-pass CTAs per SM in the pipeline (0: materialise_pipeline_shape's choice)
+#endif
 #ifndef FPO_PIPE_TWO_STREAMS
 #define FPO_PIPE_TWO_STREAMS 1  // odd frames' traversals on a second stream
 #endif
@@ -650,6 +653,7 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
             mshape.smem_per_cta = latent_pipeline_smem_bytes();
         } else {
             mshape = materialise_pipeline_shape(ctx->cfg.storage, ctx->cfg.n1, ctx->cfg.n2, PIPE_MAT_SMEM_BUDGET);
+            if (FPO_PIPE_MAT_CTAS > 0) mshape.ctas_per_sm = FPO_PIPE_MAT_CTAS;
         }
         const long need = (long)PIPE_TRAV_CTAS * (traverse_smem_bytes(ctx->n_smem_nodes, false, PIPE_TRAV_THREADS) + PIPE_STATIC_SMEM + reserved) +
                           (long)mshape.ctas_per_sm * (mshape.smem_per_cta + PIPE_STATIC_SMEM + reserved);

@@ -40,6 +40,9 @@
 #ifndef FPO_PREFETCH
 #define FPO_PREFETCH 1
 #endif
+#ifndef FPO_MAT_HALF_WARP
+#define FPO_MAT_HALF_WARP 1  // FP32 records, n2 = 5, FP32 table: half a warp per leaf
+#endif
 #ifndef FPO_FAST_EXIT
 #define FPO_FAST_EXIT 0
 #endif
@@ -206,6 +209,8 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
 
     const int warp = tid >> 5, lane = tid & 31;
     const float b_lane = lane < nb ? s_b[lane] : 0.0f;
+    const float b_lo = (lane & 15) < nb ? s_b[lane & 15] : 0.0f;              // half-warp form
+    const float b_hi = (lane & 15) + 16 < nb ? s_b[(lane & 15) + 16] : 0.0f;
     float bz[N2 > 0 ? N2 : 1];
 #pragma unroll
     for (int i = 0; i < (N2 > 0 ? N2 : 1); ++i) bz[i] = s_b[i];
@@ -227,6 +232,51 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
         const unsigned char *stage_sig = mat_smem + (size_t)s * stage_bytes;
         const unsigned char *stage_z = stage_sig + sig_bytes;
         const float *stage_scale = reinterpret_cast<const float *>(stage_z + z_bytes);
+        if constexpr (FPO_MAT_HALF_WARP && N2 == 5 && ST == FPO_STORAGE_F32) {
+            if (!p.half_table) {
+                // Half a warp per leaf, two leaves per pass: lane sl of a half
+                // forms k_sl b_sl + k_{sl+16} b_{sl+16} (the first step of the
+                // full warp's butterfly) and the butterfly continues within the
+                // half, so the density sums in the same order; z_{sl} and
+                // z_{sl+16} are the same sequential sums.  Each lane stores
+                // row[sl] and row[sl + 16].
+                const int hw = lane >> 4, sl = lane & 15;
+                for (int l0 = 2 * warp; l0 < m; l0 += 2 * (MAT_THREADS / 32)) {
+                    const int l = l0 + hw;
+                    const bool valid = l < m;
+                    const float *sg = reinterpret_cast<const float *>(stage_sig + (valid ? l : l0) * rec_sig);
+                    const float *zz = reinterpret_cast<const float *>(stage_z + (valid ? l : l0) * rec_z);
+                    const float p1 = sl < p.n1 ? __fmul_rn(sg[sl], b_lo) : 0.0f;
+                    const float p2 = sl + 16 < p.n1 ? __fmul_rn(sg[sl + 16], b_hi) : 0.0f;
+                    float part = __fadd_rn(p1, p2);
+#pragma unroll
+                    for (int o = 8; o >= 1; o >>= 1) part = __fadd_rn(part, __shfl_xor_sync(0xffffffffu, part, o));
+                    float za = 0.0f, zb = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) za = fmaf(zz[sl * 5 + i], bz[i], za);
+                    if (sl < 11) {
+#pragma unroll
+                        for (int i = 0; i < 5; ++i) zb = fmaf(zz[(sl + 16) * 5 + i], bz[i], zb);
+                    }
+                    const float za_prev = __shfl_up_sync(0xffffffffu, za, 1, 16);
+                    const float zb_prev = __shfl_up_sync(0xffffffffu, zb, 1, 16);
+                    const float za_15 = __shfl_sync(0xffffffffu, za, 15, 16);
+                    const float o1 = sl == 0 ? fmaxf(part, 0.0f) : za_prev;
+                    const float o2 = sl == 0 ? za_15 : (sl + 16 <= 27 ? zb_prev : 0.0f);
+                    if (valid) {
+                        float *row = p.table + ((size_t)first + l) * TABLE_STRIDE;
+                        row[sl] = o1;
+                        row[sl + 16] = o2;
+                    }
+                }
+                __syncthreads();  // every thread is done with stage s
+                if (tid == 0) {
+                    const uint32_t c2 = c + (uint32_t)S * gridDim.x;
+                    if (c2 < n_chunks) issue(c2, s);
+                }
+                continue;
+            }
+        }
         // One warp per leaf: lane i < n1 forms k_sigma_i b_i and a butterfly
         // sums the density; lanes 0..26 form z_{lane}(t) from n2 consecutive
         // elements.  Lane j then stores output j.
@@ -286,14 +336,16 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
 // shares the SM with the traversal (frame pipeline).
 constexpr int ML_CHUNK = 256, ML_CHUNK_PIPE = 128, ML_N2 = 5;
 
-// The 16 bytes of w as FP32 values (8 for 16-bit storage, 16 for FP8).
+// The 16 bytes of w as FP32 values (4 for FP32 storage, 8 for 16-bit, 16 for FP8).
 template <int ST>
 __device__ __forceinline__ void unpack16(const uint4 w, float *v)
 {
     const uint32_t u[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        if constexpr (ST == FPO_STORAGE_BF16) {
+        if constexpr (ST == FPO_STORAGE_F32) {
+            v[k] = __uint_as_float(u[k]);
+        } else if constexpr (ST == FPO_STORAGE_BF16) {
             v[2 * k] = __uint_as_float(u[k] << 16);
             v[2 * k + 1] = __uint_as_float(u[k] & 0xffff0000u);
         } else if constexpr (ST == FPO_STORAGE_F16) {
@@ -314,7 +366,7 @@ __device__ __forceinline__ void unpack16(const uint4 w, float *v)
 }
 
 template <int ST, int CH>
-__global__ void __launch_bounds__(CH) materialise_leaf_kernel(const __grid_constant__ MaterialiseParams p)
+__global__ void __launch_bounds__(CH, ST == FPO_STORAGE_F32 ? 4 : 1) materialise_leaf_kernel(const __grid_constant__ MaterialiseParams p)
 {
     extern __shared__ __align__(128) unsigned char mat_smem[];
     __shared__ uint64_t bars[MAT_MAX_STAGES];
@@ -323,7 +375,7 @@ __global__ void __launch_bounds__(CH) materialise_leaf_kernel(const __grid_const
     __shared__ int s_fail;
     const int tid = threadIdx.x;
     const int S = p.stages;
-    constexpr uint32_t EB = ST == FPO_STORAGE_FP8_E4M3 ? 1u : 2u;
+    constexpr uint32_t EB = ST == FPO_STORAGE_F32 ? 4u : (ST == FPO_STORAGE_FP8_E4M3 ? 1u : 2u);
     constexpr int PER = 16 / (int)EB;              // elements per 16-byte load
     constexpr bool SCALED = ST == FPO_STORAGE_FP8_E4M3;
     constexpr int SIG_ELEMS = 32;                  // n1 <= 32, padded to 16 bytes
@@ -468,10 +520,17 @@ __global__ void __launch_bounds__(CH) materialise_leaf_kernel(const __grid_const
 
 // The thread-per-leaf form applies to the reduced-precision storages with
 // n2 = 5 and density records of 32 elements (n1 from 25 or, for FP8, 17 up
-// to 32).
-static bool leaf_form(int storage, int n1, int n2)
+// to 32).  FPO_PIPE_F32_LEAF 1 also uses it for FP32 records in the frame
+// pipeline (measured slower: its 172 KB ring leaves the traversal 28 KB of
+// L1, and four warps do not keep up).
+#ifndef FPO_PIPE_F32_LEAF
+#define FPO_PIPE_F32_LEAF 0
+#endif
+static bool leaf_form(int storage, int n1, int n2, bool pipe = false)
 {
-    if (storage < FPO_STORAGE_BF16 || storage > FPO_STORAGE_FP8_E4M3 || n2 != ML_N2 || n1 < 1 || n1 > 32) return false;
+    const bool f32 = storage == FPO_STORAGE_F32 && pipe && FPO_PIPE_F32_LEAF;
+    if (!f32 && (storage < FPO_STORAGE_BF16 || storage > FPO_STORAGE_FP8_E4M3)) return false;
+    if (n2 != ML_N2 || n1 < 1 || n1 > 32) return false;
     const RecordLayout L = record_layout(storage, n1, n2);  // the kernel's fixed record strides
     const int per = 16 / L.elem_bytes;
     return L.sig_elems == 32 && L.z_elems == (27 * ML_N2 + per - 1) / per * per;
@@ -508,7 +567,7 @@ static int clamp_stages(int s)
 MatShape materialise_pipeline_shape(int storage, int n1, int n2, int smem_budget)
 {
     MatShape m{};
-    if (leaf_form(storage, n1, n2)) {  // one CTA of ML_CHUNK_PIPE threads
+    if (leaf_form(storage, n1, n2, true)) {  // one CTA of ML_CHUNK_PIPE threads
         const int stage = ML_CHUNK_PIPE * record_bytes(storage, n1, n2);
         m.ctas_per_sm = 1;
         m.stages = clamp_stages(smem_budget / stage);
@@ -526,7 +585,7 @@ MatShape materialise_pipeline_shape(int storage, int n1, int n2, int smem_budget
 // warp-cooperative form.
 static int leaf_chunk(const MaterialiseParams &p)
 {
-    if (!leaf_form(p.storage, p.n1, p.n2)) return 0;
+    if (!leaf_form(p.storage, p.n1, p.n2, p.pipeline != 0)) return 0;
     return p.pipeline ? ML_CHUNK_PIPE : ML_CHUNK;
 }
 
@@ -540,6 +599,7 @@ template <int CH>
 static void *pick_leaf(int storage)
 {
     switch (storage) {
+    case FPO_STORAGE_F32: return (void *)materialise_leaf_kernel<FPO_STORAGE_F32, ML_CHUNK_PIPE>;
     case FPO_STORAGE_BF16: return (void *)materialise_leaf_kernel<FPO_STORAGE_BF16, CH>;
     case FPO_STORAGE_F16: return (void *)materialise_leaf_kernel<FPO_STORAGE_F16, CH>;
     default: return (void *)materialise_leaf_kernel<FPO_STORAGE_FP8_E4M3, CH>;
