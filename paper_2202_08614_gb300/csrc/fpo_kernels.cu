@@ -41,7 +41,11 @@
 #define FPO_PREFETCH 1
 #endif
 #ifndef FPO_MAT_HALF_WARP
-#define FPO_MAT_HALF_WARP 1  // FP32 records, n2 = 5, FP32 table: half a warp per leaf
+// FP32 records, n2 = 5, FP32 table: half (1) or a quarter (2) of a warp per
+// leaf; 3: a quarter in the frame pipeline (fewer instructions beside the
+// traversal: 0.676 against 0.689 ms per 1080p frame) and a half alone (0.417
+// against 0.427 ms).  All forms sum in the same order.
+#define FPO_MAT_HALF_WARP 3
 #endif
 #ifndef FPO_FAST_EXIT
 #define FPO_FAST_EXIT 0
@@ -162,7 +166,7 @@ __device__ __forceinline__ float stored(const unsigned char *rec, int i)
 }
 
 template <int N2, int ST>
-__global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_constant__ MaterialiseParams p)
+__global__ void __launch_bounds__(MAT_THREADS, 8) materialise_kernel(const __grid_constant__ MaterialiseParams p)
 {
     extern __shared__ __align__(128) unsigned char mat_smem[];
     __shared__ uint64_t bars[MAT_MAX_STAGES];
@@ -211,6 +215,9 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
     const float b_lane = lane < nb ? s_b[lane] : 0.0f;
     const float b_lo = (lane & 15) < nb ? s_b[lane & 15] : 0.0f;              // half-warp form
     const float b_hi = (lane & 15) + 16 < nb ? s_b[(lane & 15) + 16] : 0.0f;
+    float bq[4];                                                             // quarter-warp form
+#pragma unroll
+    for (int k = 0; k < 4; ++k) bq[k] = (lane & 7) + 8 * k < nb ? s_b[(lane & 7) + 8 * k] : 0.0f;
     float bz[N2 > 0 ? N2 : 1];
 #pragma unroll
     for (int i = 0; i < (N2 > 0 ? N2 : 1); ++i) bz[i] = s_b[i];
@@ -232,7 +239,59 @@ __global__ void __launch_bounds__(MAT_THREADS) materialise_kernel(const __grid_c
         const unsigned char *stage_sig = mat_smem + (size_t)s * stage_bytes;
         const unsigned char *stage_z = stage_sig + sig_bytes;
         const float *stage_scale = reinterpret_cast<const float *>(stage_z + z_bytes);
-        if constexpr (FPO_MAT_HALF_WARP && N2 == 5 && ST == FPO_STORAGE_F32) {
+        if constexpr ((FPO_MAT_HALF_WARP == 2 || FPO_MAT_HALF_WARP == 3) && N2 == 5 && ST == FPO_STORAGE_F32) {
+            if (!p.half_table && (FPO_MAT_HALF_WARP == 2 || p.pipeline)) {
+                // A quarter warp (8 lanes) per leaf, four leaves per pass:
+                // lane ql forms the products of i = ql, ql + 8, ql + 16,
+                // ql + 24 and sums them as the full warp's butterfly does
+                // ((i, i + 16), then + (i + 8, i + 24)), then xor 4, 2, 1 within
+                // the quarter; it forms z_{ql + 8k}, k = 0..3, and stores
+                // row[ql + 8k].
+                const int qw = lane >> 3, ql = lane & 7;
+                for (int l0 = 4 * warp; l0 < m; l0 += 4 * (MAT_THREADS / 32)) {
+                    const int l = l0 + qw;
+                    const bool valid = l < m;
+                    const float *sg = reinterpret_cast<const float *>(stage_sig + (valid ? l : l0) * rec_sig);
+                    const float *zz = reinterpret_cast<const float *>(stage_z + (valid ? l : l0) * rec_z);
+                    float pr[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) pr[k] = ql + 8 * k < p.n1 ? __fmul_rn(sg[ql + 8 * k], bq[k]) : 0.0f;
+                    float part = __fadd_rn(__fadd_rn(pr[0], pr[2]), __fadd_rn(pr[1], pr[3]));
+#pragma unroll
+                    for (int o = 4; o >= 1; o >>= 1) part = __fadd_rn(part, __shfl_xor_sync(0xffffffffu, part, o));
+                    float zq[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        zq[k] = 0.0f;
+                        if (ql + 8 * k < 27) {
+#pragma unroll
+                            for (int i = 0; i < 5; ++i) zq[k] = fmaf(zz[(ql + 8 * k) * 5 + i], bz[i], zq[k]);
+                        }
+                    }
+                    float o[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        // row[ql + 8k] = z[ql + 8k - 1]: lane ql - 1's zq[k], or lane 7's zq[k - 1] for ql = 0
+                        const float up = __shfl_up_sync(0xffffffffu, zq[k], 1, 8);
+                        const float from7 = __shfl_sync(0xffffffffu, zq[k > 0 ? k - 1 : 0], 7, 8);
+                        const int j = ql + 8 * k;
+                        o[k] = ql == 0 ? (k == 0 ? fmaxf(part, 0.0f) : from7) : (j <= 27 ? up : 0.0f);
+                    }
+                    if (valid) {
+                        float *row = p.table + ((size_t)first + l) * TABLE_STRIDE;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) row[ql + 8 * k] = o[k];
+                    }
+                }
+                __syncthreads();  // every thread is done with stage s
+                if (tid == 0) {
+                    const uint32_t c2 = c + (uint32_t)S * gridDim.x;
+                    if (c2 < n_chunks) issue(c2, s);
+                }
+                continue;
+            }
+        }
+        if constexpr ((FPO_MAT_HALF_WARP == 1 || FPO_MAT_HALF_WARP == 3) && N2 == 5 && ST == FPO_STORAGE_F32) {
             if (!p.half_table) {
                 // Half a warp per leaf, two leaves per pass: lane sl of a half
                 // forms k_sl b_sl + k_{sl+16} b_{sl+16} (the first step of the
