@@ -47,15 +47,6 @@
 // against 0.427 ms).  All forms sum in the same order.
 #define FPO_MAT_HALF_WARP 3
 #endif
-#ifndef FPO_VISITS_DBG_ONLY
-#define FPO_VISITS_DBG_ONLY 0
-#endif
-#ifndef FPO_TABLE_PREFETCH_L2
-#define FPO_TABLE_PREFETCH_L2 0
-#endif
-#ifndef FPO_NODE_EVICT_LAST
-#define FPO_NODE_EVICT_LAST 0
-#endif
 #ifndef FPO_FAST_EXIT
 #define FPO_FAST_EXIT 0
 #endif
@@ -876,12 +867,7 @@ __device__ __forceinline__ Cube locate(const TraverseParams &p, const uint32_t *
         const uint32_t idx = node * 8 + c;
 #if FPO_NODE_SMEM == 0
         // every node slot from global memory (read-only path)
-#if FPO_NODE_EVICT_LAST
-        uint32_t sl;
-        asm("ld.global.nc.L1::evict_last.u32 %0, [%1];" : "=r"(sl) : "l"(p.nodes + idx));
-#else
         const uint32_t sl = __ldg(p.nodes + idx);
-#endif
         (void)s_nodes;
 #elif FPO_GENERIC_NODE_LOAD
         // one generic load from shared (top nodes) or global memory: no branch
@@ -1120,7 +1106,7 @@ __device__ __forceinline__ bool shade(const TraverseParams &p, const float *bsrc
         }
         if (p.flags & FPO_FLAG_MARK_LEAVES) p.leaf_mark[p.perm[leaf]] = 1;
     }
-    if (DBG || !FPO_VISITS_DBG_ONLY) ++R.n_visits;
+    ++R.n_visits;
     return R.T < p.stop_T;
 }
 
@@ -1169,10 +1155,7 @@ __device__ __forceinline__ bool pipelined_step(const TraverseParams &p, const fl
         nx = locate(p, s_nodes, s_stack, stride, Pn, D - 1 - (31 - __clz(diff)));
         if (nx.kind == ROOT_LEAF) {
             if constexpr (TM == TM_TABLE_F32) {
-                if (FPO_TABLE_PREFETCH_L2)
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(table_record(p, nx.leaf)));
-                else
-                    asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record(p, nx.leaf)));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(table_record(p, nx.leaf)));
                 if (FPO_PREFETCH_SIBLINGS)  // the aligned group of 4 lines holding it (siblings are adjacent)
                     asm volatile("cp.async.bulk.prefetch.L2.global [%0], 512;" ::"l"(table_record(p, nx.leaf & ~3u)));
             } else if constexpr (TM == TM_TABLE_F16) {
