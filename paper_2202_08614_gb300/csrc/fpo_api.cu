@@ -629,11 +629,11 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
             tl = ctx->n_leaves;
         }
     }
-    if (!ctx->aux) {
-        e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->aux2, cudaStreamNonBlocking);
+    if (!ctx->aux || !ctx->aux2 || !ctx->ev_trav[1]) {  // created once; a failed attempt is retried whole
+        if (!ctx->aux) e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !ctx->aux2) e = cudaStreamCreateWithFlags(&ctx->aux2, cudaStreamNonBlocking);
         for (cudaEvent_t *ev : {&ctx->ev_entry, &ctx->ev_mat[0], &ctx->ev_mat[1], &ctx->ev_trav[0], &ctx->ev_trav[1]})
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+            if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(e, "stream/event creation");
     }
     // Shapes that let both kernels be resident on an SM at once: the IDFT
