@@ -403,6 +403,16 @@ int fpo_decoder_grad(const fpo_mlp *w, int32_t n1, int32_t n2, uint32_t batch, c
 int fpo_decoder_forward(const fpo_mlp *w, int32_t n1, int32_t n2, uint32_t n, const float *latents,
                         float *coeffs, void *cuda_stream);
 
+/* fpo_set_coeffs of the decoder's FP32 coefficients: every leaf's latent
+ * (latents: device [n_leaves][32], upload order) decoded by the MLP `w`
+ * (FP32 master weights, as fpo_decoder_forward) straight into the context's
+ * FP32 records, with no [n_leaves][n1 + 27*n2] array in between.  The values
+ * are those fpo_decoder_forward followed by fpo_set_coeffs writes (the same
+ * arithmetic, bit for bit).  Enqueued on the stream.  Needs FP32 storage and
+ * n1 + 27*n2 <= 176 (else FPO_ERR_UNSUPPORTED).
+ * Errors: INVALID_ARG, NO_TREE, UNSUPPORTED, CUDA. */
+int fpo_set_coeffs_from_decoder(fpo_ctx *ctx, const fpo_mlp *w, const float *latents, void *cuda_stream);
+
 /* Adam step (Kingma & Ba 2015) with bias correction, step counted from 1:
  * dense over n elements (rows NULL), or over the rows of a batch (device
  * rows [n / dim], distinct; param, m, v [N][dim]; grad [n / dim][dim]).
@@ -433,7 +443,8 @@ void fpo_destroy(fpo_ctx *ctx);
 /* Message of the last failure on the calling thread ("" if none). */
 const char *fpo_last_error(void);
 
-/* ABI version: 100 * major + minor (1.1: fpo_render_frames takes frame_done). */
+/* ABI version: 100 * major + minor (1.1: fpo_render_frames takes frame_done;
+ * 1.2: fpo_set_coeffs_from_decoder). */
 int fpo_version(void);
 
 #ifdef __cplusplus

@@ -198,7 +198,7 @@ extern "C" {
 
 const char *fpo_last_error(void) { return g_err.c_str(); }
 
-int fpo_version(void) { return 101; }
+int fpo_version(void) { return 102; }
 
 int fpo_create(fpo_ctx **out, const fpo_config *cfg)
 {
@@ -794,6 +794,27 @@ int fpo_set_coeffs(fpo_ctx *ctx, const float *coeffs, void *cuda_stream)
                                      static_cast<float *>(ctx->d_z), ctx->n_leaves, ctx->cfg.n1,
                                      ctx->cfg.n2, ctx->sm_count, cuda_stream);
     if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "set_coeffs launch");
+    return FPO_OK;
+}
+
+int fpo_set_coeffs_from_decoder(fpo_ctx *ctx, const fpo_mlp *w, const float *latents, void *cuda_stream)
+{
+    if (!ctx) return fail(FPO_ERR_INVALID_ARG, "ctx is NULL");
+    if (!ctx->has_tree) return fail(FPO_ERR_NO_TREE, "set_coeffs_from_decoder before fpo_upload_tree");
+    if (ctx->cfg.storage != FPO_STORAGE_F32)
+        return fail(FPO_ERR_UNSUPPORTED, "in-place coefficient updates need FP32 storage");
+    if (!w || !w->w1 || !w->b1 || !w->w2 || !w->b2 || !w->w3 || !w->b3) return fail(FPO_ERR_INVALID_ARG, "NULL weights");
+    if (ctx->cfg.n1 + 27 * ctx->cfg.n2 > decoder_grad_max_coeffs())
+        return fail(FPO_ERR_UNSUPPORTED, "n1 + 27 n2 above the decoder's 176 outputs");
+    if (ctx->n_leaves == 0) return FPO_OK;
+    if (!latents) return fail(FPO_ERR_INVALID_ARG, "latents is NULL");
+    ctx->table_ok = false;  // the coefficients change
+    DeviceGuard g(ctx->cfg.device);
+    if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
+    const int ce = launch_decode_records(*w, ctx->cfg.n1, ctx->cfg.n2, ctx->n_leaves, latents, ctx->d_perm,
+                                         static_cast<float *>(ctx->d_sig), static_cast<float *>(ctx->d_z),
+                                         ctx->sm_count, cuda_stream);
+    if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "decode launch");
     return FPO_OK;
 }
 

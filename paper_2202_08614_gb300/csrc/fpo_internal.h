@@ -242,6 +242,8 @@ int launch_gather_rows(const void *src, void *dst, const uint32_t *perm, uint32_
 int decoder_grad_max_coeffs();
 int launch_decoder_forward(const fpo_mlp &w, int nc, uint32_t n, const float *latents, float *out, int sm_count,
                            void *stream);
+int launch_decode_records(const fpo_mlp &w, int n1, int n2, uint32_t n, const float *latents, const uint32_t *perm,
+                          float *sig, float *zc, int sm_count, void *stream);
 int launch_adam(float *param, const float *grad, float *m, float *v, uint64_t n, const uint32_t *rows, uint32_t dim,
                 float lr, float b1, float b2, float eps, uint32_t step, int sm_count, void *stream);
 

@@ -5,9 +5,10 @@
 //                       loss against target coefficients (plus an optional
 //                       extra dL/dy, e.g. from the render adjoint), and the
 //                       back-propagation to the latents and to every weight.
-//                       Each CTA keeps all weights and its own weight-gradient
-//                       sums in shared memory, walks tiles of 32 leaves, and
-//                       adds its sums to the global gradients once at the end.
+//                       Each CTA keeps all weights in shared memory, walks
+//                       tiles of 64 leaves with register-tiled products, sums
+//                       its weight gradients in registers, and adds them to
+//                       the global gradients once at the end.
 //  adam_kernel          Adam (Kingma & Ba) on a dense array or on the rows of
 //                       a batch (distinct rows).
 //  leaf_adam_kernel     Adam on the marked leaves' coefficient rows, written
@@ -21,153 +22,316 @@
 namespace fpo {
 namespace {
 
+// Tiles of TG_ROWS leaves; thread (tr, tc) = (tid >> 4, tid & 15) owns rows
+// 4 tr .. 4 tr + 3 and the outputs tc + 16 j of each activation layer, and the
+// weight-gradient entries (tc + 16 j, tr + 16 i) of each layer, summed in
+// registers over all of its CTA's tiles.  Weights are kept as [out][in] rows
+// padded to in + 1 floats, activations as [row][feature] rows padded the same
+// way: a warp then reads 16 consecutive words or a broadcast whichever index
+// it varies, so no shared-memory read has a bank conflict.
 constexpr int TG_THREADS = 256;
-constexpr int TG_ROWS = 32;   // leaves per tile
+constexpr int TG_ROWS = 64;   // leaves per tile
 constexpr int TG_MAXC = 176;  // n1 + 27 n2 <= 176 (31 + 135 = 166)
+constexpr int TG_J = TG_MAXC / 16;
+constexpr int S1 = 33, S2 = 65, SY = TG_MAXC + 1;  // padded row strides
 
-struct Smem {
-    float w1[64 * 32], b1[64], w2[64 * 64], b2[64], w3[TG_MAXC * 64], b3[TG_MAXC];
-    float g1[64 * 32], gb1[64], g2[64 * 64], gb2[64], g3[TG_MAXC * 64], gb3[TG_MAXC];
-    float x[TG_ROWS * 32], z1[TG_ROWS * 64], z2[TG_ROWS * 64], dy[TG_ROWS * TG_MAXC];
-    float d2[TG_ROWS * 64], d1[TG_ROWS * 64];
+struct GradSmem {
+    float w1[64 * S1], w2[64 * S2], w3[TG_MAXC * S2], b1[64], b2[64], b3[TG_MAXC];
+    float x[TG_ROWS * S1], h1[TG_ROWS * S2], h2[TG_ROWS * S2], dy[TG_ROWS * SY];
+    float d2[TG_ROWS * S2], d1[TG_ROWS * S2];
+    uint32_t row[TG_ROWS];
     double loss;
 };
 
 }  // namespace
 
-__global__ void __launch_bounds__(TG_THREADS) decoder_grad_kernel(const __grid_constant__ DecoderGradParams p)
+__global__ void __launch_bounds__(TG_THREADS, 1) decoder_grad_kernel(const __grid_constant__ DecoderGradParams p)
 {
     extern __shared__ __align__(16) unsigned char tg_raw[];
-    Smem &S = *reinterpret_cast<Smem *>(tg_raw);
+    GradSmem &S = *reinterpret_cast<GradSmem *>(tg_raw);
     const int tid = threadIdx.x, nc = p.nc;
-    for (int i = tid; i < 64 * 32; i += TG_THREADS) { S.w1[i] = p.w.w1[i]; S.g1[i] = 0.0f; }
-    for (int i = tid; i < 64 * 64; i += TG_THREADS) { S.w2[i] = p.w.w2[i]; S.g2[i] = 0.0f; }
-    for (int i = tid; i < nc * 64; i += TG_THREADS) { S.w3[i] = p.w.w3[i]; S.g3[i] = 0.0f; }
-    for (int i = tid; i < 64; i += TG_THREADS) { S.b1[i] = p.w.b1[i]; S.b2[i] = p.w.b2[i]; S.gb1[i] = 0.0f; S.gb2[i] = 0.0f; }
-    for (int i = tid; i < nc; i += TG_THREADS) { S.b3[i] = p.w.b3[i]; S.gb3[i] = 0.0f; }
+    const int tr = tid >> 4, tc = tid & 15;
+    for (int i = tid; i < 64 * 32; i += TG_THREADS) S.w1[(i >> 5) * S1 + (i & 31)] = p.w.w1[i];
+    for (int i = tid; i < 64 * 64; i += TG_THREADS) S.w2[(i >> 6) * S2 + (i & 63)] = p.w.w2[i];
+    for (int i = tid; i < TG_MAXC * 64; i += TG_THREADS) {
+        const int j = i >> 6;
+        S.w3[j * S2 + (i & 63)] = j < nc ? p.w.w3[i] : 0.0f;
+    }
+    for (int i = tid; i < 64; i += TG_THREADS) { S.b1[i] = p.w.b1[i]; S.b2[i] = p.w.b2[i]; }
+    for (int i = tid; i < TG_MAXC; i += TG_THREADS) S.b3[i] = i < nc ? p.w.b3[i] : 0.0f;
     if (tid == 0) S.loss = 0.0;
-    __syncthreads();
+
+    float g3[TG_J][4], g2[4][4], g1[4][2], gb = 0.0f, gb2 = 0.0f, gb1 = 0.0f, lsum = 0.0f;
+#pragma unroll
+    for (int j = 0; j < TG_J; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) g3[j][i] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) g2[j][i] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) g1[j][0] = g1[j][1] = 0.0f;
+
     const uint32_t n_tiles = (p.batch + TG_ROWS - 1) / TG_ROWS;
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint32_t r0 = tile * TG_ROWS;
         const int nr = (int)min((uint32_t)TG_ROWS, p.batch - r0);
+        __syncthreads();  // weights staged; the previous tile is done with every buffer
+        if (tid < TG_ROWS) S.row[tid] = tid < nr ? p.rows[r0 + tid] : 0u;
+        __syncthreads();
         for (int i = tid; i < TG_ROWS * 32; i += TG_THREADS) {
             const int r = i >> 5;
-            S.x[i] = r < nr ? p.latents[(size_t)p.rows[r0 + r] * 32 + (i & 31)] : 0.0f;
+            S.x[r * S1 + (i & 31)] = r < nr ? p.latents[(size_t)S.row[r] * 32 + (i & 31)] : 0.0f;
         }
         __syncthreads();
-        // z1 = W1 x + b1
-        for (int i = tid; i < TG_ROWS * 64; i += TG_THREADS) {
-            const int r = i >> 6, o = i & 63;
-            float a = S.b1[o];
-#pragma unroll 8
-            for (int k = 0; k < 32; ++k) a = fmaf(S.w1[o * 32 + k], S.x[r * 32 + k], a);
-            S.z1[i] = a;
-        }
-        __syncthreads();
-        // z2 = W2 relu(z1) + b2
-        for (int i = tid; i < TG_ROWS * 64; i += TG_THREADS) {
-            const int r = i >> 6, o = i & 63;
-            float a = S.b2[o];
-#pragma unroll 8
-            for (int k = 0; k < 64; ++k) a = fmaf(S.w2[o * 64 + k], fmaxf(S.z1[r * 64 + k], 0.0f), a);
-            S.z2[i] = a;
-        }
-        __syncthreads();
-        // y = W3 relu(z2) + b3; dy = 2 cw (y - target) + extra
-        float lsum = 0.0f;
-        for (int i = tid; i < TG_ROWS * nc; i += TG_THREADS) {
-            const int r = i / nc, j = i % nc;
-            float d = 0.0f;
-            if (r < nr) {
-                float a = S.b3[j];
-#pragma unroll 8
-                for (int k = 0; k < 64; ++k) a = fmaf(S.w3[j * 64 + k], fmaxf(S.z2[r * 64 + k], 0.0f), a);
-                const size_t row = p.rows[r0 + r];
-                const float e = a - p.targets[row * nc + j];
-                const float cw = p.coef_weight[j];
-                lsum += cw * e * e;
-                d = 2.0f * cw * e;
-                if (p.extra_dy) d += p.extra_dy[row * nc + j];
+        // h1 = relu(W1 x + b1)
+        {
+            float a[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a[i][j] = S.b1[tc + 16 * j];
+#pragma unroll 4
+            for (int k = 0; k < 32; ++k) {
+                float xv[4], wv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) xv[i] = S.x[(4 * tr + i) * S1 + k];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) wv[j] = S.w1[(tc + 16 * j) * S1 + k];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) a[i][j] = fmaf(xv[i], wv[j], a[i][j]);
             }
-            S.dy[r * TG_MAXC + j] = d;
-        }
-        atomicAdd(&S.loss, (double)lsum);
-        __syncthreads();
-        // d2 = (W3^T dy) * [z2 > 0]; g3 += dy relu(z2)^T; gb3 += dy
-        for (int i = tid; i < TG_ROWS * 64; i += TG_THREADS) {
-            const int r = i >> 6, k = i & 63;
-            float a = 0.0f;
-            for (int j = 0; j < nc; ++j) a = fmaf(S.dy[r * TG_MAXC + j], S.w3[j * 64 + k], a);
-            S.d2[i] = S.z2[i] > 0.0f ? a : 0.0f;
-        }
-        for (int i = tid; i < nc * 64; i += TG_THREADS) {
-            const int j = i >> 6, k = i & 63;
-            float a = 0.0f;
-            for (int r = 0; r < nr; ++r) a = fmaf(S.dy[r * TG_MAXC + j], fmaxf(S.z2[r * 64 + k], 0.0f), a);
-            S.g3[i] += a;
-        }
-        for (int j = tid; j < nc; j += TG_THREADS) {
-            float a = 0.0f;
-            for (int r = 0; r < nr; ++r) a += S.dy[r * TG_MAXC + j];
-            S.gb3[j] += a;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) S.h1[(4 * tr + i) * S2 + tc + 16 * j] = fmaxf(a[i][j], 0.0f);
         }
         __syncthreads();
-        // d1 = (W2^T d2) * [z1 > 0]; g2 += d2 relu(z1)^T; gb2 += d2
-        for (int i = tid; i < TG_ROWS * 64; i += TG_THREADS) {
-            const int r = i >> 6, k = i & 63;
-            float a = 0.0f;
-#pragma unroll 8
-            for (int o = 0; o < 64; ++o) a = fmaf(S.d2[r * 64 + o], S.w2[o * 64 + k], a);
-            S.d1[i] = S.z1[i] > 0.0f ? a : 0.0f;
-        }
-        for (int i = tid; i < 64 * 64; i += TG_THREADS) {
-            const int o = i >> 6, k = i & 63;
-            float a = 0.0f;
-            for (int r = 0; r < nr; ++r) a = fmaf(S.d2[r * 64 + o], fmaxf(S.z1[r * 64 + k], 0.0f), a);
-            S.g2[i] += a;
-        }
-        for (int o = tid; o < 64; o += TG_THREADS) {
-            float a = 0.0f;
-            for (int r = 0; r < nr; ++r) a += S.d2[r * 64 + o];
-            S.gb2[o] += a;
+        // h2 = relu(W2 h1 + b2)
+        {
+            float a[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a[i][j] = S.b2[tc + 16 * j];
+#pragma unroll 4
+            for (int k = 0; k < 64; ++k) {
+                float xv[4], wv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) xv[i] = S.h1[(4 * tr + i) * S2 + k];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) wv[j] = S.w2[(tc + 16 * j) * S2 + k];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) a[i][j] = fmaf(xv[i], wv[j], a[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) S.h2[(4 * tr + i) * S2 + tc + 16 * j] = fmaxf(a[i][j], 0.0f);
         }
         __syncthreads();
-        // dx = W1^T d1; g1 += d1 x^T; gb1 += d1
-        for (int i = tid; i < TG_ROWS * 32; i += TG_THREADS) {
-            const int r = i >> 5, k = i & 31;
-            if (r < nr) {
-                float a = 0.0f;
-#pragma unroll 8
-                for (int o = 0; o < 64; ++o) a = fmaf(S.d1[r * 64 + o], S.w1[o * 32 + k], a);
-                p.dlatents[(size_t)(r0 + r) * 32 + k] = a;
+        // y = W3 h2 + b3; dy = 2 cw (y - target) + extra (0 on padding rows and columns)
+        {
+            float a[4][TG_J];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < TG_J; ++j) a[i][j] = S.b3[tc + 16 * j];
+#pragma unroll 2
+            for (int k = 0; k < 64; ++k) {
+                float xv[4], wv[TG_J];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) xv[i] = S.h2[(4 * tr + i) * S2 + k];
+#pragma unroll
+                for (int j = 0; j < TG_J; ++j) wv[j] = S.w3[(tc + 16 * j) * S2 + k];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < TG_J; ++j) a[i][j] = fmaf(xv[i], wv[j], a[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = 4 * tr + i;
+                const size_t row = S.row[r];
+#pragma unroll
+                for (int j = 0; j < TG_J; ++j) {
+                    const int c = tc + 16 * j;
+                    float d = 0.0f;
+                    if (r < nr && c < nc) {
+                        const float e = a[i][j] - p.targets[row * nc + c];
+                        const float cw = p.coef_weight[c];
+                        lsum = fmaf(cw * e, e, lsum);
+                        d = 2.0f * cw * e;
+                        if (p.extra_dy) d += p.extra_dy[row * nc + c];
+                    }
+                    S.dy[r * SY + c] = d;
+                }
             }
         }
-        for (int i = tid; i < 64 * 32; i += TG_THREADS) {
-            const int o = i >> 5, k = i & 31;
-            float a = 0.0f;
-            for (int r = 0; r < nr; ++r) a = fmaf(S.d1[r * 64 + o], S.x[r * 32 + k], a);
-            S.g1[i] += a;
-        }
-        for (int o = tid; o < 64; o += TG_THREADS) {
-            float a = 0.0f;
-            for (int r = 0; r < nr; ++r) a += S.d1[r * 64 + o];
-            S.gb1[o] += a;
+        __syncthreads();
+        // d2 = (W3^T dy) * [h2 > 0];  g3 += dy h2^T;  gb3 += dy
+        {
+            float a[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a[i][j] = 0.0f;
+#pragma unroll 2
+            for (int c = 0; c < nc; ++c) {
+                float dv[4], wv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) dv[i] = S.dy[(4 * tr + i) * SY + c];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) wv[j] = S.w3[c * S2 + tc + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) a[i][j] = fmaf(dv[i], wv[j], a[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int o = (4 * tr + i) * S2 + tc + 16 * j;
+                    S.d2[o] = S.h2[o] > 0.0f ? a[i][j] : 0.0f;
+                }
+#pragma unroll 2
+            for (int r = 0; r < nr; ++r) {
+                float dv[TG_J], hv[4];
+#pragma unroll
+                for (int j = 0; j < TG_J; ++j) dv[j] = S.dy[r * SY + tc + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) hv[i] = S.h2[r * S2 + tr + 16 * i];
+#pragma unroll
+                for (int j = 0; j < TG_J; ++j)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) g3[j][i] = fmaf(dv[j], hv[i], g3[j][i]);
+            }
+            if (tid < nc)
+                for (int r = 0; r < nr; ++r) gb += S.dy[r * SY + tid];
         }
         __syncthreads();
+        // d1 = (W2^T d2) * [h1 > 0];  g2 += d2 h1^T;  gb2 += d2
+        {
+            float a[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a[i][j] = 0.0f;
+#pragma unroll 4
+            for (int o = 0; o < 64; ++o) {
+                float dv[4], wv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) dv[i] = S.d2[(4 * tr + i) * S2 + o];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) wv[j] = S.w2[o * S2 + tc + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) a[i][j] = fmaf(dv[i], wv[j], a[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int o = (4 * tr + i) * S2 + tc + 16 * j;
+                    S.d1[o] = S.h1[o] > 0.0f ? a[i][j] : 0.0f;
+                }
+#pragma unroll 4
+            for (int r = 0; r < nr; ++r) {
+                float dv[4], hv[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dv[j] = S.d2[r * S2 + tc + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) hv[i] = S.h1[r * S2 + tr + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) g2[j][i] = fmaf(dv[j], hv[i], g2[j][i]);
+            }
+            if (tid < 64)
+                for (int r = 0; r < nr; ++r) gb2 += S.d2[r * S2 + tid];
+        }
+        __syncthreads();
+        // dx = W1^T d1 (the latents' gradient);  g1 += d1 x^T;  gb1 += d1
+        {
+            float a[4][2];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i][0] = a[i][1] = 0.0f;
+#pragma unroll 4
+            for (int o = 0; o < 64; ++o) {
+                float dv[4], wv[2];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) dv[i] = S.d1[(4 * tr + i) * S2 + o];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) wv[j] = S.w1[o * S1 + tc + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) a[i][j] = fmaf(dv[i], wv[j], a[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = 4 * tr + i;
+                if (r < nr) {
+                    p.dlatents[(size_t)(r0 + r) * 32 + tc] = a[i][0];
+                    p.dlatents[(size_t)(r0 + r) * 32 + tc + 16] = a[i][1];
+                }
+            }
+#pragma unroll 4
+            for (int r = 0; r < nr; ++r) {
+                float dv[4], xv[2];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dv[j] = S.d1[r * S2 + tc + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) xv[i] = S.x[r * S1 + tr + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) g1[j][i] = fmaf(dv[j], xv[i], g1[j][i]);
+            }
+            if (tid < 64)
+                for (int r = 0; r < nr; ++r) gb1 += S.d1[r * S2 + tid];
+        }
     }
-    for (int i = tid; i < 64 * 32; i += TG_THREADS) atomicAdd(p.g.w1 + i, S.g1[i]);
-    for (int i = tid; i < 64 * 64; i += TG_THREADS) atomicAdd(p.g.w2 + i, S.g2[i]);
-    for (int i = tid; i < nc * 64; i += TG_THREADS) atomicAdd(p.g.w3 + i, S.g3[i]);
-    for (int i = tid; i < 64; i += TG_THREADS) { atomicAdd(p.g.b1 + i, S.gb1[i]); atomicAdd(p.g.b2 + i, S.gb2[i]); }
-    for (int i = tid; i < nc; i += TG_THREADS) atomicAdd(p.g.b3 + i, S.gb3[i]);
+    // this CTA's sums into the global gradients
+#pragma unroll
+    for (int j = 0; j < TG_J; ++j)
+        if (tc + 16 * j < nc) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) atomicAdd(p.g.w3 + (tc + 16 * j) * 64 + tr + 16 * i, g3[j][i]);
+        }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) atomicAdd(p.g.w2 + (tc + 16 * j) * 64 + tr + 16 * i, g2[j][i]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) atomicAdd(p.g.w1 + (tc + 16 * j) * 32 + tr + 16 * i, g1[j][i]);
+    if (tid < nc) atomicAdd(p.g.b3 + tid, gb);
+    if (tid < 64) {
+        atomicAdd(p.g.b2 + tid, gb2);
+        atomicAdd(p.g.b1 + tid, gb1);
+    }
+    // loss: warp sums, then one shared double per CTA
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    __syncthreads();
+    if ((tid & 31) == 0) atomicAdd(&S.loss, (double)lsum);
+    __syncthreads();
     if (tid == 0 && p.loss) atomicAdd(p.loss, S.loss);
 }
 
 int launch_decoder_grad(const DecoderGradParams &p, int sm_count, void *stream)
 {
     if (p.batch == 0) return (int)cudaSuccess;
-    const int smem = (int)sizeof(Smem);
+    const int smem = (int)sizeof(GradSmem);
     cudaError_t e = cudaFuncSetAttribute(decoder_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return (int)e;
     const uint32_t n_tiles = (p.batch + TG_ROWS - 1) / TG_ROWS;
@@ -183,16 +347,27 @@ int decoder_grad_max_coeffs() { return TG_MAXC; }
 // keeps the transposed weights in shared memory and walks tiles of 64 leaves;
 // each thread owns 4 rows x (outputs tc, tc + 16, ...) of a layer, so a warp
 // reads weight rows without bank conflicts and activations as broadcasts.
+// Record mode (perm != nullptr): output row i is the context's FP32 record
+// i, decoded from latent row perm[i], its first n1 values going to the
+// density records (stride ss) and the rest to the SH records (stride zs).
 constexpr int DF_ROWS = 64, DF_THREADS = 256, DF_MAXC = 176;
 
 struct DecodeSmem {
     float w1t[32 * 64], w2t[64 * 64], w3t[64 * DF_MAXC], b1[64], b2[64], b3[DF_MAXC];
     float x[DF_ROWS * 33], h1[DF_ROWS * 65], h2[DF_ROWS * 65];
+    uint32_t src[DF_ROWS];
+};
+
+struct DecodeOut {
+    float *coeffs;          // [n][nc], or nullptr in record mode
+    const uint32_t *perm;   // record -> latent row (record mode)
+    float *sig, *zc;        // FP32 records (record mode)
+    int n1, ss, zs;
 };
 
 __global__ void __launch_bounds__(DF_THREADS) decoder_forward_kernel(const fpo_mlp w, int nc, uint32_t n,
                                                                       const float *__restrict__ latents,
-                                                                      float *__restrict__ out)
+                                                                      const DecodeOut o)
 {
     extern __shared__ __align__(16) unsigned char df_raw[];
     DecodeSmem &S = *reinterpret_cast<DecodeSmem *>(df_raw);
@@ -210,10 +385,12 @@ __global__ void __launch_bounds__(DF_THREADS) decoder_forward_kernel(const fpo_m
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint32_t r0 = tile * DF_ROWS;
         const int nr = (int)min((uint32_t)DF_ROWS, n - r0);
-        __syncthreads();  // weights staged; the previous tile is done with x, h1, h2
+        __syncthreads();  // weights staged; the previous tile is done with x, h1, h2, src
+        if (tid < DF_ROWS) S.src[tid] = tid < nr ? (o.perm ? o.perm[r0 + tid] : r0 + tid) : 0u;
+        __syncthreads();
         for (int i = tid; i < DF_ROWS * 32; i += DF_THREADS) {
             const int r = i >> 5;
-            S.x[r * 33 + (i & 31)] = r < nr ? latents[(size_t)(r0 + r) * 32 + (i & 31)] : 0.0f;
+            S.x[r * 33 + (i & 31)] = r < nr ? latents[(size_t)S.src[r] * 32 + (i & 31)] : 0.0f;
         }
         __syncthreads();
         {
@@ -287,17 +464,23 @@ __global__ void __launch_bounds__(DF_THREADS) decoder_forward_kernel(const fpo_m
             for (int i = 0; i < 4; ++i) {
                 const int r = 4 * tr + i;
                 if (r < nr) {
+                    const size_t row = r0 + r;
 #pragma unroll
-                    for (int j = 0; j < J; ++j)
-                        if (tc + 16 * j < nc) out[(size_t)(r0 + r) * nc + tc + 16 * j] = a[i][j];
+                    for (int j = 0; j < J; ++j) {
+                        const int c = tc + 16 * j;
+                        if (c >= nc) continue;
+                        if (!o.perm) o.coeffs[row * nc + c] = a[i][j];
+                        else if (c < o.n1) o.sig[row * o.ss + c] = a[i][j];
+                        else o.zc[row * o.zs + (c - o.n1)] = a[i][j];
+                    }
                 }
             }
         }
     }
 }
 
-int launch_decoder_forward(const fpo_mlp &w, int nc, uint32_t n, const float *latents, float *out, int sm_count,
-                           void *stream)
+static int launch_decode(const fpo_mlp &w, int nc, uint32_t n, const float *latents, const DecodeOut &o,
+                         int sm_count, void *stream)
 {
     if (n == 0) return (int)cudaSuccess;
     const int smem = (int)sizeof(DecodeSmem);
@@ -310,8 +493,29 @@ int launch_decoder_forward(const fpo_mlp &w, int nc, uint32_t n, const float *la
     const uint32_t n_tiles = (n + DF_ROWS - 1) / DF_ROWS;
     uint64_t blocks = (uint64_t)sm_count * per_sm;
     if (blocks > n_tiles) blocks = n_tiles;
-    decoder_forward_kernel<<<(unsigned)blocks, DF_THREADS, smem, (cudaStream_t)stream>>>(w, nc, n, latents, out);
+    decoder_forward_kernel<<<(unsigned)blocks, DF_THREADS, smem, (cudaStream_t)stream>>>(w, nc, n, latents, o);
     return (int)cudaGetLastError();
+}
+
+int launch_decoder_forward(const fpo_mlp &w, int nc, uint32_t n, const float *latents, float *out, int sm_count,
+                           void *stream)
+{
+    DecodeOut o{};
+    o.coeffs = out;
+    return launch_decode(w, nc, n, latents, o, sm_count, stream);
+}
+
+int launch_decode_records(const fpo_mlp &w, int n1, int n2, uint32_t n, const float *latents, const uint32_t *perm,
+                          float *sig, float *zc, int sm_count, void *stream)
+{
+    DecodeOut o{};
+    o.perm = perm;
+    o.sig = sig;
+    o.zc = zc;
+    o.n1 = n1;
+    o.ss = sig_stride(n1);
+    o.zs = z_stride(n2);
+    return launch_decode(w, n1 + 27 * n2, n, latents, o, sm_count, stream);
 }
 
 // Adam: m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,

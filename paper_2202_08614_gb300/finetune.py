@@ -22,10 +22,8 @@ import numpy as np
 from . import fpo
 
 
-def camera_ray_batch(cams, n, gen, n_frames=60):
-    """n training rays drawn uniformly over (camera, integer frame, pixel):
-    origins, unit directions (pixel centres of the pinhole model documented
-    in fpo.h) and frame times, as CUDA tensors.  `gen`: a CUDA torch.Generator."""
+def camera_basis(cams):
+    """Eye, forward, right and up vectors of each camera: CUDA float32 [n, 12]."""
     import torch
 
     basis = []
@@ -35,7 +33,17 @@ def camera_ray_batch(cams, n, gen, n_frames=60):
         r = np.cross(f, up)
         r /= np.linalg.norm(r)
         basis.append(np.concatenate([eye, f, r, np.cross(r, f)]))
-    B = torch.as_tensor(np.stack(basis), dtype=torch.float32, device="cuda")
+    return torch.as_tensor(np.stack(basis), dtype=torch.float32, device="cuda")
+
+
+def camera_ray_batch(cams, n, gen, n_frames=60, basis=None):
+    """n training rays drawn uniformly over (camera, integer frame, pixel):
+    origins, unit directions (pixel centres of the pinhole model documented
+    in fpo.h) and frame times, as CUDA tensors.  `gen`: a CUDA torch.Generator;
+    `basis`: camera_basis(cams), if already at hand."""
+    import torch
+
+    B = camera_basis(cams) if basis is None else basis
     W, H = cams[0].width, cams[0].height
     th = np.tan(np.radians(cams[0].fov_y_deg) / 2)
     v = torch.randint(0, len(cams), (n,), device="cuda", generator=gen)

@@ -35,7 +35,7 @@ EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
            "fpo_last_error", "fpo_version", "fpo_render_noalloc", "fpo_set_coeffs",
            "fpo_dft_leaves", "fpo_union_trees", "fpo_latent_table", "fpo_decoder_grad",
            "fpo_adam", "fpo_set_latents", "fpo_render_frames", "fpo_adam_leaves",
-           "fpo_decoder_forward"]
+           "fpo_decoder_forward", "fpo_set_coeffs_from_decoder"]
 
 
 class FPOError(RuntimeError):
@@ -117,6 +117,7 @@ def lib():
         L.fpo_decoder_grad.argtypes = [C.POINTER(Mlp), C.c_int32, C.c_int32, C.c_uint32, P, P, P, P,
                                        P, C.POINTER(Mlp), P, P, P]
         L.fpo_decoder_forward.argtypes = [C.POINTER(Mlp), C.c_int32, C.c_int32, C.c_uint32, P, P, P]
+        L.fpo_set_coeffs_from_decoder.argtypes = [P, C.POINTER(Mlp), P, P]
         L.fpo_adam.argtypes = [P, P, P, P, C.c_uint64, P, C.c_uint32, C.c_float, C.c_float,
                                C.c_float, C.c_float, C.c_uint32, P]
         L.fpo_set_latents.argtypes = [P, P, C.POINTER(Decoder), P]
@@ -358,6 +359,17 @@ class Renderer:
         assert c.is_cuda and c.dtype.is_floating_point and c.is_contiguous()
         check(lib().fpo_set_coeffs(self.h, C.c_void_p(c.data_ptr()),
                                    C.c_void_p(_stream_handle(stream))))
+
+    def set_coeffs_from_decoder(self, mlp, latents, stream=None):
+        """Replaces the tree's coefficients with the decoder's FP32 decode of
+        every leaf's latent (mlp: an Mlp of FP32 device weights; latents: a
+        CUDA float32 tensor [n_leaves, 32] in upload order)."""
+        import torch
+
+        lat = latents.detach()
+        assert lat.is_cuda and lat.dtype == torch.float32 and lat.is_contiguous()
+        check(lib().fpo_set_coeffs_from_decoder(self.h, C.byref(mlp), C.c_void_p(lat.data_ptr()),
+                                                C.c_void_p(_stream_handle(stream))))
 
     def set_latents(self, latents_f16, w1, b1, w2, b2, w3, b3, stream=None):
         """LATENT storage: per-leaf FP16 latents [n_leaves, 32] (CUDA, upload

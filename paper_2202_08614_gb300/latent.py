@@ -203,11 +203,14 @@ class PixelLoss:
         self.ref.upload(tree)
         self.work = fpo.Renderer(n1=tree.n1, n2=tree.n2, idft_mode="fused")
         self.work.upload(tree)
+        from .finetune import camera_basis
+
         n, nc = tree.coeffs.shape
-        self.dec = torch.empty((n, nc), device="cuda")
         self.dy = torch.zeros((n, nc), device="cuda")
+        self.rows = None  # the rows of dy the last gradient wrote
         self.mark = torch.zeros(n, dtype=torch.uint8, device="cuda")
         self.gen = torch.Generator(device="cuda").manual_seed(seed)
+        self.basis = camera_basis(cams)
         self.last_loss = None
 
     def gradient(self, model):
@@ -217,19 +220,19 @@ class PixelLoss:
 
         from .finetune import camera_ray_batch
 
-        model.decode(out=self.dec)
-        self.work.set_coeffs(self.dec)
-        o, d, t = camera_ray_batch(self.cams, self.rays, self.gen, self.n_frames)
+        self.work.set_coeffs_from_decoder(model._mlp(model.p), model.p["lat"])
+        o, d, t = camera_ray_batch(self.cams, self.rays, self.gen, self.n_frames, basis=self.basis)
         kw = dict(rays_o=o, rays_d=d, t_per_ray=t, bg=self.bg, stop_T=self.stop_T)
         y = self.ref.render(**kw)["rgb"]
         rgb = self.work.render(**kw)["rgb"]
         diff = rgb - y
         self.last_loss = (diff * diff).sum(1).mean()
-        self.dy.zero_()
+        if self.rows is not None:  # only the last gradient's rows are non-zero
+            self.dy.index_fill_(0, self.rows.long(), 0.0)
         self.mark.zero_()
         self.work.render_backward(rgb, diff * (2.0 * self.weight / self.rays), self.dy, leaf_mark=self.mark, **kw)
-        rows = torch.nonzero(self.mark).flatten().to(torch.int32)
-        return rows, self.dy
+        self.rows = torch.nonzero(self.mark).flatten().to(torch.int32)
+        return self.rows, self.dy
 
     def close(self):
         self.ref.close()

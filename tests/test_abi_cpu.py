@@ -38,7 +38,7 @@ def test_exports_every_declared_symbol(L):
     assert set(declared) <= exported
     for name in declared:
         assert hasattr(L, name)
-    assert L.fpo_version() == 101
+    assert L.fpo_version() == 102
 
 
 def test_struct_layout_matches_header(tmp_path):

@@ -204,3 +204,50 @@ def test_decoder_forward_matches_reference():
     ref = olat.decode(P["lat"], P["w1"], P["b1"], P["w2"], P["b2"], P["w3"], P["b3"])
     # FP32 sums of at most 64 products: a few ulp of the largest partial sums
     np.testing.assert_allclose(y, ref, rtol=0, atol=2e-5 * max(1.0, np.abs(ref).max()))
+
+
+def test_set_coeffs_from_decoder_equals_decode_then_set_coeffs():
+    # the fused decode into the context's records writes what
+    # fpo_decoder_forward + fpo_set_coeffs write: renders are bit-equal; the
+    # decoded values themselves match the FP64 reference (a ragged last tile)
+    rng = np.random.default_rng(6)
+    d, xyz, _ = _smooth_tree(5)
+    n = d.shape[0]
+    m = LatentModel(n, seed=11)
+    m.p["b1"].copy_(torch.as_tensor(rng.normal(size=64) * 0.1))
+    m.p["b3"].copy_(torch.as_tensor(rng.normal(size=NC)))
+    m.p["b3"][0] = 30.0
+    empty = synth.Tree(d, xyz, np.zeros((n, NC), np.float32), 5)
+    a, b = fpo.Renderer(idft_mode="fused"), fpo.Renderer(idft_mode="fused")
+    try:
+        a.upload(empty)
+        b.upload(empty)
+        dec = m.decode()
+        a.set_coeffs(dec)
+        b.set_coeffs_from_decoder(m._mlp(m.p), m.p["lat"])
+        cam = synth.Camera(eye=synth.sphere_eye(75, 25), width=64, height=48)
+        ia = a.render(camera=cam, t=13.0)["rgb"]
+        ib = b.render(camera=cam, t=13.0)["rgb"]
+        a.status()
+        b.status()
+        assert torch.equal(ia, ib)
+        P = {k: v.double().cpu().numpy() for k, v in m.p.items()}
+        ref = olat.decode(P["lat"], P["w1"], P["b1"], P["w2"], P["b2"], P["w3"], P["b3"])
+        assert n % 64 != 0  # a ragged last tile
+        np.testing.assert_allclose(dec.double().cpu().numpy(), ref, rtol=0, atol=2e-5 * np.abs(ref).max())
+        with pytest.raises(AssertionError):
+            b.set_coeffs_from_decoder(m._mlp(m.p), m.p["lat"].half())
+        with pytest.raises(fpo.FPOError) as e:
+            fpo.check(fpo.lib().fpo_set_coeffs_from_decoder(b.h, C.byref(m._mlp(m.p)), None, None))
+        assert e.value.code == -1
+    finally:
+        a.close()
+        b.close()
+    c = fpo.Renderer(storage="bf16")
+    try:
+        c.upload(empty)
+        with pytest.raises(fpo.FPOError) as e:
+            c.set_coeffs_from_decoder(m._mlp(m.p), m.p["lat"])
+        assert e.value.code == -8
+    finally:
+        c.close()
