@@ -2070,10 +2070,158 @@ __global__ void __launch_bounds__(256) dft_tile_kernel(const float *__restrict__
     }
 }
 
+// Pipelined version of dft_tile_kernel (same ownership of coefficients by
+// lanes and warps, same summation order, so the same bits): each CTA streams
+// the frames of its tiles through a ring of DFT_STAGES stages of DFT_FPS
+// frames with cp.async (16-byte copies, hardware-tracked groups: no software
+// wait), DFT_STAGES - 1 stages ahead and across tile boundaries.  A frame of a
+// tile is 32 leaves x 28 values, 3584 contiguous bytes, kept unpadded; lane l
+// of an SH warp reads its series rotated by l / 8, which spreads a warp's
+// reads of one frame over all 32 banks.
+#ifndef FPO_DFT_FPS
+#define FPO_DFT_FPS 4
+#endif
+#ifndef FPO_DFT_STAGES
+#define FPO_DFT_STAGES 3  // measured: 3 stages (three CTAs per SM) 1.14 ms, 4 stages 1.21, 6 stages 1.22 (512K leaves)
+#endif
+constexpr int DFT_FPS = FPO_DFT_FPS, DFT_STAGES = FPO_DFT_STAGES, DFT_FRAME_FLOATS = DFT_TILE * 28;
+
+__device__ __forceinline__ void dft_issue(const float *__restrict__ values, float *ring, uint32_t n_leaves, int T,
+                                          uint32_t n_tiles, uint32_t unit, int groups)
+{
+    const uint32_t tile = blockIdx.x + (unit / groups) * gridDim.x;
+    if (tile < n_tiles) {
+        const uint32_t leaf0 = tile * DFT_TILE;
+        const int nl = (int)min((uint32_t)DFT_TILE, n_leaves - leaf0);
+        const int f0 = (int)(unit % groups) * DFT_FPS, nf = min(DFT_FPS, T - f0);
+        float *dst = ring + (size_t)(unit % DFT_STAGES) * DFT_FPS * DFT_FRAME_FLOATS;
+        for (int q = threadIdx.x; q < nf * nl * 7; q += blockDim.x) {
+            const int f = q / (nl * 7), c = q % (nl * 7);
+            const float *src = values + ((size_t)(f0 + f) * n_leaves + leaf0) * 28 + 4 * c;
+            const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + f * DFT_FRAME_FLOATS + 4 * c);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(256) dft_pipe_kernel(const float *__restrict__ values, float *__restrict__ coeffs,
+                                                       uint32_t n_leaves, int n1, int T)
+{
+    extern __shared__ __align__(16) float dft_smem[];
+    float *ring = dft_smem;                                            // [stages][frames][32 leaves][28]
+    float *s_w = ring + DFT_STAGES * DFT_FPS * DFT_FRAME_FLOATS;       // [T][32]
+    const int nc = n1 + 27 * DFT_N2;
+    float *s_out = s_w + (size_t)T * 32;                               // [32 leaves][nc]
+    const uint32_t n_tiles = (n_leaves + DFT_TILE - 1) / DFT_TILE;
+    const int groups = (T + DFT_FPS - 1) / DFT_FPS;
+    const uint32_t my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const uint32_t units = my_tiles * (uint32_t)groups;
+    for (int s = 0; s < DFT_STAGES - 1; ++s) dft_issue(values, ring, n_leaves, T, n_tiles, (uint32_t)s, groups);
+    for (int q = threadIdx.x; q < 32 * T; q += blockDim.x) {
+        const int t = q / 32, i = q % 32, nb = n1 > DFT_N2 ? n1 : DFT_N2;
+        const double u = (double)(t + 1) / (double)T;
+        const double w = (i == 0 ? 1.0 : 2.0) / (double)T;
+        s_w[q] = i < nb ? (float)(w * ((i & 1) ? sinpi((double)(i + 1) * u) : cospi((double)i * u))) : 0.0f;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int ser[4];  // this lane's series (warp 0: the density series; warps 1..7: SH series, rotated by lane / 8)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int b = warp - 1 + 7 * q;
+        ser[q] = warp == 0 ? (q == 0 ? 0 : -1) : (b <= 26 ? 1 + (b + (lane >> 3)) % 27 : -1);
+    }
+    float acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
+    for (uint32_t unit = 0; unit < units; ++unit) {
+        asm volatile("cp.async.wait_group %0;" ::"n"(DFT_STAGES - 2) : "memory");
+        __syncthreads();  // unit's frames are in; every warp is done with the stage refilled next
+        dft_issue(values, ring, n_leaves, T, n_tiles, unit + DFT_STAGES - 1, groups);
+        const uint32_t tile = blockIdx.x + (unit / groups) * gridDim.x;
+        const uint32_t leaf0 = tile * DFT_TILE;
+        const int nl = (int)min((uint32_t)DFT_TILE, n_leaves - leaf0);
+        const int g = (int)(unit % groups), f0 = g * DFT_FPS, nf = min(DFT_FPS, T - f0);
+        const float *st = ring + (size_t)(unit % DFT_STAGES) * DFT_FPS * DFT_FRAME_FLOATS;
+        if (lane < nl) {
+            for (int f = 0; f < nf; ++f) {
+                const float *xr = st + f * DFT_FRAME_FLOATS + lane * 28;
+                const float4 *wr = reinterpret_cast<const float4 *>(s_w + (size_t)(f0 + f) * 32);
+                if (warp == 0) {
+                    const float x = xr[0];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const float4 w = wr[k];
+                        acc[4 * k] = fmaf(x, w.x, acc[4 * k]);
+                        acc[4 * k + 1] = fmaf(x, w.y, acc[4 * k + 1]);
+                        acc[4 * k + 2] = fmaf(x, w.z, acc[4 * k + 2]);
+                        acc[4 * k + 3] = fmaf(x, w.w, acc[4 * k + 3]);
+                    }
+                } else {
+                    const float4 w4 = wr[0];
+                    const float w5 = s_w[(size_t)(f0 + f) * 32 + 4];
+                    const float wv[DFT_N2] = {w4.x, w4.y, w4.z, w4.w, w5};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (ser[q] < 0) continue;
+                        const float x = xr[ser[q]];
+#pragma unroll
+                        for (int i = 0; i < DFT_N2; ++i) acc[q * DFT_N2 + i] = fmaf(x, wv[i], acc[q * DFT_N2 + i]);
+                    }
+                }
+            }
+        }
+        if (g == groups - 1) {  // the tile's sums are complete: stage them, write them contiguously
+            if (lane < nl) {
+                float *o = s_out + (size_t)lane * nc;
+                if (warp == 0) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (i < n1) o[i] = acc[i];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (ser[q] < 0) continue;
+#pragma unroll
+                        for (int i = 0; i < DFT_N2; ++i) o[n1 + (ser[q] - 1) * DFT_N2 + i] = acc[q * DFT_N2 + i];
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
+            __syncthreads();
+            for (int q = threadIdx.x; q < nl * nc; q += blockDim.x) coeffs[(size_t)leaf0 * nc + q] = s_out[q];
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // nothing left in flight (the issues past the end copy nothing)
+}
+
+#ifndef FPO_DFT_PIPE
+#define FPO_DFT_PIPE 1
+#endif
+
 int launch_dft(const float *values, float *coeffs, uint32_t n_leaves, int n1, int n2, int T, int sm_count,
                void *stream)
 {
     if (n_leaves == 0) return (int)cudaSuccess;
+    // the 16-byte asynchronous copies need a 16-byte aligned base (every row
+    // offset is a multiple of 112 bytes); other bases take the tile kernel
+    if (FPO_DFT_PIPE && n2 == DFT_N2 && n1 <= 32 && (reinterpret_cast<uintptr_t>(values) & 15u) == 0) {
+        const int nc = n1 + 27 * DFT_N2;
+        const size_t smem = ((size_t)DFT_STAGES * DFT_FPS * DFT_FRAME_FLOATS + (size_t)T * 32 + (size_t)DFT_TILE * nc) *
+                            sizeof(float);
+        cudaError_t e = cudaFuncSetAttribute(dft_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dft_pipe_kernel, 256, smem);
+        if (e != cudaSuccess) return (int)e;
+        if (per_sm < 1) per_sm = 1;
+        const uint64_t n_tiles = (n_leaves + DFT_TILE - 1) / DFT_TILE;
+        uint64_t blocks = (uint64_t)sm_count * per_sm;
+        if (blocks > n_tiles) blocks = n_tiles;
+        dft_pipe_kernel<<<(unsigned)blocks, 256, smem, (cudaStream_t)stream>>>(values, coeffs, n_leaves, n1, T);
+        return (int)cudaGetLastError();
+    }
     if (n2 == DFT_N2 && n1 <= 32) {
         const int nc = n1 + 27 * DFT_N2;
         const size_t smem = ((size_t)T * 32 + DFT_TC * DFT_TILE * DFT_XPAD + (size_t)DFT_TILE * nc) * sizeof(float);

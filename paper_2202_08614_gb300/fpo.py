@@ -472,15 +472,18 @@ def latent_table(latents, w1, b1, w2, b2, w3, b3, t, period_T=60.0, n1=31, n2=5,
     return out, status
 
 
-def dft_leaves(values, n1=31, n2=5, stream=None):
+def dft_leaves(values, n1=31, n2=5, stream=None, out=None):
     """Eq. 10-12 on the GPU: values [T, n_leaves, 28] (CUDA float32) ->
-    coefficients [n_leaves, n1 + 27 n2] (canonical)."""
+    coefficients [n_leaves, n1 + 27 n2] (canonical), into `out` if given
+    (a contiguous CUDA float32 tensor of that shape)."""
     import torch
 
     v = values.contiguous()
     T, n, w = v.shape
     assert w == 28 and v.is_cuda and v.dtype == torch.float32
-    out = torch.empty((n, n1 + 27 * n2), dtype=torch.float32, device=v.device)
+    if out is None:
+        out = torch.empty((n, n1 + 27 * n2), dtype=torch.float32, device=v.device)
+    assert out.shape == (n, n1 + 27 * n2) and out.dtype == torch.float32 and out.is_cuda and out.is_contiguous()
     check(lib().fpo_dft_leaves(n1, n2, T, n, C.c_void_p(v.data_ptr() if n else None),
                                C.c_void_p(out.data_ptr() if n else None),
                                C.c_void_p(_stream_handle(stream))))

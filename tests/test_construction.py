@@ -118,6 +118,31 @@ def test_dft_leaves_matches_oracle(n1, n2, T, n):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("n1,T,n", [(31, 60, 3000), (31, 37, 70), (11, 256, 100), (31, 5, 1)])
+def test_dft_pipelined_and_tiled_kernels_agree(n1, T, n):
+    # a 16-byte aligned values array takes the cp.async-pipelined kernel, one
+    # shifted by a float the tiled kernel: same lanes, same summation order
+    torch = _cuda()
+    rng = np.random.default_rng(T + n)
+    vals = torch.as_tensor(rng.normal(size=(T, n, 28)).astype(np.float32), device="cuda")
+    shifted = torch.empty(T * n * 28 + 1, device="cuda")
+    shifted[1:] = vals.flatten()
+    mis = shifted[1:].view(T, n, 28)
+    assert vals.data_ptr() % 16 == 0 and mis.data_ptr() % 16 != 0
+    a = fpo.dft_leaves(vals, n1, 5)
+    b = fpo.dft_leaves(mis, n1, 5)
+    whole = torch.full((n + 3, n1 + 135), float("nan"), device="cuda")
+    fpo.dft_leaves(vals, n1, 5, out=whole[2:n + 2])  # into rows of a larger array
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(whole[2:n + 2], a)
+    assert whole[:2].isnan().all() and whole[n + 2:].isnan().all()
+    k_sig = oracle.dft(vals[:, :, 0].double().cpu().numpy(), n1)
+    k_z = oracle.dft(vals[:, :, 1:].reshape(T, -1).double().cpu().numpy(), 5).reshape(n, 135)
+    ref = np.concatenate([k_sig, k_z], axis=1)
+    assert np.abs(a.cpu().numpy() - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.gpu
 def test_generation_chain_reproduces_frames():
     # per-leaf values that are band-limited in time (frequency <= 2 for z,
     # <= 15 for sigma) go through union -> DFT -> IDFT exactly, so a frame
