@@ -361,15 +361,17 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
     coeffs = torch.empty((n, 166), dtype=torch.float32, device="cuda")
     ch = 1 << 19
     dft_ms = 0.0
+    dft_status = torch.zeros(1, dtype=torch.int32, device="cuda")
     for s0 in range(0, n, ch):
         vals = synth.smooth_frame_values(tree.leaf_depth[s0:s0 + ch], tree.leaf_xyz[s0:s0 + ch], body)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        fpo.dft_leaves(vals, out=coeffs[s0:s0 + ch])
+        fpo.dft_leaves(vals, out=coeffs[s0:s0 + ch], status=dft_status)
         e1.record()
         torch.cuda.synchronize()
         dft_ms += e0.elapsed_time(e1)
         del vals
+    fpo.check_status_word(dft_status)
     # Eq. 10-12 over the whole tree: 60 frames x 28 values in, 166 coefficients out per leaf
     dft_bytes = n * (60 * 28 + 166) * 4
     res["generation_dft"] = {"ms": dft_ms, "leaves": n, "frames": 60, "alg_bytes": dft_bytes,

@@ -315,9 +315,18 @@ int fpo_adam_leaves(fpo_ctx *ctx, float *param, float *grad, float *m, float *v,
  * w_i = 2 for i >= 1, so that Eq. 8 inverts it exactly for signals of
  * frequency below T/2 (the paper prints w_i = 1, under which Eq. 8 would
  * halve every non-constant term).  Runs on the current device and stream.
- * Errors: INVALID_ARG (n1 in [1, 32], n2 in [1, 16], n_frames in [1, 256]), CUDA. */
+ * With n2 = 5 and a 16-byte aligned `values`, frames are moved by bulk
+ * asynchronous copies whose waits are bounded: a copy that has not landed
+ * after 2 s makes its CTA write NaN to every coefficient of its unfinished
+ * tiles, wait (bounded) for its copies in flight, and OR the value 4 (a
+ * device-side wait gave up: FPO_ERR_DEVICE_TIMEOUT) into *status.  status: an optional
+ * device word (NULL: the NaN coefficients alone show it); flags: 0, or
+ * FPO_FLAG_TEST_DEVICE_TIMEOUT to make each CTA's first wait run out after
+ * 1 ms (tests of that path).
+ * Errors: INVALID_ARG (n1 in [1, 32], n2 in [1, 16], n_frames in [1, 256],
+ * unknown flags), CUDA. */
 int fpo_dft_leaves(int32_t n1, int32_t n2, uint32_t n_frames, uint32_t n_leaves,
-                   const float *values, float *coeffs, void *cuda_stream);
+                   const float *values, float *coeffs, uint32_t *status, uint32_t flags, void *cuda_stream);
 
 /* One frame's octree for fpo_union_trees (host arrays): leaves as in
  * fpo_tree_desc, values [n_leaves][28] = sigma, then z_{c,k} (c = 0..2,
@@ -444,7 +453,7 @@ void fpo_destroy(fpo_ctx *ctx);
 const char *fpo_last_error(void);
 
 /* ABI version: 100 * major + minor (1.1: fpo_render_frames takes frame_done;
- * 1.2: fpo_set_coeffs_from_decoder). */
+ * 1.2: fpo_set_coeffs_from_decoder; fpo_dft_leaves takes status and flags). */
 int fpo_version(void);
 
 #ifdef __cplusplus

@@ -859,9 +859,10 @@ int fpo_adam_leaves(fpo_ctx *ctx, float *param, float *grad, float *m, float *v,
 }
 
 int fpo_dft_leaves(int32_t n1, int32_t n2, uint32_t n_frames, uint32_t n_leaves, const float *values,
-                   float *coeffs, void *cuda_stream)
+                   float *coeffs, uint32_t *status, uint32_t flags, void *cuda_stream)
 {
     if (n1 < 1 || n1 > 32 || n2 < 1 || n2 > 16) return fail(FPO_ERR_INVALID_ARG, "n1 in [1, 32], n2 in [1, 16]");
+    if (flags & ~(uint32_t)FPO_FLAG_TEST_DEVICE_TIMEOUT) return fail(FPO_ERR_INVALID_ARG, "unknown flags");
     if (n_frames < 1 || n_frames > 256) return fail(FPO_ERR_INVALID_ARG, "n_frames must be in [1, 256]");
     if (n_leaves == 0) return FPO_OK;
     if (!values || !coeffs) return fail(FPO_ERR_INVALID_ARG, "NULL array");
@@ -869,7 +870,8 @@ int fpo_dft_leaves(int32_t n1, int32_t n2, uint32_t n_frames, uint32_t n_leaves,
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "device query");
-    const int ce = launch_dft(values, coeffs, n_leaves, n1, n2, (int)n_frames, sms, cuda_stream);
+    const int ce = launch_dft(values, coeffs, n_leaves, n1, n2, (int)n_frames, status,
+                              (flags & FPO_FLAG_TEST_DEVICE_TIMEOUT) != 0, sms, cuda_stream);
     if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "dft launch");
     return FPO_OK;
 }

@@ -281,8 +281,8 @@ struct MatShape {
 MatShape materialise_pipeline_shape(int storage, int n1, int n2, int smem_budget);
 int materialise_smem_bytes(const MaterialiseParams &p);  // dynamic shared memory of one CTA
 int launch_backward(const BackwardParams &q, int sm_count, void *stream);
-int launch_dft(const float *values, float *coeffs, uint32_t n_leaves, int n1, int n2, int T, int sm_count,
-               void *stream);
+int launch_dft(const float *values, float *coeffs, uint32_t n_leaves, int n1, int n2, int T, uint32_t *status,
+               bool test_timeout, int sm_count, void *stream);
 int launch_set_coeffs(const float *src, const uint32_t *perm, float *sig, float *zc, uint32_t n_leaves,
                       int n1, int n2, int sm_count, void *stream);
 int launch_leaf_adam(const LeafAdamParams &p, int sm_count, void *stream);

@@ -2070,87 +2070,110 @@ __global__ void __launch_bounds__(256) dft_tile_kernel(const float *__restrict__
     }
 }
 
-// Pipelined version of dft_tile_kernel (same ownership of coefficients by
-// lanes and warps, same summation order, so the same bits): each CTA streams
-// the frames of its tiles through a ring of DFT_STAGES stages of DFT_FPS
-// frames with cp.async (16-byte copies, hardware-tracked groups: no software
-// wait), DFT_STAGES - 1 stages ahead and across tile boundaries.  A frame of a
-// tile is 32 leaves x 28 values, 3584 contiguous bytes, kept unpadded; lane l
-// of an SH warp reads its series rotated by l / 8, which spreads a warp's
-// reads of one frame over all 32 banks.
-#ifndef FPO_DFT_FPS
-#define FPO_DFT_FPS 4
+// Bulk-copy version (the default), bit-equal to the two kernels above (each
+// coefficient is summed over t in the same order).  Thread 0 moves each frame
+// of a tile (32 leaves x 28 values: 3584 contiguous bytes) into a ring stage
+// with one bulk asynchronous copy, completion counted in bytes on the stage's
+// mbarrier, DFTB_STAGES units of DFTB_FPS frames ahead and across tile
+// boundaries (a 16-byte cp.async version of this ring, with the tile
+// kernel's eight warps, peaked at 1.14 ms on 512K leaves: the per-SM limit on
+// outstanding requests).  Nine warps share a frame's work evenly: lane l owns
+// leaf l; warps 0 and 1 the density coefficients 0..15 and 16..n1-1, warps
+// 2..8 the 27 SH series (3 or 4 each, rotated by l / 8 so a warp's reads of
+// one frame hit all 32 banks).  A wait that runs out (2 s;
+// 1 ms for the first wait with FPO_FLAG_TEST_DEVICE_TIMEOUT) sets
+// STATUS_DEVICE_TIMEOUT in *status (if given), writes NaN to every
+// coefficient of the CTA's unfinished tiles, waits (bounded) for its copies
+// in flight and returns.
+// Measured on 512K leaves x 60 frames (frames per stage x stages): 12 x 2
+// 0.79 ms, 8 x 2 0.87, 8 x 3 0.88, 10 x 2 0.85, 15 x 2 1.16, 20 x 2 1.10.
+#ifndef FPO_DFT_BULK_FPS
+#define FPO_DFT_BULK_FPS 12
 #endif
-#ifndef FPO_DFT_STAGES
-#define FPO_DFT_STAGES 3  // measured: 3 stages (three CTAs per SM) 1.14 ms, 4 stages 1.21, 6 stages 1.22 (512K leaves)
+#ifndef FPO_DFT_BULK_STAGES
+#define FPO_DFT_BULK_STAGES 2
 #endif
-constexpr int DFT_FPS = FPO_DFT_FPS, DFT_STAGES = FPO_DFT_STAGES, DFT_FRAME_FLOATS = DFT_TILE * 28;
+constexpr int DFTB_FPS = FPO_DFT_BULK_FPS, DFTB_STAGES = FPO_DFT_BULK_STAGES, DFTB_THREADS = 288;
+constexpr int DFT_FRAME_FLOATS = DFT_TILE * 28;  // one frame of a tile
 
-__device__ __forceinline__ void dft_issue(const float *__restrict__ values, float *ring, uint32_t n_leaves, int T,
-                                          uint32_t n_tiles, uint32_t unit, int groups)
+__global__ void __launch_bounds__(DFTB_THREADS) dft_bulk_kernel(const float *__restrict__ values,
+                                                                float *__restrict__ coeffs, uint32_t n_leaves,
+                                                                int n1, int T, uint32_t *status, bool test_timeout)
 {
-    const uint32_t tile = blockIdx.x + (unit / groups) * gridDim.x;
-    if (tile < n_tiles) {
-        const uint32_t leaf0 = tile * DFT_TILE;
-        const int nl = (int)min((uint32_t)DFT_TILE, n_leaves - leaf0);
-        const int f0 = (int)(unit % groups) * DFT_FPS, nf = min(DFT_FPS, T - f0);
-        float *dst = ring + (size_t)(unit % DFT_STAGES) * DFT_FPS * DFT_FRAME_FLOATS;
-        for (int q = threadIdx.x; q < nf * nl * 7; q += blockDim.x) {
-            const int f = q / (nl * 7), c = q % (nl * 7);
-            const float *src = values + ((size_t)(f0 + f) * n_leaves + leaf0) * 28 + 4 * c;
-            const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + f * DFT_FRAME_FLOATS + 4 * c);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-        }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-__global__ void __launch_bounds__(256) dft_pipe_kernel(const float *__restrict__ values, float *__restrict__ coeffs,
-                                                       uint32_t n_leaves, int n1, int T)
-{
-    extern __shared__ __align__(16) float dft_smem[];
-    float *ring = dft_smem;                                            // [stages][frames][32 leaves][28]
-    float *s_w = ring + DFT_STAGES * DFT_FPS * DFT_FRAME_FLOATS;       // [T][32]
+    extern __shared__ __align__(128) float dftb_smem[];
+    __shared__ uint64_t bars[DFTB_STAGES];
+    __shared__ uint64_t never;  // test_timeout: a barrier nothing signals
+    __shared__ int s_fail;
+    float *ring = dftb_smem;                                           // [stages][frames][32 leaves][28]
+    float *s_w = ring + DFTB_STAGES * DFTB_FPS * DFT_FRAME_FLOATS;     // [T][32]
     const int nc = n1 + 27 * DFT_N2;
     float *s_out = s_w + (size_t)T * 32;                               // [32 leaves][nc]
     const uint32_t n_tiles = (n_leaves + DFT_TILE - 1) / DFT_TILE;
-    const int groups = (T + DFT_FPS - 1) / DFT_FPS;
+    const int groups = (T + DFTB_FPS - 1) / DFTB_FPS;
     const uint32_t my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const uint32_t units = my_tiles * (uint32_t)groups;
-    for (int s = 0; s < DFT_STAGES - 1; ++s) dft_issue(values, ring, n_leaves, T, n_tiles, (uint32_t)s, groups);
+    auto unit_tile = [&](uint32_t u) { return blockIdx.x + (u / groups) * gridDim.x; };
+    auto issue = [&](uint32_t u) {
+        const uint32_t tile = unit_tile(u);
+        const uint32_t leaf0 = tile * DFT_TILE;
+        const uint32_t nl = min((uint32_t)DFT_TILE, n_leaves - leaf0);
+        const int f0 = (int)(u % groups) * DFTB_FPS, nf = min(DFTB_FPS, T - f0);
+        const int st = (int)(u % DFTB_STAGES);
+        float *dst = ring + (size_t)st * DFTB_FPS * DFT_FRAME_FLOATS;
+        ptx::mbar_arrive_expect_tx(&bars[st], (uint32_t)nf * nl * 112u);
+        for (int f = 0; f < nf; ++f)
+            ptx::bulk_g2s(dst + f * DFT_FRAME_FLOATS, values + ((size_t)(f0 + f) * n_leaves + leaf0) * 28, nl * 112u,
+                          &bars[st]);
+    };
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int st = 0; st < DFTB_STAGES; ++st) ptx::mbar_init(&bars[st], 1);
+        ptx::mbar_init(&never, 1);
+        ptx::fence_barrier_init();
+        for (uint32_t u = 0; u < (uint32_t)DFTB_STAGES && u < units; ++u) issue(u);
+    }
     for (int q = threadIdx.x; q < 32 * T; q += blockDim.x) {
         const int t = q / 32, i = q % 32, nb = n1 > DFT_N2 ? n1 : DFT_N2;
         const double u = (double)(t + 1) / (double)T;
         const double w = (i == 0 ? 1.0 : 2.0) / (double)T;
         s_w[q] = i < nb ? (float)(w * ((i & 1) ? sinpi((double)(i + 1) * u) : cospi((double)i * u))) : 0.0f;
     }
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int ser[4];  // this lane's series (warp 0: the density series; warps 1..7: SH series, rotated by lane / 8)
+    const bool dens = warp < 2;
+    const int d0 = 16 * warp;  // density warps: coefficients d0 .. d0 + 15
+    int ser[4];                // SH warps: series, or -1
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int b = warp - 1 + 7 * q;
-        ser[q] = warp == 0 ? (q == 0 ? 0 : -1) : (b <= 26 ? 1 + (b + (lane >> 3)) % 27 : -1);
+        const int b = warp - 2 + 7 * q;
+        ser[q] = !dens && b <= 26 ? 1 + (b + (lane >> 3)) % 27 : -1;
     }
-    float acc[32];
+    float acc[20];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
-    for (uint32_t unit = 0; unit < units; ++unit) {
-        asm volatile("cp.async.wait_group %0;" ::"n"(DFT_STAGES - 2) : "memory");
-        __syncthreads();  // unit's frames are in; every warp is done with the stage refilled next
-        dft_issue(values, ring, n_leaves, T, n_tiles, unit + DFT_STAGES - 1, groups);
-        const uint32_t tile = blockIdx.x + (unit / groups) * gridDim.x;
+    for (int i = 0; i < 20; ++i) acc[i] = 0.0f;
+    uint32_t unit = 0;
+    for (; unit < units; ++unit) {
+        const int st = (int)(unit % DFTB_STAGES);
+        const bool ok = test_timeout && unit == 0
+                            ? ptx::mbar_wait_bounded(&never, 0, TEST_WAIT_LIMIT_NS)
+                            : ptx::mbar_wait_bounded(&bars[st], (unit / DFTB_STAGES) & 1u, WAIT_LIMIT_NS);
+        if (!ok) s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        const uint32_t tile = unit_tile(unit);
         const uint32_t leaf0 = tile * DFT_TILE;
         const int nl = (int)min((uint32_t)DFT_TILE, n_leaves - leaf0);
-        const int g = (int)(unit % groups), f0 = g * DFT_FPS, nf = min(DFT_FPS, T - f0);
-        const float *st = ring + (size_t)(unit % DFT_STAGES) * DFT_FPS * DFT_FRAME_FLOATS;
-        if (lane < nl) {
+        const int g = (int)(unit % groups), f0 = g * DFTB_FPS, nf = min(DFTB_FPS, T - f0);
+        const float *stg = ring + (size_t)st * DFTB_FPS * DFT_FRAME_FLOATS;
+        if (lane < nl && (!dens || d0 < n1)) {
             for (int f = 0; f < nf; ++f) {
-                const float *xr = st + f * DFT_FRAME_FLOATS + lane * 28;
-                const float4 *wr = reinterpret_cast<const float4 *>(s_w + (size_t)(f0 + f) * 32);
-                if (warp == 0) {
+                const float *xr = stg + f * DFT_FRAME_FLOATS + lane * 28;
+                const float *wt = s_w + (size_t)(f0 + f) * 32;
+                if (dens) {
                     const float x = xr[0];
+                    const float4 *wr = reinterpret_cast<const float4 *>(wt + d0);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
+                    for (int k = 0; k < 4; ++k) {
                         const float4 w = wr[k];
                         acc[4 * k] = fmaf(x, w.x, acc[4 * k]);
                         acc[4 * k + 1] = fmaf(x, w.y, acc[4 * k + 1]);
@@ -2158,9 +2181,8 @@ __global__ void __launch_bounds__(256) dft_pipe_kernel(const float *__restrict__
                         acc[4 * k + 3] = fmaf(x, w.w, acc[4 * k + 3]);
                     }
                 } else {
-                    const float4 w4 = wr[0];
-                    const float w5 = s_w[(size_t)(f0 + f) * 32 + 4];
-                    const float wv[DFT_N2] = {w4.x, w4.y, w4.z, w4.w, w5};
+                    const float4 w4 = *reinterpret_cast<const float4 *>(wt);
+                    const float wv[DFT_N2] = {w4.x, w4.y, w4.z, w4.w, wt[4]};
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         if (ser[q] < 0) continue;
@@ -2171,55 +2193,69 @@ __global__ void __launch_bounds__(256) dft_pipe_kernel(const float *__restrict__
                 }
             }
         }
-        if (g == groups - 1) {  // the tile's sums are complete: stage them, write them contiguously
-            if (lane < nl) {
-                float *o = s_out + (size_t)lane * nc;
-                if (warp == 0) {
+        if (g == groups - 1 && lane < nl) {  // the tile's sums are complete: stage them
+            float *o = s_out + (size_t)lane * nc;
+            if (dens) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (i < n1) o[i] = acc[i];
-                } else {
+                for (int i = 0; i < 16; ++i)
+                    if (d0 + i < n1) o[d0 + i] = acc[i];
+            } else {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (ser[q] < 0) continue;
+                for (int q = 0; q < 4; ++q) {
+                    if (ser[q] < 0) continue;
 #pragma unroll
-                        for (int i = 0; i < DFT_N2; ++i) o[n1 + (ser[q] - 1) * DFT_N2 + i] = acc[q * DFT_N2 + i];
-                    }
+                    for (int i = 0; i < DFT_N2; ++i) o[n1 + (ser[q] - 1) * DFT_N2 + i] = acc[q * DFT_N2 + i];
                 }
             }
+        }
+        if (g == groups - 1) {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
-            __syncthreads();
+            for (int i = 0; i < 20; ++i) acc[i] = 0.0f;
+        }
+        __syncthreads();  // every thread is done with stage st (and s_out is complete)
+        if (threadIdx.x == 0 && unit + DFTB_STAGES < units) issue(unit + DFTB_STAGES);
+        if (g == groups - 1)  // written contiguously; s_out is next written a whole tile later
             for (int q = threadIdx.x; q < nl * nc; q += blockDim.x) coeffs[(size_t)leaf0 * nc + q] = s_out[q];
+    }
+    if (s_fail) {
+        // NaN into every coefficient of this CTA's unfinished tiles, then drain
+        // the copies in flight (bounded) and report
+        const float nan = __int_as_float(0x7fc00000);
+        for (uint32_t k = unit / groups; k < my_tiles; ++k) {
+            const uint32_t leaf0 = (blockIdx.x + k * gridDim.x) * DFT_TILE;
+            const uint32_t nl = min((uint32_t)DFT_TILE, n_leaves - leaf0);
+            for (uint32_t q = threadIdx.x; q < nl * (uint32_t)nc; q += blockDim.x) coeffs[(size_t)leaf0 * nc + q] = nan;
+        }
+        if (threadIdx.x == 0) {
+            for (uint32_t u = unit; u < unit + DFTB_STAGES && u < units; ++u)
+                ptx::mbar_wait_bounded(&bars[u % DFTB_STAGES], (u / DFTB_STAGES) & 1u, WAIT_LIMIT_NS);
+            if (status) atomicOr(status, STATUS_DEVICE_TIMEOUT);
         }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");  // nothing left in flight (the issues past the end copy nothing)
 }
 
-#ifndef FPO_DFT_PIPE
-#define FPO_DFT_PIPE 1
-#endif
 
-int launch_dft(const float *values, float *coeffs, uint32_t n_leaves, int n1, int n2, int T, int sm_count,
-               void *stream)
+int launch_dft(const float *values, float *coeffs, uint32_t n_leaves, int n1, int n2, int T, uint32_t *status,
+               bool test_timeout, int sm_count, void *stream)
 {
     if (n_leaves == 0) return (int)cudaSuccess;
-    // the 16-byte asynchronous copies need a 16-byte aligned base (every row
-    // offset is a multiple of 112 bytes); other bases take the tile kernel
-    if (FPO_DFT_PIPE && n2 == DFT_N2 && n1 <= 32 && (reinterpret_cast<uintptr_t>(values) & 15u) == 0) {
+    // bulk copies need a 16-byte aligned base (every frame row of a tile
+    // starts a multiple of 112 bytes further); other bases take the tile kernel
+    if (n2 == DFT_N2 && n1 <= 32 && (reinterpret_cast<uintptr_t>(values) & 15u) == 0) {
         const int nc = n1 + 27 * DFT_N2;
-        const size_t smem = ((size_t)DFT_STAGES * DFT_FPS * DFT_FRAME_FLOATS + (size_t)T * 32 + (size_t)DFT_TILE * nc) *
+        const size_t smem = ((size_t)DFTB_STAGES * DFTB_FPS * DFT_FRAME_FLOATS + (size_t)T * 32 + (size_t)DFT_TILE * nc) *
                             sizeof(float);
-        cudaError_t e = cudaFuncSetAttribute(dft_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(dft_bulk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dft_pipe_kernel, 256, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dft_bulk_kernel, DFTB_THREADS, smem);
         if (e != cudaSuccess) return (int)e;
         if (per_sm < 1) per_sm = 1;
         const uint64_t n_tiles = (n_leaves + DFT_TILE - 1) / DFT_TILE;
         uint64_t blocks = (uint64_t)sm_count * per_sm;
         if (blocks > n_tiles) blocks = n_tiles;
-        dft_pipe_kernel<<<(unsigned)blocks, 256, smem, (cudaStream_t)stream>>>(values, coeffs, n_leaves, n1, T);
+        dft_bulk_kernel<<<(unsigned)blocks, DFTB_THREADS, smem, (cudaStream_t)stream>>>(values, coeffs, n_leaves, n1, T,
+                                                                                         status, test_timeout);
         return (int)cudaGetLastError();
     }
     if (n2 == DFT_N2 && n1 <= 32) {

@@ -111,7 +111,7 @@ def lib():
         L.fpo_render_backward.argtypes = [P, C.POINTER(Rays), C.POINTER(FrameOpts), P, P, P, P]
         L.fpo_render_noalloc.argtypes = [P, C.POINTER(Rays), C.POINTER(FrameOpts), P, P]
         L.fpo_set_coeffs.argtypes = [P, P, P]
-        L.fpo_dft_leaves.argtypes = [C.c_int32, C.c_int32, C.c_uint32, C.c_uint32, P, P, P]
+        L.fpo_dft_leaves.argtypes = [C.c_int32, C.c_int32, C.c_uint32, C.c_uint32, P, P, P, C.c_uint32, P]
         L.fpo_latent_table.argtypes = [C.POINTER(Decoder), C.c_int32, C.c_int32, C.c_double,
                                        C.c_double, C.c_uint32, P, P, P, P]
         L.fpo_decoder_grad.argtypes = [C.POINTER(Mlp), C.c_int32, C.c_int32, C.c_uint32, P, P, P, P,
@@ -135,6 +135,19 @@ def lib():
         L.fpo_version.argtypes = []
         _lib = L
     return _lib
+
+
+DFT_STATUS_DEVICE_TIMEOUT = 4  # the bit fpo_dft_leaves ORs into its status word
+
+
+def check_status_word(status, stream=None):
+    """Waits for the stream and raises FPOError if a fpo_dft_leaves status
+    word (CUDA int32 [1]) reports a device-side time-out."""
+    import torch
+
+    (stream or torch.cuda.current_stream()).synchronize()
+    if int(status.item()) & DFT_STATUS_DEVICE_TIMEOUT:
+        raise FPOError(-9, "a device-side wait of the per-leaf DFT gave up after its time limit")
 
 
 def check(code: int):
@@ -472,10 +485,13 @@ def latent_table(latents, w1, b1, w2, b2, w3, b3, t, period_T=60.0, n1=31, n2=5,
     return out, status
 
 
-def dft_leaves(values, n1=31, n2=5, stream=None, out=None):
+def dft_leaves(values, n1=31, n2=5, stream=None, out=None, status=None, test_timeout=False):
     """Eq. 10-12 on the GPU: values [T, n_leaves, 28] (CUDA float32) ->
     coefficients [n_leaves, n1 + 27 n2] (canonical), into `out` if given
-    (a contiguous CUDA float32 tensor of that shape)."""
+    (a contiguous CUDA float32 tensor of that shape).  status: a CUDA int32
+    tensor of one element that a timed-out copy wait ORs its bit into (the
+    caller reads it after the stream); without one the call waits for the
+    stream and raises FPOError(FPO_ERR_DEVICE_TIMEOUT) itself."""
     import torch
 
     v = values.contiguous()
@@ -484,9 +500,16 @@ def dft_leaves(values, n1=31, n2=5, stream=None, out=None):
     if out is None:
         out = torch.empty((n, n1 + 27 * n2), dtype=torch.float32, device=v.device)
     assert out.shape == (n, n1 + 27 * n2) and out.dtype == torch.float32 and out.is_cuda and out.is_contiguous()
+    own = status is None
+    if own:
+        status = torch.zeros(1, dtype=torch.int32, device=v.device)
+    assert status.is_cuda and status.dtype == torch.int32 and status.numel() == 1
     check(lib().fpo_dft_leaves(n1, n2, T, n, C.c_void_p(v.data_ptr() if n else None),
-                               C.c_void_p(out.data_ptr() if n else None),
+                               C.c_void_p(out.data_ptr() if n else None), C.c_void_p(status.data_ptr()),
+                               FLAG_TEST_DEVICE_TIMEOUT if test_timeout else 0,
                                C.c_void_p(_stream_handle(stream))))
+    if own:
+        check_status_word(status, stream)
     return out
 
 

@@ -119,9 +119,9 @@ def test_dft_leaves_matches_oracle(n1, n2, T, n):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("n1,T,n", [(31, 60, 3000), (31, 37, 70), (11, 256, 100), (31, 5, 1)])
-def test_dft_pipelined_and_tiled_kernels_agree(n1, T, n):
-    # a 16-byte aligned values array takes the cp.async-pipelined kernel, one
-    # shifted by a float the tiled kernel: same lanes, same summation order
+def test_dft_bulk_copy_and_tiled_kernels_agree(n1, T, n):
+    # a 16-byte aligned values array takes the bulk-copy kernel, one shifted
+    # by a float the tiled kernel: same lanes, same summation order
     torch = _cuda()
     rng = np.random.default_rng(T + n)
     vals = torch.as_tensor(rng.normal(size=(T, n, 28)).astype(np.float32), device="cuda")
@@ -140,6 +140,29 @@ def test_dft_pipelined_and_tiled_kernels_agree(n1, T, n):
     k_z = oracle.dft(vals[:, :, 1:].reshape(T, -1).double().cpu().numpy(), 5).reshape(n, 135)
     ref = np.concatenate([k_sig, k_z], axis=1)
     assert np.abs(a.cpu().numpy() - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.gpu
+def test_dft_copy_wait_timeout_is_reported():
+    # every CTA's first wait runs on a barrier nothing signals (1 ms): the
+    # status word gets the time-out bit, every coefficient is NaN, the copies
+    # in flight are drained, and the next call on the same device is exact
+    torch = _cuda()
+    rng = np.random.default_rng(9)
+    T, n = 60, 5000
+    vals = torch.as_tensor(rng.normal(size=(T, n, 28)).astype(np.float32), device="cuda")
+    good = fpo.dft_leaves(vals)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = torch.zeros((n, 166), device="cuda")
+    fpo.dft_leaves(vals, out=out, status=st, test_timeout=True)
+    torch.cuda.synchronize()
+    assert int(st.item()) == fpo.DFT_STATUS_DEVICE_TIMEOUT
+    assert out.isnan().all()
+    with pytest.raises(fpo.FPOError) as e:
+        fpo.dft_leaves(vals, test_timeout=True)
+    assert e.value.code == -9
+    again = fpo.dft_leaves(vals)
+    assert torch.equal(again, good)
 
 
 @pytest.mark.gpu
