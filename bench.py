@@ -310,7 +310,7 @@ def frame_psnr(r, ot, coeffs, cams, out, torch, refs=None):
             "frames": "camera k at t = 3.75 k, k = 0..15, whole frames"}, refs
 
 
-def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, peak):
+def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, peak, fma_peak=None):
     """BF16 storage on the same tree, and the latent decoder (trained on
     coefficients produced by the generation: smooth animated fields -> per-
     leaf DFT) against the plain FP32 renderer of those coefficients."""
@@ -353,6 +353,21 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
     mv = a.elapsed_time(b) / (len(ts) * len(cams))
     res["multiview_16_views_per_t"] = {"ms_per_view": mv, "Mrays_s": n_px / mv / 1e3, "fps": 1e3 / mv,
                                        "frame_times": len(ts), "views_per_t": len(cams)}
+    # the Fourier sizes of the paper's ablation (Tab. 3) on the same leaves and
+    # coefficient distributions: frame rate and bytes per leaf (the (31, 5)
+    # entry is the headline measurement)
+    pad4 = lambda k: (k + 3) & ~3  # record strides: n1 and 27 n2 floats, each rounded up to 4
+    dims = {"31,5": {"Mrays_s": n_px / fp32_ms / 1e3, "fps": 1e3 / fp32_ms, "bytes_per_leaf": 4 * (pad4(31) + pad4(135))}}
+    for n1, n2 in ((11, 5), (21, 5), (31, 11)):
+        co = synth.draw_coefficients_blocked(1, tree.n_leaves, n1, n2)
+        r = fpo.Renderer(n1=n1, n2=n2)
+        r.upload(synth.Tree(tree.leaf_depth, tree.leaf_xyz, co, tree.max_depth, n1, n2))
+        del co
+        ms_d = time_frames(r, cams, nf, out, torch, B)
+        dims[f"{n1},{n2}"] = {"Mrays_s": n_px / ms_d / 1e3, "fps": 1e3 / ms_d,
+                              "bytes_per_leaf": r.info()["leaf_record_bytes"]}
+        r.close()
+    res["fourier_dims"] = dims
     if args.finetune_steps > 0:
         res["finetune"] = finetune_variant(args, tree, torch, fpo)
     # latent decoder on generated coefficients (same leaves)
@@ -397,6 +412,30 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     pixel_loss = float(pixel.last_loss)
+    # the training kernels' FP32 rates (flop per leaf: forward 2 (32*64 + 64*64
+    # + 64*166); the gradient three times that)
+    fwd = 2 * (32 * 64 + 64 * 64 + 64 * 166)
+    rows = torch.randperm(n, device="cuda")[:65536].to(torch.int32)
+    cw = m.default_weights(coeffs.device, sigma_weight=0.2)
+
+    def rate(f, flop, reps):
+        f()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            f()
+        b.record()
+        torch.cuda.synchronize()
+        ms_k = a.elapsed_time(b) / reps
+        tf = flop / (ms_k * 1e-3) / 1e12
+        return {"ms": ms_k, "tflops": tf, "frac_of_fp32_fma_peak": tf / fma_peak if fma_peak else None}
+
+    train_kernels = {
+        "decoder_grad_65536_leaves": rate(lambda: m.grad(rows, coeffs, cw), 3 * fwd * 65536, 10),
+        "decode_into_records_all_leaves": rate(
+            lambda: pixel.work.set_coeffs_from_decoder(m._mlp(m.p), m.p["lat"]), fwd * n, 3),
+    }
     pixel.close()
     r = fpo.Renderer(storage="latent")
     r.upload(synth.Tree(tree.leaf_depth, tree.leaf_xyz, np.zeros((0, 166), np.float32), tree.max_depth))
@@ -412,7 +451,8 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
         "single_frame_Mrays_s": n_px / msl1 / 1e3,
         "psnr_vs_fp64_oracle": frame_psnr(r, ot, co_np, cams, out, torch)[0],
         "decode_ms": ev[0].elapsed_time(ev[1]), "train_steps": args.latent_steps, "train_batch": 65536,
-        "train_s": train_s, "train_loss": hist, "bytes_per_leaf": r.info()["leaf_record_bytes"],
+        "train_s": train_s, "train_loss": hist, "training_kernels": train_kernels,
+        "bytes_per_leaf": r.info()["leaf_record_bytes"],
         "fp32_bytes_per_leaf": 672, "pixel_loss": dict(pixel_cfg, last_batch_mse=pixel_loss),
         "coefficients": "per-leaf DFT (Eq. 10-12) of smooth animated fields over the same leaves"}
     r.close()
@@ -731,9 +771,15 @@ def main():
                                                "frame_ms": {"p10": float(np.percentile(ms8, 10)),
                                                             "p50": statistics.median(ms8),
                                                             "p90": float(np.percentile(ms8, 90))}}}
+    # the FP32 FMA rate of this GPU: the denominator of the SIMT FP32 kernels' roofline
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    res["fp32_fma_peak"] = {"tflops": fpo.fma_peak_tflops(),
+                            "nominal_tflops_at_max_clock": sms * 128 * 2 * 2.07e9 / 1e12,
+                            "how": "fpo_fma_peak: two 1024-thread CTAs per SM, 16 independent FMA chains "
+                                   "per thread, 4096 steps, best of 5 launches (CUDA events)"}
     if not args.no_variants and args.storage == "f32" and args.idft == "auto":
         res["variants"] = variants(args, tree, cams, frames[W:], out, torch, fpo, n_px, t_max / K,
-                                   mean_vis, peak)
+                                   mean_vis, peak, res["fp32_fma_peak"]["tflops"])
     if rank == 0 and not args.no_cpu_baseline:
         v, rays, secs, thr = oracle_sample_rate(tree, cams, frames[W:], args.cpu_seconds)
         res["cpu_baseline"] = {"value": v, "unit": "Mrays/s", "cores": thr, "kind": "oracle",

@@ -452,8 +452,18 @@ void fpo_destroy(fpo_ctx *ctx);
 /* Message of the last failure on the calling thread ("" if none). */
 const char *fpo_last_error(void);
 
+/* Diagnostics.  FP32 FMA throughput microbenchmark: `blocks` x `threads`
+ * threads (threads a multiple of 32, at most 1024) each run 16 independent
+ * chains of `iters` fused multiply-adds and store one float into sink
+ * (device, blocks * threads floats, caller-owned); *flops (host, optional)
+ * receives the floating-point operations the launch performs (2 per FMA).
+ * Time it with events on the stream: flops / seconds is the device's FP32
+ * FMA rate, the roofline denominator of the SIMT arithmetic kernels.
+ * Errors: INVALID_ARG, CUDA. */
+int fpo_fma_peak(uint32_t blocks, uint32_t threads, uint32_t iters, float *sink, double *flops, void *cuda_stream);
+
 /* ABI version: 100 * major + minor (1.1: fpo_render_frames takes frame_done;
- * 1.2: fpo_set_coeffs_from_decoder; fpo_dft_leaves takes status and flags). */
+ * 1.2: fpo_set_coeffs_from_decoder, fpo_fma_peak; fpo_dft_leaves takes status and flags). */
 int fpo_version(void);
 
 #ifdef __cplusplus

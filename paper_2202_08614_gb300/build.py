@@ -15,7 +15,8 @@ ROOT = os.path.dirname(PKG)
 SRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libfpo.so")
-SOURCES = ["fpo_api.cu", "fpo_kernels.cu", "fpo_pack.cpp", "fpo_noalloc.cu", "fpo_union.cpp", "fpo_latent.cu", "fpo_train.cu"]
+SOURCES = ["fpo_api.cu", "fpo_kernels.cu", "fpo_pack.cpp", "fpo_noalloc.cu", "fpo_union.cpp", "fpo_latent.cu", "fpo_train.cu",
+           "fpo_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

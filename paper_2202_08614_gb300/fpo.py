@@ -35,7 +35,7 @@ EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
            "fpo_last_error", "fpo_version", "fpo_render_noalloc", "fpo_set_coeffs",
            "fpo_dft_leaves", "fpo_union_trees", "fpo_latent_table", "fpo_decoder_grad",
            "fpo_adam", "fpo_set_latents", "fpo_render_frames", "fpo_adam_leaves",
-           "fpo_decoder_forward", "fpo_set_coeffs_from_decoder"]
+           "fpo_decoder_forward", "fpo_set_coeffs_from_decoder", "fpo_fma_peak"]
 
 
 class FPOError(RuntimeError):
@@ -118,6 +118,7 @@ def lib():
                                        P, C.POINTER(Mlp), P, P, P]
         L.fpo_decoder_forward.argtypes = [C.POINTER(Mlp), C.c_int32, C.c_int32, C.c_uint32, P, P, P]
         L.fpo_set_coeffs_from_decoder.argtypes = [P, C.POINTER(Mlp), P, P]
+        L.fpo_fma_peak.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, P, C.POINTER(C.c_double), P]
         L.fpo_adam.argtypes = [P, P, P, P, C.c_uint64, P, C.c_uint32, C.c_float, C.c_float,
                                C.c_float, C.c_float, C.c_uint32, P]
         L.fpo_set_latents.argtypes = [P, P, C.POINTER(Decoder), P]
@@ -483,6 +484,28 @@ def latent_table(latents, w1, b1, w2, b2, w3, b3, t, period_T=60.0, n1=31, n2=5,
                                  C.c_void_p(out.data_ptr() if n else None),
                                  C.c_void_p(status.data_ptr()), C.c_void_p(_stream_handle(stream))))
     return out, status
+
+
+def fma_peak_tflops(iters=4096, reps=5):
+    """The device's FP32 FMA rate (TFLOP/s, best of `reps` launches of
+    fpo_fma_peak: two 1024-thread CTAs per SM), timed with CUDA events."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, threads = 2 * sms, 1024
+    sink = torch.empty(blocks * threads, device="cuda")
+    flops = C.c_double(0.0)
+    best = float("inf")
+    for rep in range(reps + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        check(lib().fpo_fma_peak(blocks, threads, iters, C.c_void_p(sink.data_ptr()), C.byref(flops),
+                                 C.c_void_p(_stream_handle(None))))
+        b.record()
+        torch.cuda.synchronize()
+        if rep:  # the first launch warms up
+            best = min(best, a.elapsed_time(b))
+    return flops.value / (best * 1e-3) / 1e12
 
 
 def dft_leaves(values, n1=31, n2=5, stream=None, out=None, status=None, test_timeout=False):
