@@ -143,6 +143,24 @@ def test_dft_bulk_copy_and_tiled_kernels_agree(n1, T, n):
 
 
 @pytest.mark.gpu
+def test_dft_full_chunk_sampled_leaves():
+    # a generation-sized chunk (256K leaves x 60 frames: 1.8 GB of values, far
+    # more than L2) through the bulk-copy kernel; 64 leaves spread over it,
+    # the first and the last included, against the FP64 DFT
+    torch = _cuda()
+    T, n = 60, 1 << 18
+    g = torch.Generator(device="cuda").manual_seed(3)
+    vals = torch.randn((T, n, 28), generator=g, device="cuda")
+    got = fpo.dft_leaves(vals)
+    pick = np.unique(np.concatenate([[0, n - 1], np.random.default_rng(3).integers(0, n, 62)]))
+    x = vals[:, torch.as_tensor(pick, device="cuda"), :].double().cpu().numpy()  # [T, m, 28]
+    m = len(pick)
+    ref = np.concatenate([oracle.dft(x[:, :, 0], 31), oracle.dft(x[:, :, 1:].reshape(T, -1), 5).reshape(m, 135)], 1)
+    g_np = got[torch.as_tensor(pick, device="cuda")].double().cpu().numpy()
+    assert np.abs(g_np - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.gpu
 def test_dft_copy_wait_timeout_is_reported():
     # every CTA's first wait runs on a barrier nothing signals (1 ms): the
     # status word gets the time-out bit, every coefficient is NaN, the copies
