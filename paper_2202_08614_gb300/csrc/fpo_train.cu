@@ -345,15 +345,19 @@ int decoder_grad_max_coeffs() { return TG_MAXC; }
 
 // FP32 decode of every leaf: y = W3 relu(W2 relu(W1 x + b1) + b2) + b3.  A CTA
 // keeps the transposed weights in shared memory and walks tiles of 64 leaves;
-// each thread owns 4 rows x (outputs tc, tc + 16, ...) of a layer, so a warp
-// reads weight rows without bank conflicts and activations as broadcasts.
+// each thread owns 4 rows x the output columns 4 tc + 64 g + e (e = 0..3; g = 0
+// for the 64-wide hidden layers, g = 0..2 for the last layer), so per input
+// feature it reads its weights with one 16-byte load per group (16 threads
+// read 256 consecutive bytes) and its 4 activations as broadcasts.  In the
+// last layer, columns 176..191 of group 2 read into the next weight row (or the
+// biases after it) and are discarded.
 // Record mode (perm != nullptr): output row i is the context's FP32 record
 // i, decoded from latent row perm[i], its first n1 values going to the
 // density records (stride ss) and the rest to the SH records (stride zs).
 constexpr int DF_ROWS = 64, DF_THREADS = 256, DF_MAXC = 176;
 
 struct DecodeSmem {
-    float w1t[32 * 64], w2t[64 * 64], w3t[64 * DF_MAXC], b1[64], b2[64], b3[DF_MAXC];
+    float w1t[32 * 64], w2t[64 * 64], w3t[64 * DF_MAXC], b1[64], b2[64], b3[DF_MAXC + 16];
     float x[DF_ROWS * 33], h1[DF_ROWS * 65], h2[DF_ROWS * 65];
     uint32_t src[DF_ROWS];
 };
@@ -365,9 +369,33 @@ struct DecodeOut {
     int n1, ss, zs;
 };
 
-__global__ void __launch_bounds__(DF_THREADS) decoder_forward_kernel(const fpo_mlp w, int nc, uint32_t n,
-                                                                      const float *__restrict__ latents,
-                                                                      const DecodeOut o)
+// a[i][4 g + e] += sum_k in[(4 tr + i) * ld_in + k] * wt[k * ldw + 4 tc + 64 g + e]
+template <int G>
+__device__ __forceinline__ void decode_layer(const float *in, int ld_in, int K, const float *wt, int ldw,
+                                             float (&a)[4][4 * G], int tr, int tc)
+{
+#pragma unroll 2
+    for (int k = 0; k < K; ++k) {
+        float xv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xv[i] = in[(4 * tr + i) * ld_in + k];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const float4 w = *reinterpret_cast<const float4 *>(wt + k * ldw + 4 * tc + 64 * g);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i][4 * g] = fmaf(xv[i], w.x, a[i][4 * g]);
+                a[i][4 * g + 1] = fmaf(xv[i], w.y, a[i][4 * g + 1]);
+                a[i][4 * g + 2] = fmaf(xv[i], w.z, a[i][4 * g + 2]);
+                a[i][4 * g + 3] = fmaf(xv[i], w.w, a[i][4 * g + 3]);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(DF_THREADS, 2) decoder_forward_kernel(const fpo_mlp w, int nc, uint32_t n,
+                                                                         const float *__restrict__ latents,
+                                                                         const DecodeOut o)
 {
     extern __shared__ __align__(16) unsigned char df_raw[];
     DecodeSmem &S = *reinterpret_cast<DecodeSmem *>(df_raw);
@@ -379,8 +407,8 @@ __global__ void __launch_bounds__(DF_THREADS) decoder_forward_kernel(const fpo_m
         S.w3t[k * DF_MAXC + c] = c < nc ? w.w3[c * 64 + k] : 0.0f;
     }
     for (int i = tid; i < 64; i += DF_THREADS) { S.b1[i] = w.b1[i]; S.b2[i] = w.b2[i]; }
-    for (int i = tid; i < DF_MAXC; i += DF_THREADS) S.b3[i] = i < nc ? w.b3[i] : 0.0f;
-    const int tr = tid >> 4, tc = tid & 15;  // rows 4 tr .. 4 tr + 3; outputs tc + 16 j
+    for (int i = tid; i < DF_MAXC + 16; i += DF_THREADS) S.b3[i] = i < nc ? w.b3[i] : 0.0f;
+    const int tr = tid >> 4, tc = tid & 15;  // rows 4 tr .. 4 tr + 3; columns 4 tc + 64 g + e
     const uint32_t n_tiles = (n + DF_ROWS - 1) / DF_ROWS;
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint32_t r0 = tile * DF_ROWS;
@@ -398,23 +426,12 @@ __global__ void __launch_bounds__(DF_THREADS) decoder_forward_kernel(const fpo_m
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) a[i][j] = S.b1[tc + 16 * j];
-#pragma unroll 4
-            for (int k = 0; k < 32; ++k) {
-                float xv[4], wv[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) xv[i] = S.x[(4 * tr + i) * 33 + k];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) wv[j] = S.w1t[k * 64 + tc + 16 * j];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) a[i][j] = fmaf(xv[i], wv[j], a[i][j]);
-            }
+                for (int e = 0; e < 4; ++e) a[i][e] = S.b1[4 * tc + e];
+            decode_layer<1>(S.x, 33, 32, S.w1t, 64, a, tr, tc);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) S.h1[(4 * tr + i) * 65 + tc + 16 * j] = fmaxf(a[i][j], 0.0f);
+                for (int e = 0; e < 4; ++e) S.h1[(4 * tr + i) * 65 + 4 * tc + e] = fmaxf(a[i][e], 0.0f);
         }
         __syncthreads();
         {
@@ -422,52 +439,29 @@ __global__ void __launch_bounds__(DF_THREADS) decoder_forward_kernel(const fpo_m
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) a[i][j] = S.b2[tc + 16 * j];
-#pragma unroll 4
-            for (int k = 0; k < 64; ++k) {
-                float xv[4], wv[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) xv[i] = S.h1[(4 * tr + i) * 65 + k];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) wv[j] = S.w2t[k * 64 + tc + 16 * j];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) a[i][j] = fmaf(xv[i], wv[j], a[i][j]);
-            }
+                for (int e = 0; e < 4; ++e) a[i][e] = S.b2[4 * tc + e];
+            decode_layer<1>(S.h1, 65, 64, S.w2t, 64, a, tr, tc);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) S.h2[(4 * tr + i) * 65 + tc + 16 * j] = fmaxf(a[i][j], 0.0f);
+                for (int e = 0; e < 4; ++e) S.h2[(4 * tr + i) * 65 + 4 * tc + e] = fmaxf(a[i][e], 0.0f);
         }
         __syncthreads();
         {
-            constexpr int J = DF_MAXC / 16;
-            float a[4][J];
+            float a[4][12];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < J; ++j) a[i][j] = S.b3[tc + 16 * j];
-#pragma unroll 2
-            for (int k = 0; k < 64; ++k) {
-                float xv[4], wv[J];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) xv[i] = S.h2[(4 * tr + i) * 65 + k];
-#pragma unroll
-                for (int j = 0; j < J; ++j) wv[j] = S.w3t[k * DF_MAXC + tc + 16 * j];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < J; ++j) a[i][j] = fmaf(xv[i], wv[j], a[i][j]);
-            }
+                for (int j = 0; j < 12; ++j) a[i][j] = S.b3[4 * tc + 64 * (j >> 2) + (j & 3)];
+            decode_layer<3>(S.h2, 65, 64, S.w3t, DF_MAXC, a, tr, tc);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int r = 4 * tr + i;
                 if (r < nr) {
                     const size_t row = r0 + r;
 #pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        const int c = tc + 16 * j;
+                    for (int j = 0; j < 12; ++j) {
+                        const int c = 4 * tc + 64 * (j >> 2) + (j & 3);
                         if (c >= nc) continue;
                         if (!o.perm) o.coeffs[row * nc + c] = a[i][j];
                         else if (c < o.n1) o.sig[row * o.ss + c] = a[i][j];
