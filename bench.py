@@ -400,7 +400,7 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
     # training: coefficient L2 (density weight 0.2) plus the rendered-pixel
     # loss every 4th step (8192 rays over the 16 ring views x 60 frames,
     # weight 10) through the render adjoint
-    m = LatentModel(n, seed=0)
+    m = LatentModel(n, seed=0, tensor_cores=True)
     m.init_output_bias(coeffs)
     pixel_cfg = dict(rays=8192, weight=10.0, every=4, start=0.1)
     pixel = PixelLoss(gen, cams, **pixel_cfg)
@@ -418,7 +418,7 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
     rows = torch.randperm(n, device="cuda")[:65536].to(torch.int32)
     cw = m.default_weights(coeffs.device, sigma_weight=0.2)
 
-    def rate(f, flop, reps):
+    def rate(f, flop, reps, tensor=False):
         f()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -429,10 +429,27 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
         torch.cuda.synchronize()
         ms_k = a.elapsed_time(b) / reps
         tf = flop / (ms_k * 1e-3) / 1e12
+        if tensor:  # BF16 tensor cores: the measured dense BF16 rate
+            return {"ms": ms_k, "tflops": tf, "frac_of_bf16_tensor_peak": tf / bf16_peak if bf16_peak else None}
         return {"ms": ms_k, "tflops": tf, "frac_of_fp32_fma_peak": tf / fma_peak if fma_peak else None}
 
+    bf16_peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16_peak = float(json.load(f)["bf16_tflops"])
+    except (OSError, ValueError, KeyError):
+        pass
+    tc = m.tensor_cores
+    m.tensor_cores = True
+    k_tc = rate(lambda: m.grad(rows, coeffs, cw), 3 * fwd * 65536, 10, tensor=True)
+    m.check_status()
+    m.tensor_cores = False
+    k_simt = rate(lambda: m.grad(rows, coeffs, cw), 3 * fwd * 65536, 10)
+    m.tensor_cores = tc
     train_kernels = {
-        "decoder_grad_65536_leaves": rate(lambda: m.grad(rows, coeffs, cw), 3 * fwd * 65536, 10),
+        "training_gradient": "tcgen05 (fpo_decoder_grad_tc, BF16 operands)" if tc else "FP32 SIMT (fpo_decoder_grad)",
+        "decoder_grad_tc_65536_leaves": k_tc,
+        "decoder_grad_simt_65536_leaves": k_simt,
         "decode_into_records_all_leaves": rate(
             lambda: pixel.work.set_coeffs_from_decoder(m._mlp(m.p), m.p["lat"]), fwd * n, 3),
     }

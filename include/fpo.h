@@ -403,6 +403,23 @@ int fpo_decoder_grad(const fpo_mlp *w, int32_t n1, int32_t n2, uint32_t batch, c
                      const float *extra_dy, const fpo_mlp *grad, float *dlatents, double *loss,
                      void *cuda_stream);
 
+/* fpo_decoder_grad on the tensor cores (tcgen05, BF16 operands, FP32
+ * accumulation in TMEM): the same loss, gradients and outputs, with every
+ * matrix product of the forward pass and of the back-propagation taken
+ * with BF16 operands (latents, weights, activations and dL/dy rounded to
+ * BF16; each bias carried to about 16 bits as a BF16 pair), so results
+ * agree with fpo_decoder_grad to the BF16 rounding of those operands.
+ * status: an optional device word that a wait for the tensor cores which
+ * runs out (2 s) ORs the value 4 into (FPO_ERR_DEVICE_TIMEOUT; the weight
+ * gradients are then left unchanged); flags: 0, or
+ * FPO_FLAG_TEST_DEVICE_TIMEOUT to make each CTA's first wait run out after
+ * 1 ms (tests of that path).  One CTA per SM holds all 512 TMEM columns.
+ * Errors: INVALID_ARG, CUDA. */
+int fpo_decoder_grad_tc(const fpo_mlp *w, int32_t n1, int32_t n2, uint32_t batch, const uint32_t *rows,
+                        const float *latents, const float *targets, const float *coef_weight,
+                        const float *extra_dy, const fpo_mlp *grad, float *dlatents, double *loss,
+                        uint32_t *status, uint32_t flags, void *cuda_stream);
+
 /* The decoded coefficients of n leaves in FP32: coeffs[i] = MLP(latents[i])
  * (device [n][32] in, device [n][n1 + 27*n2] out, canonical order), with the
  * FP32 master weights.  Used to put the decoder's current coefficients into
@@ -463,7 +480,8 @@ const char *fpo_last_error(void);
 int fpo_fma_peak(uint32_t blocks, uint32_t threads, uint32_t iters, float *sink, double *flops, void *cuda_stream);
 
 /* ABI version: 100 * major + minor (1.1: fpo_render_frames takes frame_done;
- * 1.2: fpo_set_coeffs_from_decoder, fpo_fma_peak; fpo_dft_leaves takes status and flags). */
+ * 1.2: fpo_set_coeffs_from_decoder, fpo_decoder_grad_tc, fpo_fma_peak; fpo_dft_leaves takes
+ * status and flags). */
 int fpo_version(void);
 
 #ifdef __cplusplus

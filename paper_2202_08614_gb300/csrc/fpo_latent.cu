@@ -438,6 +438,409 @@ __global__ void __launch_bounds__(128 * G, 8 / G) latent_table_kernel(const __gr
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(LT_TMEM_COLS) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core training step of the decoder: the forward pass, the weighted L2
+// loss against target coefficients (plus an optional extra dL/dy), and the
+// back-propagation to every weight, bias and latent, with BF16 operands (A
+// and B of each MMA both BF16; FP32's exponent range, so no loss scaling)
+// and FP32 accumulation in TMEM.  One warpgroup per CTA and one CTA per SM
+// (all 512 TMEM columns); thread t owns row t of a 128-leaf tile and TMEM
+// lane t.  Per tile, nine GEMMs (M = 128, no-swizzle K-major operands):
+//   Z1 = [X 1] W1'^T,  Z2 = [H1 1] W2'^T,  Y = [H2 1] W3'^T       (forward)
+//   dH2 = dY W3,  dH1 = d2 W2,  dX = d1 W1                        (data)
+//   G3 += [H2^T; 1] dY,  G2 += [H1^T; 1] d2,  G1 += [X^T; 1] d1    (weights)
+// H = relu(Z) in BF16, d2 = dH2 [Z2 > 0], d1 = dH1 [Z1 > 0], dY = 2 cw (Y -
+// target) + extra.  The weight gradients accumulate in TMEM over all of the
+// CTA's tiles, transposed (lane = input feature, column = output feature);
+// the ones row of each transposed activation makes lane 64 (32 for layer 1)
+// the bias gradient.  The transposed operands (activations and gradients
+// with the tile's rows as K) are written by the epilogues next to the
+// row-major ones.  The M = 128 A operands of the weight GEMMs hold only
+// 40 or 72 meaningful rows; the rest of each descriptor's extent reads
+// whatever lies after them in shared memory, which lands only in TMEM lanes
+// that are never read.
+namespace {
+
+constexpr int TG_K1 = 48, TG_K2 = 80, TG_NC = 176, TG_KR = 128;
+constexpr int TGO_W1 = 0;                          // [64][48]   W1 | b1 (B of Z1)
+constexpr int TGO_W2 = TGO_W1 + 64 * TG_K1 * 2;    // [64][80]   W2 | b2 (B of Z2)
+constexpr int TGO_W3 = TGO_W2 + 64 * TG_K2 * 2;    // [176][80]  W3 | b3 (B of Y)
+constexpr int TGO_W3T = TGO_W3 + TG_NC * TG_K2 * 2;  // [64][176] W3^T (B of dH2)
+constexpr int TGO_W2T = TGO_W3T + 64 * TG_NC * 2;  // [64][64]   W2^T (B of dH1)
+constexpr int TGO_W1T = TGO_W2T + 64 * 64 * 2;     // [32][64]   W1^T (B of dX)
+constexpr int TGO_XT = TGO_W1T + 32 * 64 * 2;      // [40][128]  [X^T; 1] (A of G1)
+constexpr int TGO_H1T = TGO_XT + 40 * TG_KR * 2;   // [72][128]  [H1^T; 1] (A of G2)
+constexpr int TGO_H2T = TGO_H1T + 72 * TG_KR * 2;  // [72][128]  [H2^T; 1] (A of G3)
+constexpr int TGO_A = TGO_H2T + 72 * TG_KR * 2;    // the tile's A operand: [X 1], [H1 1], [H2 1], dY, d2, d1
+constexpr int TGO_B = TGO_A + 128 * TG_NC * 2;     // the weight GEMMs' B operand: dY^T, d2^T, d1^T
+constexpr int TG_SMEM = TGO_B + TG_NC * TG_KR * 2;
+static_assert(TGO_XT + 128 * TG_KR * 2 <= TG_SMEM && TGO_H2T + 128 * TG_KR * 2 <= TG_SMEM,
+              "the weight GEMMs' A descriptors stay inside the CTA's shared memory");
+// TMEM columns: per-tile scratch (Z1, Z2, Y, dH2, dH1, dX) and the weight gradients
+constexpr uint32_t TC_SCR = 0, TC_G3 = 192, TC_G2 = 384, TC_G1 = 448, TC_COLS = 512;
+
+struct DecoderGradTcParams {
+    fpo_mlp w, g;
+    const uint32_t *rows;
+    uint32_t batch;
+    const float *latents, *targets, *coef_weight, *extra_dy;
+    float *dlatents;
+    double *loss;
+    uint32_t *status;
+    int nc;
+    int test_timeout;
+};
+
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[128 x N] (+)= A[128 x K] B[N x K]^T, BF16; acc0: accumulate from the first K slice on.
+__device__ __forceinline__ void gemm_bf16(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, int K, int N,
+                                          uint32_t acc0)
+{
+    const uint32_t idesc = idesc_bf16(128, N);
+    const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+#pragma unroll 1
+    for (int s = 0; s < K / 16; ++s) {
+        const uint64_t a = smem_desc(a_saddr + 256u * s, 128u, sbo);
+        const uint64_t b = smem_desc(b_saddr + 256u * s, 128u, sbo);
+        mma_f16(d_tmem, a, b, idesc, s > 0 ? 1u : acc0);
+    }
+}
+
+__device__ __forceinline__ void put1_bf(unsigned char *base, int row, int k, int K, float v)
+{
+    *reinterpret_cast<__nv_bfloat16 *>(base + core_off(row, k, K)) = __float2bfloat16_rn(v);
+}
+
+// 8 consecutive values of row `row` (K-chunk j) as BF16.
+__device__ __forceinline__ void put8_bf(unsigned char *base, int row, int j, int K, const float *v)
+{
+    uint32_t h[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+        h[e] = *reinterpret_cast<const uint32_t *>(&b);
+    }
+    *reinterpret_cast<uint4 *>(base + core_off(row, 8 * j, K)) = make_uint4(h[0], h[1], h[2], h[3]);
+}
+
+// K-chunk j of row `row` = {hi(b), lo(b), 0 x 6} in BF16 (hi + lo carries b
+// to about 16 bits), or {c, c, 0 x 6}: the constant columns of an A operand.
+__device__ __forceinline__ void put_pair_bf(unsigned char *base, int row, int j, int K, float a, float b)
+{
+    const __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+    *reinterpret_cast<uint4 *>(base + core_off(row, 8 * j, K)) =
+        make_uint4(*reinterpret_cast<const uint32_t *>(&p), 0u, 0u, 0u);
+}
+__device__ __forceinline__ void put_bias_bf(unsigned char *base, int row, int j, int K, float b)
+{
+    const float hi = __bfloat162float(__float2bfloat16_rn(b));
+    put_pair_bf(base, row, j, K, hi, b - hi);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(128, 1) decoder_grad_tc_kernel(const __grid_constant__ DecoderGradTcParams p)
+{
+    extern __shared__ __align__(1024) unsigned char tg_smem_raw[];
+    unsigned char *sm = tg_smem_raw + ((1024u - (ptx::smem_u32(tg_smem_raw) & 1023u)) & 1023u);
+    __shared__ uint64_t s_bar, s_never;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+    __shared__ double s_loss;
+    const int t = threadIdx.x, warp = t >> 5;
+    const int nc = p.nc;
+    if (t == 0) {
+        s_fail = 0;
+        s_loss = 0.0;
+        ptx::mbar_init(&s_bar, 1);
+        ptx::mbar_init(&s_never, 1);
+        ptx::fence_barrier_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(ptx::smem_u32(&s_tmem)),
+                     "r"(TC_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // --- weights as BF16 B operands, once per CTA
+    for (int q = t; q < 64 * (TG_K1 / 8); q += 128) {
+        const int n = q / (TG_K1 / 8), j = q % (TG_K1 / 8);
+        if (j < 4) put8_bf(sm + TGO_W1, n, j, TG_K1, p.w.w1 + n * 32 + 8 * j);
+        else if (j == 4) put_bias_bf(sm + TGO_W1, n, j, TG_K1, p.w.b1[n]);
+        else put_pair_bf(sm + TGO_W1, n, j, TG_K1, 0.0f, 0.0f);
+    }
+    for (int q = t; q < 64 * (TG_K2 / 8); q += 128) {
+        const int n = q / (TG_K2 / 8), j = q % (TG_K2 / 8);
+        if (j < 8) put8_bf(sm + TGO_W2, n, j, TG_K2, p.w.w2 + n * 64 + 8 * j);
+        else if (j == 8) put_bias_bf(sm + TGO_W2, n, j, TG_K2, p.w.b2[n]);
+        else put_pair_bf(sm + TGO_W2, n, j, TG_K2, 0.0f, 0.0f);
+    }
+    for (int q = t; q < TG_NC * (TG_K2 / 8); q += 128) {
+        const int n = q / (TG_K2 / 8), j = q % (TG_K2 / 8);
+        if (n >= nc || j == 9) put_pair_bf(sm + TGO_W3, n, j, TG_K2, 0.0f, 0.0f);
+        else if (j < 8) put8_bf(sm + TGO_W3, n, j, TG_K2, p.w.w3 + n * 64 + 8 * j);
+        else put_bias_bf(sm + TGO_W3, n, j, TG_K2, p.w.b3[n]);
+    }
+    for (int q = t; q < 64 * TG_NC; q += 128) {  // W3^T[k][j] = W3[j][k]
+        const int k = q / TG_NC, j = q % TG_NC;
+        put1_bf(sm + TGO_W3T, k, j, TG_NC, j < nc ? p.w.w3[j * 64 + k] : 0.0f);
+    }
+    for (int q = t; q < 64 * 64; q += 128) {  // W2^T[k][o] = W2[o][k]
+        const int k = q >> 6, o = q & 63;
+        put1_bf(sm + TGO_W2T, k, o, 64, p.w.w2[o * 64 + k]);
+    }
+    for (int q = t; q < 32 * 64; q += 128) {  // W1^T[k][o] = W1[o][k]
+        const int k = q >> 6, o = q & 63;
+        put1_bf(sm + TGO_W1T, k, o, 64, p.w.w1[o * 32 + k]);
+    }
+    // the transposed activations' rows past the ones row, inside their allocation
+    for (int q = t; q < 7 * TG_KR; q += 128) {
+        put1_bf(sm + TGO_XT, 33 + q / TG_KR, q % TG_KR, TG_KR, 0.0f);
+        put1_bf(sm + TGO_H1T, 65 + q / TG_KR, q % TG_KR, TG_KR, 0.0f);
+        put1_bf(sm + TGO_H2T, 65 + q / TG_KR, q % TG_KR, TG_KR, 0.0f);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+
+    const uint32_t tm = s_tmem;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;  // this warp's lane quarter
+    const uint32_t sa = ptx::smem_u32(sm);
+    uint32_t phase = 0;
+    bool first_wait = p.test_timeout != 0;
+    auto hand_off = [&]() {  // generic smem writes and TMEM reads before the next MMAs
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+    };
+    auto wait_mmas = [&]() -> bool {  // bounded; CTA-uniform outcome
+        const bool ok = first_wait ? ptx::mbar_wait_bounded(&s_never, 0, TEST_WAIT_LIMIT_NS)
+                                   : ptx::mbar_wait_bounded(&s_bar, phase, LT_WAIT_NS);
+        first_wait = false;
+        if (!ok) s_fail = 1;
+        __syncthreads();
+        fence_after();
+        if (s_fail) return false;
+        phase ^= 1u;
+        return true;
+    };
+    const uint32_t n_tiles = (p.batch + 127) / 128;
+    float lsum = 0.0f;
+    uint32_t acc_w = 0;  // the weight gradients accumulate from the CTA's second tile on
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const uint32_t r0 = tile * 128;
+        const bool valid = r0 + (uint32_t)t < p.batch;
+        const size_t row = valid ? p.rows[r0 + t] : 0;
+        const float one = valid ? 1.0f : 0.0f;
+        // X: [x 1] (A of Z1) and [X^T; 1] (A of G1)
+        {
+            float x[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) x[k] = valid ? p.latents[row * 32 + k] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) put8_bf(sm + TGO_A, t, j, TG_K1, x + 8 * j);
+            put_pair_bf(sm + TGO_A, t, 4, TG_K1, one, one);
+            put_pair_bf(sm + TGO_A, t, 5, TG_K1, 0.0f, 0.0f);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) put1_bf(sm + TGO_XT, k, t, TG_KR, x[k]);
+            put1_bf(sm + TGO_XT, 32, t, TG_KR, one);
+        }
+        hand_off();
+        if (t == 0) {
+            fence_after();
+            gemm_bf16(tm + TC_SCR, sa + TGO_A, sa + TGO_W1, TG_K1, 64, 0);
+            mma_commit(&s_bar);
+        }
+        if (!wait_mmas()) break;
+        // H1 = relu(Z1): [H1 1] (A of Z2), [H1^T; 1] (A of G2), the mask of Z1 > 0
+        uint32_t m1[2], m2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tmem_ld32(tm + lane_off + TC_SCR + 32 * h, v);
+            m1[h] = 0;
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                if (v[e] > 0.0f) m1[h] |= 1u << e;
+                v[e] = fmaxf(v[e], 0.0f);
+                put1_bf(sm + TGO_H1T, 32 * h + e, t, TG_KR, v[e]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) put8_bf(sm + TGO_A, t, 4 * h + c, TG_K2, v + 8 * c);
+        }
+        put_pair_bf(sm + TGO_A, t, 8, TG_K2, one, one);
+        put_pair_bf(sm + TGO_A, t, 9, TG_K2, 0.0f, 0.0f);
+        put1_bf(sm + TGO_H1T, 64, t, TG_KR, one);
+        hand_off();
+        if (t == 0) {
+            fence_after();
+            gemm_bf16(tm + TC_SCR, sa + TGO_A, sa + TGO_W2, TG_K2, 64, 0);
+            mma_commit(&s_bar);
+        }
+        if (!wait_mmas()) break;
+        // H2 = relu(Z2) in place of H1 (Z2 is done with it)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tmem_ld32(tm + lane_off + TC_SCR + 32 * h, v);
+            m2[h] = 0;
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                if (v[e] > 0.0f) m2[h] |= 1u << e;
+                v[e] = fmaxf(v[e], 0.0f);
+                put1_bf(sm + TGO_H2T, 32 * h + e, t, TG_KR, v[e]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) put8_bf(sm + TGO_A, t, 4 * h + c, TG_K2, v + 8 * c);
+        }
+        put1_bf(sm + TGO_H2T, 64, t, TG_KR, one);
+        hand_off();
+        if (t == 0) {
+            fence_after();
+            gemm_bf16(tm + TC_SCR, sa + TGO_A, sa + TGO_W3, TG_K2, TG_NC, 0);
+            mma_commit(&s_bar);
+        }
+        if (!wait_mmas()) break;
+        // dY = 2 cw (Y - target) + extra: dY (A of dH2, over the H2 it replaces) and dY^T (B of G3)
+#pragma unroll 1
+        for (int c = 0; c < TG_NC / 32 + 1; ++c) {
+            float v[32];
+            tmem_ld32(tm + lane_off + TC_SCR + 32 * c, v);  // columns 176..191: unused scratch
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const int j = 32 * c + e;
+                float d = 0.0f;
+                if (valid && j < nc) {
+                    const float err = v[e] - p.targets[row * nc + j];
+                    const float cw = p.coef_weight[j];
+                    lsum = fmaf(cw * err, err, lsum);
+                    d = 2.0f * cw * err;
+                    if (p.extra_dy) d += p.extra_dy[row * nc + j];
+                }
+                v[e] = d;
+                if (j < TG_NC) put1_bf(sm + TGO_B, j, t, TG_KR, d);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (4 * c + q < TG_NC / 8) put8_bf(sm + TGO_A, t, 4 * c + q, TG_NC, v + 8 * q);
+        }
+        hand_off();
+        if (t == 0) {
+            fence_after();
+            gemm_bf16(tm + TC_SCR, sa + TGO_A, sa + TGO_W3T, TG_NC, 64, 0);
+            gemm_bf16(tm + TC_G3, sa + TGO_H2T, sa + TGO_B, TG_KR, TG_NC, acc_w);
+            mma_commit(&s_bar);
+        }
+        if (!wait_mmas()) break;
+        // d2 = dH2 [Z2 > 0]: A of dH1 (over dY) and d2^T (B of G2, over dY^T)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tmem_ld32(tm + lane_off + TC_SCR + 32 * h, v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                v[e] = (m2[h] >> e) & 1u ? v[e] : 0.0f;
+                put1_bf(sm + TGO_B, 32 * h + e, t, TG_KR, v[e]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) put8_bf(sm + TGO_A, t, 4 * h + c, 64, v + 8 * c);
+        }
+        hand_off();
+        if (t == 0) {
+            fence_after();
+            gemm_bf16(tm + TC_SCR, sa + TGO_A, sa + TGO_W2T, 64, 64, 0);
+            gemm_bf16(tm + TC_G2, sa + TGO_H1T, sa + TGO_B, TG_KR, 64, acc_w);
+            mma_commit(&s_bar);
+        }
+        if (!wait_mmas()) break;
+        // d1 = dH1 [Z1 > 0]: A of dX and d1^T (B of G1)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tmem_ld32(tm + lane_off + TC_SCR + 32 * h, v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                v[e] = (m1[h] >> e) & 1u ? v[e] : 0.0f;
+                put1_bf(sm + TGO_B, 32 * h + e, t, TG_KR, v[e]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) put8_bf(sm + TGO_A, t, 4 * h + c, 64, v + 8 * c);
+        }
+        hand_off();
+        if (t == 0) {
+            fence_after();
+            gemm_bf16(tm + TC_SCR, sa + TGO_A, sa + TGO_W1T, 64, 32, 0);
+            gemm_bf16(tm + TC_G1, sa + TGO_XT, sa + TGO_B, TG_KR, 64, acc_w);
+            mma_commit(&s_bar);
+        }
+        if (!wait_mmas()) break;
+        // dL/d(latent) of the tile's rows
+        {
+            float v[32];
+            tmem_ld32(tm + lane_off + TC_SCR, v);
+            if (valid) {  // (scalar stores: the caller's array needs only float alignment)
+#pragma unroll
+                for (int k = 0; k < 32; ++k) p.dlatents[(size_t)(r0 + t) * 32 + k] = v[k];
+            }
+        }
+        fence_before();  // TMEM reads done before the next tile's MMAs
+        acc_w = 1;
+    }
+    if (!s_fail) {
+        // the weight gradients: lane k of G3 / G2 / G1 is input feature k, lane
+        // 64 (32 for G1) the bias; column j / o the output feature
+#pragma unroll 1
+        for (int c = 0; c < TG_NC / 32 + 1; ++c) {
+            float v[32];
+            tmem_ld32(tm + lane_off + TC_G3 + 32 * c, v);  // columns past 175 belong to G3's padding
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const int j = 32 * c + e;
+                if (j >= nc) continue;
+                if (t < 64) atomicAdd(p.g.w3 + j * 64 + t, v[e]);
+                else if (t == 64) atomicAdd(p.g.b3 + j, v[e]);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tmem_ld32(tm + lane_off + TC_G2 + 32 * h, v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const int o = 32 * h + e;
+                if (t < 64) atomicAdd(p.g.w2 + o * 64 + t, v[e]);
+                else if (t == 64) atomicAdd(p.g.b2 + o, v[e]);
+            }
+            tmem_ld32(tm + lane_off + TC_G1 + 32 * h, v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const int o = 32 * h + e;
+                if (t < 32) atomicAdd(p.g.w1 + o * 32 + t, v[e]);
+                else if (t == 32) atomicAdd(p.g.b1 + o, v[e]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        if ((t & 31) == 0) atomicAdd(&s_loss, (double)lsum);
+    } else if (t == 0) {
+        // the commit whose wait gave up: wait for it once more (bounded)
+        // before TMEM is freed
+        ptx::mbar_wait_bounded(&s_bar, phase, LT_WAIT_NS);
+        if (p.status) atomicOr(p.status, STATUS_DEVICE_TIMEOUT);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0 && p.loss && !s_fail) atomicAdd(p.loss, s_loss);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(TC_COLS) : "memory");
+}
+
 // cuTensorMapEncodeTiled from the driver, looked up once.
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
@@ -497,6 +900,48 @@ int launch_latent_table(const LatentParams &pin, int sm_count, void *stream)
 int latent_pipeline_smem_bytes() { return lt_smem<LT_GROUPS_PIPE>(); }
 
 }  // namespace fpo
+
+extern "C" int fpo_decoder_grad_tc(const fpo_mlp *w, int32_t n1, int32_t n2, uint32_t batch, const uint32_t *rows,
+                                   const float *latents, const float *targets, const float *coef_weight,
+                                   const float *extra_dy, const fpo_mlp *grad, float *dlatents, double *loss,
+                                   uint32_t *status, uint32_t flags, void *cuda_stream)
+{
+    using namespace fpo;
+    if (!w || !grad || !w->w1 || !w->b1 || !w->w2 || !w->b2 || !w->w3 || !w->b3 || !grad->w1 || !grad->b1 ||
+        !grad->w2 || !grad->b2 || !grad->w3 || !grad->b3)
+        return set_last_error(FPO_ERR_INVALID_ARG, "NULL weights");
+    if (n1 < 1 || n2 < 1 || n1 + 27 * n2 > TG_NC) return set_last_error(FPO_ERR_INVALID_ARG, "n1 + 27 n2 must be in [28, 176]");
+    if (flags & ~(uint32_t)FPO_FLAG_TEST_DEVICE_TIMEOUT) return set_last_error(FPO_ERR_INVALID_ARG, "unknown flags");
+    if (batch == 0) return FPO_OK;
+    if (!rows || !latents || !targets || !coef_weight || !dlatents) return set_last_error(FPO_ERR_INVALID_ARG, "NULL array");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return set_last_error(FPO_ERR_CUDA, cudaGetErrorString(e));
+    DecoderGradTcParams p{};
+    p.w = *w;
+    p.g = *grad;
+    p.rows = rows;
+    p.batch = batch;
+    p.latents = latents;
+    p.targets = targets;
+    p.coef_weight = coef_weight;
+    p.extra_dy = extra_dy;
+    p.dlatents = dlatents;
+    p.loss = loss;
+    p.status = status;
+    p.nc = n1 + 27 * n2;
+    p.test_timeout = (flags & FPO_FLAG_TEST_DEVICE_TIMEOUT) != 0;
+    const int smem = TG_SMEM + 1024;  // + alignment slack
+    e = cudaFuncSetAttribute(decoder_grad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return set_last_error(FPO_ERR_CUDA, cudaGetErrorString(e));
+    const uint32_t n_tiles = (batch + 127) / 128;
+    const uint32_t blocks = n_tiles < (uint32_t)sms ? n_tiles : (uint32_t)sms;
+    decoder_grad_tc_kernel<<<blocks, 128, smem, (cudaStream_t)cuda_stream>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_last_error(FPO_ERR_CUDA, cudaGetErrorString(e));
+    return FPO_OK;
+}
 
 using namespace fpo;
 

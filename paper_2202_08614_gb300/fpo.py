@@ -35,7 +35,7 @@ EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
            "fpo_last_error", "fpo_version", "fpo_render_noalloc", "fpo_set_coeffs",
            "fpo_dft_leaves", "fpo_union_trees", "fpo_latent_table", "fpo_decoder_grad",
            "fpo_adam", "fpo_set_latents", "fpo_render_frames", "fpo_adam_leaves",
-           "fpo_decoder_forward", "fpo_set_coeffs_from_decoder", "fpo_fma_peak"]
+           "fpo_decoder_forward", "fpo_set_coeffs_from_decoder", "fpo_fma_peak", "fpo_decoder_grad_tc"]
 
 
 class FPOError(RuntimeError):
@@ -116,6 +116,8 @@ def lib():
                                        C.c_double, C.c_uint32, P, P, P, P]
         L.fpo_decoder_grad.argtypes = [C.POINTER(Mlp), C.c_int32, C.c_int32, C.c_uint32, P, P, P, P,
                                        P, C.POINTER(Mlp), P, P, P]
+        L.fpo_decoder_grad_tc.argtypes = [C.POINTER(Mlp), C.c_int32, C.c_int32, C.c_uint32, P, P, P, P,
+                                          P, C.POINTER(Mlp), P, P, P, C.c_uint32, P]
         L.fpo_decoder_forward.argtypes = [C.POINTER(Mlp), C.c_int32, C.c_int32, C.c_uint32, P, P, P]
         L.fpo_set_coeffs_from_decoder.argtypes = [P, C.POINTER(Mlp), P, P]
         L.fpo_fma_peak.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, P, C.POINTER(C.c_double), P]

@@ -22,9 +22,14 @@ from . import fpo
 
 
 class LatentModel:
-    def __init__(self, n_leaves: int, n1: int = 31, n2: int = 5, seed: int = 0, device="cuda"):
+    def __init__(self, n_leaves: int, n1: int = 31, n2: int = 5, seed: int = 0, device="cuda",
+                 tensor_cores: bool = False):
+        """tensor_cores: take the gradients with fpo_decoder_grad_tc (tcgen05,
+        BF16 operands) instead of fpo_decoder_grad (FP32 SIMT)."""
         import torch
 
+        self.tensor_cores = tensor_cores
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)  # fpo_decoder_grad_tc's status word
         self.n, self.n1, self.n2 = n_leaves, n1, n2
         self.nc = n1 + 27 * n2
         g = torch.Generator(device=device).manual_seed(seed)
@@ -83,14 +88,22 @@ class LatentModel:
         dl = torch.empty((b, 32), device=rows.device)
         loss = torch.zeros(1, dtype=torch.float64, device=rows.device)
         w, g = self._mlp(self.p), self._mlp(self.g)
-        fpo.check(fpo.lib().fpo_decoder_grad(
-            C.byref(w), self.n1, self.n2, b, C.c_void_p(rows.data_ptr()),
-            C.c_void_p(self.p["lat"].data_ptr()), C.c_void_p(targets.data_ptr()),
-            C.c_void_p(coef_weight.data_ptr()),
-            C.c_void_p(extra_dy.data_ptr() if extra_dy is not None else None), C.byref(g),
-            C.c_void_p(dl.data_ptr()), C.c_void_p(loss.data_ptr()),
-            C.c_void_p(fpo._stream_handle(stream))))
+        args = (C.byref(w), self.n1, self.n2, b, C.c_void_p(rows.data_ptr()),
+                C.c_void_p(self.p["lat"].data_ptr()), C.c_void_p(targets.data_ptr()),
+                C.c_void_p(coef_weight.data_ptr()),
+                C.c_void_p(extra_dy.data_ptr() if extra_dy is not None else None), C.byref(g),
+                C.c_void_p(dl.data_ptr()), C.c_void_p(loss.data_ptr()))
+        if self.tensor_cores:
+            fpo.check(fpo.lib().fpo_decoder_grad_tc(*args, C.c_void_p(self.status.data_ptr()), 0,
+                                                    C.c_void_p(fpo._stream_handle(stream))))
+        else:
+            fpo.check(fpo.lib().fpo_decoder_grad(*args, C.c_void_p(fpo._stream_handle(stream))))
         return dl, loss
+
+    def check_status(self, stream=None):
+        """Waits for the stream and raises FPOError if a tensor-core gradient
+        step reported a device-side time-out."""
+        fpo.check_status_word(self.status, stream)
 
     def decode(self, out=None, stream=None):
         """FP32 coefficients of every leaf [n, nc] (fpo_decoder_forward)."""
@@ -172,6 +185,8 @@ class LatentModel:
             loss = self.step(rows, targets, coef_weight, lr_w * f, lr_lat * f, pixel=px)
             if log_every and (s % log_every == 0 or s == steps - 1):
                 hist.append((s, float(loss.item()) / batch))
+        if self.tensor_cores:
+            self.check_status()
         return hist
 
     def inference_arrays(self):

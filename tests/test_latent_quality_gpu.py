@@ -56,7 +56,7 @@ def test_latent_decoder_quality_and_gain_on_a_generated_body():
     gen = synth.Tree(d, xyz, coeffs.cpu().numpy(), DEPTH)
     cams = synth.ring_cameras(16, W, H)
 
-    m = LatentModel(n, seed=0)
+    m = LatentModel(n, seed=0, tensor_cores=True)
     m.init_output_bias(coeffs)
     pixel = PixelLoss(gen, cams, rays=8192, weight=10.0, every=4, start=0.1)
     try:

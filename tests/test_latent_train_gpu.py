@@ -251,3 +251,114 @@ def test_set_coeffs_from_decoder_equals_decode_then_set_coeffs():
         assert e.value.code == -8
     finally:
         c.close()
+
+
+def _bf16(a):
+    """Round-to-nearest-even to BF16, as FP64 (host)."""
+    x = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    x = (x + 0x7FFF + ((x >> 16) & 1)) & 0xFFFF0000
+    return x.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _tc_emulation(P, r, tgt, cw, extra):
+    """The tensor-core step in FP64 with BF16 operands where the kernel rounds
+    them: latents, weights, hidden activations, dL/dy, d2, d1 (biases exact)."""
+    x = _bf16(P["lat"][r])
+    w1, w2, w3 = _bf16(P["w1"]), _bf16(P["w2"]), _bf16(P["w3"])
+    z1 = x @ w1.T + P["b1"]
+    h1 = _bf16(np.maximum(z1, 0))
+    z2 = h1 @ w2.T + P["b2"]
+    h2 = _bf16(np.maximum(z2, 0))
+    y = h2 @ w3.T + P["b3"]
+    e = y - tgt[r]
+    L = float((cw * e * e).sum())
+    dy = _bf16(2 * cw * e + (extra[r] if extra is not None else 0))
+    d2 = _bf16((dy @ w3) * (z2 > 0))
+    d1 = _bf16((d2 @ w2) * (z1 > 0))
+    g = {"w3": dy.T @ h2, "b3": dy.sum(0), "w2": d2.T @ h1, "b2": d2.sum(0), "w1": d1.T @ x, "b1": d1.sum(0),
+         "dx": d1 @ w1}
+    # sum of |terms| of every element: a BF16 operand that rounds the other way
+    # (its FP32 sum landed on the other side of a rounding point) moves an
+    # element by about 2^-8 of the terms it enters
+    a = np.abs
+    terms = {"w3": a(dy).T @ a(h2), "b3": a(dy).sum(0), "w2": a(d2).T @ a(h1), "b2": a(d2).sum(0),
+             "w1": a(d1).T @ a(x), "b1": a(d1).sum(0), "dx": a(d1) @ a(w1)}
+    return L, g, terms
+
+
+@pytest.mark.parametrize("b", [1, 333, 20000])
+def test_decoder_grad_tensor_cores(b):
+    # fpo_decoder_grad_tc against an FP64 reference that rounds the operands
+    # to BF16 where the kernel does (element-wise, within 2^-6 of the element's
+    # sum of |terms|: FP32 accumulation order, and the odd BF16 rounding that
+    # goes the other way, compounded over the layers), and against the FP64
+    # gradient itself (the BF16 operand error)
+    rng = np.random.default_rng(b)
+    n = max(2000, b + 10)
+    m = LatentModel(n, seed=2, tensor_cores=True)
+    m.p["b1"].copy_(torch.as_tensor(rng.normal(size=64) * 0.1))
+    m.p["b2"].copy_(torch.as_tensor(rng.normal(size=64) * 0.1))
+    m.p["b3"].copy_(torch.as_tensor(rng.normal(size=NC)))
+    tgt = torch.as_tensor(rng.normal(size=(n, NC)), dtype=torch.float32, device="cuda")
+    cw = torch.as_tensor(rng.uniform(0.5, 2, NC), dtype=torch.float32, device="cuda")
+    extra = torch.as_tensor(rng.normal(size=(n, NC)) * 0.01, dtype=torch.float32, device="cuda")
+    rows = torch.as_tensor(rng.permutation(n)[:b], dtype=torch.int32, device="cuda")
+    dl, loss = m.grad(rows, tgt, cw, extra_dy=extra)
+    m.check_status()
+    P = {k: v.double().cpu().numpy() for k, v in m.p.items()}
+    r = rows.cpu().numpy()
+    T, CW, E = tgt.double().cpu().numpy(), cw.double().cpu().numpy(), extra.double().cpu().numpy()
+    L, g, terms = _tc_emulation(P, r, T, CW, E)
+    got = {k: v.double().cpu().numpy() for k, v in m.g.items()}
+    got["dx"] = dl.double().cpu().numpy()
+    assert abs(loss.item() - L) <= 1e-3 * L
+    for k in ("w1", "b1", "w2", "b2", "w3", "b3", "dx"):
+        excess = np.abs(got[k] - g[k]) - (2.0 ** -6 * terms[k] + 1e-6 * np.abs(g[k]).max())
+        assert excess.max() <= 0, (k, excess.max())
+    # against the FP64 gradient: BF16 operands (and the ReLU masks they flip)
+    # move every matrix by a few 2^-8; the kernel is no further from it than
+    # exact arithmetic on the same BF16 operands is
+    L64, dx64, g64 = olat.loss_grad(P["lat"][r], P["w1"], P["b1"], P["w2"], P["b2"], P["w3"], P["b3"],
+                                    T[r], CW)
+    _, dxe, ge = _backprop_dy(P, r, E[r])
+    g64 = {k: g64[k] + ge[k] for k in ge}
+    g64["dx"] = dx64 + dxe
+    for k in ("w1", "b1", "w2", "b2", "w3", "b3", "dx"):
+        nrm = np.linalg.norm(g64[k])
+        rel_gpu, rel_emu = np.linalg.norm(got[k] - g64[k]) / nrm, np.linalg.norm(g[k] - g64[k]) / nrm
+        print(f"{k}: |tc - fp64| / |fp64| = {rel_gpu:.2e} (BF16 emulation {rel_emu:.2e})")
+        assert rel_emu <= 0.1 and rel_gpu <= 1.05 * rel_emu + 1e-3, (k, rel_gpu, rel_emu)
+
+
+def test_decoder_grad_tensor_cores_timeout_is_reported():
+    # each CTA's first wait (on a barrier nothing signals) runs out after 1 ms:
+    # the status word gets the time-out bit, the weight gradients stay as they
+    # were, and the next call is exact
+    rng = np.random.default_rng(5)
+    n, b = 3000, 1000
+    m = LatentModel(n, seed=4, tensor_cores=True)
+    tgt = torch.as_tensor(rng.normal(size=(n, NC)), dtype=torch.float32, device="cuda")
+    cw = torch.ones(NC, device="cuda")
+    rows = torch.as_tensor(rng.permutation(n)[:b], dtype=torch.int32, device="cuda")
+    ref_dl, _ = m.grad(rows, tgt, cw)
+    ref_g = {k: v.clone() for k, v in m.g.items()}
+    m.check_status()
+    for v in m.g.values():
+        v.zero_()
+    dl = torch.empty((b, 32), device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    w, g = m._mlp(m.p), m._mlp(m.g)
+    fpo.check(fpo.lib().fpo_decoder_grad_tc(
+        C.byref(w), N1, N2, b, C.c_void_p(rows.data_ptr()), C.c_void_p(m.p["lat"].data_ptr()),
+        C.c_void_p(tgt.data_ptr()), C.c_void_p(cw.data_ptr()), None, C.byref(g), C.c_void_p(dl.data_ptr()),
+        C.c_void_p(loss.data_ptr()), C.c_void_p(m.status.data_ptr()), fpo.FLAG_TEST_DEVICE_TIMEOUT, None))
+    with pytest.raises(fpo.FPOError) as e:
+        m.check_status()
+    assert e.value.code == -9
+    assert all(int(torch.count_nonzero(v)) == 0 for v in m.g.values())
+    m.status.zero_()
+    dl2, _ = m.grad(rows, tgt, cw)
+    m.check_status()
+    assert torch.equal(dl2, ref_dl)
+    for k in ref_g:  # float atomics: the sums' order may differ between runs
+        assert torch.allclose(m.g[k], ref_g[k], rtol=1e-5, atol=1e-6 * float(ref_g[k].abs().max()))

@@ -137,6 +137,32 @@ def test_root_leaf_and_single_deep_leaf():
         assert (ref["visit_count"] == 1).sum() > n // 4
 
 
+def test_cluster_at_the_maximum_depth():
+    # 8^3 adjacent depth-12 leaves (the deepest level) inside an otherwise
+    # empty depth-3 cell, surrounded by depth-3 leaves: rays aimed at the
+    # cluster walk from coarse leaves into it and step between neighbours at
+    # the maximum stack depth
+    rng = np.random.default_rng(12)
+    c0 = 7 * 256 + 120  # depth-12 coordinate of the cluster's corner, inside depth-3 cell (3, 3, 3)
+    g = np.arange(8)
+    deep = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3) + c0
+    coarse = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    coarse = coarse[(coarse != 3).any(1) & (rng.uniform(size=len(coarse)) < 0.3)]
+    d = np.concatenate([np.full(len(deep), 12), np.full(len(coarse), 3)]).astype(np.uint8)
+    xyz = np.concatenate([deep, coarse]).astype(np.uint32)
+    co = synth.draw_coefficients(rng, len(d))
+    co[: len(deep), 0] += 1200.0  # sigma delta about 0.3 per 1/4096 cell: translucent
+    tree = synth.Tree(d, xyz, co, 12)
+    centre = (c0 + 4.0) / 4096.0
+    n = 2048
+    dirs = rng.normal(size=(n, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    o = centre - 1.2 * dirs + rng.uniform(-4.5, 4.5, (n, 3)) / 4096.0
+    gpu, ref = gu.render_both(tree, rays_o=o, rays_d=dirs, t=21.0, visit_cap=96)
+    gu.compare(gpu, ref)
+    assert (ref["visit_count"] >= 8).sum() > n // 8  # many rays cross several deep leaves
+
+
 def test_ragged_and_tiny_images():
     tree = synth.shell_tree()
     for w, h in [(1, 1), (7, 3), (37, 23), (130, 5)]:
