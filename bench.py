@@ -402,7 +402,7 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
     # weight 10) through the render adjoint
     m = LatentModel(n, seed=0, tensor_cores=True)
     m.init_output_bias(coeffs)
-    pixel_cfg = dict(rays=8192, weight=10.0, every=4, start=0.1)
+    pixel_cfg = dict(rays=8192, weight=10.0, every=4, start=0.1, tensor_cores=True)
     pixel = PixelLoss(gen, cams, **pixel_cfg)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -452,7 +452,11 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
         "decoder_grad_simt_65536_leaves": k_simt,
         "decode_into_records_all_leaves": rate(
             lambda: pixel.work.set_coeffs_from_decoder(m._mlp(m.p), m.p["lat"]), fwd * n, 3),
+        "decode_into_records_tc_all_leaves": rate(
+            lambda: pixel.work.set_coeffs_from_decoder(m._mlp(m.p), m.p["lat"], tensor_cores=True), fwd * n, 3,
+            tensor=True),
     }
+    pixel.work.status()
     pixel.close()
     r = fpo.Renderer(storage="latent")
     r.upload(synth.Tree(tree.leaf_depth, tree.leaf_xyz, np.zeros((0, 166), np.float32), tree.max_depth))

@@ -165,8 +165,11 @@ enum {
      * The pass stops, waits (with its normal limit) for the copies or MMAs it
      * has in flight, and the call then reports FPO_ERR_DEVICE_TIMEOUT through
      * fpo_status_sync; the frame's pixels are undefined, and the context
-     * renders normally afterwards. */
-    FPO_FLAG_TEST_DEVICE_TIMEOUT = 64
+     * renders normally afterwards.  (fpo_dft_leaves, fpo_decoder_grad_tc and
+     * fpo_set_coeffs_from_decoder take it too, each as it documents.) */
+    FPO_FLAG_TEST_DEVICE_TIMEOUT = 64,
+    /* fpo_set_coeffs_from_decoder: decode on the tensor cores. */
+    FPO_FLAG_TENSOR_CORES = 128
 };
 
 /* Per-call options.  bg: background colour added with the final
@@ -429,15 +432,22 @@ int fpo_decoder_grad_tc(const fpo_mlp *w, int32_t n1, int32_t n2, uint32_t batch
 int fpo_decoder_forward(const fpo_mlp *w, int32_t n1, int32_t n2, uint32_t n, const float *latents,
                         float *coeffs, void *cuda_stream);
 
-/* fpo_set_coeffs of the decoder's FP32 coefficients: every leaf's latent
+/* fpo_set_coeffs of the decoder's coefficients: every leaf's latent
  * (latents: device [n_leaves][32], upload order) decoded by the MLP `w`
- * (FP32 master weights, as fpo_decoder_forward) straight into the context's
- * FP32 records, with no [n_leaves][n1 + 27*n2] array in between.  The values
- * are those fpo_decoder_forward followed by fpo_set_coeffs writes (the same
- * arithmetic, bit for bit).  Enqueued on the stream.  Needs FP32 storage and
- * n1 + 27*n2 <= 176 (else FPO_ERR_UNSUPPORTED).
- * Errors: INVALID_ARG, NO_TREE, UNSUPPORTED, CUDA. */
-int fpo_set_coeffs_from_decoder(fpo_ctx *ctx, const fpo_mlp *w, const float *latents, void *cuda_stream);
+ * (FP32 master weights) straight into the context's FP32 records, with no
+ * [n_leaves][n1 + 27*n2] array in between.  flags = 0: in FP32, the values
+ * fpo_decoder_forward followed by fpo_set_coeffs writes (the same
+ * arithmetic, bit for bit).  FPO_FLAG_TENSOR_CORES: on the tensor cores with
+ * the inference decoder's numerics (FP16 latents, weights and hidden
+ * activations, FP32 accumulation; the last layer unfolded): what the LATENT
+ * storage would render before the IDFT folding; an operand beyond the FP16
+ * range or a wait that runs out (2 s; 1 ms for the first with
+ * FPO_FLAG_TEST_DEVICE_TIMEOUT) is reported through fpo_status_sync as
+ * FPO_ERR_RANGE / FPO_ERR_DEVICE_TIMEOUT.  Enqueued on the stream.  Needs
+ * FP32 storage and n1 + 27*n2 <= 176 (else FPO_ERR_UNSUPPORTED).
+ * Errors: INVALID_ARG (including unknown flags), NO_TREE, UNSUPPORTED, CUDA. */
+int fpo_set_coeffs_from_decoder(fpo_ctx *ctx, const fpo_mlp *w, const float *latents, uint32_t flags,
+                                void *cuda_stream);
 
 /* Adam step (Kingma & Ba 2015) with bias correction, step counted from 1:
  * dense over n elements (rows NULL), or over the rows of a batch (device

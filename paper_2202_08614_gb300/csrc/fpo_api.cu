@@ -797,7 +797,15 @@ int fpo_set_coeffs(fpo_ctx *ctx, const float *coeffs, void *cuda_stream)
     return FPO_OK;
 }
 
-int fpo_set_coeffs_from_decoder(fpo_ctx *ctx, const fpo_mlp *w, const float *latents, void *cuda_stream)
+}  // extern "C"
+namespace fpo {
+// fpo_latent.cu: the decode into the records on the tensor cores
+int launch_decode_records_tc(const fpo_mlp &w, int n1, int n2, uint32_t n, const float *latents, const uint32_t *perm,
+                             float *sig, float *zc, uint32_t *status, bool test_timeout, int sm_count, void *stream);
+}  // namespace fpo
+extern "C" {
+
+int fpo_set_coeffs_from_decoder(fpo_ctx *ctx, const fpo_mlp *w, const float *latents, uint32_t flags, void *cuda_stream)
 {
     if (!ctx) return fail(FPO_ERR_INVALID_ARG, "ctx is NULL");
     if (!ctx->has_tree) return fail(FPO_ERR_NO_TREE, "set_coeffs_from_decoder before fpo_upload_tree");
@@ -808,12 +816,19 @@ int fpo_set_coeffs_from_decoder(fpo_ctx *ctx, const fpo_mlp *w, const float *lat
         return fail(FPO_ERR_UNSUPPORTED, "n1 + 27 n2 above the decoder's 176 outputs");
     if (ctx->n_leaves == 0) return FPO_OK;
     if (!latents) return fail(FPO_ERR_INVALID_ARG, "latents is NULL");
+    if (flags & ~(uint32_t)(FPO_FLAG_TENSOR_CORES | FPO_FLAG_TEST_DEVICE_TIMEOUT))
+        return fail(FPO_ERR_INVALID_ARG, "unknown flags");
     ctx->table_ok = false;  // the coefficients change
     DeviceGuard g(ctx->cfg.device);
     if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
-    const int ce = launch_decode_records(*w, ctx->cfg.n1, ctx->cfg.n2, ctx->n_leaves, latents, ctx->d_perm,
-                                         static_cast<float *>(ctx->d_sig), static_cast<float *>(ctx->d_z),
-                                         ctx->sm_count, cuda_stream);
+    const int ce = (flags & FPO_FLAG_TENSOR_CORES)
+                       ? launch_decode_records_tc(*w, ctx->cfg.n1, ctx->cfg.n2, ctx->n_leaves, latents, ctx->d_perm,
+                                                  static_cast<float *>(ctx->d_sig), static_cast<float *>(ctx->d_z),
+                                                  ctx->d_status, (flags & FPO_FLAG_TEST_DEVICE_TIMEOUT) != 0,
+                                                  ctx->sm_count, cuda_stream)
+                       : launch_decode_records(*w, ctx->cfg.n1, ctx->cfg.n2, ctx->n_leaves, latents, ctx->d_perm,
+                                               static_cast<float *>(ctx->d_sig), static_cast<float *>(ctx->d_z),
+                                               ctx->sm_count, cuda_stream);
     if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "decode launch");
     return FPO_OK;
 }

@@ -541,12 +541,71 @@ __device__ __forceinline__ void put_bias_bf(unsigned char *base, int row, int j,
     put_pair_bf(base, row, j, K, hi, b - hi);
 }
 
+// Rows owned by the lanes of a warp (lane r: row offset off_r, validity ok_r)
+// moved in coalesced pieces through a per-warp shared tile of H rows x 33
+// floats: for each row, the 32 lanes move 32 consecutive floats (columns col0
+// + lane, those below ncols), and the tile turns them into each lane's own
+// 32 values (H = 32: one pass; H = 16: two passes of half the rows).
+template <int H>
+__device__ __forceinline__ void warp_load_rows(float v[32], const float *__restrict__ base, size_t off, bool ok,
+                                               int col0, int ncols, float *tile)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 0; h < 32 / H; ++h) {
+#pragma unroll 4
+        for (int i = 0; i < H; ++i) {
+            const int r = H * h + i;
+            const size_t o = __shfl_sync(0xffffffffu, off, r);
+            const bool k = __shfl_sync(0xffffffffu, ok, r);
+            const int c = col0 + lane;
+            tile[i * 33 + lane] = k && c < ncols ? base[o + c] : 0.0f;
+        }
+        __syncwarp();
+        if ((lane / H) == h) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = tile[(lane - H * h) * 33 + e];
+        }
+        __syncwarp();
+    }
+}
+
+// The inverse: each lane's 32 values of its row to columns col0 + e (those
+// below ncols) of its row, where a column j goes to base_lo[off_lo + j] for
+// j < split and to base_hi[off_hi + j - split] otherwise (H as above).
+template <int H>
+__device__ __forceinline__ void warp_store_rows(const float v[32], float *base_lo, size_t off_lo, float *base_hi,
+                                                size_t off_hi, int split, bool ok, int col0, int ncols, float *tile)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = 0; h < 32 / H; ++h) {
+        if ((lane / H) == h) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) tile[(lane - H * h) * 33 + e] = v[e];
+        }
+        __syncwarp();
+#pragma unroll 4
+        for (int i = 0; i < H; ++i) {
+            const int r = H * h + i;
+            const size_t olo = __shfl_sync(0xffffffffu, off_lo, r), ohi = __shfl_sync(0xffffffffu, off_hi, r);
+            const bool k = __shfl_sync(0xffffffffu, ok, r);
+            const int c = col0 + lane;
+            if (k && c < ncols) {
+                const float x = tile[i * 33 + lane];
+                if (c < split) base_lo[olo + c] = x;
+                else base_hi[ohi + c - split] = x;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(128, 1) decoder_grad_tc_kernel(const __grid_constant__ DecoderGradTcParams p)
 {
-    extern __shared__ __align__(1024) unsigned char tg_smem_raw[];
-    unsigned char *sm = tg_smem_raw + ((1024u - (ptx::smem_u32(tg_smem_raw) & 1023u)) & 1023u);
+    extern __shared__ __align__(128) unsigned char sm[];
     __shared__ uint64_t s_bar, s_never;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
@@ -841,6 +900,228 @@ __global__ void __launch_bounds__(128, 1) decoder_grad_tc_kernel(const __grid_co
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(TC_COLS) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Decode of every leaf into a render context's FP32 records on the tensor
+// cores, with the numerics of the inference decoder (FP16 latents, weights
+// rounded to BF16 and then FP16, FP16 hidden activations, biases as FP16
+// hi/lo pairs, FP32 accumulation) but the last layer unfolded (all
+// n1 + 27 n2 coefficients): what the pixel loss of the decoder's training
+// renders.  DR_GROUPS independent warpgroup pipelines per CTA, one CTA per SM,
+// each with 96 TMEM columns (Z1 and Z2 in the first 64; the last layer in two
+// halves, columns 0..95 and 96..175 of Y, each in the 96) and one
+// shared-memory region for its tile's A operands; the next tile's latents
+// are gathered while the last layer runs.  Tile rows are records: row
+// i gathers latent perm[i] and writes record i (density values at stride ss,
+// SH values at stride zs).
+namespace {
+constexpr int DR_GROUPS = 4, DR_NC = 176, DR_COLS = 96, DR_NH0 = 96, DR_NH1 = DR_NC - DR_NH0;
+constexpr int DRO_W1 = 0;                        // [64][48]  W1 | b1
+constexpr int DRO_W2 = DRO_W1 + 64 * K1 * 2;     // [64][80]  W2 | b2
+constexpr int DRO_W3 = DRO_W2 + 64 * K2 * 2;     // [176][80] W3 | b3
+constexpr int DRO_A = DRO_W3 + DR_NC * K2 * 2;   // per group: [128][80] (X, then H1, then H2)
+constexpr int DR_GROUP_BYTES = 128 * K2 * 2;
+constexpr int DRO_ROWS = DRO_A + DR_GROUPS * DR_GROUP_BYTES;  // per warp: 32 x 33 floats
+constexpr int DR_SMEM = DRO_ROWS + DR_GROUPS * 4 * 32 * 33 * 4;
+
+struct DecodeTcParams {
+    fpo_mlp w;                  // FP32 master weights
+    const float *latents;       // [n][32] FP32, upload order
+    const uint32_t *perm;       // record -> latent row
+    float *sig, *zc;            // FP32 records
+    uint32_t n;
+    int n1, nc, ss, zs;
+    uint32_t *status;
+    int test_timeout;
+};
+}  // namespace
+
+__global__ void __launch_bounds__(128 * DR_GROUPS, 1) decode_records_tc_kernel(const __grid_constant__ DecodeTcParams p)
+{
+    extern __shared__ __align__(1024) unsigned char dr_smem_raw[];
+    unsigned char *sm = dr_smem_raw + ((1024u - (ptx::smem_u32(dr_smem_raw) & 1023u)) & 1023u);
+    __shared__ uint64_t s_bar[DR_GROUPS];
+    __shared__ uint64_t s_never;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail[DR_GROUPS];
+    __shared__ int s_range;
+    const int tid = threadIdx.x, warp = tid >> 5, group = tid >> 7, m = tid & 127;
+    const int nc = p.nc;
+    if (tid == 0) {
+        s_range = 0;
+        for (int g = 0; g < DR_GROUPS; ++g) {
+            s_fail[g] = 0;
+            ptx::mbar_init(&s_bar[g], 1);
+        }
+        ptx::mbar_init(&s_never, 1);
+        ptx::fence_barrier_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(ptx::smem_u32(&s_tmem)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // weights as FP16 B operands, through BF16 as the inference decoder holds
+    // them (values beyond the FP16 range are reported)
+    auto wv = [&](float x) {
+        x = __bfloat162float(__float2bfloat16_rn(x));
+        if (!(fabsf(x) <= F16_MAX)) s_range = 1;
+        return x;
+    };
+    auto bv = [&](float x) {  // biases stay FP32 (an FP16 hi/lo pair in the operand)
+        if (!(fabsf(x) <= F16_MAX)) s_range = 1;
+        return x;
+    };
+    for (int q = tid; q < 64 * (K1 / 8); q += 128 * DR_GROUPS) {
+        const int n = q / (K1 / 8), j = q % (K1 / 8);
+        if (j < 4) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = wv(p.w.w1[n * 32 + 8 * j + e]);
+            put8(sm + DRO_W1, n, j, K1, v);
+        } else if (j == 4) put_bias_chunk(sm + DRO_W1, n, j, K1, bv(p.w.b1[n]), false);
+        else put_zero_chunk(sm + DRO_W1, n, j, K1);
+    }
+    for (int q = tid; q < 64 * (K2 / 8); q += 128 * DR_GROUPS) {
+        const int n = q / (K2 / 8), j = q % (K2 / 8);
+        if (j < 8) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = wv(p.w.w2[n * 64 + 8 * j + e]);
+            put8(sm + DRO_W2, n, j, K2, v);
+        } else if (j == 8) put_bias_chunk(sm + DRO_W2, n, j, K2, bv(p.w.b2[n]), false);
+        else put_zero_chunk(sm + DRO_W2, n, j, K2);
+    }
+    for (int q = tid; q < DR_NC * (K2 / 8); q += 128 * DR_GROUPS) {
+        const int n = q / (K2 / 8), j = q % (K2 / 8);
+        if (n >= nc || j == 9) put_zero_chunk(sm + DRO_W3, n, j, K2);
+        else if (j < 8) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = wv(p.w.w3[n * 64 + 8 * j + e]);
+            put8(sm + DRO_W3, n, j, K2, v);
+        } else put_bias_chunk(sm + DRO_W3, n, j, K2, bv(p.w.b3[n]), false);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = s_tmem + (uint32_t)DR_COLS * (uint32_t)group;
+    const uint32_t my_lane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    unsigned char *ga = sm + DRO_A + group * DR_GROUP_BYTES;
+    float *rows_tile = reinterpret_cast<float *>(sm + DRO_ROWS) + warp * 32 * 33;
+    const uint32_t sa_a = ptx::smem_u32(ga), sa_w1 = ptx::smem_u32(sm + DRO_W1), sa_w2 = ptx::smem_u32(sm + DRO_W2),
+                   sa_w3 = ptx::smem_u32(sm + DRO_W3);
+    uint32_t phase = 0;
+    __half2 hmax = __float2half2_rn(0.0f);
+    bool first_wait = p.test_timeout != 0;
+    auto issue_layer = [&](uint32_t b_addr, int K, int N) {
+        if (m == 0) {
+            fence_after();
+            gemm(tmem, sa_a, b_addr, K, N);
+            mma_commit(&s_bar[group]);
+        }
+    };
+    auto wait_layer = [&]() -> bool {
+        const bool ok = first_wait ? ptx::mbar_wait_bounded(&s_never, 0, TEST_WAIT_LIMIT_NS)
+                                   : ptx::mbar_wait_bounded(&s_bar[group], phase, LT_WAIT_NS);
+        first_wait = false;
+        if (!ok) s_fail[group] = 1;
+        group_sync(group);
+        fence_after();
+        if (s_fail[group]) return false;
+        phase ^= 1u;
+        return true;
+    };
+    auto run_layer = [&](uint32_t b_addr, int K, int N) -> bool {
+        issue_layer(b_addr, K, N);
+        return wait_layer();
+    };
+    auto hand_off = [&]() {
+        fence_async_smem();
+        fence_before();
+        group_sync(group);
+    };
+    const uint32_t n_tiles = (p.n + 127) / 128;
+    const uint32_t first = blockIdx.x * DR_GROUPS + group, step = gridDim.x * DR_GROUPS;
+    // this thread's row of a tile: the gathered FP32 latent (all zero past the end)
+    auto gather = [&](uint32_t tile, float x[32]) {
+        const uint32_t rec = tile * 128 + (uint32_t)m;
+        const bool ok = tile < n_tiles && rec < p.n;
+        const size_t src = ok ? p.perm[rec] : 0;
+        warp_load_rows<32>(x, p.latents, src * 32, ok, 0, 32, rows_tile);
+    };
+    float xn[32];
+    gather(first, xn);
+    for (uint32_t tile = first; tile < n_tiles; tile += step) {
+        const uint32_t rec = tile * 128 + (uint32_t)m;
+        const bool valid = rec < p.n;
+        {
+            __half2 hx = __float2half2_rn(0.0f);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {  // FP16 latents, as the inference decoder holds them
+                put8(ga, m, j, K1, xn + 8 * j);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) hx = __hmax2(hx, __float2half2_rn(fabsf(xn[8 * j + e])));
+            }
+            hmax = __hmax2(hmax, hx);
+            put_bias_chunk(ga, m, 4, K1, 0.0f, true);
+            put_zero_chunk(ga, m, 5, K1);
+        }
+        hand_off();
+        if (!run_layer(sa_w1, K1, 64)) break;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tmem_ld32(my_lane + 32 * h, v);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) put8_relu(ga, m, 4 * h + c, K2, v + 8 * c, hmax);
+        }
+        put_bias_chunk(ga, m, 8, K2, 0.0f, true);
+        put_zero_chunk(ga, m, 9, K2);
+        hand_off();
+        if (!run_layer(sa_w2, K2, 64)) break;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tmem_ld32(my_lane + 32 * h, v);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) put8_relu(ga, m, 4 * h + c, K2, v + 8 * c, hmax);
+        }
+        hand_off();
+        // Y -> record `rec` in two halves: columns < n1 to the density record,
+        // the rest to the SH record; the next tile's latents are gathered
+        // while the first half's MMAs run
+        bool ok = true;
+#pragma unroll 1
+        for (int half = 0; half < 2 && ok; ++half) {
+            const int n_cols = half ? DR_NH1 : DR_NH0, col0 = half ? DR_NH0 : 0;
+            issue_layer(sa_w3 + (uint32_t)core_off(col0, 0, K2), K2, n_cols);
+            if (half == 0) gather(tile + step, xn);
+            if (!(ok = wait_layer())) break;
+#pragma unroll 1
+            for (int c = 0; c < DR_NH0 / 32; ++c) {
+                float v[32];
+                tmem_ld32(my_lane + 32 * c, v);  // columns past n_cols: the group's unused scratch
+                warp_store_rows<32>(v, p.sig, (size_t)rec * p.ss, p.zc, (size_t)rec * p.zs, p.n1, valid,
+                                    col0 + 32 * c, col0 + n_cols < nc ? col0 + n_cols : nc, rows_tile);
+            }
+            fence_before();  // TMEM reads done before the group's next MMAs
+            group_sync(group);
+        }
+        if (!ok) break;
+    }
+    if (p.status && (!(__low2float(hmax) <= F16_MAX) || !(__high2float(hmax) <= F16_MAX) || (tid == 0 && s_range)))
+        atomicOr(p.status, STATUS_FP16_RANGE);
+    if (s_fail[group] && m == 0) {
+        ptx::mbar_wait_bounded(&s_bar[group], phase, LT_WAIT_NS);
+        if (p.status) atomicOr(p.status, STATUS_DEVICE_TIMEOUT);
+    }
+    __syncthreads();
+    fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(512u) : "memory");
+}
+
 // cuTensorMapEncodeTiled from the driver, looked up once.
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
@@ -899,6 +1180,33 @@ int launch_latent_table(const LatentParams &pin, int sm_count, void *stream)
 
 int latent_pipeline_smem_bytes() { return lt_smem<LT_GROUPS_PIPE>(); }
 
+int launch_decode_records_tc(const fpo_mlp &w, int n1, int n2, uint32_t n, const float *latents, const uint32_t *perm,
+                             float *sig, float *zc, uint32_t *status, bool test_timeout, int sm_count, void *stream)
+{
+    if (n == 0) return (int)cudaSuccess;
+    DecodeTcParams p{};
+    p.w = w;
+    p.latents = latents;
+    p.perm = perm;
+    p.sig = sig;
+    p.zc = zc;
+    p.n = n;
+    p.n1 = n1;
+    p.nc = n1 + 27 * n2;
+    p.ss = sig_stride(n1);
+    p.zs = z_stride(n2);
+    p.status = status;
+    p.test_timeout = test_timeout;
+    const int smem = DR_SMEM + 1024;
+    cudaError_t e = cudaFuncSetAttribute(decode_records_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return (int)e;
+    const uint32_t n_tiles = (n + 127) / 128;
+    const uint32_t need = (n_tiles + DR_GROUPS - 1) / DR_GROUPS;
+    const uint32_t blocks = need < (uint32_t)sm_count ? need : (uint32_t)sm_count;
+    decode_records_tc_kernel<<<blocks, 128 * DR_GROUPS, smem, (cudaStream_t)stream>>>(p);
+    return (int)cudaGetLastError();
+}
+
 }  // namespace fpo
 
 extern "C" int fpo_decoder_grad_tc(const fpo_mlp *w, int32_t n1, int32_t n2, uint32_t batch, const uint32_t *rows,
@@ -932,7 +1240,7 @@ extern "C" int fpo_decoder_grad_tc(const fpo_mlp *w, int32_t n1, int32_t n2, uin
     p.status = status;
     p.nc = n1 + 27 * n2;
     p.test_timeout = (flags & FPO_FLAG_TEST_DEVICE_TIMEOUT) != 0;
-    const int smem = TG_SMEM + 1024;  // + alignment slack
+    const int smem = TG_SMEM;
     e = cudaFuncSetAttribute(decoder_grad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return set_last_error(FPO_ERR_CUDA, cudaGetErrorString(e));
     const uint32_t n_tiles = (batch + 127) / 128;

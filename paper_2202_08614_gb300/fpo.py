@@ -27,7 +27,7 @@ IDFT = {"auto": 0, "fused": 1, "materialise": 2}
 TABLE = {"auto": 0, "f32": 1, "f16": 2}
 RAYS_CAMERA, RAYS_EXPLICIT = 0, 1
 FLAG_RECORD_VISITS, FLAG_OUT_T, FLAG_MARK_LEAVES, FLAG_STATS, FLAG_REUSE_TABLE = 1, 2, 4, 8, 16
-FLAG_FP64_GRADCHECK, FLAG_TEST_DEVICE_TIMEOUT = 32, 64
+FLAG_FP64_GRADCHECK, FLAG_TEST_DEVICE_TIMEOUT, FLAG_TENSOR_CORES = 32, 64, 128
 
 # Every symbol include/fpo.h declares.
 EXPORTS = ["fpo_create", "fpo_validate_tree", "fpo_upload_tree", "fpo_render",
@@ -119,7 +119,7 @@ def lib():
         L.fpo_decoder_grad_tc.argtypes = [C.POINTER(Mlp), C.c_int32, C.c_int32, C.c_uint32, P, P, P, P,
                                           P, C.POINTER(Mlp), P, P, P, C.c_uint32, P]
         L.fpo_decoder_forward.argtypes = [C.POINTER(Mlp), C.c_int32, C.c_int32, C.c_uint32, P, P, P]
-        L.fpo_set_coeffs_from_decoder.argtypes = [P, C.POINTER(Mlp), P, P]
+        L.fpo_set_coeffs_from_decoder.argtypes = [P, C.POINTER(Mlp), P, C.c_uint32, P]
         L.fpo_fma_peak.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32, P, C.POINTER(C.c_double), P]
         L.fpo_adam.argtypes = [P, P, P, P, C.c_uint64, P, C.c_uint32, C.c_float, C.c_float,
                                C.c_float, C.c_float, C.c_uint32, P]
@@ -376,15 +376,18 @@ class Renderer:
         check(lib().fpo_set_coeffs(self.h, C.c_void_p(c.data_ptr()),
                                    C.c_void_p(_stream_handle(stream))))
 
-    def set_coeffs_from_decoder(self, mlp, latents, stream=None):
-        """Replaces the tree's coefficients with the decoder's FP32 decode of
-        every leaf's latent (mlp: an Mlp of FP32 device weights; latents: a
-        CUDA float32 tensor [n_leaves, 32] in upload order)."""
+    def set_coeffs_from_decoder(self, mlp, latents, stream=None, tensor_cores=False, test_timeout=False):
+        """Replaces the tree's coefficients with the decoder's decode of every
+        leaf's latent (mlp: an Mlp of FP32 device weights; latents: a CUDA
+        float32 tensor [n_leaves, 32] in upload order): in FP32, or with
+        tensor_cores on tcgen05 with the inference decoder's FP16 numerics
+        (errors then through status())."""
         import torch
 
         lat = latents.detach()
         assert lat.is_cuda and lat.dtype == torch.float32 and lat.is_contiguous()
-        check(lib().fpo_set_coeffs_from_decoder(self.h, C.byref(mlp), C.c_void_p(lat.data_ptr()),
+        flags = (FLAG_TENSOR_CORES if tensor_cores else 0) | (FLAG_TEST_DEVICE_TIMEOUT if test_timeout else 0)
+        check(lib().fpo_set_coeffs_from_decoder(self.h, C.byref(mlp), C.c_void_p(lat.data_ptr()), flags,
                                                 C.c_void_p(_stream_handle(stream))))
 
     def set_latents(self, latents_f16, w1, b1, w2, b2, w3, b3, stream=None):

@@ -207,12 +207,15 @@ class PixelLoss:
     gradient takes as its extra dL/dy."""
 
     def __init__(self, tree, cams, rays=8192, weight=1.0, every=4, start=0.0, seed=0, n_frames=60,
-                 bg=(1.0, 1.0, 1.0), stop_T=1e-4):
+                 bg=(1.0, 1.0, 1.0), stop_T=1e-4, tensor_cores=False):
         """tree: the target Fourier PlenOctree (leaf structure and target
-        coefficients, host arrays); cams: the training cameras."""
+        coefficients, host arrays); cams: the training cameras; tensor_cores:
+        decode the current coefficients on tcgen05 with the inference
+        decoder's FP16 numerics (else in FP32)."""
         import torch
 
         self.cams, self.rays, self.weight, self.every, self.start = cams, rays, weight, every, start
+        self.tensor_cores = tensor_cores
         self.n_frames, self.bg, self.stop_T = n_frames, tuple(bg), float(stop_T)
         self.ref = fpo.Renderer(n1=tree.n1, n2=tree.n2, idft_mode="fused")
         self.ref.upload(tree)
@@ -235,7 +238,7 @@ class PixelLoss:
 
         from .finetune import camera_ray_batch
 
-        self.work.set_coeffs_from_decoder(model._mlp(model.p), model.p["lat"])
+        self.work.set_coeffs_from_decoder(model._mlp(model.p), model.p["lat"], tensor_cores=self.tensor_cores)
         o, d, t = camera_ray_batch(self.cams, self.rays, self.gen, self.n_frames, basis=self.basis)
         kw = dict(rays_o=o, rays_d=d, t_per_ray=t, bg=self.bg, stop_T=self.stop_T)
         y = self.ref.render(**kw)["rgb"]
@@ -247,6 +250,8 @@ class PixelLoss:
         self.mark.zero_()
         self.work.render_backward(rgb, diff * (2.0 * self.weight / self.rays), self.dy, leaf_mark=self.mark, **kw)
         self.rows = torch.nonzero(self.mark).flatten().to(torch.int32)
+        if self.tensor_cores:
+            self.work.status()  # the decode's FP16 range and time-out reports (the stream is idle here)
         return self.rows, self.dy
 
     def close(self):

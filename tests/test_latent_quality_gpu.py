@@ -58,7 +58,7 @@ def test_latent_decoder_quality_and_gain_on_a_generated_body():
 
     m = LatentModel(n, seed=0, tensor_cores=True)
     m.init_output_bias(coeffs)
-    pixel = PixelLoss(gen, cams, rays=8192, weight=10.0, every=4, start=0.1)
+    pixel = PixelLoss(gen, cams, rays=8192, weight=10.0, every=4, start=0.1, tensor_cores=True)
     try:
         hist = m.fit(coeffs, steps=4000, batch=65536, lr_w=1e-3, lr_lat=1e-1, decay=0.05,
                      coef_weight=m.default_weights(coeffs.device, sigma_weight=0.2),

@@ -238,7 +238,7 @@ def test_set_coeffs_from_decoder_equals_decode_then_set_coeffs():
         with pytest.raises(AssertionError):
             b.set_coeffs_from_decoder(m._mlp(m.p), m.p["lat"].half())
         with pytest.raises(fpo.FPOError) as e:
-            fpo.check(fpo.lib().fpo_set_coeffs_from_decoder(b.h, C.byref(m._mlp(m.p)), None, None))
+            fpo.check(fpo.lib().fpo_set_coeffs_from_decoder(b.h, C.byref(m._mlp(m.p)), None, 0, None))
         assert e.value.code == -1
     finally:
         a.close()
@@ -362,3 +362,63 @@ def test_decoder_grad_tensor_cores_timeout_is_reported():
     assert torch.equal(dl2, ref_dl)
     for k in ref_g:  # float atomics: the sums' order may differ between runs
         assert torch.allclose(m.g[k], ref_g[k], rtol=1e-5, atol=1e-6 * float(ref_g[k].abs().max()))
+
+
+def _f16(a):
+    return np.asarray(a, np.float64).astype(np.float16).astype(np.float64)
+
+
+def test_decode_into_records_on_the_tensor_cores():
+    # fpo_set_coeffs_from_decoder(FPO_FLAG_TENSOR_CORES) against an FP64 decode
+    # with the kernel's roundings (FP16 latents, weights through BF16 to FP16,
+    # FP16 hidden activations; exact biases): both coefficient sets rendered
+    # through the fused per-visit IDFT agree to FP32 accumulation order and
+    # the odd FP16 rounding that goes the other way; against the FP32 decode
+    # they differ by the FP16 operands
+    rng = np.random.default_rng(8)
+    d, xyz, _ = _smooth_tree(5)
+    n = d.shape[0]
+    m = LatentModel(n, seed=12)
+    m.p["b1"].copy_(torch.as_tensor(rng.normal(size=64) * 0.1))
+    m.p["b3"].copy_(torch.as_tensor(rng.normal(size=NC)))
+    m.p["b3"][0] = 30.0
+    P = {k: v.double().cpu().numpy() for k, v in m.p.items()}
+    wq = {k: _f16(_bf16(P[k])) for k in ("w1", "w2", "w3")}
+    z1 = _f16(P["lat"]) @ wq["w1"].T + P["b1"]
+    z2 = _f16(np.maximum(z1, 0)) @ wq["w2"].T + P["b2"]
+    emu = _f16(np.maximum(z2, 0)) @ wq["w3"].T + P["b3"]
+    empty = synth.Tree(d, xyz, np.zeros((n, NC), np.float32), 5)
+    cams = [synth.Camera(eye=synth.sphere_eye(a, 20), width=64, height=48) for a in (15, 135, 255)]
+    rs = [fpo.Renderer(idft_mode="fused") for _ in range(3)]
+    try:
+        for r in rs:
+            r.upload(empty)
+        rs[0].set_coeffs_from_decoder(m._mlp(m.p), m.p["lat"], tensor_cores=True)
+        rs[1].set_coeffs(torch.as_tensor(emu, dtype=torch.float32, device="cuda"))
+        rs[2].set_coeffs_from_decoder(m._mlp(m.p), m.p["lat"])
+        for cam in cams:
+            img = [r.render(camera=cam, t=27.0)["rgb"].double().cpu().numpy() for r in rs]
+            for r in rs:
+                r.status()
+            assert np.abs(img[0] - img[1]).max() <= 1e-4
+            assert np.abs(img[0] - img[2]).max() <= 2e-2 and np.mean((img[0] - img[2]) ** 2) <= 1e-5
+        # the failure path: every group's first wait runs out (1 ms)
+        rs[0].set_coeffs_from_decoder(m._mlp(m.p), m.p["lat"], tensor_cores=True, test_timeout=True)
+        with pytest.raises(fpo.FPOError) as e:
+            rs[0].status()
+        assert e.value.code == -9
+        # an operand beyond the FP16 range is reported
+        big = {k: v.clone() for k, v in m.p.items()}
+        big["w2"][3, 5] = 1.0e6
+        rs[0].set_coeffs_from_decoder(m._mlp(big), m.p["lat"], tensor_cores=True)
+        with pytest.raises(fpo.FPOError) as e:
+            rs[0].status()
+        assert e.value.code == -10
+        rs[0].set_coeffs_from_decoder(m._mlp(m.p), m.p["lat"], tensor_cores=True)
+        again = rs[0].render(camera=cams[0], t=27.0)["rgb"].double().cpu().numpy()
+        rs[0].status()
+        ref = rs[1].render(camera=cams[0], t=27.0)["rgb"].double().cpu().numpy()
+        assert np.abs(again - ref).max() <= 1e-4
+    finally:
+        for r in rs:
+            r.close()
