@@ -797,14 +797,6 @@ int fpo_set_coeffs(fpo_ctx *ctx, const float *coeffs, void *cuda_stream)
     return FPO_OK;
 }
 
-}  // extern "C"
-namespace fpo {
-// fpo_latent.cu: the decode into the records on the tensor cores
-int launch_decode_records_tc(const fpo_mlp &w, int n1, int n2, uint32_t n, const float *latents, const uint32_t *perm,
-                             float *sig, float *zc, uint32_t *status, bool test_timeout, int sm_count, void *stream);
-}  // namespace fpo
-extern "C" {
-
 int fpo_set_coeffs_from_decoder(fpo_ctx *ctx, const fpo_mlp *w, const float *latents, uint32_t flags, void *cuda_stream)
 {
     if (!ctx) return fail(FPO_ERR_INVALID_ARG, "ctx is NULL");

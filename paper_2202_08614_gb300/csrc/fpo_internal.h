@@ -244,6 +244,10 @@ int launch_decoder_forward(const fpo_mlp &w, int nc, uint32_t n, const float *la
                            void *stream);
 int launch_decode_records(const fpo_mlp &w, int n1, int n2, uint32_t n, const float *latents, const uint32_t *perm,
                           float *sig, float *zc, int sm_count, void *stream);
+// The same on the tensor cores with the inference decoder's FP16 numerics
+// (fpo_latent.cu); FP16-range and time-out reports go to *status.
+int launch_decode_records_tc(const fpo_mlp &w, int n1, int n2, uint32_t n, const float *latents, const uint32_t *perm,
+                             float *sig, float *zc, uint32_t *status, bool test_timeout, int sm_count, void *stream);
 int launch_adam(float *param, const float *grad, float *m, float *v, uint64_t n, const uint32_t *rows, uint32_t dim,
                 float lr, float b1, float b2, float eps, uint32_t step, int sm_count, void *stream);
 
