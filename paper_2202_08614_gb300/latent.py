@@ -78,7 +78,9 @@ class LatentModel:
 
     def grad(self, rows, targets, coef_weight, extra_dy=None, stream=None, accumulate=False):
         """Weight gradients into self.g (zeroed first unless `accumulate`);
-        returns (dlatents of the batch rows, loss tensor)."""
+        returns (dlatents of the batch rows, loss tensor).  With tensor_cores,
+        a device-side time-out is reported by check_status() (fit calls it at
+        its end)."""
         import torch
 
         if not accumulate:
