@@ -229,14 +229,16 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
  * of rays (camera or explicit rays without per-ray times) and the same
  * options, which carry no debug outputs (flags must be 0; opts->events are
  * ignored).  frame_done: NULL, or host array [n_frames] of cudaEvent_t
- * handles (NULL entries allowed); event k is recorded on cuda_stream once
- * frame k's pixels are written, so a caller can read frame k back while
- * later frames render.  The result equals n_frames calls of fpo_render.  In the table
- * mode the work is pipelined: the per-frame table of frame k+1 is computed
- * on an internal stream, into a second table, while frame k is traversed;
- * even frames are traversed on cuda_stream and odd frames on another
- * internal stream, so that consecutive traversals may overlap (the call
- * orders all of it after cuda_stream's previous work and before everything
+ * handles (NULL entries allowed); event k is recorded once frame k's pixels
+ * are written (on the stream that traversed it), so a caller can read frame
+ * k back while later frames render.  The result equals n_frames calls of
+ * fpo_render.  In the table mode the work is pipelined over four slots:
+ * frame k uses slot k mod 4, with its own table (the context keeps four:
+ * 4 x n_leaves x 128 bytes, 64 for an FP16 table), traversal stream (slot 0:
+ * cuda_stream; the others internal) and tile counter; the tables of the
+ * next frames are computed on another internal stream while earlier frames
+ * are traversed, and consecutive traversals may overlap (the call orders
+ * all of it after cuda_stream's previous work and before everything
  * enqueued on cuda_stream after the call).  Both kernels
  * share every SM: the call picks their launch shapes itself (two 384-thread
  * traversal CTAs and one or two IDFT CTAs per SM, or for LATENT storage one

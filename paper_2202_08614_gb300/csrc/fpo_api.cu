@@ -72,6 +72,14 @@ void dfree(T *&p)
 #ifndef FPO_PIPE_MAT_CTAS
 #define FPO_PIPE_MAT_CTAS 0  // IDFT-pass CTAs per SM in the pipeline (0: materialise_pipeline_shape's choice)
 #endif
+#ifndef FPO_PIPE_DEPTH
+// Tables (and traversal streams) in flight in fpo_render_frames.  Measured
+// (FP32 / BF16 1080p frames, ms): depth 2 0.675 / 0.516, 3 0.656 / 0.486,
+// 4 0.639 / 0.457, 6 0.648 / 0.465, 8 0.649 / 0.469.
+#define FPO_PIPE_DEPTH 4
+#endif
+constexpr int PIPE_MAX = 8;
+static_assert(FPO_PIPE_DEPTH >= 2 && FPO_PIPE_DEPTH <= PIPE_MAX, "pipeline depth");
 #ifndef FPO_PIPE_TWO_STREAMS
 #define FPO_PIPE_TWO_STREAMS 1  // odd frames' traversals on a second stream
 #endif
@@ -124,11 +132,12 @@ struct fpo_ctx {
     bool half_table = false;  // the per-frame table holds FP16 (64 B per leaf)
     bool table_ok = false;    // d_table holds the IDFT pass of table_t for the current coefficients
     double table_t = 0.0;
-    float *d_table2 = nullptr;
-    size_t table2_leaves = 0;
-    cudaStream_t aux = nullptr;   // IDFT passes / decodes
-    cudaStream_t aux2 = nullptr;  // traversals of the odd frames
-    cudaEvent_t ev_entry = nullptr, ev_mat[2] = {nullptr, nullptr}, ev_trav[2] = {nullptr, nullptr};
+    // slot b of the pipeline: frames b, b + depth, ... (slot 0: d_table, the caller's stream)
+    float *d_ptable[PIPE_MAX] = {};       // slots 1.. : their tables
+    size_t ptable_leaves[PIPE_MAX] = {};
+    cudaStream_t aux = nullptr;           // IDFT passes / decodes
+    cudaStream_t trav[PIPE_MAX] = {};     // slots 1.. : their traversal streams
+    cudaEvent_t ev_entry = nullptr, ev_mat[PIPE_MAX] = {}, ev_trav[PIPE_MAX] = {};
 
     void free_tree()
     {
@@ -144,8 +153,10 @@ struct fpo_ctx {
         dfree(d_table);
         table_leaves = 0;
         table_ok = false;
-        dfree(d_table2);
-        table2_leaves = 0;
+        for (int b = 1; b < PIPE_MAX; ++b) {
+            dfree(d_ptable[b]);
+            ptable_leaves[b] = 0;
+        }
         has_tree = false;
     }
 };
@@ -236,9 +247,9 @@ int fpo_create(fpo_ctx **out, const fpo_config *cfg)
                     (cfg->table_precision == FPO_TABLE_AUTO && cfg->storage != FPO_STORAGE_F32);
     e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, cfg->device);
     if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaDeviceGetAttribute"); }
-    e = cudaMalloc((void **)&c->d_status, 8 * sizeof(uint32_t));
+    e = cudaMalloc((void **)&c->d_status, 32 * sizeof(uint32_t));
     if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(status)"); }
-    e = cudaMemset(c->d_status, 0, 8 * sizeof(uint32_t));
+    e = cudaMemset(c->d_status, 0, 32 * sizeof(uint32_t));
     if (e != cudaSuccess) { cudaFree(c->d_status); delete c; return cuda_fail(e, "cudaMemset"); }
     *out = c;
     g_err.clear();
@@ -619,9 +630,9 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
     DeviceGuard g(ctx->cfg.device);
     if (!g.ok) return fail(FPO_ERR_CUDA, "cudaSetDevice failed");
     cudaError_t e = cudaSuccess;
-    for (int b = 0; b < 2; ++b) {
-        float *&tb = b ? ctx->d_table2 : ctx->d_table;
-        size_t &tl = b ? ctx->table2_leaves : ctx->table_leaves;
+    for (int b = 0; b < FPO_PIPE_DEPTH; ++b) {
+        float *&tb = b ? ctx->d_ptable[b] : ctx->d_table;
+        size_t &tl = b ? ctx->ptable_leaves[b] : ctx->table_leaves;
         if (tl < ctx->n_leaves) {
             dfree(tb);
             e = cudaMalloc((void **)&tb, table_alloc_bytes(ctx));
@@ -629,11 +640,15 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
             tl = ctx->n_leaves;
         }
     }
-    if (!ctx->aux || !ctx->aux2 || !ctx->ev_trav[1]) {  // created once; a failed attempt is retried whole
+    if (!ctx->aux || !ctx->trav[FPO_PIPE_DEPTH - 1] || !ctx->ev_trav[FPO_PIPE_DEPTH - 1]) {
+        // created once; a failed attempt is retried whole
         if (!ctx->aux) e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
-        if (e == cudaSuccess && !ctx->aux2) e = cudaStreamCreateWithFlags(&ctx->aux2, cudaStreamNonBlocking);
-        for (cudaEvent_t *ev : {&ctx->ev_entry, &ctx->ev_mat[0], &ctx->ev_mat[1], &ctx->ev_trav[0], &ctx->ev_trav[1]})
-            if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e == cudaSuccess && !ctx->ev_entry) e = cudaEventCreateWithFlags(&ctx->ev_entry, cudaEventDisableTiming);
+        for (int b = 0; b < FPO_PIPE_DEPTH && e == cudaSuccess; ++b) {
+            if (b && !ctx->trav[b]) e = cudaStreamCreateWithFlags(&ctx->trav[b], cudaStreamNonBlocking);
+            if (e == cudaSuccess && !ctx->ev_mat[b]) e = cudaEventCreateWithFlags(&ctx->ev_mat[b], cudaEventDisableTiming);
+            if (e == cudaSuccess && !ctx->ev_trav[b]) e = cudaEventCreateWithFlags(&ctx->ev_trav[b], cudaEventDisableTiming);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "stream/event creation");
     }
     // Shapes that let both kernels be resident on an SM at once: the IDFT
@@ -665,23 +680,26 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
         if (config < 0 || config > max_smem) overlap = false;
         else carveout = (int)(config * 100 / max_smem);
     }
-    ctx->table_ok = false;  // the pipeline writes both tables
+    ctx->table_ok = false;  // the pipeline writes every slot's table
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    // The table pass of frame k + 1 runs on the auxiliary stream while frame
-    // k is traversed; two tables alternate.  The traversals of even frames
-    // run on the caller's stream and those of odd frames on a second stream
-    // (with their own tile counters), so that one traversal can fill the SMs
-    // that the last warps of the previous one leave idle.  Table b is
-    // rewritten only after the traversal that read it (event ev_trav[b]),
-    // and the caller's stream waits for the last odd traversal at the end.
-    if ((e = cudaEventRecord(ctx->ev_entry, s)) != cudaSuccess || (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_entry, 0)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(ctx->aux2, ctx->ev_entry, 0)) != cudaSuccess)
+    // Frame k takes slot b = k mod depth: the slot's table and traversal
+    // stream (slot 0: d_table and the caller's stream) and tile counter.  The
+    // table passes run in order on the auxiliary stream, ahead of the
+    // traversals; the traversals of consecutive frames run on different
+    // streams, so that the next ones fill the SMs that the last warps of the
+    // earlier ones leave idle.  Table b is rewritten only after the
+    // traversal that read it (event ev_trav[b]), and the caller's stream
+    // waits for every slot's last traversal at the end.
+    if ((e = cudaEventRecord(ctx->ev_entry, s)) != cudaSuccess || (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_entry, 0)) != cudaSuccess)
         return cuda_fail(e, "stream ordering");
+    for (int b = 1; b < FPO_PIPE_DEPTH; ++b)
+        if ((e = cudaStreamWaitEvent(ctx->trav[b], ctx->ev_entry, 0)) != cudaSuccess) return cuda_fail(e, "stream ordering");
     for (uint32_t k = 0; k < n_frames; ++k) {
-        const int b = (int)(k & 1);
-        float *tbl = b ? ctx->d_table2 : ctx->d_table;
-        cudaStream_t ts = (FPO_PIPE_TWO_STREAMS && b) ? ctx->aux2 : s;
-        if (k >= 2 && (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_trav[b], 0)) != cudaSuccess) return cuda_fail(e, "wait");
+        const int b = (int)(k % FPO_PIPE_DEPTH);
+        float *tbl = b ? ctx->d_ptable[b] : ctx->d_table;
+        cudaStream_t ts = FPO_PIPE_TWO_STREAMS && b ? ctx->trav[b] : s;
+        if (k >= FPO_PIPE_DEPTH && (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_trav[b], 0)) != cudaSuccess)
+            return cuda_fail(e, "wait");
         int ce = overlap ? launch_table_pass(ctx, frames[k].t, tbl, mshape.ctas_per_sm, ctx->aux, mshape.stages, carveout, false)
                          : launch_table_pass(ctx, frames[k].t, tbl, 0, ctx->aux, 0, 0, false);
         if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "IDFT table launch");
@@ -690,7 +708,7 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
             return cuda_fail(e, "stream ordering");
         TraverseParams p = traverse_params(ctx, &frames[k], &o1, out_rgb + (size_t)k * R * 3, R);
         p.table = reinterpret_cast<const float4 *>(tbl);
-        p.tiles = ctx->d_status + ((FPO_PIPE_TWO_STREAMS && b) ? 5 : 1);
+        p.tiles = ctx->d_status + 1 + (FPO_PIPE_TWO_STREAMS ? 2 * b : 0);  // this slot's tile counter and finished warps
         if (overlap) {
             p.block_threads = PIPE_TRAV_THREADS;
             p.max_ctas_per_sm = PIPE_TRAV_CTAS;
@@ -703,8 +721,8 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
             return cuda_fail(e, "cudaEventRecord(frame_done)");
     }
     // everything above is ordered before the caller's later work
-    if (n_frames >= 2 && (e = cudaStreamWaitEvent(s, ctx->ev_trav[1], 0)) != cudaSuccess)
-        return cuda_fail(e, "stream ordering");
+    for (uint32_t b = 1; b < FPO_PIPE_DEPTH && b < n_frames; ++b)
+        if ((e = cudaStreamWaitEvent(s, ctx->ev_trav[b], 0)) != cudaSuccess) return cuda_fail(e, "stream ordering");
     return FPO_OK;
 }
 
@@ -914,9 +932,12 @@ void fpo_destroy(fpo_ctx *ctx)
         ctx->free_tree();
         dfree(ctx->d_status);
         if (ctx->aux) cudaStreamDestroy(ctx->aux);
-        if (ctx->aux2) cudaStreamDestroy(ctx->aux2);
-        for (cudaEvent_t e : {ctx->ev_entry, ctx->ev_mat[0], ctx->ev_mat[1], ctx->ev_trav[0], ctx->ev_trav[1]})
-            if (e) cudaEventDestroy(e);
+        if (ctx->ev_entry) cudaEventDestroy(ctx->ev_entry);
+        for (int b = 0; b < PIPE_MAX; ++b) {
+            if (ctx->trav[b]) cudaStreamDestroy(ctx->trav[b]);
+            if (ctx->ev_mat[b]) cudaEventDestroy(ctx->ev_mat[b]);
+            if (ctx->ev_trav[b]) cudaEventDestroy(ctx->ev_trav[b]);
+        }
     }
     delete ctx;
 }
