@@ -31,7 +31,7 @@ def _per_frame(r, cams, times):
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16", "f16", "fp8"])
-@pytest.mark.parametrize("n_frames", [1, 2, 7])
+@pytest.mark.parametrize("n_frames", [1, 2, 4, 7, 9])
 def test_frames_equal_single_renders(storage, n_frames):
     tree = synth.random_tree(11, max_depth=7, p_split=0.6, p_empty=0.3)
     cams = synth.ring_cameras(8, 160, 96)
@@ -54,6 +54,37 @@ def test_frames_equal_single_renders(storage, n_frames):
         ref = gu.oracle.render(gu.oracle_tree(tree), tree.coeffs, camera=cs[-1], t=times[-1])["rgb"]
         d = np.abs(a[-1].cpu().numpy() - ref)
         assert d.mean() <= 1e-5
+
+
+@pytest.mark.parametrize("n_frames", [3, 11])
+def test_frame_done_events_cover_their_frame(n_frames):
+    # each frame read back on a copy stream that waits only for that frame's
+    # completion event (as an end-to-end caller does) equals its own
+    # single-frame render
+    tree = synth.random_tree(13, max_depth=7, p_split=0.6, p_empty=0.3)
+    cams = synth.ring_cameras(8, 320, 180)
+    times = [1.0 + 5.3 * i for i in range(n_frames)]
+    cs = [cams[i % 8] for i in range(n_frames)]
+    r = fpo.Renderer()
+    try:
+        r.upload(tree)
+        ref = _per_frame(r, cs, times)
+        r.status()
+        out = torch.empty_like(ref)
+        host = torch.empty(ref.shape, dtype=torch.float32, pin_memory=True)
+        evs = [torch.cuda.Event() for _ in range(n_frames)]
+        copy = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        r.render_frames(cs, times, out=out, frame_events=evs)
+        with torch.cuda.stream(copy):
+            for k in range(n_frames):
+                copy.wait_event(evs[k])
+                host[k].copy_(out[k], non_blocking=True)
+        copy.synchronize()
+        r.status()
+        assert torch.equal(host, ref.cpu())
+    finally:
+        r.close()
 
 
 @pytest.mark.parametrize("depth", [5, 7])
