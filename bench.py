@@ -334,25 +334,37 @@ def variants(args, tree, cams, frames, out, torch, fpo, n_px, fp32_ms, n_vis, pe
                                                    2 * TABLE_VALUES_PER_LEAF, r.info()["n_nodes"], n_px, peak)
     r.close()
     # multi-view rendering of one frame time: the 16 ring views of each t share
-    # one IDFT pass (FPO_FLAG_REUSE_TABLE)
+    # one IDFT pass, in one fpo_render_frames call per t (the views' traversals
+    # overlap), or as fpo_render calls with FPO_FLAG_REUSE_TABLE
     r = fpo.Renderer()
     r.upload(tree)
     ts = [float(t) for t in range(0, 60, 6)]
+    outv = torch.empty((len(cams), n_px, 3), dtype=torch.float32, device="cuda")
+    r.render_frames(cams, [ts[0]] * len(cams), out=outv)
     for cam in cams[:3]:
         r.render(camera=cam, t=ts[0], out=out, reuse_table=True)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for t in ts:
+        r.render_frames(cams, [t] * len(cams), out=outv)
+    b.record()
+    c, d = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c.record()
+    for t in ts:
         for cam in cams:
             r.render(camera=cam, t=t, out=out, reuse_table=True)
-    b.record()
+    d.record()
     torch.cuda.synchronize()
     r.status()
     r.close()
     mv = a.elapsed_time(b) / (len(ts) * len(cams))
+    mv1 = c.elapsed_time(d) / (len(ts) * len(cams))
     res["multiview_16_views_per_t"] = {"ms_per_view": mv, "Mrays_s": n_px / mv / 1e3, "fps": 1e3 / mv,
-                                       "frame_times": len(ts), "views_per_t": len(cams)}
+                                       "frame_times": len(ts), "views_per_t": len(cams),
+                                       "calls": "one fpo_render_frames call per t",
+                                       "single_view_calls": {"ms_per_view": mv1, "Mrays_s": n_px / mv1 / 1e3,
+                                                             "calls": "fpo_render with the table reused"}}
     # the Fourier sizes of the paper's ablation (Tab. 3) on the same leaves and
     # coefficient distributions: frame rate and bytes per leaf (the (31, 5)
     # entry is the headline measurement)

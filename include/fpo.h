@@ -237,7 +237,8 @@ int fpo_render(fpo_ctx *ctx, const fpo_rays *rays, const fpo_frame_opts *opts,
  * 4 x n_leaves x 128 bytes, 64 for an FP16 table), traversal stream (slot 0:
  * cuda_stream; the others internal) and tile counter; the tables of the
  * next frames are computed on another internal stream while earlier frames
- * are traversed, and consecutive traversals may overlap (the call orders
+ * are traversed (frames that all share one t, bit-equal, take a single
+ * table pass), and consecutive traversals may overlap (the call orders
  * all of it after cuda_stream's previous work and before everything
  * enqueued on cuda_stream after the call).  Both kernels
  * share every SM: the call picks their launch shapes itself (two 384-thread

@@ -694,17 +694,27 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
         return cuda_fail(e, "stream ordering");
     for (int b = 1; b < FPO_PIPE_DEPTH; ++b)
         if ((e = cudaStreamWaitEvent(ctx->trav[b], ctx->ev_entry, 0)) != cudaSuccess) return cuda_fail(e, "stream ordering");
+    // Views of one frame time (every t bit-equal): one table pass, and every
+    // traversal of the call reads that table (nothing rewrites it before the
+    // call's end, after which the caller's stream has waited for them all).
+    bool one_t = n_frames > 1;
+    for (uint32_t k = 1; k < n_frames && one_t; ++k)
+        one_t = memcmp(&frames[k].t, &frames[0].t, sizeof(double)) == 0;
     for (uint32_t k = 0; k < n_frames; ++k) {
         const int b = (int)(k % FPO_PIPE_DEPTH);
-        float *tbl = b ? ctx->d_ptable[b] : ctx->d_table;
+        float *tbl = one_t ? ctx->d_table : (b ? ctx->d_ptable[b] : ctx->d_table);
         cudaStream_t ts = FPO_PIPE_TWO_STREAMS && b ? ctx->trav[b] : s;
-        if (k >= FPO_PIPE_DEPTH && (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_trav[b], 0)) != cudaSuccess)
-            return cuda_fail(e, "wait");
-        int ce = overlap ? launch_table_pass(ctx, frames[k].t, tbl, mshape.ctas_per_sm, ctx->aux, mshape.stages, carveout, false)
-                         : launch_table_pass(ctx, frames[k].t, tbl, 0, ctx->aux, 0, 0, false);
-        if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "IDFT table launch");
-        if ((e = cudaEventRecord(ctx->ev_mat[b], ctx->aux)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(ts, ctx->ev_mat[b], 0)) != cudaSuccess)
+        int ce = cudaSuccess;
+        if (!one_t || k == 0) {
+            if (k >= FPO_PIPE_DEPTH && (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_trav[b], 0)) != cudaSuccess)
+                return cuda_fail(e, "wait");
+            ce = overlap ? launch_table_pass(ctx, frames[k].t, tbl, mshape.ctas_per_sm, ctx->aux, mshape.stages, carveout, false)
+                             : launch_table_pass(ctx, frames[k].t, tbl, 0, ctx->aux, 0, 0, false);
+            if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "IDFT table launch");
+            if ((e = cudaEventRecord(ctx->ev_mat[b], ctx->aux)) != cudaSuccess)
+                return cuda_fail(e, "stream ordering");
+        }
+        if ((e = cudaStreamWaitEvent(ts, ctx->ev_mat[one_t ? 0 : b], 0)) != cudaSuccess)
             return cuda_fail(e, "stream ordering");
         TraverseParams p = traverse_params(ctx, &frames[k], &o1, out_rgb + (size_t)k * R * 3, R);
         p.table = reinterpret_cast<const float4 *>(tbl);

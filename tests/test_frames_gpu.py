@@ -56,6 +56,27 @@ def test_frames_equal_single_renders(storage, n_frames):
         assert d.mean() <= 1e-5
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("n_frames", [2, 5, 9])
+def test_views_of_one_frame_time(storage, n_frames):
+    # every frame at the same t: one table pass serves all the call's
+    # traversals; each view equals its own single-frame render, and a
+    # following call at another t recomputes the table
+    tree = synth.random_tree(17, max_depth=7, p_split=0.6, p_empty=0.3)
+    cams = synth.ring_cameras(12, 160, 96)
+    cs = [cams[i % 12] for i in range(n_frames)]
+    r = fpo.Renderer(storage=storage)
+    try:
+        r.upload(tree)
+        for t in (12.5, 40.25):
+            a = r.render_frames(cs, [t] * n_frames)
+            b = _per_frame(r, cs, [t] * n_frames)
+            r.status()
+            assert torch.equal(a, b)
+    finally:
+        r.close()
+
+
 @pytest.mark.parametrize("n_frames", [3, 11])
 def test_frame_done_events_cover_their_frame(n_frames):
     # each frame read back on a copy stream that waits only for that frame's
