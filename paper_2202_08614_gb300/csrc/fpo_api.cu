@@ -80,8 +80,8 @@ void dfree(T *&p)
 #endif
 constexpr int PIPE_MAX = 8;
 static_assert(FPO_PIPE_DEPTH >= 2 && FPO_PIPE_DEPTH <= PIPE_MAX, "pipeline depth");
-#ifndef FPO_PIPE_TWO_STREAMS
-#define FPO_PIPE_TWO_STREAMS 1  // odd frames' traversals on a second stream
+#ifndef FPO_PIPE_SLOT_STREAMS
+#define FPO_PIPE_SLOT_STREAMS 1  // each pipeline slot's traversals on its own stream (0: all on the caller's)
 #endif
 #ifndef FPO_PIPE_MAT_SMEM_KB
 #define FPO_PIPE_MAT_SMEM_KB 88
@@ -703,13 +703,13 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
     for (uint32_t k = 0; k < n_frames; ++k) {
         const int b = (int)(k % FPO_PIPE_DEPTH);
         float *tbl = one_t ? ctx->d_table : (b ? ctx->d_ptable[b] : ctx->d_table);
-        cudaStream_t ts = FPO_PIPE_TWO_STREAMS && b ? ctx->trav[b] : s;
+        cudaStream_t ts = FPO_PIPE_SLOT_STREAMS && b ? ctx->trav[b] : s;
         int ce = cudaSuccess;
         if (!one_t || k == 0) {
             if (k >= FPO_PIPE_DEPTH && (e = cudaStreamWaitEvent(ctx->aux, ctx->ev_trav[b], 0)) != cudaSuccess)
                 return cuda_fail(e, "wait");
             ce = overlap ? launch_table_pass(ctx, frames[k].t, tbl, mshape.ctas_per_sm, ctx->aux, mshape.stages, carveout, false)
-                             : launch_table_pass(ctx, frames[k].t, tbl, 0, ctx->aux, 0, 0, false);
+                         : launch_table_pass(ctx, frames[k].t, tbl, 0, ctx->aux, 0, 0, false);
             if (ce != cudaSuccess) return cuda_fail((cudaError_t)ce, "IDFT table launch");
             if ((e = cudaEventRecord(ctx->ev_mat[b], ctx->aux)) != cudaSuccess)
                 return cuda_fail(e, "stream ordering");
@@ -718,7 +718,7 @@ int fpo_render_frames(fpo_ctx *ctx, const fpo_rays *frames, uint32_t n_frames, c
             return cuda_fail(e, "stream ordering");
         TraverseParams p = traverse_params(ctx, &frames[k], &o1, out_rgb + (size_t)k * R * 3, R);
         p.table = reinterpret_cast<const float4 *>(tbl);
-        p.tiles = ctx->d_status + 1 + (FPO_PIPE_TWO_STREAMS ? 2 * b : 0);  // this slot's tile counter and finished warps
+        p.tiles = ctx->d_status + 1 + (FPO_PIPE_SLOT_STREAMS ? 2 * b : 0);  // this slot's tile counter and finished warps
         if (overlap) {
             p.block_threads = PIPE_TRAV_THREADS;
             p.max_ctas_per_sm = PIPE_TRAV_CTAS;
