@@ -75,7 +75,7 @@ void dfree(T *&p)
 #ifndef FPO_PIPE_DEPTH
 // Tables (and traversal streams) in flight in fpo_render_frames.  Measured
 // (FP32 / BF16 1080p frames, ms): depth 2 0.675 / 0.516, 3 0.656 / 0.486,
-// 4 0.639 / 0.457, 6 0.648 / 0.465, 8 0.649 / 0.469.
+// 4 0.639 / 0.457, 5 0.653 / 0.480, 6 0.648 / 0.465, 8 0.649 / 0.469.
 #define FPO_PIPE_DEPTH 4
 #endif
 constexpr int PIPE_MAX = 8;
